@@ -1,0 +1,102 @@
+"""The oracle's pins must catch plausible mistakes.  Each case plants one
+mistake (a flipped sign, a wrong index, a dropped term, a non-strict
+comparison, ...) in a temporary copy of the oracle's C source, builds it, and
+requires at least one pin of tests/test_oracle_pins.py to fail against it.
+CPU only; the committed oracle is never modified."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from oracle.build import SRC
+
+from . import test_oracle_pins as P
+
+ALL_K = range(7)
+
+PIN_GROUPS = {
+    "residual": [(P.test_residual_matches_dense, {"k": k}) for k in ALL_K] + [(P.test_example1_residual_exact_rational, {})],
+    "sumsq": [(P.test_sumsq_tree_order_pinned, {}), (P.test_sumsq_error_bound, {"n": 4096 + 7}),
+              (P.test_tau_formula_and_infinity_norm_criterion, {}), (P.test_example1_golden_trace, {})],
+    "dilate": [(P.test_dilation_is_graph_ball, {"k": k, "layers": 2}) for k in ALL_K],
+    "expand": [(P.test_example1_golden_trace, {}), (P.test_paper_expansion_brute_force_random, {}),
+               (P.test_strict_thresholds_at_equality, {})],
+    "gradient": [(P.test_gradient_definition, {"k": k}) for k in ALL_K] + [(P.test_gradient_five_point_formula, {}),
+                                                                          (P.test_mark_gradient_edges_and_monotone, {}),
+                                                                          (P.test_strict_thresholds_at_equality, {})],
+    "extract": [(P.test_extract_matches_dense_blocks, {"k": k}) for k in ALL_K] + [(P.test_extract_empty_and_full, {})],
+    "pcg": [(P.test_pcg_matches_dense_lu, {"k": k}) for k in ALL_K] + [(P.test_pcg_manufactured_and_warm_start, {}),
+                                                                       (P.test_pcg_status_codes, {}),
+                                                                       (P.test_pcg_finite_termination, {})],
+    "alg1": [(P.test_local_then_global_agrees_with_global, {}), (P.test_local_then_global_edge_cases, {}),
+             (P.test_rtilde_identity_and_bound, {}), (P.test_example1_local_solve_converges_without_global, {})],
+    "adjoint": [(P.test_adjoint_gradient_matches_finite_differences, {})],
+}
+
+# (name, pin group, original text, mutated text)
+MUTANTS = [
+    ("residual_sign", "residual", "s = fma(-av[e], x[ci[e]], s);", "s = fma(av[e], x[ci[e]], s);"),
+    ("residual_drop_b", "residual", "double s = b[i];\n        for (int32_t e = rp[i]; e < rp[i + 1]; ++e)\n            s = fma(-av[e], x[ci[e]], s);",
+     "double s = 0.0;\n        for (int32_t e = rp[i]; e < rp[i + 1]; ++e)\n            s = fma(-av[e], x[ci[e]], s);"),
+    ("residual_wrong_index", "residual", "s = fma(-av[e], x[ci[e]], s);", "s = fma(-av[e], x[i], s);"),
+    ("tree_drop_level", "sumsq", "for (int s = 512; s >= 1; s >>= 1)", "for (int s = 512; s > 1; s >>= 1)"),
+    ("tree_sequential", "sumsq", "for (int s = 512; s >= 1; s >>= 1)\n            for (int i = 0; i < s; ++i) v[i] = v[i] + v[i + s];",
+     "for (int i = 1; i < 1024; ++i) v[0] = v[0] + v[i];"),
+    ("tau_no_sqrt", "sumsq", "return (eps * sqrt(S)) / sqrt((double)n);", "return (eps * S) / sqrt((double)n);"),
+    ("dilate_self", "dilate", "if (ci[e] != i && av[e] != 0.0 && in[ci[e]]) m = 1;", "if (ci[e] != i && av[e] != 0.0 && in[i]) m = 1;"),
+    ("dilate_one_sided", "dilate", "if (ci[e] != i && av[e] != 0.0 && in[ci[e]]) m = 1;", "if (ci[e] > i && av[e] != 0.0 && in[ci[e]]) m = 1;"),
+    ("expand_wrong_x", "expand", "t = t + fabs(av[e] * x0[i]);", "t = t + fabs(av[e] * x0[j]);"),
+    ("expand_drop_r", "expand", "double c = fabs(r0[j]) + t;", "double c = t;"),
+    ("expand_async", "expand", "if (c > tau) { add[j] = 1; ++k0; }", "if (c > tau) { add[j] = 1; mask[j] = 1; ++k0; }"),
+    ("expand_nonstrict", "expand", "if (c > tau) { add[j] = 1; ++k0; }", "if (c >= tau) { add[j] = 1; ++k0; }"),
+    ("residual_nonstrict", "expand", "mask[i] = fabs(r[i]) > tau ? 1 : 0;", "mask[i] = fabs(r[i]) >= tau ? 1 : 0;"),
+    ("gradient_no_abs", "gradient", "s = s + fabs(x[i] - x[j]);", "s = s + (x[i] - x[j]);"),
+    ("gradient_wrong_index", "gradient", "s = s + fabs(x[i] - x[j]);", "s = s + fabs(x[i] - x[e]);"),
+    ("mark_gradient_nonstrict", "gradient", "mask[i] = g[i] > thr ? 1 : 0;", "mask[i] = g[i] >= thr ? 1 : 0;"),
+    ("extract_rhs_index", "extract", "else s = fma(-av[e], x0[j], s);", "else s = fma(-av[e], x0[i], s);"),
+    ("extract_global_col", "extract", "bci[nz] = g2l[j];", "bci[nz] = j < K ? j : 0;"),
+    ("extract_rhs_sign", "extract", "else s = fma(-av[e], x0[j], s);", "else s = fma(av[e], x0[j], s);"),
+    ("pcg_beta_inverted", "pcg", "double beta = rz_new / rz;", "double beta = rz / rz_new;"),
+    ("pcg_r_sign", "pcg", "r[i] -= alpha * q[i]; }", "r[i] += alpha * q[i]; }"),
+    ("pcg_no_precond", "pcg", "dinv[i] = 1.0 / d;", "dinv[i] = 1.0 / (d * d);"),
+    ("assemble_index", "alg1", "for (int32_t l = 0; l < K; ++l) xt[l2g[l]] = xbar[l];", "for (int32_t l = 0; l < K; ++l) xt[l] = xbar[l];"),
+    ("alg1_skip_local", "alg1", "if (K > 0) {\n        status = orc_pcg(K,", "if (K < 0) {\n        status = orc_pcg(K,"),
+    ("adjoint_wrong_k", "adjoint", "double dT = 2.0 * k[m] * k[m] / (den * den);", "double dT = 2.0 * k[c] * k[c] / (den * den);"),
+    ("adjoint_drop_boundary", "adjoint", "s += 2.0 * lam[c] * x[c];", "s += 0.0 * lam[c] * x[c];"),
+]
+
+
+def _build_mutant(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    mut = src.replace(old, new, 1)
+    cpath = tmp_path / f"{name}.c"
+    cpath.write_text(mut)
+    so = tmp_path / f"{name}.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so), str(cpath), "-lm"],
+                   check=True, capture_output=True)
+    return str(so)
+
+
+@pytest.mark.parametrize("name,group,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_mutant(tmp_path, name, group, old, new):
+    so = _build_mutant(tmp_path, name, old, new)
+    saved = oracle._lib
+    oracle._lib = oracle.load(so)
+    caught = []
+    try:
+        for fn, kw in PIN_GROUPS[group]:
+            try:
+                fn(**kw)
+            except (AssertionError, ValueError, FloatingPointError, IndexError, ZeroDivisionError, np_linalg_error()):
+                caught.append(fn.__name__)
+                break
+    finally:
+        oracle._lib = saved
+    assert caught, f"no pin in group {group!r} caught mutant {name!r}"
+
+
+def np_linalg_error():
+    import numpy as np
+    return np.linalg.LinAlgError

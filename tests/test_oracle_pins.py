@@ -1,0 +1,522 @@
+"""Pins of the oracle against facts fixed outside it: the paper's worked
+Example 1, exact rational arithmetic, dense linear algebra, brute-force set
+definitions and closed forms.  CPU only."""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small_ops():
+    return [oracle.from_stencil(gen.random_stencil_2d(s, nx, ny)) for s, nx, ny in
+            [(0, 7, 5), (1, 9, 9), (2, 1, 6), (3, 6, 1), (4, 12, 10)]] + \
+           [oracle.from_stencil(gen.random_stencil_3d(5, 4, 3, 5)), oracle.from_stencil(gen.random_stencil_3d(6, 5, 5, 2))]
+
+
+# ------------------------------------------------------------------ Example 1
+
+def test_example1_residual_exact_rational():
+    """r0 = b - A x0 = A (x - x0) with b = A x: compare with exact rational
+    arithmetic (Sec. 2.3.2, Example 1)."""
+    e = gen.example1()
+    A = oracle.csr(e["rowptr"], e["col"], e["val"])
+    r = oracle.residual(A, e["b"], e["x0"])
+    n = 9
+    Af = [[Fraction(0)] * n for _ in range(n)]
+    for i in range(n):
+        Af[i][i] = Fraction(1)
+    for i in range(1, n):
+        Af[i - 1][i] = Af[i][i - 1] = Fraction(-1, i + 1)
+    x = [Fraction(1, 10 ** (i + 1)) for i in range(n)]
+    x0 = [Fraction(1), Fraction(1, 10)] + [Fraction(1001, 10 ** (i + 4)) for i in range(2, n)]
+    for i in range(n):
+        exact = sum(Af[i][j] * (x[j] - x0[j]) for j in range(n))
+        # b = A x is rounded once per entry, so allow a few ulps of |b|
+        assert abs(float(exact) - r[i]) <= 4e-16 * max(1.0, abs(e["b"][i])) + 1e-13 * abs(float(exact))
+    # the printed r_2 = 3.66e-1 is a slip: the exact value is 0.36 + 1e-6/3
+    assert r[1] == pytest.approx(0.36 + 1e-6 / 3, rel=1e-12)
+
+
+def test_example1_golden_trace():
+    """Alg 3 on Example 1 reproduces the paper's printed threshold, initial
+    bad points and the full table of the extension process."""
+    g = json.load(open(os.path.join(GOLD, "example1.json")))
+    e = gen.example1()
+    A = oracle.csr(e["rowptr"], e["col"], e["val"])
+    tau = oracle.tau_eps_normb(e["b"], g["eps"])
+    # printed values are rounded to 3 (residuals, tau) or 4 (table) digits
+    assert float(f"{tau:.2e}") == g["tau_printed"]
+    r = oracle.residual(A, e["b"], e["x0"])
+    for i, (ri, pi) in enumerate(zip(r, g["r0_printed"])):
+        if i == 1:
+            continue  # typesetting slip, checked against the closed form above
+        assert float(f"{ri:.2e}") == pi
+    mask0 = (np.abs(r) > tau).astype(np.uint8)
+    assert list(np.flatnonzero(mask0) + 1) == g["initial_omega_1based"]
+    mask = mask0.copy()
+    for rd in g["rounds"]:
+        new, added, c = oracle.expand_paper(A, r, e["x0"], tau, mask, 1)
+        cand = list(np.flatnonzero(~np.isnan(c[0])) + 1)
+        assert cand == rd["N"]
+        assert list(np.flatnonzero(new & ~mask) + 1) == rd["N_local"]
+        assert list(np.flatnonzero(new) + 1) == rd["omega"]
+        assert int(new.sum()) == rd["K"]
+        for j, cv in rd["c"].items():
+            assert float(f"{c[0][int(j) - 1]:.3e}") == cv
+        assert added == (1 if rd["N_local"] else 0)
+        mask = new
+    full = oracle.mark_residual(A, e["b"], e["x0"], oracle.THR_EPS_NORMB, g["eps"], oracle.EXP_PAPER, g["E_max"])
+    assert list(np.flatnonzero(full["mask"]) + 1) == g["final_omega_1based"]
+    assert full["K"] == g["K"]
+    assert full["rounds"] == 3
+    assert full["tau"] == tau
+
+
+def test_example1_local_solve_converges_without_global():
+    """After solving on Omega = {1..6} the assembled iterate already meets the
+    criterion (the paper's claim that x~ is often the final solution)."""
+    e = gen.example1()
+    A = oracle.csr(e["rowptr"], e["col"], e["val"])
+    x, st, mask = oracle.solve_local_then_global(A, e["b"], e["x0"], oracle.MARK_RESIDUAL, oracle.THR_EPS_NORMB,
+                                                 1e-5, oracle.EXP_PAPER, 6, tol=1e-5, tol_local=1e-10)
+    assert st["K"] == 6 and st["early_exit"] == 1 and st["it_global"] == 0
+    assert st["relres_tilde"] <= 1e-5
+    assert np.allclose(x[:6], np.linalg.solve(e["A"][:6, :6], e["b"][:6] - e["A"][:6, 6:] @ e["x0"][6:]), rtol=1e-8)
+    assert np.array_equal(x[6:], e["x0"][6:])
+
+
+# ------------------------------------------------------------------ residual
+
+@pytest.mark.parametrize("k", range(7))
+def test_residual_matches_dense(k):
+    A = small_ops()[k]
+    rng = np.random.default_rng(k)
+    x = rng.standard_normal(A.n)
+    b = rng.standard_normal(A.n)
+    r = oracle.residual(A, b, x)
+    ref = b - A.dense() @ x
+    scale = np.abs(A.dense()) @ np.abs(x) + np.abs(b)
+    assert np.all(np.abs(r - ref) <= 8e-16 * scale)
+
+
+def test_residual_canonical_order_is_fma_chain_from_b():
+    """R1 fixes r = b; r = fma(-a_ij, x_j, r) ascending.  A 1x3 row where the
+    fused chain and a separately rounded sum differ pins both the fusion and
+    the start value."""
+    # row: a = [1, 1, 1] on columns 0..2 (one row of a 3-column operator)
+    rp = np.array([0, 3, 4, 5], np.int32)
+    ci = np.array([0, 1, 2, 1, 2], np.int32)
+    av = np.array([1.0, 1.0, 1.0, 1.0, 1.0])
+    A = oracle.csr(rp, ci, av)
+    t = 1.0 + 2.0 ** -30
+    x = np.array([t, -t, 2.0 ** -60])
+    b = np.array([t * t, 0.0, 0.0])
+    # chain: fma(-1, t, t*t) = t*t - t exactly rounded; + t; - 2^-60
+    s = b[0]
+    s = math.fma(-1.0, x[0], s) if hasattr(math, "fma") else float(Fraction(s) - Fraction(x[0]))
+    s = float(Fraction(s) - Fraction(x[1]))
+    s = float(Fraction(s) - Fraction(x[2]))
+    r = oracle.residual(A, b, x)
+    assert r[0] == s
+
+
+# ------------------------------------------------------------------ threshold
+
+def test_sumsq_tree_order_pinned():
+    """Four squares of 2^-54 placed at 1, 257, 513, 769 next to 1.0 at 0: the
+    canonical stride-halving tree first pairs them (1+513, 257+769, then the
+    two partials) and gives 1 + 2^-52; a sequential sum would give 1.0."""
+    b = np.zeros(1024)
+    b[0] = 1.0
+    for i in (1, 257, 513, 769):
+        b[i] = 2.0 ** -27
+    assert oracle.sumsq(b) == 1.0 + 2.0 ** -52
+    seq = 0.0
+    for v in b:
+        seq += v * v
+    assert seq == 1.0
+
+
+@pytest.mark.parametrize("n", [1, 5, 1023, 1024, 1025, 4096 + 7, 1 << 20])
+def test_sumsq_error_bound(n):
+    rng = np.random.default_rng(n)
+    b = rng.standard_normal(n) * np.exp(rng.uniform(-3, 3, n))
+    exact = math.fsum(float(v) * float(v) for v in b) if n < 5000 else math.fsum((b * b).tolist())
+    depth = max(1, math.ceil(math.log2(max(n, 2)))) + 1
+    assert abs(oracle.sumsq(b) - exact) <= depth * 2.0 ** -52 * exact
+    assert oracle.sumsq(np.ones(n)) == float(n)
+
+
+def test_tau_formula_and_infinity_norm_criterion():
+    """tau = eps ||b||/sqrt(N), and ||r||_inf <= tau implies ||r||_2 <= eps ||b||_2
+    (Sec. 2.3.1)."""
+    op = gen.random_stencil_2d(3, 20, 16)
+    A = oracle.from_stencil(op)
+    rng = np.random.default_rng(0)
+    xs = rng.standard_normal(A.n)
+    b = A.dense() @ xs
+    eps = 1e-6
+    tau = oracle.tau_eps_normb(b, eps)
+    assert tau == pytest.approx(eps * np.linalg.norm(b) / math.sqrt(A.n), rel=1e-14)
+    # perturb the exact solution so that no point is bad
+    x0 = xs + 1e-3 * eps * rng.standard_normal(A.n) / (1.0 + np.abs(A.dense()).sum(1).max())
+    m = oracle.mark_residual(A, b, x0, oracle.THR_EPS_NORMB, eps, oracle.EXP_NONE, 0)
+    assert m["K"] == 0
+    assert oracle.relres(A, b, x0) <= eps
+
+
+# ------------------------------------------------------------------ marking sets
+
+def _adjacency(A):
+    Ad = A.dense()
+    adj = (Ad != 0).astype(int)
+    np.fill_diagonal(adj, 0)
+    return adj
+
+
+@pytest.mark.parametrize("k", range(7))
+@pytest.mark.parametrize("layers", [0, 1, 2, 3])
+def test_dilation_is_graph_ball(k, layers):
+    A = small_ops()[k]
+    rng = np.random.default_rng(10 * k + layers)
+    mask = (rng.uniform(size=A.n) < 0.1).astype(np.uint8)
+    ref = mask.astype(int)
+    adj = _adjacency(A)
+    for _ in range(layers):
+        ref = ((ref + adj @ ref) > 0).astype(int)
+    assert np.array_equal(oracle.dilate(A, mask, layers), ref.astype(np.uint8))
+
+
+@pytest.mark.parametrize("k", range(7))
+def test_mark_residual_rel_max_brute_force(k):
+    A = small_ops()[k]
+    rng = np.random.default_rng(k)
+    x0 = rng.standard_normal(A.n)
+    b = rng.standard_normal(A.n)
+    m = oracle.mark_residual(A, b, x0, oracle.THR_REL_MAX, 0.3, oracle.EXP_DILATE, 1)
+    r = b - A.dense() @ x0
+    tau = 0.3 * np.abs(r).max()
+    assert m["tau"] == pytest.approx(tau, rel=1e-14)
+    away = np.abs(np.abs(r) - tau) > 1e-12 * tau
+    base = (np.abs(r) > tau).astype(int)
+    ref = ((base + _adjacency(A) @ base) > 0)
+    # every point whose decision is not within rounding of tau agrees
+    near = ~away
+    ok = (m["mask"].astype(bool) == ref) | near | (_adjacency(A) @ near.astype(int) > 0)
+    assert ok.all()
+
+
+def test_paper_expansion_brute_force_random():
+    """Alg 3 expansion vs a direct NumPy restatement of its set rule on a
+    random operator (candidate = neighbour of the domain; add when
+    |r_j| + sum_{i in domain} |a_ji x_i| > tau; synchronous rounds)."""
+    for s in range(6):
+        A = small_ops()[s % 7]
+        Ad = A.dense()
+        rng = np.random.default_rng(100 + s)
+        x0 = rng.standard_normal(A.n)
+        b = Ad @ x0 + (rng.uniform(size=A.n) < 0.15) * rng.standard_normal(A.n)
+        r = b - Ad @ x0
+        tau = 0.05 * np.abs(r).max()
+        mask = (np.abs(r) > tau).astype(np.uint8)
+        got, rounds, _ = oracle.expand_paper(A, oracle.residual(A, b, x0), x0, tau, mask, 4)
+        ref = mask.astype(bool)
+        adj = _adjacency(A).astype(bool)
+        for _ in range(4):
+            cand = ~ref & (adj[:, ref].any(1))
+            c = np.abs(r) + (np.abs(Ad[:, ref] * x0[ref][None, :])).sum(1)
+            add = cand & (c > tau)
+            if not add.any():
+                break
+            ref = ref | add
+        assert np.array_equal(got.astype(bool), ref)
+
+
+@pytest.mark.parametrize("k", range(7))
+def test_gradient_definition(k):
+    A = small_ops()[k]
+    x = np.random.default_rng(k).standard_normal(A.n)
+    g = oracle.gradient(A, x)
+    Ad = A.dense()
+    ref = np.array([sum(abs(x[i] - x[j]) for j in range(A.n) if Ad[i, j] != 0) for i in range(A.n)])
+    assert np.allclose(g, ref, rtol=1e-15, atol=0)
+
+
+def test_gradient_five_point_formula():
+    """For the 5-point scheme g_{p,q} is the sum of the four face jumps
+    (Sec. 2.2, Fig. 'Gradient for five-point scheme')."""
+    nx, ny = 11, 8
+    A = oracle.from_stencil(gen.random_stencil_2d(1, nx, ny))
+    X = np.random.default_rng(2).standard_normal((ny, nx))
+    g = oracle.gradient(A, X.ravel()).reshape(ny, nx)
+    ref = np.zeros_like(X)
+    ref[:, 1:] += np.abs(X[:, 1:] - X[:, :-1])
+    ref[:, :-1] += np.abs(X[:, :-1] - X[:, 1:])
+    ref[1:, :] += np.abs(X[1:, :] - X[:-1, :])
+    ref[:-1, :] += np.abs(X[:-1, :] - X[1:, :])
+    assert np.allclose(g, ref, rtol=1e-15)
+
+
+def test_mark_gradient_edges_and_monotone():
+    """alpha = 1 gives the empty set, alpha = 0 every point with g > 0, and
+    eta(alpha) does not increase with alpha (Sec. 3.5.1)."""
+    op = gen.random_stencil_2d(7, 30, 20)
+    A = oracle.from_stencil(op)
+    x = np.random.default_rng(3).standard_normal(A.n)
+    x[:50] = 1.0  # a flat patch where g may vanish
+    assert oracle.mark_gradient(A, x, 1.0)["K"] == 0
+    m0 = oracle.mark_gradient(A, x, 0.0)
+    assert np.array_equal(m0["mask"].astype(bool), m0["g"] > 0)
+    Ks = [oracle.mark_gradient(A, x, a)["K"] for a in [0.0, 1e-6, 1e-3, 0.1, 0.3, 0.6, 0.9, 1.0]]
+    assert all(a >= b for a, b in zip(Ks, Ks[1:]))
+    g = oracle.gradient(A, x)
+    m = oracle.mark_gradient(A, x, 0.25)
+    assert m["gmax"] == g.max()
+    assert np.array_equal(m["mask"].astype(bool), g > 0.25 * g.max())
+
+
+# ------------------------------------------------------------------ extraction
+
+@pytest.mark.parametrize("k", range(7))
+def test_extract_matches_dense_blocks(k):
+    A = small_ops()[k]
+    Ad = A.dense()
+    rng = np.random.default_rng(k)
+    mask = (rng.uniform(size=A.n) < 0.4).astype(np.uint8)
+    b, x0 = rng.standard_normal(A.n), rng.standard_normal(A.n)
+    s = oracle.extract(A, mask, b, x0)
+    om = np.flatnonzero(mask)
+    rest = np.flatnonzero(mask == 0)
+    assert s["K"] == len(om)
+    assert np.array_equal(s["l2g"], om)
+    assert np.array_equal(s["g2l"][om], np.arange(len(om))) and (s["g2l"][rest] == -1).all()
+    B = s["B"].dense() if s["K"] else np.zeros((0, 0))
+    assert np.array_equal(B, Ad[np.ix_(om, om)])  # values are copied exactly
+    ref = b[om] - Ad[np.ix_(om, rest)] @ x0[rest]
+    scale = np.abs(b[om]) + np.abs(Ad[np.ix_(om, rest)]) @ np.abs(x0[rest])
+    assert np.all(np.abs(s["rhs"] - ref) <= 8e-16 * scale + 0)
+    assert np.array_equal(s["xL0"], x0[om])
+    for l in range(s["K"]):  # columns ascending within each row
+        cols = s["B"].col[s["B"].rowptr[l]:s["B"].rowptr[l + 1]]
+        assert np.all(np.diff(cols) > 0)
+
+
+def test_extract_empty_and_full():
+    A = small_ops()[1]
+    b, x0 = np.ones(A.n), np.zeros(A.n)
+    s0 = oracle.extract(A, np.zeros(A.n, np.uint8), b, x0)
+    assert s0["K"] == 0 and len(s0["rhs"]) == 0
+    s1 = oracle.extract(A, np.ones(A.n, np.uint8), b, x0)
+    assert s1["K"] == A.n and np.array_equal(s1["B"].dense(), A.dense()) and np.array_equal(s1["rhs"], b)
+
+
+# ------------------------------------------------------------------ operator
+
+@pytest.mark.parametrize("k", range(7))
+def test_generated_operator_is_spd_symmetric_dominant(k):
+    Ad = small_ops()[k].dense()
+    assert np.array_equal(Ad, Ad.T)
+    off = np.abs(Ad).sum(1) - np.abs(np.diag(Ad))
+    assert np.all(np.diag(Ad) > off)
+    assert np.linalg.eigvalsh(Ad).min() > 0
+    np.linalg.cholesky(Ad)
+
+
+def test_stencil_csr_rows_sorted_and_exact():
+    op = gen.random_stencil_3d(1, 4, 5, 3)
+    A = oracle.from_stencil(op)
+    for i in range(A.n):
+        c = A.col[A.rowptr[i]:A.rowptr[i + 1]]
+        assert np.all(np.diff(c) > 0)
+    Ad = A.dense()
+    nx, ny, nz = op.shape
+    i = 1 + nx * (1 + ny * 1)
+    assert Ad[i, i + 1] == -op.Tx[i] and Ad[i, i - 1] == -op.Tx[i - 1]
+    assert Ad[i, i + nx * ny] == -op.Tz[i] and Ad[i, i] == op.D[i]
+
+
+# ------------------------------------------------------------------ solves
+
+@pytest.mark.parametrize("k", range(7))
+def test_pcg_matches_dense_lu(k):
+    A = small_ops()[k]
+    Ad = A.dense()
+    rng = np.random.default_rng(k)
+    b = rng.standard_normal(A.n)
+    x, st, it, rr = oracle.pcg(A, b, np.zeros(A.n), tol=1e-13)
+    assert st == oracle.OK and rr <= 1e-13
+    xs = np.linalg.solve(Ad, b)
+    assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+def test_pcg_manufactured_and_warm_start():
+    op = gen.random_stencil_2d(11, 16, 16)
+    A = oracle.from_stencil(op)
+    xs = np.random.default_rng(1).standard_normal(A.n)
+    b = A.dense() @ xs
+    x, st, it_cold, rr = oracle.pcg(A, b, np.zeros(A.n), tol=1e-12)
+    assert st == oracle.OK and np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs)
+    x2, st2, it_warm, _ = oracle.pcg(A, b, xs + 1e-8, tol=1e-12)
+    assert st2 == oracle.OK and it_warm < it_cold
+    x3, st3, it3, _ = oracle.pcg(A, b, xs, tol=1e-12)
+    assert it3 == 0 and np.array_equal(x3, xs)
+
+
+def test_pcg_status_codes():
+    op = gen.random_stencil_2d(2, 10, 10)
+    A = oracle.from_stencil(op)
+    b = np.ones(A.n)
+    _, st, it, _ = oracle.pcg(A, b, np.zeros(A.n), tol=1e-14, maxit=2)
+    assert st == oracle.NOT_CONVERGED and it == 2
+    neg = oracle.csr(A.rowptr, A.col, -A.val)  # negative definite: p^T A p < 0
+    _, st, _, _ = oracle.pcg(neg, b, np.zeros(A.n), tol=1e-8)
+    assert st == oracle.BREAKDOWN
+    x, st, it, _ = oracle.pcg(A, np.zeros(A.n), np.ones(A.n), tol=1e-8)
+    assert st == oracle.OK and not x.any()
+
+
+def test_local_then_global_agrees_with_global():
+    """Local-then-global and a plain global solve reach the same solution to
+    within the solver tolerance (the paper's e_1^0, e_2^0 comparison)."""
+    d = gen.cfg1_heat2d(seed=3, n=48, radius=5)
+    A = oracle.from_stencil(d["op"])
+    tol = 1e-10
+    xg, st, _, _ = oracle.pcg(A, d["b"], d["x0"], tol=tol)
+    for mode in (oracle.MARK_RESIDUAL, oracle.MARK_GRADIENT):
+        x, s, mask = oracle.solve_local_then_global(A, d["b"], d["x0"], mode, alpha=0.6, grad_layers=1, tol=tol)
+        assert s["status"] == 0 and s["relres_final"] <= tol
+        assert 0 < s["K"] < A.n
+        assert np.linalg.norm(x - xg) <= 50 * tol * np.linalg.norm(xg)
+
+
+def test_local_then_global_edge_cases():
+    d = gen.cfg1_heat2d(seed=4, n=24, radius=3)
+    A = oracle.from_stencil(d["op"])
+    # K = N (beta = 0 marks every point with r != 0, dilation fills the rest):
+    x, s, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], thr_param=0.0, exp_rounds=60, tol=1e-9)
+    assert s["K"] == A.n and s["early_exit"] == 1 and s["it_global"] == 0 and s["relres_tilde"] <= 1e-9
+    # K = 0: x~ = x0 and the global solve does all the work
+    x, s, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], thr_param=2.0, exp_rounds=0, tol=1e-9)
+    assert s["K"] == 0 and s["it_local"] == 0 and s["relres_tilde"] == pytest.approx(oracle.relres(A, d["b"], d["x0"]))
+
+
+def test_rtilde_identity_and_bound():
+    """r~_j = r0_j - sum_l a_{j,i_l}(xbar_l - x0_{i_l}) (Sec. 2.3.2) and the
+    bound |r~_j| <= |r0_j| + sum_l |a_{j,i_l} x0_{i_l}| under the paper's
+    assumption |xbar_l - x0_{i_l}| <= |x0_{i_l}|."""
+    d = gen.cfg1_heat2d(seed=5, n=32, radius=4)
+    A = oracle.from_stencil(d["op"])
+    Ad = A.dense()
+    m = oracle.mark_residual(A, d["b"], d["x0"], oracle.THR_REL_MAX, 1e-2, oracle.EXP_DILATE, 1)
+    s = oracle.extract(A, m["mask"], d["b"], d["x0"])
+    xbar, st, _, _ = oracle.pcg(s["B"], s["rhs"], s["xL0"], tol=1e-12)
+    xt = oracle.assemble(d["x0"], s["l2g"], xbar)
+    rt = oracle.residual(A, d["b"], xt)
+    om = s["l2g"]
+    ident = m["r"] - Ad[:, om] @ (xbar - d["x0"][om])
+    assert np.allclose(rt, ident, atol=1e-12 * np.abs(d["b"]).max())
+    assert np.abs(rt[om]).max() <= 1e-10 * np.linalg.norm(s["rhs"])  # local equations solved
+    # the bound needs the assumption at every domain point coupled to row j
+    holds = np.abs(xbar - d["x0"][om]) <= np.abs(d["x0"][om])
+    rows = ~((Ad[:, om] != 0) & ~holds[None, :]).any(1)
+    assert rows.sum() > 0.5 * A.n and (~holds).any()
+    bound = np.abs(m["r"]) + np.abs(Ad[:, om] * d["x0"][om][None, :]).sum(1)
+    assert np.all((np.abs(rt) <= bound * (1 + 1e-12) + 1e-15)[rows])
+
+
+# ------------------------------------------------------------------ adjoint
+
+def _dense_op(k, dt=1.0):
+    return oracle.from_stencil(gen.operator_2d(k, dt)).dense()
+
+
+def test_adjoint_gradient_matches_finite_differences():
+    n = 8
+    rng = np.random.default_rng(0)
+    k = np.exp(rng.uniform(-0.5, 0.5, (n, n)))
+    b = rng.uniform(0.5, 1.5, n * n)
+    xt = rng.standard_normal(n * n) * 0.1
+
+    def loss(kk):
+        x = np.linalg.solve(_dense_op(kk), b)
+        return float(((x - xt) ** 2).sum())
+
+    A = _dense_op(k)
+    x = np.linalg.solve(A, b)
+    lam = np.linalg.solve(A.T, 2.0 * (x - xt))
+    dk = oracle.adjoint_grad_k_2d(n, n, k.ravel(), x, lam)
+    for c in [0, 5, 9, 27, 36, 63]:
+        h = 1e-6 * k.flat[c]
+        kp, km = k.copy(), k.copy()
+        kp.flat[c] += h
+        km.flat[c] -= h
+        fd = (loss(kp) - loss(km)) / (2 * h)
+        assert dk[c] == pytest.approx(fd, rel=2e-6, abs=1e-12)
+    # dL/db = lambda
+    e = np.zeros(n * n)
+    e[17] = 1e-6
+    fd_b = (float(((np.linalg.solve(A, b + e) - xt) ** 2).sum()) - float(((np.linalg.solve(A, b - e) - xt) ** 2).sum())) / 2e-6
+    assert lam[17] == pytest.approx(fd_b, rel=1e-6)
+
+
+def test_strict_thresholds_at_equality():
+    """Alg 2 and Alg 3 use strict '>': a value equal to the threshold is not
+    marked, one just above is."""
+    # 3-point chain, a_21 = -0.5, x0_1 = 0.5, r0 = (1, 0, 0): c_2 = 0 + 0.25
+    rp = np.array([0, 2, 5, 7], np.int32)
+    ci = np.array([0, 1, 0, 1, 2, 1, 2], np.int32)
+    av = np.array([1.0, -0.5, -0.5, 1.0, -0.5, -0.5, 1.0])
+    A = oracle.csr(rp, ci, av)
+    r0 = np.array([1.0, 0.0, 0.0])
+    x0 = np.array([0.5, 0.0, 0.0])
+    m0 = np.array([1, 0, 0], np.uint8)
+    same, added, c = oracle.expand_paper(A, r0, x0, 0.25, m0, 1)
+    assert c[0][1] == 0.25 and added == 0 and list(same) == [1, 0, 0]
+    grown, added, _ = oracle.expand_paper(A, r0, x0, np.nextafter(0.25, 0.0), m0, 1)
+    assert added == 1 and list(grown) == [1, 1, 0]
+    # residual threshold: |r_i| = tau exactly is not a bad point
+    b = np.array([2.0, 1.0, 0.5])
+    m = oracle.mark_residual(A, b, np.zeros(3), oracle.THR_REL_MAX, 0.5, oracle.EXP_NONE, 0)
+    assert m["tau"] == 1.0 and list(m["mask"]) == [1, 0, 0]
+    # gradient threshold: g_i = alpha * g_max exactly is not marked
+    g = oracle.gradient(A, np.array([0.0, 1.0, 1.0]))
+    assert list(g) == [1.0, 1.0, 0.0]
+    mg = oracle.mark_gradient(A, np.array([0.0, 1.0, 1.0]), 1.0)
+    assert mg["K"] == 0
+    mg = oracle.mark_gradient(A, np.array([0.0, 1.0, 3.0]), 0.5)   # g = (1, 3, 2), thr 1.5
+    assert list(mg["mask"]) == [0, 1, 1]
+
+
+def _dense_to_csr(M):
+    rp, ci, av = [0], [], []
+    for i in range(M.shape[0]):
+        for j in range(M.shape[1]):
+            if M[i, j] != 0.0:
+                ci.append(j)
+                av.append(M[i, j])
+        rp.append(len(ci))
+    return oracle.csr(rp, ci, av)
+
+
+def test_pcg_finite_termination():
+    """Jacobi-PCG finishes in at most as many steps as D^-1 A has distinct
+    eigenvalues: one step for a diagonal matrix, two for
+    A = D^1/2 ((1-rho) I + rho 1 1^T) D^1/2 (unit-diagonal core)."""
+    rng = np.random.default_rng(0)
+    d = rng.uniform(1.0, 100.0, 40)
+    b = rng.standard_normal(40)
+    x, st, it, rr = oracle.pcg(_dense_to_csr(np.diag(d)), b, np.zeros(40), tol=1e-13)
+    assert st == oracle.OK and it == 1 and np.allclose(x, b / d, rtol=1e-15)
+    S = np.diag(np.sqrt(d))
+    M = S @ (0.7 * np.eye(40) + 0.3 * np.ones((40, 40))) @ S
+    M = 0.5 * (M + M.T)
+    x, st, it, rr = oracle.pcg(_dense_to_csr(M), b, np.zeros(40), tol=1e-12)
+    assert st == oracle.OK and it == 2 and rr <= 1e-12
