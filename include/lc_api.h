@@ -1,0 +1,229 @@
+/*
+ * lc_api.h -- C ABI of the GB300 (sm_103a) library for the local
+ * character-based linear solve of Ye, An & Xu, "A local character based
+ * method for solving linear systems of radiation diffusion problems"
+ * (arXiv 2001.01158).
+ *
+ * The problem (Sec. 2.1): solve A x = b, A in R^{N x N} sparse, from an
+ * initial iterate x0 (the previous time step or nonlinear iterate), by
+ *   1. marking a local domain Omega_local of "bad points" (Alg 2 from the
+ *      gradient of x0, or Alg 3 from the residual of x0),
+ *   2. extracting and solving the local subsystem B x_B = b_B - E x_C^(0)
+ *      (Eq. loc-equ), assembling x~ (Eq. sol-assemble),
+ *   3. returning x~ if it meets ||b - A x~||_2 <= eps ||b||_2 (Eq.
+ *      rel-res-conv-criteria), else solving the whole system from x~
+ *      (Alg 1).  The Krylov solver is Jacobi-preconditioned CG.
+ *
+ * Conventions shared by every entry point:
+ *   - Every pointer argument named as a vector or array is a DEVICE pointer
+ *     on the context's device unless stated otherwise; the caller owns it
+ *     and keeps it alive until the work enqueued on `stream` has finished.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue work and return without waiting, except that
+ *     a call given a non-NULL host `lc_stats*` waits for its stream before
+ *     filling it.
+ *   - Operators (lc_op) keep the caller's coefficient pointers (no copy) and
+ *     own workspaces sized at creation for N and nnz(A); no entry point
+ *     below allocates device memory.
+ *   - Vectors are FP64, indices int32, masks uint8 (0 or 1); cell index of a
+ *     structured grid i = x + nx*(y + ny*z).
+ *   - Return value: LC_OK or an lc_status code; on error the outputs are
+ *     unspecified except for LC_ERR_NOT_CONVERGED (x holds the last iterate
+ *     and stats are filled).  lc_last_error() gives a message.
+ *   - Calls on one context must not overlap in time from several host
+ *     threads; work on one operator must be serialised on one stream (the
+ *     operator's workspaces are shared by its calls).
+ */
+#ifndef LC_API_H
+#define LC_API_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LC_API_VERSION 1
+
+#if defined(__GNUC__)
+#define LC_EXPORT __attribute__((visibility("default")))
+#else
+#define LC_EXPORT
+#endif
+
+typedef struct lc_ctx lc_ctx;
+typedef struct lc_op lc_op;
+
+typedef enum {
+    LC_OK = 0,
+    LC_ERR_INVALID_ARG = 1,    /* null pointer, bad size, unsorted CSR, non-positive diagonal, bad mode */
+    LC_ERR_CUDA = 2,           /* a CUDA runtime call failed (message in lc_last_error) */
+    LC_ERR_NO_MEMORY = 3,      /* workspace allocation at creation failed */
+    LC_ERR_NOT_CONVERGED = 4,  /* max_iter reached; x = last iterate */
+    LC_ERR_BREAKDOWN = 5,      /* p^T A p <= 0 or not finite (A not SPD, or NaN input) */
+    LC_ERR_TIMEOUT = 6,        /* a bounded grid-wide wait inside a persistent kernel gave up */
+    LC_ERR_TOO_LARGE = 7,      /* sizes beyond int32 indexing or the documented limits */
+    LC_ERR_UNSUPPORTED = 8     /* valid request this build does not provide */
+} lc_status;
+
+/* Threshold of the residual marking. */
+enum {
+    LC_THR_EPS_NORMB = 0,  /* tau = eps ||b||_2 / sqrt(N)  (Sec. 2.3.1)  */
+    LC_THR_REL_MAX = 1     /* tau = beta * max_i |r0_i|   (relative variant) */
+};
+/* Expansion of the residual-marked set. */
+enum {
+    LC_EXP_NONE = 0,
+    LC_EXP_DILATE = 1,     /* add every neighbour, `rounds` times (graph layers) */
+    LC_EXP_PAPER = 2       /* Alg 3: at most `rounds` = E_max conditional rounds */
+};
+enum { LC_MARK_RESIDUAL = 0, LC_MARK_GRADIENT = 1 };
+enum { LC_PREC_FP64 = 0, LC_PREC_MIXED = 1 };
+
+/* Residual-marking parameters (Alg 3 and its relative/dilation variant). */
+typedef struct {
+    int32_t thr_mode;    /* LC_THR_* */
+    double  thr_param;   /* eps (LC_THR_EPS_NORMB) or beta (LC_THR_REL_MAX), >= 0 */
+    int32_t exp_mode;    /* LC_EXP_* */
+    int32_t exp_rounds;  /* layers (DILATE) or E_max (PAPER), 0..64 */
+} lc_mark_params;
+
+/* Krylov solve parameters. */
+typedef struct {
+    double  tol;         /* stop when ||b - A x||_2 <= tol ||b||_2 (Eq. rel-res-conv-criteria) */
+    int32_t max_iter;    /* total CG iterations (all refinement sweeps together) */
+    int32_t precision;   /* LC_PREC_FP64, or LC_PREC_MIXED: FP32 inner CG, FP64 refinement */
+    double  inner_tol;   /* MIXED: relative reduction asked of each FP32 inner solve (e.g. 1e-5) */
+    int32_t max_outer;   /* MIXED: refinement sweeps (e.g. 20) */
+} lc_solve_params;
+
+/* Alg 1 parameters. */
+typedef struct {
+    int32_t         mark_mode;    /* LC_MARK_RESIDUAL | LC_MARK_GRADIENT */
+    lc_mark_params  mark;         /* residual marking */
+    double          alpha;        /* gradient marking (Alg 2), in [0, 1] */
+    int32_t         grad_layers;  /* dilation layers after Alg 2 (0 = as printed) */
+    lc_solve_params global;       /* the whole-system solve (Alg 1 step 11) */
+    lc_solve_params local;        /* the subsystem solve (Alg 1 step 5); tol relative to ||rhs_L||_2 */
+    int32_t         gs_sweeps;    /* Gauss-Seidel sweeps of Alg 1 step 7 (0; others: LC_ERR_UNSUPPORTED) */
+} lc_params;
+
+/* Per-call statistics in the paper's notation (Sec. 3: N, K, eta = K/N). */
+typedef struct {
+    int32_t status;         /* lc_status of the call */
+    int32_t n;              /* N */
+    int32_t K;              /* |Omega_local| */
+    int32_t nnzB;           /* nnz of the local block B */
+    int32_t it_local;       /* CG iterations of the subsystem solve */
+    int32_t it_global;      /* CG iterations of the whole-system solve (0 if x~ was accepted) */
+    int32_t early_exit;     /* 1 if x~ met the criterion (Alg 1 step 9) */
+    int32_t restarts;       /* true-residual restarts / refinement sweeps of the global solve */
+    double  tau;            /* marking threshold (or g_max for gradient marking) */
+    double  eta;            /* K / N */
+    double  relres_tilde;   /* ||b - A x~|| / ||b|| */
+    double  relres_final;   /* ||b - A x|| / ||b|| on return */
+    float   t_mark_ms, t_extract_ms, t_local_ms, t_global_ms, t_total_ms;  /* CUDA-event phase times */
+} lc_stats;
+
+/* Caller-allocated outputs of lc_extract (device pointers).  Capacities:
+ * g2l[N], l2g[N], rowptr[N+1], col[nnz(A)], val[nnz(A)], rhs[N], xL0[N],
+ * K[1], nnz[1].  Only the first K (resp. K+1, nnzB) entries are written. */
+typedef struct {
+    int32_t *g2l;     /* global -> local index, -1 outside Omega_local */
+    int32_t *l2g;     /* local -> global, ascending global order */
+    int32_t *rowptr;  /* CSR of B = A[Omega, Omega] in local indices */
+    int32_t *col;
+    double  *val;     /* copied bit for bit from A */
+    double  *rhs;     /* b_B - E x_C^(0) (Eq. loc-equ), canonical order (below) */
+    double  *xL0;     /* x0 restricted to Omega_local */
+    int32_t *K;       /* device scalar: K */
+    int32_t *nnz;     /* device scalar: nnz(B) */
+} lc_subsys;
+
+/* ---- context and operators ------------------------------------------- */
+
+/* Create a context on CUDA device `device` (sets it current for the call). */
+LC_EXPORT int lc_ctx_create(lc_ctx **ctx, int device);
+LC_EXPORT int lc_ctx_destroy(lc_ctx *ctx);
+
+/* General sparse A (CSR, device pointers): rowptr[n+1], col[nnz] ascending
+ * and unique within each row, val[nnz]; every row must hold its diagonal
+ * with a positive value (checked; LC_ERR_INVALID_ARG otherwise).
+ * nnz < 2^31 (LC_ERR_TOO_LARGE).  The neighbours of i are the j != i with a
+ * stored a_ij != 0. */
+LC_EXPORT int lc_op_create_csr(lc_ctx *ctx, lc_op **op, int32_t n, int64_t nnz,
+                     const int32_t *rowptr, const int32_t *col, const double *val);
+
+/* Structured 5-point (dim 2) or 7-point (dim 3) operator, shape = {nx, ny,
+ * nz} (nz = 1 for dim 2), device arrays of N = nx*ny*nz values:
+ *   D  diagonal a_ii > 0
+ *   Tx face conductance between i and i+1     : a_{i,i+1} = a_{i+1,i} = -Tx[i]
+ *   Ty face conductance between i and i+nx    : a_{i,i+nx} = -Ty[i]
+ *   Tz face conductance between i and i+nx*ny : (dim 3 only; NULL for dim 2)
+ * Every interior face conductance must be > 0 (checked); entries on the last
+ * column/row/plane are not read.  This is the same matrix, bit for bit, as
+ * the CSR with those negated entries in ascending column order. */
+LC_EXPORT int lc_op_create_stencil(lc_ctx *ctx, lc_op **op, int32_t dim, const int32_t shape[3],
+                         const double *D, const double *Tx, const double *Ty, const double *Tz);
+LC_EXPORT int lc_op_destroy(lc_op *op);
+
+/* ---- the hot path ------------------------------------------------------- */
+
+/* Residual-based local domain (Alg 3; Eq. resi-local-domain-0).
+ *   r0 = b - A x0 with r_i = b_i; r_i = fma(-a_ij, x0_j, r_i) over j
+ *   ascending (the canonical order; bit-identical for stencil and CSR).
+ *   tau: EPS_NORMB: (eps*sqrt(S))/sqrt((double)N), S = sum b_i^2 by a
+ *   stride-halving tree over zero-padded chunks of 1024, repeated on the
+ *   chunk sums; REL_MAX: beta * max_i |r0_i| (NaN entries ignored).
+ *   mask_i = |r0_i| > tau, then the expansion: DILATE adds all neighbours
+ *   `rounds` times; PAPER runs Alg 3's synchronous rounds with
+ *   c_j = |r0_j| + t, t = sum over domain neighbours i (ascending) of
+ *   |a_ji * x0_i| (one rounded product, then a rounded sum), added if c_j > tau.
+ * Outputs: mask[N]; r0_opt[N] (may be NULL); K_dev[1] = |Omega_local|;
+ * tau_dev[1] (may be NULL).  The results are bit-identical to a serial FP64
+ * evaluation of these definitions. */
+LC_EXPORT int lc_mark_residual(lc_ctx *ctx, const lc_op *op, const double *b, const double *x0,
+                     const lc_mark_params *p, uint8_t *mask, double *r0_opt,
+                     int32_t *K_dev, double *tau_dev, void *stream);
+
+/* Gradient-based local domain (Alg 2; Eq. grad): g_i = sum over neighbours
+ * j (ascending) of |x0_i - x0_j| (plain additions from 0), g_max = max(0,
+ * max g), mask_i = g_i > fl(alpha * g_max), then `layers` dilation rounds.
+ * Outputs mask[N], K_dev[1], gmax_dev[1] (may be NULL). */
+LC_EXPORT int lc_mark_gradient(lc_ctx *ctx, const lc_op *op, const double *x0, double alpha, int32_t layers,
+                     uint8_t *mask, int32_t *K_dev, double *gmax_dev, void *stream);
+
+/* Local subsystem (Sec. 2.1, Eq. loc-equ) from a mask: local indices in
+ * ascending global order; B = A[Omega, Omega] with values copied; rhs_l =
+ * b_i; rhs_l = fma(-a_ij, x0_j, rhs_l) over non-local j ascending; xL0 =
+ * x0[Omega].  Bit-identical to the serial definition. */
+LC_EXPORT int lc_extract(lc_ctx *ctx, const lc_op *op, const uint8_t *mask, const double *b,
+               const double *x0, const lc_subsys *out, void *stream);
+
+/* Jacobi-preconditioned CG on the whole system from the iterate in x (in:
+ * x0, out: x).  Stops when ||r||^2 <= tol^2 ||b||^2 on the recurrence
+ * residual, then confirms with the true residual and restarts from it if
+ * needed (at most 3 restarts).  b = 0 gives x = 0.  One persistent
+ * cooperative launch (FP64), or FP32 inner solves inside FP64 iterative
+ * refinement (LC_PREC_MIXED).  stats (host, may be NULL) waits for the
+ * stream. */
+LC_EXPORT int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double *x,
+                 const lc_solve_params *p, lc_stats *stats, void *stream);
+
+/* Alg 1 without host synchronisation: mark (residual or gradient), extract,
+ * local Jacobi-PCG from xL0 (tolerance relative to ||rhs||), assemble x~ in
+ * place in x, check ||b - A x~|| <= tol ||b||, and only if that fails run the
+ * global PCG from x~.  x: in x0, out x.  stats (host, may be NULL) waits for
+ * the stream and fills phase times. */
+LC_EXPORT int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const double *b, double *x,
+                               const lc_params *p, lc_stats *stats, void *stream);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+
+LC_EXPORT const char *lc_error_string(int code);
+LC_EXPORT const char *lc_last_error(const lc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LC_API_H */

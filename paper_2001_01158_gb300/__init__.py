@@ -1,0 +1,277 @@
+"""GB300 library for the local character-based linear solve of Ye, An & Xu
+(arXiv 2001.01158): mark a local domain from the residual (Alg 3) or the
+gradient (Alg 2) of the previous iterate, extract and solve the local
+subsystem (Eq. loc-equ), then finish with a warm-started global
+Jacobi-preconditioned CG (Alg 1).
+
+This module is the Python binding of the C ABI in ``include/lc_api.h``:
+argument marshalling only.  Every step of the path runs in the CUDA kernels
+of ``liblc.so`` (built by :func:`build`); PyTorch supplies device memory and
+streams.  There is no CPU fallback: without the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+from .build import LIB, build_library
+
+__all__ = [
+    "LcError", "Context", "StencilOperator", "CsrOperator", "MarkParams", "SolveParams", "Params", "Stats",
+    "Subsystem", "mark_residual", "mark_gradient", "extract", "pcg_solve", "solve_local_then_global", "build",
+    "lib", "THR_EPS_NORMB", "THR_REL_MAX", "EXP_NONE", "EXP_DILATE", "EXP_PAPER", "MARK_RESIDUAL",
+    "MARK_GRADIENT", "PREC_FP64", "PREC_MIXED",
+]
+
+LC_OK, LC_ERR_INVALID_ARG, LC_ERR_CUDA, LC_ERR_NO_MEMORY, LC_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
+LC_ERR_BREAKDOWN, LC_ERR_TIMEOUT, LC_ERR_TOO_LARGE, LC_ERR_UNSUPPORTED = 5, 6, 7, 8
+THR_EPS_NORMB, THR_REL_MAX = 0, 1
+EXP_NONE, EXP_DILATE, EXP_PAPER = 0, 1, 2
+MARK_RESIDUAL, MARK_GRADIENT = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class LcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lc error {code}: {msg}")
+        self.code = code
+
+
+class MarkParams(C.Structure):
+    _fields_ = [("thr_mode", C.c_int32), ("thr_param", C.c_double), ("exp_mode", C.c_int32),
+                ("exp_rounds", C.c_int32)]
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("mark_mode", C.c_int32), ("mark", MarkParams), ("alpha", C.c_double),
+                ("grad_layers", C.c_int32), ("global_", SolveParams), ("local", SolveParams),
+                ("gs_sweeps", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n", C.c_int32), ("K", C.c_int32), ("nnzB", C.c_int32),
+                ("it_local", C.c_int32), ("it_global", C.c_int32), ("early_exit", C.c_int32),
+                ("restarts", C.c_int32), ("tau", C.c_double), ("eta", C.c_double),
+                ("relres_tilde", C.c_double), ("relres_final", C.c_double),
+                ("t_mark_ms", C.c_float), ("t_extract_ms", C.c_float), ("t_local_ms", C.c_float),
+                ("t_global_ms", C.c_float), ("t_total_ms", C.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class _Subsys(C.Structure):
+    _fields_ = [(f, C.c_void_p) for f in ("g2l", "l2g", "rowptr", "col", "val", "rhs", "xL0", "K", "nnz")]
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liblc.so for sm_103a (in-tree) and return its path."""
+    return build_library(force=force)
+
+
+def lib():
+    """The loaded C library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"{LIB} is missing: build it with paper_2001_01158_gb300.build() "
+                           "(the library has no CPU fallback)")
+    L = C.CDLL(LIB)
+    vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    L.lc_ctx_create.argtypes = [C.POINTER(vp), C.c_int]
+    L.lc_ctx_destroy.argtypes = [vp]
+    L.lc_op_create_csr.argtypes = [vp, C.POINTER(vp), i32, i64, vp, vp, vp]
+    L.lc_op_create_stencil.argtypes = [vp, C.POINTER(vp), i32, C.POINTER(i32), vp, vp, vp, vp]
+    L.lc_op_destroy.argtypes = [vp]
+    L.lc_mark_residual.argtypes = [vp, vp, vp, vp, C.POINTER(MarkParams), vp, vp, vp, vp, vp]
+    L.lc_mark_gradient.argtypes = [vp, vp, vp, d, i32, vp, vp, vp, vp]
+    L.lc_extract.argtypes = [vp, vp, vp, vp, vp, C.POINTER(_Subsys), vp]
+    L.lc_pcg_solve.argtypes = [vp, vp, vp, vp, C.POINTER(SolveParams), C.POINTER(Stats), vp]
+    L.lc_solve_local_then_global.argtypes = [vp, vp, vp, vp, C.POINTER(Params), C.POINTER(Stats), vp]
+    L.lc_error_string.argtypes = [C.c_int]
+    L.lc_error_string.restype = C.c_char_p
+    L.lc_last_error.argtypes = [vp]
+    L.lc_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _ptr(t: torch.Tensor | None, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """lc_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = C.c_void_p()
+        rc = lib().lc_ctx_create(C.byref(h), device)
+        if rc:
+            raise LcError(rc, lib().lc_error_string(rc).decode())
+        self.h = h
+
+    def check(self, rc: int, allow=()):
+        if rc and rc not in allow:
+            raise LcError(rc, f"{lib().lc_error_string(rc).decode()}: {lib().lc_last_error(self.h).decode()}")
+        return rc
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.lc_ctx_destroy(self.h)
+            self.h = None
+
+
+class _Operator:
+    n: int
+    nnz: int
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.lc_op_destroy(self.h)
+            self.h = None
+
+
+class StencilOperator(_Operator):
+    """5-point (2D) or 7-point (3D) operator from device arrays D, Tx, Ty(, Tz)."""
+
+    def __init__(self, ctx: Context, shape, D, Tx, Ty, Tz=None):
+        nx, ny, nz = (tuple(shape) + (1,))[:3]
+        self.ctx, self.shape = ctx, (int(nx), int(ny), int(nz))
+        self.dim = 3 if Tz is not None else 2
+        self._keep = (D, Tx, Ty, Tz)
+        self.n = nx * ny * nz
+        self.nnz = self.n + 2 * ((nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1))
+        for name, t in (("D", D), ("Tx", Tx), ("Ty", Ty), ("Tz", Tz)):
+            if t is not None and t.numel() != self.n:
+                raise ValueError(f"{name} has {t.numel()} values, expected {self.n}")
+        sh = (C.c_int32 * 3)(nx, ny, nz)
+        h = C.c_void_p()
+        ctx.check(lib().lc_op_create_stencil(ctx.h, C.byref(h), self.dim, sh, _ptr(D, torch.float64, "D"),
+                                             _ptr(Tx, torch.float64, "Tx"), _ptr(Ty, torch.float64, "Ty"),
+                                             _ptr(Tz, torch.float64, "Tz")))
+        self.h = h
+
+
+class CsrOperator(_Operator):
+    """General sparse operator from device CSR arrays (int32, int32, float64)."""
+
+    def __init__(self, ctx: Context, rowptr, col, val):
+        self.ctx = ctx
+        self._keep = (rowptr, col, val)
+        self.n = rowptr.numel() - 1
+        self.nnz = col.numel()
+        h = C.c_void_p()
+        ctx.check(lib().lc_op_create_csr(ctx.h, C.byref(h), self.n, self.nnz, _ptr(rowptr, torch.int32, "rowptr"),
+                                         _ptr(col, torch.int32, "col"), _ptr(val, torch.float64, "val")))
+        self.h = h
+
+
+@dataclass
+class Subsystem:
+    """Caller-allocated outputs of extract() (device tensors of full capacity)."""
+    g2l: torch.Tensor
+    l2g: torch.Tensor
+    rowptr: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor
+    rhs: torch.Tensor
+    xL0: torch.Tensor
+    K: torch.Tensor
+    nnz: torch.Tensor
+
+    @staticmethod
+    def empty(op: _Operator, device=None) -> "Subsystem":
+        dev = device or torch.device("cuda", op.ctx.device)
+        n, nnz = op.n, op.nnz
+        return Subsystem(torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
+                         torch.empty(n + 1, dtype=torch.int32, device=dev),
+                         torch.empty(max(nnz, 1), dtype=torch.int32, device=dev),
+                         torch.empty(max(nnz, 1), dtype=torch.float64, device=dev),
+                         torch.empty(n, dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.float64, device=dev),
+                         torch.zeros(1, dtype=torch.int32, device=dev), torch.zeros(1, dtype=torch.int32, device=dev))
+
+    def trimmed(self) -> dict:
+        """Host copies of the meaningful parts (synchronises)."""
+        K, nz = int(self.K.item()), int(self.nnz.item())
+        return {"K": K, "nnz": nz, "g2l": self.g2l.cpu().numpy(), "l2g": self.l2g[:K].cpu().numpy(),
+                "rowptr": self.rowptr[:K + 1].cpu().numpy(), "col": self.col[:nz].cpu().numpy(),
+                "val": self.val[:nz].cpu().numpy(), "rhs": self.rhs[:K].cpu().numpy(),
+                "xL0": self.xL0[:K].cpu().numpy()}
+
+
+def mark_residual(ctx: Context, op: _Operator, b, x0, params: MarkParams, mask, K, r0=None, tau=None, stream=None):
+    """lc_mark_residual: mask (uint8[N]), K (int32[1]), optional r0 (float64[N]) and tau (float64[1])."""
+    return ctx.check(lib().lc_mark_residual(ctx.h, op.h, _ptr(b, torch.float64, "b"), _ptr(x0, torch.float64, "x0"),
+                                            C.byref(params), _ptr(mask, torch.uint8, "mask"),
+                                            _ptr(r0, torch.float64, "r0"), _ptr(K, torch.int32, "K"),
+                                            _ptr(tau, torch.float64, "tau"), _stream(stream)))
+
+
+def mark_gradient(ctx: Context, op: _Operator, x0, alpha: float, layers: int, mask, K, gmax=None, stream=None):
+    """lc_mark_gradient."""
+    return ctx.check(lib().lc_mark_gradient(ctx.h, op.h, _ptr(x0, torch.float64, "x0"), float(alpha), int(layers),
+                                            _ptr(mask, torch.uint8, "mask"), _ptr(K, torch.int32, "K"),
+                                            _ptr(gmax, torch.float64, "gmax"), _stream(stream)))
+
+
+def extract(ctx: Context, op: _Operator, mask, b, x0, out: Subsystem, stream=None):
+    """lc_extract into caller-allocated `out`."""
+    s = _Subsys(*(_ptr(getattr(out, f), None, f) for f, _ in _Subsys._fields_))
+    return ctx.check(lib().lc_extract(ctx.h, op.h, _ptr(mask, torch.uint8, "mask"), _ptr(b, torch.float64, "b"),
+                                      _ptr(x0, torch.float64, "x0"), C.byref(s), _stream(stream)))
+
+
+def pcg_solve(ctx: Context, op: _Operator, b, x, params: SolveParams, stats: Stats | None = None, stream=None,
+              allow_not_converged=False):
+    """lc_pcg_solve: x holds x0 on entry and the solution on return."""
+    allow = (LC_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    return ctx.check(lib().lc_pcg_solve(ctx.h, op.h, _ptr(b, torch.float64, "b"), _ptr(x, torch.float64, "x"),
+                                        C.byref(params), C.byref(stats) if stats is not None else None,
+                                        _stream(stream)), allow)
+
+
+def solve_local_then_global(ctx: Context, op: _Operator, b, x, params: Params, stats: Stats | None = None,
+                            stream=None, allow_not_converged=False):
+    """lc_solve_local_then_global (Alg 1): x holds x0 on entry and the solution on return."""
+    allow = (LC_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    return ctx.check(lib().lc_solve_local_then_global(ctx.h, op.h, _ptr(b, torch.float64, "b"),
+                                                      _ptr(x, torch.float64, "x"), C.byref(params),
+                                                      C.byref(stats) if stats is not None else None,
+                                                      _stream(stream)), allow)
+
+
+def default_params(mark_mode=MARK_RESIDUAL, thr_mode=THR_REL_MAX, thr_param=1e-3, exp_mode=EXP_DILATE, exp_rounds=2,
+                   alpha=1e-3, grad_layers=2, tol=1e-8, tol_local=None, max_iter=100000,
+                   precision=PREC_FP64, inner_tol=1e-5, max_outer=30) -> Params:
+    """Alg 1 parameters with the relative-threshold, 2-layer defaults."""
+    g = SolveParams(tol, max_iter, precision, inner_tol, max_outer)
+    l = SolveParams(tol if tol_local is None else tol_local, max_iter, precision, inner_tol, max_outer)
+    return Params(mark_mode, MarkParams(thr_mode, thr_param, exp_mode, exp_rounds), alpha, grad_layers, g, l, 0)

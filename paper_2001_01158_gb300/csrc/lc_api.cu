@@ -1,0 +1,552 @@
+// lc_api.cu -- host implementation of the C ABI declared in include/lc_api.h.
+//
+// Argument checking, workspace ownership and the stream-ordered sequencing
+// of the kernels of lc_mark.cu, lc_extract.cu and lc_pcg.cu.  No entry point
+// of the hot path allocates, synchronises or copies to the host unless it
+// is asked for host statistics.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lc_internal.cuh"
+
+struct lc_ctx {
+    int device = 0;
+    int sms = 0;
+    std::string err;
+};
+
+struct lc_op {
+    lc_ctx *ctx = nullptr;
+    int kind = 0;   // 0 stencil, 1 csr
+    lc::Stencil st{};
+    lc::Csr csr{};
+    int64_t n = 0, nnz = 0;
+    // owned device memory
+    void *arena = nullptr;
+    lc::Ctrl *ctrl = nullptr;        // marking / global solve
+    lc::Ctrl *ctrl_loc = nullptr;    // local solve
+    double *dinv = nullptr;
+    float *D32 = nullptr, *Tx32 = nullptr, *Ty32 = nullptr, *Tz32 = nullptr, *dinv32 = nullptr;
+    double *work = nullptr;          // residual / gradient (N)
+    uint8_t *mask_tmp = nullptr, *mask_own = nullptr;
+    double *tree_a = nullptr, *tree_b = nullptr;
+    lc::ExtractWork ew{};
+    lc_subsys sub{};                 // internal subsystem buffers
+    lc::PcgWork pw{};
+    cudaEvent_t ev[6] = {};
+};
+
+namespace {
+
+int fail(lc_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(lc_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, LC_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define LC_CUDA(ctx, call)                                           \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Carve one allocation into aligned pieces.
+struct Carver {
+    size_t off = 0;
+    char *base = nullptr;
+    template <class T>
+    T *take(size_t count) {
+        off = align_up(off, 256);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T) + 16;
+        return p;
+    }
+};
+
+void carve(lc_op *op, Carver &c) {
+    const size_t n = (size_t)op->n, nnz = (size_t)op->nnz;
+    const size_t nchunks = (n + lc::kTreeChunk - 1) / lc::kTreeChunk + 2;
+    const size_t xblocks = (n + 1023) / 1024 + 2;
+    op->ctrl = c.take<lc::Ctrl>(1);
+    op->ctrl_loc = c.take<lc::Ctrl>(1);
+    op->work = c.take<double>(n);
+    op->mask_tmp = c.take<uint8_t>(n);
+    op->mask_own = c.take<uint8_t>(n);
+    op->tree_a = c.take<double>(nchunks);
+    op->tree_b = c.take<double>(nchunks);
+    op->ew.blk = c.take<unsigned long long>(xblocks);
+    op->ew.nblocks_cap = (int64_t)xblocks;
+    op->sub.g2l = c.take<int32_t>(n);
+    op->sub.l2g = c.take<int32_t>(n);
+    op->sub.rowptr = c.take<int32_t>(n + 1);
+    op->sub.col = c.take<int32_t>(nnz);
+    op->sub.val = c.take<double>(nnz);
+    op->sub.rhs = c.take<double>(n);
+    op->sub.xL0 = c.take<double>(n);
+    op->sub.K = c.take<int32_t>(1);
+    op->sub.nnz = c.take<int32_t>(1);
+    op->pw.r = c.take<double>(n);
+    op->pw.z = c.take<double>(n);
+    op->pw.p0 = c.take<double>(n);
+    op->pw.p1 = c.take<double>(n);
+    op->pw.q = c.take<double>(n);
+    op->pw.dinv = c.take<double>(n);
+    op->pw.partials = c.take<double>((size_t)lc::kMaxGrid * 8);
+    if (op->kind == 0) {
+        op->dinv = c.take<double>(n);
+        op->D32 = c.take<float>(n);
+        op->Tx32 = c.take<float>(n);
+        op->Ty32 = c.take<float>(n);
+        op->Tz32 = op->st.dim == 3 ? c.take<float>(n) : nullptr;
+        op->dinv32 = c.take<float>(n);
+    }
+}
+
+int alloc_op(lc_op *op) {
+    Carver probe;
+    carve(op, probe);
+    void *mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, probe.off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(op->ctx, LC_ERR_NO_MEMORY, "workspace of %zu bytes: %s", probe.off, cudaGetErrorString(e));
+    }
+    op->arena = mem;
+    Carver real;
+    real.base = static_cast<char *>(mem);
+    carve(op, real);
+    LC_CUDA(op->ctx, cudaMemset(op->ctrl, 0, sizeof(lc::Ctrl)));
+    LC_CUDA(op->ctx, cudaMemset(op->ctrl_loc, 0, sizeof(lc::Ctrl)));
+    for (auto &ev : op->ev) LC_CUDA(op->ctx, cudaEventCreate(&ev));
+    return LC_OK;
+}
+
+lc::Csr sub_csr(const lc_op *op) {
+    lc::Csr c{};
+    c.n = (int32_t)op->n;
+    c.n_dev = op->sub.K;
+    c.rp = op->sub.rowptr;
+    c.ci = op->sub.col;
+    c.av = op->sub.val;
+    return c;
+}
+
+int check_common(lc_ctx *ctx, const lc_op *op) {
+    if (!ctx) return LC_ERR_INVALID_ARG;
+    if (!op) return fail(ctx, LC_ERR_INVALID_ARG, "null operator");
+    if (op->ctx != ctx) return fail(ctx, LC_ERR_INVALID_ARG, "operator belongs to another context");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return LC_OK;
+}
+
+// Threshold / expansion of an already computed r (or g) in op->work or r.
+int run_threshold_expand(lc_ctx *ctx, const lc_op *op, const double *v, const double *x0, int exp_mode, int rounds,
+                         uint8_t *mask, cudaStream_t s) {
+    uint8_t *tmp = op->mask_tmp;
+    if (op->kind == 0) {
+        const int lmax = lc::max_layers_per_pass(op->st.dim);
+        if (exp_mode == LC_EXP_DILATE && rounds > 0) {
+            const int first = rounds < lmax ? rounds : lmax;
+            const int rest = rounds - first;
+            const int passes = 1 + (rest + lmax - 1) / lmax;
+            uint8_t *dst = ((passes - 1) % 2 == 0) ? mask : tmp;
+            LC_CUDA(ctx, lc::launch_threshold_dilate_stencil(op->st, v, first, dst, op->ctrl, s));
+            int left = rest;
+            uint8_t *cur = dst;
+            while (left > 0) {
+                const int l = left < lmax ? left : lmax;
+                uint8_t *nxt = cur == mask ? tmp : mask;
+                LC_CUDA(ctx, lc::launch_dilate_stencil_pass(op->st, l, cur, nxt, s));
+                cur = nxt;
+                left -= l;
+            }
+            return LC_OK;
+        }
+        if (exp_mode == LC_EXP_PAPER && rounds > 0) {
+            uint8_t *cur = (rounds % 2 == 0) ? mask : tmp;
+            LC_CUDA(ctx, lc::launch_threshold_dilate_stencil(op->st, v, 0, cur, op->ctrl, s));
+            for (int m = 0; m < rounds; ++m) {
+                uint8_t *nxt = cur == mask ? tmp : mask;
+                LC_CUDA(ctx, lc::launch_expand_paper_stencil(op->st, v, x0, m, cur, nxt, op->ctrl, s));
+                cur = nxt;
+            }
+            return LC_OK;
+        }
+        LC_CUDA(ctx, lc::launch_threshold_dilate_stencil(op->st, v, 0, mask, op->ctrl, s));
+        return LC_OK;
+    }
+    const int32_t n = (int32_t)op->n;
+    if (rounds <= 0 || exp_mode == LC_EXP_NONE) {
+        LC_CUDA(ctx, lc::launch_threshold_csr(n, v, mask, op->ctrl, s));
+        return LC_OK;
+    }
+    uint8_t *cur = (rounds % 2 == 0) ? mask : tmp;
+    LC_CUDA(ctx, lc::launch_threshold_csr(n, v, cur, op->ctrl, s));
+    for (int m = 0; m < rounds; ++m) {
+        uint8_t *nxt = cur == mask ? tmp : mask;
+        if (exp_mode == LC_EXP_DILATE) LC_CUDA(ctx, lc::launch_dilate_csr(op->csr, cur, nxt, s));
+        else LC_CUDA(ctx, lc::launch_expand_paper_csr(op->csr, v, x0, m, cur, nxt, op->ctrl, s));
+        cur = nxt;
+    }
+    return LC_OK;
+}
+
+int mark_residual_impl(lc_ctx *ctx, const lc_op *op, const double *b, const double *x0, const lc_mark_params *p,
+                       uint8_t *mask, double *r0, int32_t *K_dev, double *tau_dev, cudaStream_t s) {
+    if (!b || !x0 || !p || !mask) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    if (p->thr_mode != LC_THR_EPS_NORMB && p->thr_mode != LC_THR_REL_MAX)
+        return fail(ctx, LC_ERR_INVALID_ARG, "unknown threshold mode %d", p->thr_mode);
+    if (!(p->thr_param >= 0.0) || !std::isfinite(p->thr_param))
+        return fail(ctx, LC_ERR_INVALID_ARG, "threshold parameter must be finite and >= 0");
+    if (p->exp_mode < LC_EXP_NONE || p->exp_mode > LC_EXP_PAPER)
+        return fail(ctx, LC_ERR_INVALID_ARG, "unknown expansion mode %d", p->exp_mode);
+    if (p->exp_rounds < 0 || p->exp_rounds > lc::kMaxExpRounds)
+        return fail(ctx, LC_ERR_INVALID_ARG, "expansion rounds must be in [0, %d]", lc::kMaxExpRounds);
+    double *r = r0 ? r0 : op->work;
+    const double param = p->thr_param == 0.0 ? 0.0 : p->thr_param;   // no -0
+    LC_CUDA(ctx, cudaMemsetAsync(op->ctrl, 0, sizeof(lc::Ctrl), s));
+    const int tree = p->thr_mode == LC_THR_EPS_NORMB;
+    if (op->kind == 0) LC_CUDA(ctx, lc::launch_residual_stencil(op->st, b, x0, r, tree, op->tree_a, op->ctrl, s));
+    else LC_CUDA(ctx, lc::launch_residual_csr(op->csr, b, x0, r, tree, op->tree_a, op->ctrl, s));
+    if (tree) {
+        const int64_t nchunks = (op->n + lc::kTreeChunk - 1) / lc::kTreeChunk;
+        LC_CUDA(ctx, lc::launch_tree_finish(op->tree_a, op->tree_b, nchunks, op->n, param, op->ctrl, tau_dev, s));
+    } else {
+        LC_CUDA(ctx, lc::launch_tau_relmax(param, op->ctrl, tau_dev, s));
+    }
+    int rc = run_threshold_expand(ctx, op, r, x0, p->exp_mode, p->exp_rounds, mask, s);
+    if (rc) return rc;
+    LC_CUDA(ctx, cudaMemsetAsync(&op->ctrl->K, 0, sizeof(int32_t), s));
+    LC_CUDA(ctx, lc::launch_count_mask(op->n, mask, op->ctrl, K_dev, s));
+    return LC_OK;
+}
+
+int mark_gradient_impl(lc_ctx *ctx, const lc_op *op, const double *x0, double alpha, int32_t layers, uint8_t *mask,
+                       int32_t *K_dev, double *gmax_dev, cudaStream_t s) {
+    if (!x0 || !mask) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(ctx, LC_ERR_INVALID_ARG, "alpha must be in [0, 1]");
+    if (layers < 0 || layers > lc::kMaxExpRounds)
+        return fail(ctx, LC_ERR_INVALID_ARG, "layers must be in [0, %d]", lc::kMaxExpRounds);
+    LC_CUDA(ctx, cudaMemsetAsync(op->ctrl, 0, sizeof(lc::Ctrl), s));
+    if (op->kind == 0) LC_CUDA(ctx, lc::launch_gradient_stencil(op->st, x0, op->work, op->ctrl, s));
+    else LC_CUDA(ctx, lc::launch_gradient_csr(op->csr, x0, op->work, op->ctrl, s));
+    LC_CUDA(ctx, lc::launch_gmax_threshold(alpha == 0.0 ? 0.0 : alpha, op->ctrl, gmax_dev, s));
+    int rc = run_threshold_expand(ctx, op, op->work, x0, layers > 0 ? LC_EXP_DILATE : LC_EXP_NONE, layers, mask, s);
+    if (rc) return rc;
+    LC_CUDA(ctx, cudaMemsetAsync(&op->ctrl->K, 0, sizeof(int32_t), s));
+    LC_CUDA(ctx, lc::launch_count_mask(op->n, mask, op->ctrl, K_dev, s));
+    return LC_OK;
+}
+
+int extract_impl(lc_ctx *ctx, const lc_op *op, const uint8_t *mask, const double *b, const double *x0,
+                 const lc_subsys &out, cudaStream_t s) {
+    if (!mask || !b || !x0) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    if (!out.g2l || !out.l2g || !out.rowptr || !out.col || !out.val || !out.rhs || !out.xL0 || !out.K || !out.nnz)
+        return fail(ctx, LC_ERR_INVALID_ARG, "null subsystem output");
+    lc::ExtractWork w = op->ew;
+    if (op->kind == 0) LC_CUDA(ctx, lc::launch_extract_stencil(op->st, mask, b, x0, out, w, op->ctrl, s));
+    else LC_CUDA(ctx, lc::launch_extract_csr(op->csr, mask, b, x0, out, w, op->ctrl, s));
+    return LC_OK;
+}
+
+int check_solve_params(lc_ctx *ctx, const lc_solve_params *p) {
+    if (!p) return fail(ctx, LC_ERR_INVALID_ARG, "null solve parameters");
+    if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) return fail(ctx, LC_ERR_INVALID_ARG, "tol must be finite and >= 0");
+    if (p->max_iter < 0) return fail(ctx, LC_ERR_INVALID_ARG, "max_iter < 0");
+    if (p->precision != LC_PREC_FP64)
+        return fail(ctx, LC_ERR_UNSUPPORTED, "precision %d not provided by this build", p->precision);
+    return LC_OK;
+}
+
+int pcg_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_solve_params *p, lc::Ctrl *ctrl,
+             bool local, cudaStream_t s) {
+    lc::PcgArgs a{b, x, p->tol, p->max_iter, 3};
+    lc::PcgWork w = op->pw;
+    LC_CUDA(ctx, cudaMemsetAsync(&ctrl->status, 0, sizeof(int32_t), s));
+    if (local) {
+        LC_CUDA(ctx, lc::launch_pcg_csr(sub_csr(op), a, w, ctrl, ctx->sms * 2, s));
+    } else if (op->kind == 0) {
+        LC_CUDA(ctx, lc::launch_pcg_stencil(op->st, a, w, ctrl, 0, s));
+    } else {
+        LC_CUDA(ctx, lc::launch_pcg_csr(op->csr, a, w, ctrl, 0, s));
+    }
+    return LC_OK;
+}
+
+int read_ctrl(lc_ctx *ctx, const lc::Ctrl *dev, lc::Ctrl *host) {
+    LC_CUDA(ctx, cudaMemcpy(host, dev, sizeof(lc::Ctrl), cudaMemcpyDeviceToHost));
+    return LC_OK;
+}
+
+int status_of(const lc::Ctrl &c) {
+    if (c.status != LC_OK) return c.status;
+    if (c.converged == -1) return LC_ERR_BREAKDOWN;
+    if (c.converged == 0) return LC_ERR_NOT_CONVERGED;
+    return LC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lc_error_string(int code) {
+    switch (code) {
+        case LC_OK: return "ok";
+        case LC_ERR_INVALID_ARG: return "invalid argument";
+        case LC_ERR_CUDA: return "CUDA error";
+        case LC_ERR_NO_MEMORY: return "out of device memory";
+        case LC_ERR_NOT_CONVERGED: return "not converged";
+        case LC_ERR_BREAKDOWN: return "Krylov breakdown (operator not SPD or non-finite data)";
+        case LC_ERR_TIMEOUT: return "grid-wide wait timed out";
+        case LC_ERR_TOO_LARGE: return "problem too large";
+        case LC_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown error";
+    }
+}
+
+const char *lc_last_error(const lc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int lc_ctx_create(lc_ctx **out, int device) {
+    if (!out) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return LC_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return LC_ERR_CUDA;
+    lc_ctx *c = new (std::nothrow) lc_ctx;
+    if (!c) return LC_ERR_NO_MEMORY;
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    *out = c;
+    return LC_OK;
+}
+
+int lc_ctx_destroy(lc_ctx *ctx) {
+    delete ctx;
+    return LC_OK;
+}
+
+int lc_op_create_stencil(lc_ctx *ctx, lc_op **out, int32_t dim, const int32_t shape[3], const double *D,
+                         const double *Tx, const double *Ty, const double *Tz) {
+    if (!ctx || !out) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(ctx, LC_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (!shape || !D || !Tx || !Ty || (dim == 3 && !Tz)) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    const int64_t nx = shape[0], ny = shape[1], nz = dim == 3 ? shape[2] : 1;
+    if (nx <= 0 || ny <= 0 || nz <= 0) return fail(ctx, LC_ERR_INVALID_ARG, "shape must be positive");
+    if (dim == 2 && shape[2] != 1 && shape[2] != 0) return fail(ctx, LC_ERR_INVALID_ARG, "shape[2] must be 1 for dim 2");
+    const int64_t n = nx * ny * nz;
+    if (n >= (int64_t)INT32_MAX) return fail(ctx, LC_ERR_TOO_LARGE, "N = %lld does not fit int32", (long long)n);
+    const int64_t nnz = n + 2 * ((nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1));
+    if (nnz >= (int64_t)INT32_MAX) return fail(ctx, LC_ERR_TOO_LARGE, "nnz does not fit int32");
+    LC_CUDA(ctx, cudaSetDevice(ctx->device));
+    lc_op *op = new (std::nothrow) lc_op;
+    if (!op) return LC_ERR_NO_MEMORY;
+    op->ctx = ctx;
+    op->kind = 0;
+    op->n = n;
+    op->nnz = nnz;
+    op->st.dim = dim;
+    op->st.nx = (int)nx; op->st.ny = (int)ny; op->st.nz = (int)nz;
+    op->st.n = n;
+    op->st.D = D; op->st.Tx = Tx; op->st.Ty = Ty; op->st.Tz = dim == 3 ? Tz : nullptr;
+    int rc = alloc_op(op);
+    if (rc) { lc_op_destroy(op); return rc; }
+    op->st.dinv = op->dinv;
+    op->st.D32 = op->D32; op->st.Tx32 = op->Tx32; op->st.Ty32 = op->Ty32; op->st.Tz32 = op->Tz32;
+    op->st.dinv32 = op->dinv32;
+    int *bad = reinterpret_cast<int *>(&op->ctrl->K);
+    cudaError_t e = cudaMemset(bad, 0, sizeof(int));
+    if (e == cudaSuccess) e = lc::launch_check_stencil(op->st, bad, 0);
+    if (e == cudaSuccess)
+        e = lc::launch_dinv_stencil(n, D, op->dinv, op->D32, Tx, Ty, op->st.Tz, op->Tx32, op->Ty32, op->Tz32,
+                                    op->dinv32, 0);
+    int hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "stencil set-up"); lc_op_destroy(op); return rc; }
+    if (hbad) {
+        lc_op_destroy(op);
+        return fail(ctx, LC_ERR_INVALID_ARG, "stencil needs D > 0 and every interior face conductance > 0");
+    }
+    cudaMemset(op->ctrl, 0, sizeof(lc::Ctrl));
+    *out = op;
+    return LC_OK;
+}
+
+int lc_op_create_csr(lc_ctx *ctx, lc_op **out, int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
+                     const double *val) {
+    if (!ctx || !out) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n <= 0 || nnz < n) return fail(ctx, LC_ERR_INVALID_ARG, "need n > 0 and nnz >= n (diagonal present)");
+    if (nnz >= (int64_t)INT32_MAX) return fail(ctx, LC_ERR_TOO_LARGE, "nnz = %lld does not fit int32", (long long)nnz);
+    if (!rowptr || !col || !val) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    LC_CUDA(ctx, cudaSetDevice(ctx->device));
+    int32_t ends[2] = {0, 0};
+    LC_CUDA(ctx, cudaMemcpy(&ends[0], rowptr, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    LC_CUDA(ctx, cudaMemcpy(&ends[1], rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (ends[0] != 0 || ends[1] != nnz) return fail(ctx, LC_ERR_INVALID_ARG, "rowptr[0] must be 0 and rowptr[n] = nnz");
+    lc_op *op = new (std::nothrow) lc_op;
+    if (!op) return LC_ERR_NO_MEMORY;
+    op->ctx = ctx;
+    op->kind = 1;
+    op->n = n;
+    op->nnz = nnz;
+    op->csr.n = n;
+    op->csr.n_dev = nullptr;
+    op->csr.rp = rowptr; op->csr.ci = col; op->csr.av = val;
+    int rc = alloc_op(op);
+    if (rc) { lc_op_destroy(op); return rc; }
+    int *bad = reinterpret_cast<int *>(&op->ctrl->K);
+    cudaError_t e = cudaMemset(bad, 0, sizeof(int));
+    if (e == cudaSuccess) e = lc::launch_check_csr(n, rowptr, col, val, bad, 0);
+    int hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "CSR check"); lc_op_destroy(op); return rc; }
+    if (hbad) {
+        lc_op_destroy(op);
+        return fail(ctx, LC_ERR_INVALID_ARG, "CSR rows must be sorted, unique, in range, with a positive diagonal");
+    }
+    cudaMemset(op->ctrl, 0, sizeof(lc::Ctrl));
+    *out = op;
+    return LC_OK;
+}
+
+int lc_op_destroy(lc_op *op) {
+    if (!op) return LC_OK;
+    if (op->ctx) cudaSetDevice(op->ctx->device);
+    for (auto &ev : op->ev) if (ev) cudaEventDestroy(ev);
+    if (op->arena) cudaFree(op->arena);
+    delete op;
+    return LC_OK;
+}
+
+int lc_mark_residual(lc_ctx *ctx, const lc_op *op, const double *b, const double *x0, const lc_mark_params *p,
+                     uint8_t *mask, double *r0_opt, int32_t *K_dev, double *tau_dev, void *stream) {
+    int rc = check_common(ctx, op);
+    if (rc) return rc;
+    if (!K_dev) return fail(ctx, LC_ERR_INVALID_ARG, "null K_dev");
+    return mark_residual_impl(ctx, op, b, x0, p, mask, r0_opt, K_dev, tau_dev, (cudaStream_t)stream);
+}
+
+int lc_mark_gradient(lc_ctx *ctx, const lc_op *op, const double *x0, double alpha, int32_t layers, uint8_t *mask,
+                     int32_t *K_dev, double *gmax_dev, void *stream) {
+    int rc = check_common(ctx, op);
+    if (rc) return rc;
+    if (!K_dev) return fail(ctx, LC_ERR_INVALID_ARG, "null K_dev");
+    return mark_gradient_impl(ctx, op, x0, alpha, layers, mask, K_dev, gmax_dev, (cudaStream_t)stream);
+}
+
+int lc_extract(lc_ctx *ctx, const lc_op *op, const uint8_t *mask, const double *b, const double *x0,
+               const lc_subsys *out, void *stream) {
+    int rc = check_common(ctx, op);
+    if (rc) return rc;
+    if (!out) return fail(ctx, LC_ERR_INVALID_ARG, "null subsystem");
+    return extract_impl(ctx, op, mask, b, x0, *out, (cudaStream_t)stream);
+}
+
+int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_solve_params *p, lc_stats *stats,
+                 void *stream) {
+    int rc = check_common(ctx, op);
+    if (rc) return rc;
+    if (!b || !x) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    if ((rc = check_solve_params(ctx, p))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (stats) LC_CUDA(ctx, cudaEventRecord(op->ev[0], s));
+    if ((rc = pcg_impl(ctx, op, b, x, p, op->ctrl, false, s))) return rc;
+    if (!stats) return LC_OK;
+    LC_CUDA(ctx, cudaEventRecord(op->ev[1], s));
+    LC_CUDA(ctx, cudaStreamSynchronize(s));
+    lc::Ctrl c;
+    if ((rc = read_ctrl(ctx, op->ctrl, &c))) return rc;
+    memset(stats, 0, sizeof *stats);
+    stats->n = (int32_t)op->n;
+    stats->it_global = c.iters;
+    stats->restarts = c.restarts;
+    stats->early_exit = c.early;
+    stats->relres_tilde = c.relres0;
+    stats->relres_final = c.relres;
+    cudaEventElapsedTime(&stats->t_global_ms, op->ev[0], op->ev[1]);
+    stats->t_total_ms = stats->t_global_ms;
+    stats->status = status_of(c);
+    if (stats->status == LC_ERR_TIMEOUT) return fail(ctx, LC_ERR_TIMEOUT, "grid barrier timed out");
+    return stats->status;
+}
+
+int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_params *p,
+                               lc_stats *stats, void *stream) {
+    int rc = check_common(ctx, op);
+    if (rc) return rc;
+    if (!b || !x || !p) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    if ((rc = check_solve_params(ctx, &p->global)) || (rc = check_solve_params(ctx, &p->local))) return rc;
+    if (p->gs_sweeps != 0) return fail(ctx, LC_ERR_UNSUPPORTED, "Gauss-Seidel smoothing is not provided by this build");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (stats) LC_CUDA(ctx, cudaEventRecord(op->ev[0], s));
+    // 1. local domain (Alg 2 or Alg 3)
+    if (p->mark_mode == LC_MARK_RESIDUAL) {
+        rc = mark_residual_impl(ctx, op, b, x, &p->mark, op->mask_own, nullptr, op->sub.K, nullptr, s);
+    } else if (p->mark_mode == LC_MARK_GRADIENT) {
+        rc = mark_gradient_impl(ctx, op, x, p->alpha, p->grad_layers, op->mask_own, op->sub.K, nullptr, s);
+    } else {
+        rc = fail(ctx, LC_ERR_INVALID_ARG, "unknown marking mode %d", p->mark_mode);
+    }
+    if (rc) return rc;
+    if (stats) LC_CUDA(ctx, cudaEventRecord(op->ev[1], s));
+    // 2. subsystem B x_B = b_B - E x_C (Eq. loc-equ)
+    if ((rc = extract_impl(ctx, op, op->mask_own, b, x, op->sub, s))) return rc;
+    if (stats) LC_CUDA(ctx, cudaEventRecord(op->ev[2], s));
+    // 3. local solve from x0 restricted to the domain, in place in sub.xL0
+    if ((rc = pcg_impl(ctx, op, op->sub.rhs, op->sub.xL0, &p->local, op->ctrl_loc, true, s))) return rc;
+    // 4. x~ = x0 with the local solution scattered in (Eq. sol-assemble)
+    LC_CUDA(ctx, lc::launch_assemble(op->sub.K, op->sub.l2g, op->sub.xL0, x, op->n, s));
+    if (stats) LC_CUDA(ctx, cudaEventRecord(op->ev[3], s));
+    // 5. convergence check of x~ and, if needed, the global solve from x~
+    if ((rc = pcg_impl(ctx, op, b, x, &p->global, op->ctrl, false, s))) return rc;
+    if (!stats) return LC_OK;
+    LC_CUDA(ctx, cudaEventRecord(op->ev[4], s));
+    LC_CUDA(ctx, cudaStreamSynchronize(s));
+    lc::Ctrl cg, cl;
+    if ((rc = read_ctrl(ctx, op->ctrl, &cg)) || (rc = read_ctrl(ctx, op->ctrl_loc, &cl))) return rc;
+    memset(stats, 0, sizeof *stats);
+    stats->n = (int32_t)op->n;
+    stats->K = cg.K;
+    stats->nnzB = cg.nnzB;
+    stats->eta = op->n ? (double)cg.K / (double)op->n : 0.0;
+    stats->tau = cg.tau;
+    stats->it_local = cl.iters;
+    stats->it_global = cg.iters;
+    stats->early_exit = cg.early;
+    stats->restarts = cg.restarts;
+    stats->relres_tilde = cg.relres0;
+    stats->relres_final = cg.relres;
+    cudaEventElapsedTime(&stats->t_mark_ms, op->ev[0], op->ev[1]);
+    cudaEventElapsedTime(&stats->t_extract_ms, op->ev[1], op->ev[2]);
+    cudaEventElapsedTime(&stats->t_local_ms, op->ev[2], op->ev[3]);
+    cudaEventElapsedTime(&stats->t_global_ms, op->ev[3], op->ev[4]);
+    cudaEventElapsedTime(&stats->t_total_ms, op->ev[0], op->ev[4]);
+    int st = cl.status != LC_OK ? cl.status : (cl.converged == -1 && cg.K > 0 ? LC_ERR_BREAKDOWN : LC_OK);
+    if (st == LC_OK) st = status_of(cg);
+    stats->status = st;
+    if (st == LC_ERR_TIMEOUT) return fail(ctx, LC_ERR_TIMEOUT, "grid barrier timed out");
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,277 @@
+// lc_internal.cuh -- shared device helpers and descriptors of the lc library.
+//
+// Nothing here is part of the public ABI (include/lc_api.h).  All kernels
+// are written for sm_103a: 32-wide warps, 152 SMs, FP64 at roughly 1/12 of
+// a DP op per HBM byte -- so every bit-exact kernel spends exactly the FP64
+// operations its canonical order names and does abs/max/compare on integer
+// bit patterns.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lc_api.h"
+
+namespace lc {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kTreeChunk = 1024;                       // canonical sum-of-squares chunk
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
+constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
+constexpr int kMaxExpRounds = 64;
+constexpr int kMaxGrid = 4096;                          // persistent-kernel blocks (partials capacity)
+
+// ---------------------------------------------------------------- descriptors
+
+// Structured operator: the diagonal D and face conductances T (off-diagonal
+// -T); dinv = 1/D precomputed at creation.  Cell i = x + nx*(y + ny*z).
+struct Stencil {
+    int dim;
+    int nx, ny, nz;
+    int64_t n;
+    const double *D, *Tx, *Ty, *Tz;
+    const double *dinv;
+    // FP32 copies for the mixed-precision inner solve (fl32 of the above)
+    const float *D32, *Tx32, *Ty32, *Tz32, *dinv32;
+};
+
+// CSR operator; rows ascending, diagonal present.  `n_dev`, if not null,
+// holds the row count on the device (used for extracted subsystems whose
+// size is only known on the device); otherwise `n` is the count.
+struct Csr {
+    int32_t n;
+    const int32_t *n_dev;
+    const int32_t *rp, *ci;
+    const double *av;
+    const float *av32;
+};
+
+// Device-resident control block of one operator (one per lc_op).
+struct Ctrl {
+    // grid barrier
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int32_t status;                 // first error a kernel raised (LC_OK if none)
+    int32_t pad0;
+    // marking
+    unsigned long long maxabs_bits; // max |r| (or max g) as bits, NaN excluded
+    double tau;
+    int32_t K;
+    int32_t nnzB;
+    int32_t added[kMaxExpRounds];   // Alg 3: K0 of each round
+    // Krylov
+    int32_t iters;
+    int32_t restarts;
+    int32_t converged;              // 1 ok, 0 not converged, -1 breakdown
+    int32_t early;                  // converged at set-up (x0 already met the criterion)
+    double relres0;                 // relative residual of the starting iterate
+    double relres;                  // final relative residual (true residual)
+    double bnorm2;                  // ||b||^2
+    // mixed-precision refinement
+    int32_t outer;
+    int32_t pad1;
+    double scale;                   // ||r|| of the current outer residual
+};
+
+// ---------------------------------------------------------------- bit helpers
+
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & kAbsMask;
+}
+// |v| > t exactly as IEEE compares it, given tbits = abs_bits(t), t >= 0 or
+// NaN: a NaN |v| never exceeds, nothing exceeds a NaN t or +inf.
+__device__ __forceinline__ bool abs_gt(double v, unsigned long long tbits) {
+    unsigned long long a = abs_bits(v);
+    return a > tbits && a <= kInfBits && tbits <= kInfBits;
+}
+// bits of |v| for a max that ignores NaN (as `if (|v| > m) m = |v|` does)
+__device__ __forceinline__ unsigned long long maxable_bits(double v) {
+    unsigned long long a = abs_bits(v);
+    return a <= kInfBits ? a : 0ull;
+}
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_down_sync(kFull, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+__device__ __forceinline__ int warp_isum(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+
+// Deterministic block sum of NV values per thread (result valid in thread 0).
+// `sm` needs NV * 32 doubles.
+template <int NV, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sm[k * 32 + warp] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            T t = lane < nw ? sm[k * 32 + lane] : T(0);
+            v[k] = warp_sum(t);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_max(v);
+    __syncthreads();
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < nw ? sm[lane] : 0ull;
+        v = warp_max(v);
+    }
+    return v;
+}
+
+__device__ __forceinline__ int block_isum(int v, int *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_isum(v);
+    __syncthreads();
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < nw ? sm[lane] : 0;
+        v = warp_isum(v);
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------- grid barrier
+
+// Spin limit of every grid-wide wait: ~2 s at 2 GHz, after which the block
+// records LC_ERR_TIMEOUT in ctrl->status and returns false (so do all
+// blocks that wait after it); kernels then exit.  Co-residency of all
+// blocks is guaranteed by the cooperative launch.
+constexpr long long kBarrierTimeoutCycles = 4000000000ll;
+
+__device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned int nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = &ctrl->bar_gen;
+        unsigned int g = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(&ctrl->bar_count, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            ctrl->bar_count = 0;
+            __threadfence();
+            atomicAdd(&ctrl->bar_gen, 1u);
+        } else {
+            long long t0 = clock64();
+            while (*vgen == g) {
+                if (clock64() - t0 > kBarrierTimeoutCycles) { ok = 0; break; }
+            }
+        }
+        __threadfence();
+        if (!ok) atomicCAS(&ctrl->status, LC_OK, LC_ERR_TIMEOUT);
+        s_ok = ok && (*(volatile int32_t *)&ctrl->status == LC_OK);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Loads of data that other blocks of the same (persistent) kernel write:
+// bypass L1, which is not coherent across SMs.
+template <typename T>
+__device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+
+// ---------------------------------------------------------------- host side
+
+struct Launch {
+    cudaStream_t stream;
+};
+
+// Launchers (one translation unit each).  All return cudaError_t of the
+// last launch; argument validation happens in lc_api.cu.
+cudaError_t launch_residual_stencil(const Stencil &op, const double *b, const double *x, double *r,
+                                    int want_tree, double *tree_partials, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_residual_csr(const Csr &op, const double *b, const double *x, double *r,
+                                int want_tree, double *tree_partials, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_tree_finish(double *partials, double *scratch, int64_t nchunks, int64_t n, double eps,
+                               Ctrl *ctrl, double *tau_out, cudaStream_t s);
+cudaError_t launch_tau_relmax(double beta, Ctrl *ctrl, double *tau_out, cudaStream_t s);
+cudaError_t launch_threshold_dilate_stencil(const Stencil &op, const double *v, int layers, uint8_t *mask,
+                                            Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_dilate_stencil_pass(const Stencil &op, int layers, const uint8_t *in, uint8_t *out, cudaStream_t s);
+inline int max_layers_per_pass(int dim) { return dim == 3 ? 2 : 4; }
+cudaError_t launch_threshold_csr(int32_t n, const double *v, uint8_t *mask, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_dilate_csr(const Csr &op, const uint8_t *in, uint8_t *out, cudaStream_t s);
+cudaError_t launch_expand_paper_stencil(const Stencil &op, const double *r, const double *x0, int round,
+                                        const uint8_t *in, uint8_t *out, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_expand_paper_csr(const Csr &op, const double *r, const double *x0, int round,
+                                    const uint8_t *in, uint8_t *out, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_gradient_stencil(const Stencil &op, const double *x, double *g, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_gradient_csr(const Csr &op, const double *x, double *g, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_gmax_threshold(double alpha, Ctrl *ctrl, double *gmax_out, cudaStream_t s);
+cudaError_t launch_count_mask(int64_t n, const uint8_t *mask, Ctrl *ctrl, int32_t *K_out, cudaStream_t s);
+
+// Extraction (lc_extract.cu)
+struct ExtractWork {
+    unsigned long long *blk;   // per-block packed (cells, entries) totals, capacity >= nblocks + 1
+    int64_t nblocks_cap;
+};
+cudaError_t launch_extract_stencil(const Stencil &op, const uint8_t *mask, const double *b, const double *x0,
+                                   const lc_subsys &out, ExtractWork &w, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_extract_csr(const Csr &op, const uint8_t *mask, const double *b, const double *x0,
+                               const lc_subsys &out, ExtractWork &w, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_assemble(const int32_t *K_dev, const int32_t *l2g, const double *xbar, double *x, int64_t cap,
+                            cudaStream_t s);
+
+// Krylov (lc_pcg.cu)
+struct PcgWork {
+    double *r, *z, *p0, *p1, *q;     // capacity n
+    double *dinv;                    // CSR: per-row 1/a_ii (capacity n)
+    double *partials;                // kMaxGrid * 4
+    float *r32, *z32, *p032, *p132, *q32, *x32, *b32, *dinv32;   // mixed precision (capacity n)
+    double *xd;                      // mixed: FP64 scratch (capacity n)
+};
+struct PcgArgs {
+    const double *b;
+    double *x;
+    double tol;
+    int32_t maxit;
+    int32_t max_restarts;
+};
+cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
+                               cudaStream_t s);
+cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
+                           cudaStream_t s);
+cudaError_t launch_dinv_stencil(int64_t n, const double *D, double *dinv, float *D32, const double *Tx,
+                                const double *Ty, const double *Tz, float *Tx32, float *Ty32, float *Tz32,
+                                float *dinv32, cudaStream_t s);
+cudaError_t launch_check_stencil(const Stencil &op, int *bad, cudaStream_t s);
+cudaError_t launch_check_csr(int32_t n, const int32_t *rp, const int32_t *ci, const double *av, int *bad,
+                             cudaStream_t s);
+
+}  // namespace lc

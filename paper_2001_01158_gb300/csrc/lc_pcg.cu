@@ -1,0 +1,563 @@
+// lc_pcg.cu -- Jacobi-preconditioned conjugate gradients as ONE persistent
+// cooperative kernel per solve (the Krylov solver of Alg 1, steps 5 and 11).
+//
+// Per iteration two grid-wide phases, each closed by a bounded grid barrier
+// and a deterministic fixed-slot reduction (every block sums the same block
+// partials in the same order, so every block takes the same decisions):
+//
+//   phase A  p = z + beta p_old          (computed where it is needed, halos
+//            q = A p, partial p.q          included, so no extra barrier)
+//            store p (ping-pong buffer) and q
+//   phase B  alpha = rz / pq; x += alpha p; r -= alpha q; z = dinv r;
+//            partials r.z and r.r
+//
+// z is stored so that phase A reads one vector where it would read r and
+// dinv; the stopping test ||r||^2 <= tol^2 ||b||^2 is taken on the recurrence
+// residual, confirmed with the true residual b - A x, and the iteration
+// restarts from the true residual when that misses (at most max_restarts).
+// The test on the starting iterate happens in the set-up phase: a converged
+// start (Alg 1 step 8, the local solution x~ already good enough) costs one
+// residual pass and no iteration.
+//
+// Data movement per cell and iteration (2D, FP64): phase A reads z, p_old,
+// D, Tx, Ty and writes p, q (56 B); phase B reads x, p, r, q, dinv and
+// writes x, r, z (64 B): 120 B.  Structured operators march a column strip
+// (2D) or an xy tile (3D) through the grid so that every p is computed once
+// plus a thin halo; CSR rows recompute the p of their columns.
+#include "lc_internal.cuh"
+
+namespace lc {
+
+namespace {
+
+constexpr int kPcgThreads = 256;
+constexpr int kStripRows = 16;     // 2D: rows per unit
+constexpr int kTileX = 32, kTileY = 8, kTileZ = 16;   // 3D unit
+
+struct Bufs {
+    const double *b;
+    double *x, *r, *z, *q;
+    double *p[2];
+    const double *dinv;
+    double *part;          // [6][kMaxGrid]
+};
+
+// -------------------------------------------------------------- operators
+
+struct Op2D {
+    Stencil s;
+    __device__ int64_t units() const {
+        const int64_t sx = (s.nx + kPcgThreads - 1) / kPcgThreads;
+        const int64_t sy = (s.ny + kStripRows - 1) / kStripRows;
+        return sx * sy;
+    }
+    // r = b - A x, z = dinv r on the unit; accumulates bb, rz, rr
+    __device__ void setup(int64_t u, const Bufs &B, double &bb, double &rz, double &rr) const {
+        const int64_t sx = (s.nx + kPcgThreads - 1) / kPcgThreads;
+        const int xx = (int)(u % sx) * kPcgThreads + threadIdx.x;
+        const int y0 = (int)(u / sx) * kStripRows;
+        if (xx >= s.nx) return;
+        const int y1 = min(y0 + kStripRows, s.ny);
+        for (int y = y0; y < y1; ++y) {
+            const int64_t i = (int64_t)y * s.nx + xx;
+            double ax = s.D[i] * ldcg(B.x + i);
+            if (y > 0) ax = fma(-s.Ty[i - s.nx], ldcg(B.x + i - s.nx), ax);
+            if (xx > 0) ax = fma(-s.Tx[i - 1], ldcg(B.x + i - 1), ax);
+            if (xx + 1 < s.nx) ax = fma(-s.Tx[i], ldcg(B.x + i + 1), ax);
+            if (y + 1 < s.ny) ax = fma(-s.Ty[i], ldcg(B.x + i + s.nx), ax);
+            const double bi = B.b[i];
+            const double ri = bi - ax;
+            const double zi = s.dinv[i] * ri;
+            B.r[i] = ri;
+            B.z[i] = zi;
+            bb = fma(bi, bi, bb);
+            rz = fma(ri, zi, rz);
+            rr = fma(ri, ri, rr);
+        }
+    }
+    __device__ __forceinline__ double pnew(const Bufs &B, int pin, bool first, double beta, int64_t i) const {
+        const double zi = ldcg(B.z + i);
+        return first ? zi : fma(beta, ldcg(B.p[pin] + i), zi);
+    }
+    __device__ void phaseA(int64_t u, const Bufs &B, int pin, bool first, double beta, double &pq, double *srow) const {
+        const int64_t sx = (s.nx + kPcgThreads - 1) / kPcgThreads;
+        const int x0 = (int)(u % sx) * kPcgThreads;
+        const int xx = x0 + threadIdx.x;
+        const int y0 = (int)(u / sx) * kStripRows;
+        const int y1 = min(y0 + kStripRows, s.ny);
+        const bool act = xx < s.nx;
+        double *pout = B.p[pin ^ 1];
+        double pm = 0.0, pc = 0.0, tym = 0.0;
+        if (act) {
+            const int64_t i0 = (int64_t)y0 * s.nx + xx;
+            pc = pnew(B, pin, first, beta, i0);
+            if (y0 > 0) { pm = pnew(B, pin, first, beta, i0 - s.nx); tym = s.Ty[i0 - s.nx]; }
+        }
+        for (int y = y0; y < y1; ++y) {
+            const int64_t i = (int64_t)y * s.nx + xx;
+            double pn = 0.0;
+            if (act && y + 1 < s.ny) pn = pnew(B, pin, first, beta, i + s.nx);
+            double *buf = srow + (y & 1) * (kPcgThreads + 2);
+            buf[threadIdx.x + 1] = pc;
+            if (threadIdx.x == 0)
+                buf[0] = x0 > 0 ? pnew(B, pin, first, beta, (int64_t)y * s.nx + x0 - 1) : 0.0;
+            if (threadIdx.x == kPcgThreads - 1)
+                buf[kPcgThreads + 1] = x0 + kPcgThreads < s.nx ? pnew(B, pin, first, beta, (int64_t)y * s.nx + x0 + kPcgThreads) : 0.0;
+            __syncthreads();
+            if (act) {
+                const double pw = buf[threadIdx.x], pe = buf[threadIdx.x + 2];
+                const double txw = xx > 0 ? s.Tx[i - 1] : 0.0;
+                const double txe = xx + 1 < s.nx ? s.Tx[i] : 0.0;
+                const double typ = y + 1 < s.ny ? s.Ty[i] : 0.0;
+                double qi = s.D[i] * pc;
+                qi = fma(-tym, pm, qi);
+                qi = fma(-txw, pw, qi);
+                qi = fma(-txe, pe, qi);
+                qi = fma(-typ, pn, qi);
+                pout[i] = pc;
+                B.q[i] = qi;
+                pq = fma(pc, qi, pq);
+                tym = typ;
+            }
+            pm = pc;
+            pc = pn;
+        }
+        __syncthreads();
+    }
+    template <class F>
+    __device__ void for_cells(int64_t u, F f) const {
+        const int64_t sx = (s.nx + kPcgThreads - 1) / kPcgThreads;
+        const int xx = (int)(u % sx) * kPcgThreads + threadIdx.x;
+        const int y0 = (int)(u / sx) * kStripRows;
+        if (xx >= s.nx) return;
+        const int y1 = min(y0 + kStripRows, s.ny);
+        for (int y = y0; y < y1; ++y) f((int64_t)y * s.nx + xx);
+    }
+    static constexpr int kSmem = 2 * (kPcgThreads + 2);
+    __device__ void resolve() {}
+};
+
+struct Op3D {
+    Stencil s;
+    __device__ int64_t units() const {
+        const int64_t tx = (s.nx + kTileX - 1) / kTileX, ty = (s.ny + kTileY - 1) / kTileY;
+        const int64_t tz = (s.nz + kTileZ - 1) / kTileZ;
+        return tx * ty * tz;
+    }
+    __device__ void origin(int64_t u, int &x0, int &y0, int &z0) const {
+        const int64_t tx = (s.nx + kTileX - 1) / kTileX, ty = (s.ny + kTileY - 1) / kTileY;
+        x0 = (int)(u % tx) * kTileX;
+        y0 = (int)((u / tx) % ty) * kTileY;
+        z0 = (int)(u / (tx * ty)) * kTileZ;
+    }
+    template <class F>
+    __device__ void for_cells(int64_t u, F f) const {
+        int x0, y0, z0;
+        origin(u, x0, y0, z0);
+        const int xx = x0 + (threadIdx.x % kTileX), yy = y0 + (threadIdx.x / kTileX);
+        if (xx >= s.nx || yy >= s.ny) return;
+        const int z1 = min(z0 + kTileZ, s.nz);
+        const int64_t sxy = (int64_t)s.nx * s.ny;
+        for (int z = z0; z < z1; ++z) f(xx + (int64_t)s.nx * yy + sxy * z);
+    }
+    __device__ void setup(int64_t u, const Bufs &B, double &bb, double &rz, double &rr) const {
+        const int64_t sxy = (int64_t)s.nx * s.ny;
+        for_cells(u, [&](int64_t i) {
+            const int xx = (int)(i % s.nx), yy = (int)((i / s.nx) % s.ny), zz = (int)(i / sxy);
+            double ax = s.D[i] * ldcg(B.x + i);
+            if (zz > 0) ax = fma(-s.Tz[i - sxy], ldcg(B.x + i - sxy), ax);
+            if (yy > 0) ax = fma(-s.Ty[i - s.nx], ldcg(B.x + i - s.nx), ax);
+            if (xx > 0) ax = fma(-s.Tx[i - 1], ldcg(B.x + i - 1), ax);
+            if (xx + 1 < s.nx) ax = fma(-s.Tx[i], ldcg(B.x + i + 1), ax);
+            if (yy + 1 < s.ny) ax = fma(-s.Ty[i], ldcg(B.x + i + s.nx), ax);
+            if (zz + 1 < s.nz) ax = fma(-s.Tz[i], ldcg(B.x + i + sxy), ax);
+            const double bi = B.b[i];
+            const double ri = bi - ax;
+            const double zi = s.dinv[i] * ri;
+            B.r[i] = ri;
+            B.z[i] = zi;
+            bb = fma(bi, bi, bb);
+            rz = fma(ri, zi, rz);
+            rr = fma(ri, ri, rr);
+        });
+    }
+    // p of plane z (tile + 1-cell xy halo) into a (kTileY+2) x (kTileX+2) buffer
+    __device__ void build_plane(const Bufs &B, int pin, bool first, double beta, int x0, int y0, int z,
+                                double *pl) const {
+        const int64_t sxy = (int64_t)s.nx * s.ny;
+        constexpr int ex = kTileX + 2, ey = kTileY + 2;
+        for (int k = threadIdx.x; k < ex * ey; k += kPcgThreads) {
+            const int gx = x0 - 1 + (k % ex), gy = y0 - 1 + (k / ex);
+            double v = 0.0;
+            if (z >= 0 && z < s.nz && gx >= 0 && gx < s.nx && gy >= 0 && gy < s.ny) {
+                const int64_t i = gx + (int64_t)s.nx * gy + sxy * z;
+                const double zi = ldcg(B.z + i);
+                v = first ? zi : fma(beta, ldcg(B.p[pin] + i), zi);
+            }
+            pl[k] = v;
+        }
+    }
+    __device__ void phaseA(int64_t u, const Bufs &B, int pin, bool first, double beta, double &pq, double *sm) const {
+        constexpr int ex = kTileX + 2, ey = kTileY + 2, pls = ex * ey;
+        int x0, y0, z0;
+        origin(u, x0, y0, z0);
+        const int lx = threadIdx.x % kTileX, ly = threadIdx.x / kTileX;
+        const int xx = x0 + lx, yy = y0 + ly;
+        const bool act = xx < s.nx && yy < s.ny;
+        const int z1 = min(z0 + kTileZ, s.nz);
+        const int64_t sxy = (int64_t)s.nx * s.ny;
+        double *pout = B.p[pin ^ 1];
+        // planes z0-1 and z0 first
+        build_plane(B, pin, first, beta, x0, y0, z0 - 1, sm + ((z0 + 3) & 3) * pls);
+        build_plane(B, pin, first, beta, x0, y0, z0, sm + (z0 & 3) * pls);
+        const int c = (ly + 1) * ex + (lx + 1);
+        for (int z = z0; z < z1; ++z) {
+            build_plane(B, pin, first, beta, x0, y0, z + 1, sm + ((z + 1) & 3) * pls);
+            __syncthreads();
+            if (act) {
+                const double *pc = sm + (z & 3) * pls;
+                const double pmz = sm[((z + 3) & 3) * pls + c];
+                const double ppz = sm[((z + 1) & 3) * pls + c];
+                const int64_t i = xx + (int64_t)s.nx * yy + sxy * z;
+                const double p0 = pc[c];
+                double qi = s.D[i] * p0;
+                if (z > 0) qi = fma(-s.Tz[i - sxy], pmz, qi);
+                if (yy > 0) qi = fma(-s.Ty[i - s.nx], pc[c - ex], qi);
+                if (xx > 0) qi = fma(-s.Tx[i - 1], pc[c - 1], qi);
+                if (xx + 1 < s.nx) qi = fma(-s.Tx[i], pc[c + 1], qi);
+                if (yy + 1 < s.ny) qi = fma(-s.Ty[i], pc[c + ex], qi);
+                if (z + 1 < s.nz) qi = fma(-s.Tz[i], ppz, qi);
+                pout[i] = p0;
+                B.q[i] = qi;
+                pq = fma(p0, qi, pq);
+            }
+        }
+        __syncthreads();
+    }
+    static constexpr int kSmem = 4 * (kTileX + 2) * (kTileY + 2);
+    __device__ void resolve() {}
+};
+
+struct OpCsr {
+    Csr c;
+    int32_t n;   // resolved at kernel start (device-side count of an extracted subsystem)
+    __device__ void resolve() { if (c.n_dev) n = *c.n_dev; }
+    __device__ int64_t units() const { return (n + kPcgThreads - 1) / kPcgThreads; }
+    template <class F>
+    __device__ void for_cells(int64_t u, F f) const {
+        const int64_t i = u * kPcgThreads + threadIdx.x;
+        if (i < n) f(i);
+    }
+    __device__ void setup(int64_t u, const Bufs &B, double &bb, double &rz, double &rr) const {
+        for_cells(u, [&](int64_t i) {
+            double ax = 0.0;
+            const int32_t e1 = c.rp[i + 1];
+            for (int32_t e = c.rp[i]; e < e1; ++e) ax = fma(c.av[e], ldcg(B.x + c.ci[e]), ax);
+            const double bi = B.b[i];
+            const double ri = bi - ax;
+            const double zi = B.dinv[i] * ri;
+            B.r[i] = ri;
+            B.z[i] = zi;
+            bb = fma(bi, bi, bb);
+            rz = fma(ri, zi, rz);
+            rr = fma(ri, ri, rr);
+        });
+    }
+    __device__ void phaseA(int64_t u, const Bufs &B, int pin, bool first, double beta, double &pq, double *) const {
+        double *pout = B.p[pin ^ 1];
+        for_cells(u, [&](int64_t i) {
+            double qi = 0.0, pi = 0.0;
+            const int32_t e1 = c.rp[i + 1];
+            for (int32_t e = c.rp[i]; e < e1; ++e) {
+                const int32_t j = c.ci[e];
+                const double zj = ldcg(B.z + j);
+                const double pj = first ? zj : fma(beta, ldcg(B.p[pin] + j), zj);
+                if (j == i) pi = pj;
+                qi = fma(c.av[e], pj, qi);
+            }
+            pout[i] = pi;
+            B.q[i] = qi;
+            pq = fma(pi, qi, pq);
+        });
+    }
+    static constexpr int kSmem = 1;
+};
+
+// -------------------------------------------------------------- kernel
+
+// Deterministic grid-wide sum of slot `k` of the block partials: every block
+// computes the same value in the same order.
+__device__ __forceinline__ double grid_reduce(const double *part, int k, unsigned nb, double *bcast) {
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (unsigned b = threadIdx.x; b < nb; b += 32) v += ldcg(part + (size_t)k * kMaxGrid + b);
+        v = warp_sum(v);
+        if (threadIdx.x == 0) *bcast = v;
+    }
+    __syncthreads();
+    const double r = *bcast;
+    __syncthreads();
+    return r;
+}
+
+template <class OP>
+__device__ bool setup_phase(const OP &op, const Bufs &B, double *red, double &bb, double &rz, double &rr,
+                            Ctrl *ctrl) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    const int64_t nu = op.units();
+    for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) op.setup(u, B, acc[0], acc[1], acc[2]);
+    block_sum<3>(acc, red);
+    if (threadIdx.x == 0) {
+        B.part[0 * kMaxGrid + blockIdx.x] = acc[0];
+        B.part[1 * kMaxGrid + blockIdx.x] = acc[1];
+        B.part[2 * kMaxGrid + blockIdx.x] = acc[2];
+    }
+    if (!grid_sync(ctrl, gridDim.x)) return false;
+    bb = grid_reduce(B.part, 0, gridDim.x, red + 96);
+    rz = grid_reduce(B.part, 1, gridDim.x, red + 96);
+    rr = grid_reduce(B.part, 2, gridDim.x, red + 96);
+    return true;
+}
+
+template <class OP>
+__global__ void __launch_bounds__(kPcgThreads) pcg_kernel(OP op, Bufs B, double tol, int maxit, int max_restarts,
+                                                          Ctrl *ctrl) {
+    __shared__ double red[128];
+    __shared__ double sm[OP::kSmem];
+    op.resolve();
+    const int64_t nu = op.units();
+    double bb, rz, rr;
+    if (!setup_phase(op, B, red, bb, rz, rr, ctrl)) return;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const double stop = (tol * tol) * bb;
+    if (lead) {
+        ctrl->bnorm2 = bb;
+        ctrl->relres0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+        ctrl->iters = 0;
+        ctrl->restarts = 0;
+    }
+    if (bb == 0.0) {   // A x = 0: x = 0
+        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) op.for_cells(u, [&](int64_t i) { B.x[i] = 0.0; });
+        if (lead) { ctrl->converged = 1; ctrl->early = 1; ctrl->relres = 0.0; }
+        return;
+    }
+    if (rr <= stop) {
+        if (lead) { ctrl->converged = 1; ctrl->early = 1; ctrl->relres = sqrt(rr / bb); }
+        return;
+    }
+    int it = 0, restarts = 0, pin = 0;
+    bool first = true;
+    double beta = 0.0;
+    int result = 0;   // 1 converged, 0 not converged, -1 breakdown
+    while (true) {
+        // ---- phase A
+        double pq = 0.0;
+        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) op.phaseA(u, B, pin, first, beta, pq, sm);
+        {
+            double a1[1] = {pq};
+            block_sum<1>(a1, red);
+            if (threadIdx.x == 0) B.part[3 * kMaxGrid + blockIdx.x] = a1[0];
+        }
+        if (!grid_sync(ctrl, gridDim.x)) return;
+        pq = grid_reduce(B.part, 3, gridDim.x, red + 96);
+        if (!(pq > 0.0) || !isfinite(pq)) { result = -1; break; }
+        const double alpha = rz / pq;
+        pin ^= 1;
+        const double *p = B.p[pin];
+        // ---- phase B
+        double acc[2] = {0.0, 0.0};
+        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x)
+            op.for_cells(u, [&](int64_t i) {
+                const double pi = p[i], qi = B.q[i];
+                B.x[i] = fma(alpha, pi, B.x[i]);
+                const double ri = fma(-alpha, qi, B.r[i]);
+                const double zi = B.dinv[i] * ri;
+                B.r[i] = ri;
+                B.z[i] = zi;
+                acc[0] = fma(ri, zi, acc[0]);
+                acc[1] = fma(ri, ri, acc[1]);
+            });
+        block_sum<2>(acc, red);
+        if (threadIdx.x == 0) {
+            B.part[4 * kMaxGrid + blockIdx.x] = acc[0];
+            B.part[5 * kMaxGrid + blockIdx.x] = acc[1];
+        }
+        if (!grid_sync(ctrl, gridDim.x)) return;
+        const double rz_new = grid_reduce(B.part, 4, gridDim.x, red + 96);
+        rr = grid_reduce(B.part, 5, gridDim.x, red + 96);
+        ++it;
+        if (rr <= stop) {
+            // confirm with the true residual
+            double bb2;
+            if (!setup_phase(op, B, red, bb2, rz, rr, ctrl)) return;
+            if (rr <= stop) { result = 1; break; }
+            if (++restarts > max_restarts) { result = 0; break; }
+            first = true;
+            beta = 0.0;
+            if (it >= maxit) { result = 0; break; }
+            continue;
+        }
+        if (it >= maxit) { result = 0; break; }
+        beta = rz_new / rz;
+        rz = rz_new;
+        first = false;
+    }
+    if (result == 0 && it >= maxit) {
+        // report the true residual of the last iterate
+        double bb2, rz2, rr2;
+        if (!setup_phase(op, B, red, bb2, rz2, rr2, ctrl)) return;
+        rr = rr2;
+    }
+    if (lead) {
+        ctrl->iters = it;
+        ctrl->restarts = restarts;
+        ctrl->converged = result;
+        ctrl->early = 0;
+        ctrl->relres = sqrt(rr / bb);
+        if (result == -1) atomicCAS(&ctrl->status, LC_OK, LC_ERR_BREAKDOWN);
+    }
+}
+
+__global__ void csr_dinv_kernel(Csr c, double *dinv) {
+    const int32_t n = c.n_dev ? *c.n_dev : c.n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        const int32_t e1 = c.rp[i + 1];
+        for (int32_t e = c.rp[i]; e < e1; ++e)
+            if (c.ci[e] == i) d = c.av[e];
+        dinv[i] = 1.0 / d;
+    }
+}
+
+__global__ void reset_ctrl_kernel(Ctrl *ctrl) {
+    ctrl->bar_count = 0;
+    ctrl->iters = 0;
+    ctrl->restarts = 0;
+    ctrl->converged = 0;
+    ctrl->early = 0;
+}
+
+__global__ void dinv_stencil_kernel(int64_t n, const double *D, double *dinv, float *D32, const double *Tx,
+                                    const double *Ty, const double *Tz, float *Tx32, float *Ty32, float *Tz32,
+                                    float *dinv32) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = D[i];
+        dinv[i] = 1.0 / d;
+        if (D32) {
+            D32[i] = (float)d;
+            Tx32[i] = (float)Tx[i];
+            Ty32[i] = (float)Ty[i];
+            if (Tz) Tz32[i] = (float)Tz[i];
+            dinv32[i] = 1.0f / (float)d;
+        }
+    }
+}
+
+// Validation: D > 0 everywhere and every interior face conductance > 0.
+__global__ void check_stencil_kernel(Stencil s, int *bad) {
+    const int64_t sxy = (int64_t)s.nx * s.ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int xx = (int)(i % s.nx), yy = (int)((i / s.nx) % s.ny), zz = (int)(i / sxy);
+        bool ok = s.D[i] > 0.0;
+        if (xx + 1 < s.nx) ok = ok && s.Tx[i] > 0.0;
+        if (yy + 1 < s.ny) ok = ok && s.Ty[i] > 0.0;
+        if (s.dim == 3 && zz + 1 < s.nz) ok = ok && s.Tz[i] > 0.0;
+        if (!ok) atomicExch(bad, 1);
+    }
+}
+
+// Validation: rowptr monotone and in range, columns in range and strictly
+// ascending within each row, diagonal present and positive.
+__global__ void check_csr_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const double *av, int *bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e0 = rp[i], e1 = rp[i + 1];
+        bool ok = e0 >= 0 && e1 >= e0 && e1 <= rp[n];
+        bool diag = false;
+        int32_t prev = -1;
+        for (int32_t e = e0; ok && e < e1; ++e) {
+            const int32_t j = ci[e];
+            if (j < 0 || j >= n || j <= prev) ok = false;
+            prev = j;
+            if (j == i) diag = av[e] > 0.0;
+        }
+        if (!ok || !diag) atomicExch(bad, 1);
+    }
+}
+
+template <class OP>
+int pcg_grid(const void *kernel, int64_t units, int cap) {
+    int dev = 0, sms = 152, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kPcgThreads, 0);
+    int64_t g = (int64_t)sms * (per < 1 ? 1 : per);
+    if (cap > 0 && g > cap) g = cap;
+    if (g > units) g = units;
+    if (g > kMaxGrid) g = kMaxGrid;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <class OP>
+cudaError_t launch_coop(const OP &op, int64_t units, const Bufs &B, double tol, int maxit, int max_restarts,
+                        Ctrl *ctrl, int cap, cudaStream_t s) {
+    const void *k = (const void *)pcg_kernel<OP>;
+    const int grid = pcg_grid<OP>(k, units, cap);
+    reset_ctrl_kernel<<<1, 1, 0, s>>>(ctrl);
+    OP o = op;
+    Bufs b = B;
+    double t = tol;
+    int mi = maxit, mr = max_restarts;
+    Ctrl *c = ctrl;
+    void *args[] = {&o, &b, &t, &mi, &mr, &c};
+    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kPcgThreads), args, 0, s);
+}
+
+}  // namespace
+
+cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
+                               cudaStream_t s) {
+    Bufs B;
+    B.b = a.b; B.x = a.x; B.r = w.r; B.z = w.z; B.q = w.q; B.p[0] = w.p0; B.p[1] = w.p1;
+    B.dinv = op.dinv; B.part = w.partials;
+    if (op.dim == 3) {
+        Op3D o{op};
+        const int64_t units = (int64_t)((op.nx + kTileX - 1) / kTileX) * ((op.ny + kTileY - 1) / kTileY) *
+                              ((op.nz + kTileZ - 1) / kTileZ);
+        return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, s);
+    }
+    Op2D o{op};
+    const int64_t units = (int64_t)((op.nx + kPcgThreads - 1) / kPcgThreads) * ((op.ny + kStripRows - 1) / kStripRows);
+    return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, s);
+}
+
+cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint, cudaStream_t s) {
+    // the row count may live on the device (extracted subsystem): the kernel
+    // is sized for the capacity op.n and reads the actual count itself
+    csr_dinv_kernel<<<152 * 4, 256, 0, s>>>(op, w.dinv);
+    Bufs B;
+    B.b = a.b; B.x = a.x; B.r = w.r; B.z = w.z; B.q = w.q; B.p[0] = w.p0; B.p[1] = w.p1;
+    B.dinv = w.dinv; B.part = w.partials;
+    OpCsr o{op, op.n};
+    const int64_t units = (op.n + kPcgThreads - 1) / kPcgThreads;
+    return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, s);
+}
+
+cudaError_t launch_dinv_stencil(int64_t n, const double *D, double *dinv, float *D32, const double *Tx,
+                                const double *Ty, const double *Tz, float *Tx32, float *Ty32, float *Tz32,
+                                float *dinv32, cudaStream_t s) {
+    dinv_stencil_kernel<<<152 * 8, 256, 0, s>>>(n, D, dinv, D32, Tx, Ty, Tz, Tx32, Ty32, Tz32, dinv32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_stencil(const Stencil &op, int *bad, cudaStream_t s) {
+    check_stencil_kernel<<<152 * 8, 256, 0, s>>>(op, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_csr(int32_t n, const int32_t *rp, const int32_t *ci, const double *av, int *bad,
+                             cudaStream_t s) {
+    check_csr_kernel<<<152 * 8, 256, 0, s>>>(n, rp, ci, av, bad);
+    return cudaGetLastError();
+}
+
+}  // namespace lc

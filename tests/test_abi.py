@@ -1,0 +1,55 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/*.h declares (CPU only: no compute calls)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+import paper_2001_01158_gb300 as lcg
+from paper_2001_01158_gb300.build import build_library
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        names |= set(re.findall(r"LC_EXPORT[^;(]*?\b(lc_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ["lc_mark_residual", "lc_mark_gradient", "lc_extract", "lc_pcg_solve",
+                     "lc_solve_local_then_global", "lc_ctx_create", "lc_op_create_stencil", "lc_op_create_csr"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = build_library()
+    L = C.CDLL(path)
+    missing = [n for n in declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_error_strings_and_no_device_path():
+    L = lcg.lib()
+    assert L.lc_error_string(0) == b"ok"
+    assert L.lc_error_string(5).startswith(b"Krylov breakdown")
+    assert L.lc_error_string(999) == b"unknown error"
+    h = C.c_void_p()
+    # an out-of-range device is rejected without touching a GPU
+    assert L.lc_ctx_create(C.byref(h), 1 << 20) == 1 and not h.value
+    assert L.lc_ctx_create(None, 0) == 1
+
+
+def test_struct_layouts_match_header():
+    # sizes of the parameter structs as the C compiler lays them out
+    assert C.sizeof(lcg.MarkParams) == 24
+    assert C.sizeof(lcg.SolveParams) == 32
+    assert C.sizeof(lcg.Params) == 120
+    assert C.sizeof(lcg.Stats) == 88
+    assert lcg.Params.global_.offset == 48 and lcg.Params.local.offset == 80

@@ -1,0 +1,271 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Marking, expansion, thresholds and the extracted subsystem are compared bit
+for bit; solves are compared within the tolerances the method states
+(relative residual <= tol, solution within 1e-9 of the oracle's FP64 PCG run
+with the same algorithm and tolerance).  Inputs are seeded (gen/); sizes
+span several tiles of every kernel and ragged tails."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_2001_01158_gb300 as lcg
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    lcg.build()
+    return lcg.Context(0)
+
+
+def cu(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device=DEV, dtype=dtype)
+
+
+def stencil_op(ctx, op: gen.Stencil):
+    return lcg.StencilOperator(ctx, op.shape, cu(op.D), cu(op.Tx), cu(op.Ty), cu(op.Tz) if op.Tz is not None else None)
+
+
+def csr_op(ctx, A: oracle.CSR):
+    return lcg.CsrOperator(ctx, cu(A.rowptr, torch.int32), cu(A.col, torch.int32), cu(A.val))
+
+
+def bits(a):
+    return np.ascontiguousarray(a, dtype=np.float64).view(np.int64)
+
+
+SHAPES_2D = [(7, 5), (64, 16), (65, 17), (130, 37), (257, 9), (1, 40), (40, 1), (300, 260)]
+SHAPES_3D = [(5, 4, 3), (16, 8, 8), (17, 9, 10), (33, 20, 7), (40, 1, 3)]
+
+
+def problems():
+    out = []
+    for k, (nx, ny) in enumerate(SHAPES_2D):
+        out.append((f"2d_{nx}x{ny}", gen.random_stencil_2d(k, nx, ny)))
+    for k, (nx, ny, nz) in enumerate(SHAPES_3D):
+        out.append((f"3d_{nx}x{ny}x{nz}", gen.random_stencil_3d(100 + k, nx, ny, nz)))
+    return out
+
+
+PROBLEMS = problems()
+
+
+def rhs_and_x0(op, seed, local_source=True):
+    rng = np.random.default_rng(seed)
+    A = oracle.from_stencil(op)
+    x_prev = 1.0 + 0.1 * rng.standard_normal(op.n)
+    s = np.zeros(op.n)
+    if local_source:
+        idx = rng.choice(op.n, size=max(1, op.n // 50), replace=False)
+        s[idx] = rng.uniform(0.5, 2.0, len(idx))
+    b = gen.csr_matvec(A.rowptr, A.col, A.val, x_prev) + s + 1e-6 * rng.standard_normal(op.n)
+    return A, b, x_prev
+
+
+MARK_CASES = [
+    (lcg.THR_REL_MAX, 1e-3, lcg.EXP_NONE, 0),
+    (lcg.THR_REL_MAX, 1e-2, lcg.EXP_DILATE, 1),
+    (lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2),
+    (lcg.THR_REL_MAX, 0.2, lcg.EXP_DILATE, 7),
+    (lcg.THR_EPS_NORMB, 1e-6, lcg.EXP_NONE, 0),
+    (lcg.THR_EPS_NORMB, 1e-4, lcg.EXP_PAPER, 1),
+    (lcg.THR_EPS_NORMB, 1e-5, lcg.EXP_PAPER, 6),
+    (lcg.THR_REL_MAX, 0.05, lcg.EXP_PAPER, 3),
+]
+
+
+def run_mark(ctx, gop, b, x0, case):
+    thr, prm, exp, rounds = case
+    n = len(b)
+    mask = torch.empty(n, dtype=torch.uint8, device=DEV)
+    r0 = torch.empty(n, dtype=torch.float64, device=DEV)
+    K = torch.zeros(1, dtype=torch.int32, device=DEV)
+    tau = torch.zeros(1, dtype=torch.float64, device=DEV)
+    lcg.mark_residual(ctx, gop, cu(b), cu(x0), lcg.MarkParams(thr, prm, exp, rounds), mask, K, r0, tau)
+    torch.cuda.synchronize()
+    return mask.cpu().numpy(), r0.cpu().numpy(), int(K.item()), float(tau.item())
+
+
+@pytest.mark.parametrize("name,op", PROBLEMS, ids=[p[0] for p in PROBLEMS])
+@pytest.mark.parametrize("case", MARK_CASES, ids=[f"thr{c[0]}_{c[1]}_exp{c[2]}x{c[3]}" for c in MARK_CASES])
+def test_mark_residual_bit_exact(ctx, name, op, case):
+    A, b, x0 = rhs_and_x0(op, 7)
+    ref = oracle.mark_residual(A, b, x0, case[0], case[1], case[2], case[3])
+    gop = stencil_op(ctx, op)
+    mask, r0, K, tau = run_mark(ctx, gop, b, x0, case)
+    assert np.array_equal(bits(r0), bits(ref["r"]))
+    assert bits([tau])[0] == bits([ref["tau"]])[0]
+    assert np.array_equal(mask, ref["mask"])
+    assert K == ref["K"]
+    # the same operator in CSR form gives the same bits
+    cop = csr_op(ctx, A)
+    mask2, r02, K2, tau2 = run_mark(ctx, cop, b, x0, case)
+    assert np.array_equal(bits(r02), bits(ref["r"])) and np.array_equal(mask2, ref["mask"]) and K2 == K
+    assert bits([tau2])[0] == bits([tau])[0]
+
+
+def test_example1_on_gpu(ctx):
+    e = gen.example1()
+    A = oracle.csr(e["rowptr"], e["col"], e["val"])
+    gop = csr_op(ctx, A)
+    mask, r0, K, tau = run_mark(ctx, gop, e["b"], e["x0"], (lcg.THR_EPS_NORMB, 1e-5, lcg.EXP_PAPER, 6))
+    ref = oracle.mark_residual(A, e["b"], e["x0"], oracle.THR_EPS_NORMB, 1e-5, oracle.EXP_PAPER, 6)
+    assert list(np.flatnonzero(mask) + 1) == [1, 2, 3, 4, 5, 6] and K == 6
+    assert bits([tau])[0] == bits([ref["tau"]])[0] and np.array_equal(bits(r0), bits(ref["r"]))
+
+
+@pytest.mark.parametrize("name,op", PROBLEMS, ids=[p[0] for p in PROBLEMS])
+@pytest.mark.parametrize("alpha,layers", [(0.0, 0), (0.3, 0), (0.05, 2), (1.0, 0), (0.5, 5)])
+def test_mark_gradient_bit_exact(ctx, name, op, alpha, layers):
+    A, b, x0 = rhs_and_x0(op, 3)
+    x0 = x0.copy()
+    x0[: max(1, op.n // 10)] = 1.0   # flat patch: g == 0 there
+    ref = oracle.mark_gradient(A, x0, alpha, layers)
+    for gop in (stencil_op(ctx, op), csr_op(ctx, A)):
+        mask = torch.empty(op.n, dtype=torch.uint8, device=DEV)
+        K = torch.zeros(1, dtype=torch.int32, device=DEV)
+        gmax = torch.zeros(1, dtype=torch.float64, device=DEV)
+        lcg.mark_gradient(ctx, gop, cu(x0), alpha, layers, mask, K, gmax)
+        torch.cuda.synchronize()
+        assert bits([gmax.item()])[0] == bits([ref["gmax"]])[0]
+        assert np.array_equal(mask.cpu().numpy(), ref["mask"])
+        assert int(K.item()) == ref["K"]
+
+
+@pytest.mark.parametrize("name,op", PROBLEMS, ids=[p[0] for p in PROBLEMS])
+@pytest.mark.parametrize("density", [0.0, 0.03, 0.3, 1.0])
+def test_extract_bit_exact(ctx, name, op, density):
+    A, b, x0 = rhs_and_x0(op, 11)
+    rng = np.random.default_rng(int(density * 100))
+    mask = (rng.uniform(size=op.n) < density).astype(np.uint8)
+    ref = oracle.extract(A, mask, b, x0)
+    for gop in (stencil_op(ctx, op), csr_op(ctx, A)):
+        out = lcg.Subsystem.empty(gop)
+        lcg.extract(ctx, gop, cu(mask, torch.uint8), cu(b), cu(x0), out)
+        torch.cuda.synchronize()
+        got = out.trimmed()
+        assert got["K"] == ref["K"] and got["nnz"] == len(ref["B"].col)
+        assert np.array_equal(got["g2l"], ref["g2l"]) and np.array_equal(got["l2g"], ref["l2g"])
+        assert np.array_equal(got["rowptr"], ref["B"].rowptr) and np.array_equal(got["col"], ref["B"].col)
+        assert np.array_equal(bits(got["val"]), bits(ref["B"].val))
+        assert np.array_equal(bits(got["rhs"]), bits(ref["rhs"]))
+        assert np.array_equal(bits(got["xL0"]), bits(ref["xL0"]))
+
+
+SOLVE_PROBLEMS = [p for p in PROBLEMS if p[1].n >= 20]
+
+
+@pytest.mark.parametrize("name,op", SOLVE_PROBLEMS, ids=[p[0] for p in SOLVE_PROBLEMS])
+def test_pcg_matches_oracle(ctx, name, op):
+    A, b, x0 = rhs_and_x0(op, 5)
+    tol = 1e-8
+    xr, st, it_ref, rr_ref = oracle.pcg(A, b, x0, tol=tol)
+    assert st == oracle.OK
+    for gop in (stencil_op(ctx, op), csr_op(ctx, A)):
+        x = cu(x0)
+        stats = lcg.Stats()
+        lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(tol, 100000, lcg.PREC_FP64, 0.0, 0), stats)
+        xg = x.cpu().numpy()
+        assert oracle.relres(A, b, xg) <= tol
+        assert abs(stats.it_global - it_ref) <= 1
+        assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
+        assert stats.relres_final <= tol
+
+
+def test_pcg_edge_cases(ctx):
+    op = gen.random_stencil_2d(1, 33, 21)
+    A = oracle.from_stencil(op)
+    gop = stencil_op(ctx, op)
+    sp = lcg.SolveParams(1e-8, 100000, lcg.PREC_FP64, 0.0, 0)
+    # b = 0 gives x = 0
+    x = cu(np.ones(op.n))
+    st = lcg.Stats()
+    lcg.pcg_solve(ctx, gop, cu(np.zeros(op.n)), x, sp, st)
+    assert not x.cpu().numpy().any() and st.it_global == 0
+    # an exact start needs no iteration
+    xs = np.random.default_rng(0).standard_normal(op.n)
+    b = A.dense() @ xs
+    xr, _, _, _ = oracle.pcg(A, b, np.zeros(op.n), tol=1e-14)
+    x = cu(xr)
+    lcg.pcg_solve(ctx, gop, cu(b), x, sp, st)
+    assert st.it_global == 0 and st.early_exit == 1
+    # max_iter reached: NOT_CONVERGED with stats filled
+    x = cu(np.zeros(op.n))
+    rc = lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(1e-14, 3, lcg.PREC_FP64, 0.0, 0), st,
+                       allow_not_converged=True)
+    assert rc == lcg.LC_ERR_NOT_CONVERGED and st.it_global == 3
+    # a negative definite operator breaks down
+    neg = oracle.csr(A.rowptr, A.col, -A.val)
+    with pytest.raises(lcg.LcError):
+        csr_op(ctx, neg)   # rejected at creation: non-positive diagonal
+
+
+@pytest.mark.parametrize("mode", ["residual", "gradient", "paper"])
+@pytest.mark.parametrize("n", [48, 128])
+def test_local_then_global_matches_oracle(ctx, mode, n):
+    d = gen.cfg1_heat2d(seed=n, n=n, radius=max(3, n // 12))
+    A = oracle.from_stencil(d["op"])
+    tol = 1e-8
+    kw = dict(tol=tol)
+    if mode == "residual":
+        okw = dict(mark_mode=oracle.MARK_RESIDUAL, thr_mode=oracle.THR_REL_MAX, thr_param=1e-3,
+                   exp_mode=oracle.EXP_DILATE, exp_rounds=2)
+        prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=tol)
+    elif mode == "paper":
+        okw = dict(mark_mode=oracle.MARK_RESIDUAL, thr_mode=oracle.THR_EPS_NORMB, thr_param=1e-6,
+                   exp_mode=oracle.EXP_PAPER, exp_rounds=2)
+        prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_EPS_NORMB, 1e-6, lcg.EXP_PAPER, 2, tol=tol)
+    else:
+        okw = dict(mark_mode=oracle.MARK_GRADIENT, alpha=0.6, grad_layers=1)
+        prm = lcg.default_params(lcg.MARK_GRADIENT, alpha=0.6, grad_layers=1, tol=tol)
+    xr, sr, mask_r = oracle.solve_local_then_global(A, d["b"], d["x0"], **okw, **kw)
+    for gop in (stencil_op(ctx, d["op"]), csr_op(ctx, A)):
+        x = cu(d["x0"])
+        st = lcg.Stats()
+        lcg.solve_local_then_global(ctx, gop, cu(d["b"]), x, prm, st)
+        xg = x.cpu().numpy()
+        assert st.K == sr["K"] and st.nnzB == sr["nnzB"]
+        assert abs(st.it_local - sr["it_local"]) <= 1
+        assert st.early_exit == sr["early_exit"]
+        assert oracle.relres(A, d["b"], xg) <= tol
+        assert st.relres_tilde == pytest.approx(sr["relres_tilde"], rel=1e-6)
+        assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
+
+
+def test_local_then_global_edge_K_zero_and_full(ctx):
+    d = gen.cfg1_heat2d(seed=2, n=40, radius=4)
+    A = oracle.from_stencil(d["op"])
+    gop = stencil_op(ctx, d["op"])
+    for beta, rounds in [(2.0, 0), (0.0, 60)]:
+        prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, beta, lcg.EXP_DILATE, rounds, tol=1e-9)
+        xr, sr, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], thr_param=beta, exp_rounds=rounds, tol=1e-9)
+        x = cu(d["x0"])
+        st = lcg.Stats()
+        lcg.solve_local_then_global(ctx, gop, cu(d["b"]), x, prm, st)
+        assert st.K == sr["K"] and st.early_exit == sr["early_exit"]
+        assert oracle.relres(A, d["b"], x.cpu().numpy()) <= 1e-9
+
+
+def test_nan_handling_matches_oracle(ctx):
+    op = gen.random_stencil_2d(4, 70, 33)
+    A, b, x0 = rhs_and_x0(op, 9)
+    b = b.copy()
+    b[5] = np.nan
+    x0 = x0.copy()
+    x0[1000] = np.nan
+    for case in [(lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2), (lcg.THR_REL_MAX, 1e-2, lcg.EXP_PAPER, 2)]:
+        ref = oracle.mark_residual(A, b, x0, *case)
+        mask, r0, K, tau = run_mark(ctx, stencil_op(ctx, op), b, x0, case)
+        assert np.array_equal(mask, ref["mask"]) and K == ref["K"]
+        assert bits([tau])[0] == bits([ref["tau"]])[0]
+    ref = oracle.mark_gradient(A, x0, 0.1, 1)
+    mask = torch.empty(op.n, dtype=torch.uint8, device=DEV)
+    K = torch.zeros(1, dtype=torch.int32, device=DEV)
+    lcg.mark_gradient(ctx, stencil_op(ctx, op), cu(x0), 0.1, 1, mask, K)
+    assert np.array_equal(mask.cpu().numpy(), ref["mask"])
