@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Benchmark of the local character-based solve on one GB300 (or N replicas).
+
+Workload (one "step" = one system of the sequence solved end to end by the
+hot path): a 2048 x 2048 5-point backward-Euler diffusion operator with
+discontinuous conductivity (background 1, 64 seeded rectangles, k
+log-uniform in [1, 1e3]) and a Gaussian hot front (sigma = 30 cells) that
+moves 8 cells per step over 20 steps.  System n is A x = x^{n-1}/dt + s^n,
+started from the reference solution x^{n-1} (computed once, before timing,
+by the global PCG of this library and kept resident in HBM).  Each step runs
+Alg 1: residual marking (tau = 1e-3 max|r0|, 2 dilation layers), extraction,
+local Jacobi-PCG, assembly, the check of x~ and the warm-started global
+Jacobi-PCG to relres 1e-8.  The same systems are also solved by plain global
+Jacobi-PCG and by Alg 1 with gradient marking, for comparison.
+
+The JSON line reports time-to-solution per system (lower is better), the
+roofline of the dominant kernel (the global PCG kernel), the kernel count,
+SM clocks sampled during the timed region, an end-to-end figure through the
+C ABI with host buffers, and the oracle timed on the host cores.
+
+`--impl reference` times the oracle (plain serial FP64 CPU code) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solution per system and SpMV HBM GB/s: local-first vs global PCG at relres 1e-8"
+UNIT = "ms/system"
+WORKLOAD = ("2D 2048x2048 5-point FP64 diffusion, 64 rectangles k in [1,1e3], Gaussian front sigma=30 moving "
+            "8 cells/step, 20 backward-Euler steps; Alg 1 with residual marking (1e-3 max|r|, 2 layers), "
+            "Jacobi-PCG to relres 1e-8")
+
+# Bytes the global PCG kernel must move per cell (2D FP64): set-up / true
+# residual pass reads b, x, D, Tx, Ty, dinv and writes r, z (64 B); each
+# iteration moves 120 B (phase A: z, p_old, D, Tx, Ty in, p, q out; phase B:
+# x, p, r, q, dinv in, x, r, z out).
+SETUP_BYTES = 64
+ITER_BYTES = 120
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["lc", "reference"], default="lc")
+    ap.add_argument("--n", type=int, default=2048, help="grid side")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- utilities
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        rank = int(os.environ.get("RANK", "0"))
+        local = int(os.environ.get("LOCAL_RANK", str(rank)))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "lc" else "gloo")
+        return rank, ws, local
+    return 0, 1, 0
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws, device=None):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_digest() -> str:
+    with open(os.path.join(ROOT, "paper_2001_01158_gb300", "csrc", "lc_pcg.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic_per_cell_iter():
+    """DRAM bytes per cell and iteration of the global PCG kernel from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "pcg_stencil2d_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as f:
+        for ln in f:
+            if "=" in ln and not ln.lstrip().startswith("#"):
+                k, v = ln.split("=", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("lc_pcg_cu_sha256_16") != source_digest():
+        return None
+    try:
+        return float(vals["dram_bytes_per_cell_iter"]), float(vals.get("dram_bytes_per_cell_setup", "nan"))
+    except (KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------- oracle side
+
+def oracle_sample(n_full: int, n: int | None = None):
+    """Alg 1 of the oracle on the same workload family at a reduced
+    resolution n x n (default n_full/2), system 1 (x0 = 0, b = s^1), scaled to
+    ms per n_full^2 system by the cell count (the operator's mass term keeps
+    the Jacobi-PCG iteration count essentially independent of the grid size).
+    Returns (ms_per_system, sample, stats)."""
+    import gen
+    import oracle
+    n = n or max(64, n_full // 2)
+    d = gen.cfg2_fronts2d(seed=0, n=n)
+    A = oracle.from_stencil(d["op"])
+    b = d["seq"].source(1)
+    import numpy as np
+    x0 = np.zeros(A.n)
+    t = time.perf_counter()
+    x, st, _ = oracle.solve_local_then_global(A, b, x0, tol=1e-8)
+    dt = time.perf_counter() - t
+    scale = (n_full * n_full) / float(n * n)
+    sample = (f"oracle Alg 1 (serial FP64 C, 1 thread) on system 1 of the same workload at {n}x{n} "
+              f"(K={st['K']}, {st['it_local']}+{st['it_global']} CG iterations, {dt:.1f} s), "
+              f"scaled x{scale:g} by cell count to one {n_full}x{n_full} system")
+    return dt * 1e3 * scale, sample, st
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return
+    from oracle.build import build_oracle
+    build_oracle()
+    # size each step so the whole run stays near two minutes: time a small
+    # probe, then take the largest n_full/2^j whose predicted time fits
+    budget = 120.0 / max(1, args.warmup + args.steps)
+    t = time.perf_counter()
+    oracle_sample(args.n, 128)
+    per_cell = (time.perf_counter() - t) / (128 * 128)
+    n = max(64, args.n // 2)
+    while n > 128 and per_cell * n * n > budget:
+        n //= 2
+    times = []
+    sample = ""
+    for k in range(args.warmup + args.steps):
+        ms, sample, _ = oracle_sample(args.n, n)
+        if k >= args.warmup:
+            times.append(ms)
+    v = statistics.mean(times) if times else float("nan")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("2048x2048", f"{args.n}x{args.n}"), "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU side
+
+def run_gpu(args, rank, ws, local):
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2001_01158_gb300 as lcg
+
+    lcg.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    d = gen.cfg2_fronts2d(seed=rank, n=args.n)
+    op, seq = d["op"], d["seq"]
+    N = op.n
+    T = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)  # noqa: E731
+    ctx = lcg.Context(local)
+    gop = lcg.StencilOperator(ctx, op.shape, T(op.D), T(op.Tx), T(op.Ty))
+    sp = lcg.SolveParams(1e-8, 200000, lcg.PREC_FP64, 0.0, 0)
+
+    # the sequence's reference states, resident in HBM
+    nsys = seq.steps
+    xs = [torch.zeros(N, dtype=torch.float64, device=dev)]
+    bs = []
+    for k in range(1, nsys + 1):
+        b = xs[-1] / op.meta["dt"] + T(seq.source(k))
+        x = xs[-1].clone()
+        lcg.pcg_solve(ctx, gop, b, x, sp)
+        bs.append(b)
+        xs.append(x)
+    torch.cuda.synchronize(dev)
+
+    prm_res = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8)
+    prm_grad = lcg.default_params(lcg.MARK_GRADIENT, alpha=1e-3, grad_layers=2, tol=1e-8)
+    work = torch.empty(N, dtype=torch.float64, device=dev)
+
+    def system(k):
+        j = k % nsys
+        return bs[j], xs[j]
+
+    def solve(kind, k, stats):
+        b, x0 = system(k)
+        work.copy_(x0, non_blocking=True)
+        if kind == "global":
+            lcg.pcg_solve(ctx, gop, b, work, sp, stats)
+        else:
+            lcg.solve_local_then_global(ctx, gop, b, work, prm_res if kind == "res" else prm_grad, stats)
+
+    def timed_loop(kind, steps, warmup, clocks=None):
+        st = lcg.Stats()
+        for k in range(warmup):
+            solve(kind, k, st)
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+        per = []
+        launches0 = lcg.kernel_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps):
+            solve(kind, warmup + k, st)
+            per.append(st.as_dict())
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+        launches = lcg.kernel_launch_count() - launches0
+        ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+        return ms, per, launches
+
+    with ClockSampler(local) as cs:
+        ms_res, per_res, launches = timed_loop("res", args.steps, args.warmup)
+    clocks = cs.summary()
+    ms_glob, per_glob, _ = timed_loop("global", args.steps, args.warmup)
+    ms_grad, per_grad, _ = timed_loop("grad", args.steps, args.warmup)
+
+    # roofline of the dominant kernel: the global PCG launch inside Alg 1,
+    # timed by CUDA events the library records on the launching stream
+    def pcg_bytes(s):
+        checks = 1 + (0 if s["early_exit"] else 1 + s["restarts"])
+        return N * (SETUP_BYTES * checks + ITER_BYTES * s["it_global"])
+
+    byts = sum(pcg_bytes(s) for s in per_res)
+    t_pcg = sum(s["t_global_ms"] for s in per_res) * 1e-3
+    achieved = byts / t_pcg / 1e9 if t_pcg > 0 else 0.0
+    peak, peak_kind = measured_peaks()
+    tr = ncu_traffic_per_cell_iter()
+    mean_it = statistics.mean(s["it_global"] for s in per_res)
+    traffic = None
+    if tr is not None:
+        bpc_iter, bpc_setup = tr
+        traffic = float(N * (bpc_iter * mean_it + (bpc_setup if math.isfinite(bpc_setup) else SETUP_BYTES) * 2))
+    # GB/s of the plain global PCG (the "SpMV HBM GB/s" half of the metric)
+    byts_g = sum(pcg_bytes(s) for s in per_glob)
+    t_g = sum(s["t_global_ms"] for s in per_glob) * 1e-3
+    gbs_global = byts_g / t_g / 1e9 if t_g > 0 else 0.0
+
+    # end to end through the C ABI with host buffers
+    b_h = [bs[j].cpu().pin_memory() for j in range(nsys)]
+    x_h = [xs[j].cpu().pin_memory() for j in range(nsys)]
+    out_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    b_d = torch.empty(N, dtype=torch.float64, device=dev)
+    st = lcg.Stats()
+
+    def e2e_step(k):
+        j = k % nsys
+        b_d.copy_(b_h[j], non_blocking=True)
+        work.copy_(x_h[j], non_blocking=True)
+        lcg.solve_local_then_global(ctx, gop, b_d, work, prm_res, st)
+        out_h.copy_(work, non_blocking=True)
+        torch.cuda.synchronize(dev)
+
+    for k in range(args.warmup):
+        e2e_step(k)
+    barrier(ws)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        e2e_step(args.warmup + k)
+    barrier(ws)
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, ws, dev)
+
+    total_sys = args.steps * ws
+    value = ms_res / total_sys
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_res / args.steps, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("2048x2048", f"{args.n}x{args.n}"), "N": N,
+                   "systems": nsys, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (operator + 20 resident systems + PCG vectors > 1 GB)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "pcg_kernel<Op2D> (global Jacobi-PCG)",
+                     "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_cell_iter": ITER_BYTES},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": {"value": e2e_ms / total_sys, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * N,
+                "d2h_bytes_per_step": 8 * N},
+        "global_pcg": {"value": ms_glob / total_sys, "unit": UNIT,
+                       "iterations": statistics.mean(s["it_global"] for s in per_glob), "hbm_gbs": gbs_global},
+        "local_first_residual": {
+            "value": value, "eta": statistics.mean(s["eta"] for s in per_res),
+            "it_local": statistics.mean(s["it_local"] for s in per_res),
+            "it_global": mean_it, "early_exit_frac": statistics.mean(s["early_exit"] for s in per_res),
+            "t_mark_ms": statistics.mean(s["t_mark_ms"] for s in per_res),
+            "t_extract_ms": statistics.mean(s["t_extract_ms"] for s in per_res),
+            "t_local_ms": statistics.mean(s["t_local_ms"] for s in per_res),
+            "t_global_ms": statistics.mean(s["t_global_ms"] for s in per_res),
+            "relres_max": max(s["relres_final"] for s in per_res)},
+        "local_first_gradient": {
+            "value": ms_grad / total_sys, "eta": statistics.mean(s["eta"] for s in per_grad),
+            "it_local": statistics.mean(s["it_local"] for s in per_grad),
+            "it_global": statistics.mean(s["it_global"] for s in per_grad),
+            "relres_max": max(s["relres_final"] for s in per_grad)},
+        "speedup_vs_global_pcg": ms_glob / ms_res,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle.build import build_oracle
+        build_oracle()
+        ms, sample, _ = oracle_sample(args.n)
+        res["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+def main():
+    args = parse()
+    rank, ws, local = dist_init(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, ws)
+        else:
+            run_gpu(args, rank, ws, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -223,6 +223,11 @@ LC_EXPORT int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const dou
 LC_EXPORT const char *lc_error_string(int code);
 LC_EXPORT const char *lc_last_error(const lc_ctx *ctx);
 
+/* Number of CUDA kernels this library has launched in this process since it
+ * was loaded (all contexts and devices; memsets and copies not counted).
+ * For accounting only: a benchmark reads it before and after a timed region. */
+LC_EXPORT int64_t lc_kernel_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

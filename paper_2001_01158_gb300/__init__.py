@@ -105,6 +105,8 @@ def lib():
     L.lc_error_string.restype = C.c_char_p
     L.lc_last_error.argtypes = [vp]
     L.lc_last_error.restype = C.c_char_p
+    L.lc_kernel_launch_count.argtypes = []
+    L.lc_kernel_launch_count.restype = C.c_int64
     _lib = L
     return L
 
@@ -266,6 +268,11 @@ def solve_local_then_global(ctx: Context, op: _Operator, b, x, params: Params, s
                                                       _ptr(x, torch.float64, "x"), C.byref(params),
                                                       C.byref(stats) if stats is not None else None,
                                                       _stream(stream)), allow)
+
+
+def kernel_launch_count() -> int:
+    """Kernels this library has launched in this process (lc_kernel_launch_count)."""
+    return int(lib().lc_kernel_launch_count())
 
 
 def default_params(mark_mode=MARK_RESIDUAL, thr_mode=THR_REL_MAX, thr_param=1e-3, exp_mode=EXP_DILATE, exp_rounds=2,

@@ -11,7 +11,14 @@
 #include <new>
 #include <string>
 
+#include <atomic>
+
 #include "lc_internal.cuh"
+
+namespace lc {
+static std::atomic<long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace lc
 
 struct lc_ctx {
     int device = 0;
@@ -322,6 +329,8 @@ const char *lc_error_string(int code) {
 }
 
 const char *lc_last_error(const lc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t lc_kernel_launch_count(void) { return (int64_t)lc::g_launches.load(std::memory_order_relaxed); }
 
 int lc_ctx_create(lc_ctx **out, int device) {
     if (!out) return LC_ERR_INVALID_ARG;

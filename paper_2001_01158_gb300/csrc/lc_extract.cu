@@ -254,8 +254,11 @@ cudaError_t run_maps(const OP &op, int64_t n, const uint8_t *mask, const lc_subs
     const int64_t nb = (n + kXChunk - 1) / kXChunk;
     if (nb + 1 > w.nblocks_cap) return cudaErrorInvalidValue;
     count_kernel<OP, DIM><<<(unsigned)nb, kXThreads, 0, s>>>(op, n, mask, w.blk);
+    note_launches(1);
     scan_blocks_kernel<<<1, 1024, 0, s>>>(w.blk, nb, out.rowptr, out.K, out.nnz, ctrl);
+    note_launches(1);
     write_maps_kernel<OP, DIM><<<(unsigned)nb, kXThreads, 0, s>>>(op, n, mask, w.blk, out.g2l, out.l2g, out.rowptr);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -272,6 +275,7 @@ cudaError_t launch_extract_stencil(const Stencil &op, const uint8_t *mask, const
     else
         gather_stencil_kernel<2><<<flat_grid(op.n), 256, 0, s>>>(op, out.K, out.l2g, out.g2l, out.rowptr, b, x0, out.col,
                                                                   out.val, out.rhs, out.xL0);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -281,12 +285,14 @@ cudaError_t launch_extract_csr(const Csr &op, const uint8_t *mask, const double 
     if (e != cudaSuccess) return e;
     gather_csr_kernel<<<flat_grid(op.n), 256, 0, s>>>(op, out.K, out.l2g, out.g2l, out.rowptr, b, x0, out.col, out.val,
                                                       out.rhs, out.xL0);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assemble(const int32_t *K_dev, const int32_t *l2g, const double *xbar, double *x, int64_t cap,
                             cudaStream_t s) {
     assemble_kernel<<<flat_grid(cap), 256, 0, s>>>(K_dev, l2g, xbar, x);
+    note_launches(1);
     return cudaGetLastError();
 }
 

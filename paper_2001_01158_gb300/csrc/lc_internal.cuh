@@ -212,6 +212,9 @@ struct Launch {
     cudaStream_t stream;
 };
 
+// Accounting of kernel launches (lc_kernel_launch_count).
+void note_launches(int n);
+
 // Launchers (one translation unit each).  All return cudaError_t of the
 // last launch; argument validation happens in lc_api.cu.
 cudaError_t launch_residual_stencil(const Stencil &op, const double *b, const double *x, double *r,

@@ -417,11 +417,11 @@ cudaError_t launch_residual_stencil(const Stencil &op, const double *b, const do
                                     double *tree_partials, Ctrl *ctrl, cudaStream_t s) {
     const int nb = (int)((op.n + kTreeChunk - 1) / kTreeChunk);
     if (op.dim == 3) {
-        if (want_tree) residual_stencil_kernel<3, true><<<nb, kResThreads, 0, s>>>(op, b, x, r, tree_partials, ctrl);
-        else residual_stencil_kernel<3, false><<<nb, kResThreads, 0, s>>>(op, b, x, r, tree_partials, ctrl);
+        if (want_tree) { residual_stencil_kernel<3, true><<<nb, kResThreads, 0, s>>>(op, b, x, r, tree_partials, ctrl); note_launches(1); }
+        else { residual_stencil_kernel<3, false><<<nb, kResThreads, 0, s>>>(op, b, x, r, tree_partials, ctrl); note_launches(1); }
     } else {
-        if (want_tree) residual_stencil_kernel<2, true><<<nb, kResThreads, 0, s>>>(op, b, x, r, tree_partials, ctrl);
-        else residual_stencil_kernel<2, false><<<nb, kResThreads, 0, s>>>(op, b, x, r, tree_partials, ctrl);
+        if (want_tree) { residual_stencil_kernel<2, true><<<nb, kResThreads, 0, s>>>(op, b, x, r, tree_partials, ctrl); note_launches(1); }
+        else { residual_stencil_kernel<2, false><<<nb, kResThreads, 0, s>>>(op, b, x, r, tree_partials, ctrl); note_launches(1); }
     }
     return cudaGetLastError();
 }
@@ -429,8 +429,8 @@ cudaError_t launch_residual_stencil(const Stencil &op, const double *b, const do
 cudaError_t launch_residual_csr(const Csr &op, const double *b, const double *x, double *r, int want_tree,
                                 double *tree_partials, Ctrl *ctrl, cudaStream_t s) {
     const int nb = (int)((op.n + kTreeChunk - 1) / kTreeChunk);
-    if (want_tree) residual_csr_kernel<true><<<nb, kResThreads, 0, s>>>(op, b, x, r, tree_partials, ctrl);
-    else residual_csr_kernel<false><<<nb, kResThreads, 0, s>>>(op, b, x, r, tree_partials, ctrl);
+    if (want_tree) { residual_csr_kernel<true><<<nb, kResThreads, 0, s>>>(op, b, x, r, tree_partials, ctrl); note_launches(1); }
+    else { residual_csr_kernel<false><<<nb, kResThreads, 0, s>>>(op, b, x, r, tree_partials, ctrl); note_launches(1); }
     return cudaGetLastError();
 }
 
@@ -443,20 +443,24 @@ cudaError_t launch_tree_finish(double *partials, double *scratch, int64_t nchunk
     while (m > 1) {
         const int64_t nb = (m + kTreeChunk - 1) / kTreeChunk;
         tree_level_kernel<<<(unsigned)nb, kResThreads, 0, s>>>(in, m, out);
+        note_launches(1);
         double *t = in; in = out; out = t;
         m = nb;
     }
     tau_eps_kernel<<<1, 1, 0, s>>>(in, n, eps, ctrl, tau_out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tau_relmax(double beta, Ctrl *ctrl, double *tau_out, cudaStream_t s) {
     tau_relmax_kernel<<<1, 1, 0, s>>>(beta, ctrl, tau_out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gmax_threshold(double alpha, Ctrl *ctrl, double *gmax_out, cudaStream_t s) {
     gmax_threshold_kernel<<<1, 1, 0, s>>>(alpha, ctrl, gmax_out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -475,6 +479,7 @@ cudaError_t launch_threshold_dilate_stencil(const Stencil &op, const double *v, 
     const size_t smem = 2 * (size_t)g.ex * g.ey * g.ez;
     const unsigned nb = (unsigned)((int64_t)ntx * nty * ntz);
     threshold_dilate_kernel<true><<<nb, 256, smem, s>>>(op, g, v, nullptr, mask, ctrl);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -490,46 +495,52 @@ cudaError_t launch_dilate_stencil_pass(const Stencil &op, int layers, const uint
     const size_t smem = 2 * (size_t)g.ex * g.ey * g.ez;
     const unsigned nb = (unsigned)((int64_t)ntx * nty * ntz);
     threshold_dilate_kernel<false><<<nb, 256, smem, s>>>(op, g, nullptr, in, out, nullptr);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_threshold_csr(int32_t n, const double *v, uint8_t *mask, Ctrl *ctrl, cudaStream_t s) {
     threshold_flat_kernel<<<flat_grid(n), 256, 0, s>>>(n, v, mask, ctrl);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dilate_csr(const Csr &op, const uint8_t *in, uint8_t *out, cudaStream_t s) {
     dilate_csr_kernel<<<flat_grid(op.n), 256, 0, s>>>(op, in, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_expand_paper_stencil(const Stencil &op, const double *r, const double *x0, int round,
                                         const uint8_t *in, uint8_t *out, Ctrl *ctrl, cudaStream_t s) {
-    if (op.dim == 3) expand_paper_stencil_kernel<3><<<flat_grid(op.n), 256, 0, s>>>(op, r, x0, round, in, out, ctrl);
-    else expand_paper_stencil_kernel<2><<<flat_grid(op.n), 256, 0, s>>>(op, r, x0, round, in, out, ctrl);
+    if (op.dim == 3) { expand_paper_stencil_kernel<3><<<flat_grid(op.n), 256, 0, s>>>(op, r, x0, round, in, out, ctrl); note_launches(1); }
+    else { expand_paper_stencil_kernel<2><<<flat_grid(op.n), 256, 0, s>>>(op, r, x0, round, in, out, ctrl); note_launches(1); }
     return cudaGetLastError();
 }
 
 cudaError_t launch_expand_paper_csr(const Csr &op, const double *r, const double *x0, int round, const uint8_t *in,
                                     uint8_t *out, Ctrl *ctrl, cudaStream_t s) {
     expand_paper_csr_kernel<<<flat_grid(op.n), 256, 0, s>>>(op, r, x0, round, in, out, ctrl);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gradient_stencil(const Stencil &op, const double *x, double *g, Ctrl *ctrl, cudaStream_t s) {
-    if (op.dim == 3) gradient_stencil_kernel<3><<<flat_grid(op.n), 256, 0, s>>>(op, x, g, ctrl);
-    else gradient_stencil_kernel<2><<<flat_grid(op.n), 256, 0, s>>>(op, x, g, ctrl);
+    if (op.dim == 3) { gradient_stencil_kernel<3><<<flat_grid(op.n), 256, 0, s>>>(op, x, g, ctrl); note_launches(1); }
+    else { gradient_stencil_kernel<2><<<flat_grid(op.n), 256, 0, s>>>(op, x, g, ctrl); note_launches(1); }
     return cudaGetLastError();
 }
 
 cudaError_t launch_gradient_csr(const Csr &op, const double *x, double *g, Ctrl *ctrl, cudaStream_t s) {
     gradient_csr_kernel<<<flat_grid(op.n), 256, 0, s>>>(op, x, g, ctrl);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_count_mask(int64_t n, const uint8_t *mask, Ctrl *ctrl, int32_t *K_out, cudaStream_t s) {
     count_mask_kernel<<<flat_grid((n + 15) / 16), 256, 0, s>>>(n, mask, ctrl);
-    if (K_out) copy_k_kernel<<<1, 1, 0, s>>>(ctrl, K_out);
+    note_launches(1);
+    if (K_out) { copy_k_kernel<<<1, 1, 0, s>>>(ctrl, K_out); note_launches(1); }
     return cudaGetLastError();
 }
 

@@ -37,101 +37,122 @@ constexpr int kTileX = 32, kTileY = 8, kTileZ = 16;   // 3D unit
 struct Bufs {
     const double *b;
     double *x, *r, *z, *q;
-    double *p[2];
+    double *p0, *p1;
     const double *dinv;
     double *part;          // [6][kMaxGrid]
 };
 
 // -------------------------------------------------------------- operators
+//
+// Every operator provides, for the calling block:
+//   setup_block     r = b - A x, z = dinv r over its cells; sums b.b, r.z, r.r
+//   phaseA_block    p = z + beta p_old, q = A p over its cells; sums p.q
+//   each_cell(f)    f(i) for its cells (phase B), in the same cell-to-thread
+//                   mapping as phase A, so the p and q a thread stored are
+//                   the ones it reads back.
 
+// 2D: the grid is cut into column strips of kPcgThreads cells (one thread
+// per column); the strip-major list of (strip, row) pairs is split evenly
+// into contiguous ranges, one per block, and a block marches down its rows.
+// p of the row above and below lives in registers, the two x-neighbours come
+// from a shared-memory row (double-buffered: one barrier per row).
 struct Op2D {
     Stencil s;
-    __device__ int64_t units() const {
-        const int64_t sx = (s.nx + kPcgThreads - 1) / kPcgThreads;
-        const int64_t sy = (s.ny + kStripRows - 1) / kStripRows;
-        return sx * sy;
-    }
-    // r = b - A x, z = dinv r on the unit; accumulates bb, rz, rr
-    __device__ void setup(int64_t u, const Bufs &B, double &bb, double &rz, double &rr) const {
-        const int64_t sx = (s.nx + kPcgThreads - 1) / kPcgThreads;
-        const int xx = (int)(u % sx) * kPcgThreads + threadIdx.x;
-        const int y0 = (int)(u / sx) * kStripRows;
-        if (xx >= s.nx) return;
-        const int y1 = min(y0 + kStripRows, s.ny);
-        for (int y = y0; y < y1; ++y) {
-            const int64_t i = (int64_t)y * s.nx + xx;
-            double ax = s.D[i] * ldcg(B.x + i);
-            if (y > 0) ax = fma(-s.Ty[i - s.nx], ldcg(B.x + i - s.nx), ax);
-            if (xx > 0) ax = fma(-s.Tx[i - 1], ldcg(B.x + i - 1), ax);
-            if (xx + 1 < s.nx) ax = fma(-s.Tx[i], ldcg(B.x + i + 1), ax);
-            if (y + 1 < s.ny) ax = fma(-s.Ty[i], ldcg(B.x + i + s.nx), ax);
-            const double bi = B.b[i];
-            const double ri = bi - ax;
-            const double zi = s.dinv[i] * ri;
-            B.r[i] = ri;
-            B.z[i] = zi;
-            bb = fma(bi, bi, bb);
-            rz = fma(ri, zi, rz);
-            rr = fma(ri, ri, rr);
+    __device__ __forceinline__ int strips() const { return (s.nx + kPcgThreads - 1) / kPcgThreads; }
+    template <class F>
+    __device__ __forceinline__ void each_segment(F f) const {
+        const int64_t rs = (int64_t)strips() * s.ny;
+        const int64_t lo = rs * blockIdx.x / gridDim.x, hi = rs * (blockIdx.x + 1) / gridDim.x;
+        if (lo >= hi) return;
+        const int st0 = (int)(lo / s.ny), st1 = (int)((hi - 1) / s.ny);
+        for (int st = st0; st <= st1; ++st) {
+            const int y0 = st == st0 ? (int)(lo % s.ny) : 0;
+            const int y1 = st == st1 ? (int)((hi - 1) % s.ny) + 1 : s.ny;
+            f(st * kPcgThreads, y0, y1);
         }
     }
-    __device__ __forceinline__ double pnew(const Bufs &B, int pin, bool first, double beta, int64_t i) const {
-        const double zi = ldcg(B.z + i);
-        return first ? zi : fma(beta, ldcg(B.p[pin] + i), zi);
-    }
-    __device__ void phaseA(int64_t u, const Bufs &B, int pin, bool first, double beta, double &pq, double *srow) const {
-        const int64_t sx = (s.nx + kPcgThreads - 1) / kPcgThreads;
-        const int x0 = (int)(u % sx) * kPcgThreads;
-        const int xx = x0 + threadIdx.x;
-        const int y0 = (int)(u / sx) * kStripRows;
-        const int y1 = min(y0 + kStripRows, s.ny);
-        const bool act = xx < s.nx;
-        double *pout = B.p[pin ^ 1];
-        double pm = 0.0, pc = 0.0, tym = 0.0;
-        if (act) {
-            const int64_t i0 = (int64_t)y0 * s.nx + xx;
-            pc = pnew(B, pin, first, beta, i0);
-            if (y0 > 0) { pm = pnew(B, pin, first, beta, i0 - s.nx); tym = s.Ty[i0 - s.nx]; }
-        }
-        for (int y = y0; y < y1; ++y) {
-            const int64_t i = (int64_t)y * s.nx + xx;
-            double pn = 0.0;
-            if (act && y + 1 < s.ny) pn = pnew(B, pin, first, beta, i + s.nx);
-            double *buf = srow + (y & 1) * (kPcgThreads + 2);
-            buf[threadIdx.x + 1] = pc;
-            if (threadIdx.x == 0)
-                buf[0] = x0 > 0 ? pnew(B, pin, first, beta, (int64_t)y * s.nx + x0 - 1) : 0.0;
-            if (threadIdx.x == kPcgThreads - 1)
-                buf[kPcgThreads + 1] = x0 + kPcgThreads < s.nx ? pnew(B, pin, first, beta, (int64_t)y * s.nx + x0 + kPcgThreads) : 0.0;
-            __syncthreads();
-            if (act) {
-                const double pw = buf[threadIdx.x], pe = buf[threadIdx.x + 2];
-                const double txw = xx > 0 ? s.Tx[i - 1] : 0.0;
-                const double txe = xx + 1 < s.nx ? s.Tx[i] : 0.0;
-                const double typ = y + 1 < s.ny ? s.Ty[i] : 0.0;
-                double qi = s.D[i] * pc;
-                qi = fma(-tym, pm, qi);
-                qi = fma(-txw, pw, qi);
-                qi = fma(-txe, pe, qi);
-                qi = fma(-typ, pn, qi);
-                pout[i] = pc;
-                B.q[i] = qi;
-                pq = fma(pc, qi, pq);
-                tym = typ;
+    __device__ void setup_block(const Bufs &B, double &bb, double &rz, double &rr) const {
+        each_segment([&](int x0, int y0, int y1) {
+            const int xx = x0 + threadIdx.x;
+            if (xx >= s.nx) return;
+            for (int y = y0; y < y1; ++y) {
+                const int64_t i = (int64_t)y * s.nx + xx;
+                double ax = s.D[i] * ldcg(B.x + i);
+                if (y > 0) ax = fma(-s.Ty[i - s.nx], ldcg(B.x + i - s.nx), ax);
+                if (xx > 0) ax = fma(-s.Tx[i - 1], ldcg(B.x + i - 1), ax);
+                if (xx + 1 < s.nx) ax = fma(-s.Tx[i], ldcg(B.x + i + 1), ax);
+                if (y + 1 < s.ny) ax = fma(-s.Ty[i], ldcg(B.x + i + s.nx), ax);
+                const double bi = B.b[i];
+                const double ri = bi - ax;
+                const double zi = s.dinv[i] * ri;
+                B.r[i] = ri;
+                B.z[i] = zi;
+                bb = fma(bi, bi, bb);
+                rz = fma(ri, zi, rz);
+                rr = fma(ri, ri, rr);
             }
-            pm = pc;
-            pc = pn;
-        }
-        __syncthreads();
+        });
+    }
+    __device__ __forceinline__ double pnew(const Bufs &B, const double *pold, bool first, double beta,
+                                           int64_t i) const {
+        const double zi = ldcg(B.z + i);
+        return first ? zi : fma(beta, ldcg(pold + i), zi);
+    }
+    __device__ void phaseA_block(const Bufs &B, const double *pold, double *pout, bool first, double beta,
+                                 double &pq, double *srow) const {
+        each_segment([&](int x0, int y0, int y1) {
+            const int xx = x0 + threadIdx.x;
+            const bool act = xx < s.nx;
+            const bool hw = threadIdx.x == 0 && x0 > 0;
+            const bool he = threadIdx.x == kPcgThreads - 1 && x0 + kPcgThreads < s.nx;
+            double pm = 0.0, pc = 0.0, tym = 0.0;
+            if (act) {
+                const int64_t i0 = (int64_t)y0 * s.nx + xx;
+                pc = pnew(B, pold, first, beta, i0);
+                if (y0 > 0) { pm = pnew(B, pold, first, beta, i0 - s.nx); tym = s.Ty[i0 - s.nx]; }
+            }
+            for (int y = y0; y < y1; ++y) {
+                const int64_t i = (int64_t)y * s.nx + xx;
+                // every load of this row first, then one barrier
+                double pn = 0.0, d = 0.0, txw = 0.0, txe = 0.0, typ = 0.0, halo = 0.0;
+                if (act) {
+                    if (y + 1 < s.ny) { pn = pnew(B, pold, first, beta, i + s.nx); typ = s.Ty[i]; }
+                    d = s.D[i];
+                    if (xx > 0) txw = s.Tx[i - 1];
+                    if (xx + 1 < s.nx) txe = s.Tx[i];
+                }
+                if (hw) halo = pnew(B, pold, first, beta, (int64_t)y * s.nx + x0 - 1);
+                if (he) halo = pnew(B, pold, first, beta, (int64_t)y * s.nx + x0 + kPcgThreads);
+                double *buf = srow + (y & 1) * (kPcgThreads + 2);
+                buf[threadIdx.x + 1] = pc;
+                if (threadIdx.x == 0) buf[0] = halo;
+                if (threadIdx.x == kPcgThreads - 1) buf[kPcgThreads + 1] = halo;
+                __syncthreads();
+                if (act) {
+                    double qi = d * pc;
+                    qi = fma(-tym, pm, qi);
+                    qi = fma(-txw, buf[threadIdx.x], qi);
+                    qi = fma(-txe, buf[threadIdx.x + 2], qi);
+                    qi = fma(-typ, pn, qi);
+                    pout[i] = pc;
+                    B.q[i] = qi;
+                    pq = fma(pc, qi, pq);
+                }
+                tym = typ;
+                pm = pc;
+                pc = pn;
+            }
+            __syncthreads();
+        });
     }
     template <class F>
-    __device__ void for_cells(int64_t u, F f) const {
-        const int64_t sx = (s.nx + kPcgThreads - 1) / kPcgThreads;
-        const int xx = (int)(u % sx) * kPcgThreads + threadIdx.x;
-        const int y0 = (int)(u / sx) * kStripRows;
-        if (xx >= s.nx) return;
-        const int y1 = min(y0 + kStripRows, s.ny);
-        for (int y = y0; y < y1; ++y) f((int64_t)y * s.nx + xx);
+    __device__ __forceinline__ void each_cell(F f) const {
+        each_segment([&](int x0, int y0, int y1) {
+            const int xx = x0 + threadIdx.x;
+            if (xx >= s.nx) return;
+#pragma unroll 4
+            for (int y = y0; y < y1; ++y) f((int64_t)y * s.nx + xx);
+        });
     }
     static constexpr int kSmem = 2 * (kPcgThreads + 2);
     __device__ void resolve() {}
@@ -160,9 +181,14 @@ struct Op3D {
         const int64_t sxy = (int64_t)s.nx * s.ny;
         for (int z = z0; z < z1; ++z) f(xx + (int64_t)s.nx * yy + sxy * z);
     }
-    __device__ void setup(int64_t u, const Bufs &B, double &bb, double &rz, double &rr) const {
+    template <class F>
+    __device__ __forceinline__ void each_cell(F f) const {
+        const int64_t nu = units();
+        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) for_cells(u, f);
+    }
+    __device__ void setup_block(const Bufs &B, double &bb, double &rz, double &rr) const {
         const int64_t sxy = (int64_t)s.nx * s.ny;
-        for_cells(u, [&](int64_t i) {
+        each_cell([&](int64_t i) {
             const int xx = (int)(i % s.nx), yy = (int)((i / s.nx) % s.ny), zz = (int)(i / sxy);
             double ax = s.D[i] * ldcg(B.x + i);
             if (zz > 0) ax = fma(-s.Tz[i - sxy], ldcg(B.x + i - sxy), ax);
@@ -182,7 +208,7 @@ struct Op3D {
         });
     }
     // p of plane z (tile + 1-cell xy halo) into a (kTileY+2) x (kTileX+2) buffer
-    __device__ void build_plane(const Bufs &B, int pin, bool first, double beta, int x0, int y0, int z,
+    __device__ void build_plane(const Bufs &B, const double *pold, bool first, double beta, int x0, int y0, int z,
                                 double *pl) const {
         const int64_t sxy = (int64_t)s.nx * s.ny;
         constexpr int ex = kTileX + 2, ey = kTileY + 2;
@@ -192,12 +218,18 @@ struct Op3D {
             if (z >= 0 && z < s.nz && gx >= 0 && gx < s.nx && gy >= 0 && gy < s.ny) {
                 const int64_t i = gx + (int64_t)s.nx * gy + sxy * z;
                 const double zi = ldcg(B.z + i);
-                v = first ? zi : fma(beta, ldcg(B.p[pin] + i), zi);
+                v = first ? zi : fma(beta, ldcg(pold + i), zi);
             }
             pl[k] = v;
         }
     }
-    __device__ void phaseA(int64_t u, const Bufs &B, int pin, bool first, double beta, double &pq, double *sm) const {
+    __device__ void phaseA_block(const Bufs &B, const double *pold, double *pout, bool first, double beta,
+                                 double &pq, double *sm) const {
+        const int64_t nu = units();
+        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) phaseA_unit(u, B, pold, pout, first, beta, pq, sm);
+    }
+    __device__ void phaseA_unit(int64_t u, const Bufs &B, const double *pold, double *pout, bool first, double beta,
+                                double &pq, double *sm) const {
         constexpr int ex = kTileX + 2, ey = kTileY + 2, pls = ex * ey;
         int x0, y0, z0;
         origin(u, x0, y0, z0);
@@ -206,13 +238,12 @@ struct Op3D {
         const bool act = xx < s.nx && yy < s.ny;
         const int z1 = min(z0 + kTileZ, s.nz);
         const int64_t sxy = (int64_t)s.nx * s.ny;
-        double *pout = B.p[pin ^ 1];
         // planes z0-1 and z0 first
-        build_plane(B, pin, first, beta, x0, y0, z0 - 1, sm + ((z0 + 3) & 3) * pls);
-        build_plane(B, pin, first, beta, x0, y0, z0, sm + (z0 & 3) * pls);
+        build_plane(B, pold, first, beta, x0, y0, z0 - 1, sm + ((z0 + 3) & 3) * pls);
+        build_plane(B, pold, first, beta, x0, y0, z0, sm + (z0 & 3) * pls);
         const int c = (ly + 1) * ex + (lx + 1);
         for (int z = z0; z < z1; ++z) {
-            build_plane(B, pin, first, beta, x0, y0, z + 1, sm + ((z + 1) & 3) * pls);
+            build_plane(B, pold, first, beta, x0, y0, z + 1, sm + ((z + 1) & 3) * pls);
             __syncthreads();
             if (act) {
                 const double *pc = sm + (z & 3) * pls;
@@ -244,12 +275,12 @@ struct OpCsr {
     __device__ void resolve() { if (c.n_dev) n = *c.n_dev; }
     __device__ int64_t units() const { return (n + kPcgThreads - 1) / kPcgThreads; }
     template <class F>
-    __device__ void for_cells(int64_t u, F f) const {
-        const int64_t i = u * kPcgThreads + threadIdx.x;
-        if (i < n) f(i);
+    __device__ __forceinline__ void each_cell(F f) const {
+        for (int64_t i = blockIdx.x * (int64_t)kPcgThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kPcgThreads)
+            f(i);
     }
-    __device__ void setup(int64_t u, const Bufs &B, double &bb, double &rz, double &rr) const {
-        for_cells(u, [&](int64_t i) {
+    __device__ void setup_block(const Bufs &B, double &bb, double &rz, double &rr) const {
+        each_cell([&](int64_t i) {
             double ax = 0.0;
             const int32_t e1 = c.rp[i + 1];
             for (int32_t e = c.rp[i]; e < e1; ++e) ax = fma(c.av[e], ldcg(B.x + c.ci[e]), ax);
@@ -263,15 +294,15 @@ struct OpCsr {
             rr = fma(ri, ri, rr);
         });
     }
-    __device__ void phaseA(int64_t u, const Bufs &B, int pin, bool first, double beta, double &pq, double *) const {
-        double *pout = B.p[pin ^ 1];
-        for_cells(u, [&](int64_t i) {
+    __device__ void phaseA_block(const Bufs &B, const double *pold, double *pout, bool first, double beta,
+                                 double &pq, double *) const {
+        each_cell([&](int64_t i) {
             double qi = 0.0, pi = 0.0;
             const int32_t e1 = c.rp[i + 1];
             for (int32_t e = c.rp[i]; e < e1; ++e) {
                 const int32_t j = c.ci[e];
                 const double zj = ldcg(B.z + j);
-                const double pj = first ? zj : fma(beta, ldcg(B.p[pin] + j), zj);
+                const double pj = first ? zj : fma(beta, ldcg(pold + j), zj);
                 if (j == i) pi = pj;
                 qi = fma(c.av[e], pj, qi);
             }
@@ -304,8 +335,7 @@ template <class OP>
 __device__ bool setup_phase(const OP &op, const Bufs &B, double *red, double &bb, double &rz, double &rr,
                             Ctrl *ctrl) {
     double acc[3] = {0.0, 0.0, 0.0};
-    const int64_t nu = op.units();
-    for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) op.setup(u, B, acc[0], acc[1], acc[2]);
+    op.setup_block(B, acc[0], acc[1], acc[2]);
     block_sum<3>(acc, red);
     if (threadIdx.x == 0) {
         B.part[0 * kMaxGrid + blockIdx.x] = acc[0];
@@ -325,7 +355,6 @@ __global__ void __launch_bounds__(kPcgThreads) pcg_kernel(OP op, Bufs B, double 
     __shared__ double red[128];
     __shared__ double sm[OP::kSmem];
     op.resolve();
-    const int64_t nu = op.units();
     double bb, rz, rr;
     if (!setup_phase(op, B, red, bb, rz, rr, ctrl)) return;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -337,7 +366,7 @@ __global__ void __launch_bounds__(kPcgThreads) pcg_kernel(OP op, Bufs B, double 
         ctrl->restarts = 0;
     }
     if (bb == 0.0) {   // A x = 0: x = 0
-        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) op.for_cells(u, [&](int64_t i) { B.x[i] = 0.0; });
+        op.each_cell([&](int64_t i) { B.x[i] = 0.0; });
         if (lead) { ctrl->converged = 1; ctrl->early = 1; ctrl->relres = 0.0; }
         return;
     }
@@ -352,7 +381,9 @@ __global__ void __launch_bounds__(kPcgThreads) pcg_kernel(OP op, Bufs B, double 
     while (true) {
         // ---- phase A
         double pq = 0.0;
-        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) op.phaseA(u, B, pin, first, beta, pq, sm);
+        const double *pold = pin ? B.p1 : B.p0;
+        double *pout = pin ? B.p0 : B.p1;
+        op.phaseA_block(B, pold, pout, first, beta, pq, sm);
         {
             double a1[1] = {pq};
             block_sum<1>(a1, red);
@@ -363,20 +394,19 @@ __global__ void __launch_bounds__(kPcgThreads) pcg_kernel(OP op, Bufs B, double 
         if (!(pq > 0.0) || !isfinite(pq)) { result = -1; break; }
         const double alpha = rz / pq;
         pin ^= 1;
-        const double *p = B.p[pin];
+        const double *p = pout;
         // ---- phase B
         double acc[2] = {0.0, 0.0};
-        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x)
-            op.for_cells(u, [&](int64_t i) {
-                const double pi = p[i], qi = B.q[i];
-                B.x[i] = fma(alpha, pi, B.x[i]);
-                const double ri = fma(-alpha, qi, B.r[i]);
-                const double zi = B.dinv[i] * ri;
-                B.r[i] = ri;
-                B.z[i] = zi;
-                acc[0] = fma(ri, zi, acc[0]);
-                acc[1] = fma(ri, ri, acc[1]);
-            });
+        op.each_cell([&](int64_t i) {
+            const double pi = p[i], qi = B.q[i];
+            B.x[i] = fma(alpha, pi, B.x[i]);
+            const double ri = fma(-alpha, qi, B.r[i]);
+            const double zi = B.dinv[i] * ri;
+            B.r[i] = ri;
+            B.z[i] = zi;
+            acc[0] = fma(ri, zi, acc[0]);
+            acc[1] = fma(ri, ri, acc[1]);
+        });
         block_sum<2>(acc, red);
         if (threadIdx.x == 0) {
             B.part[4 * kMaxGrid + blockIdx.x] = acc[0];
@@ -503,12 +533,14 @@ cudaError_t launch_coop(const OP &op, int64_t units, const Bufs &B, double tol, 
     const void *k = (const void *)pcg_kernel<OP>;
     const int grid = pcg_grid<OP>(k, units, cap);
     reset_ctrl_kernel<<<1, 1, 0, s>>>(ctrl);
+    note_launches(1);
     OP o = op;
     Bufs b = B;
     double t = tol;
     int mi = maxit, mr = max_restarts;
     Ctrl *c = ctrl;
     void *args[] = {&o, &b, &t, &mi, &mr, &c};
+    note_launches(1);
     return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kPcgThreads), args, 0, s);
 }
 
@@ -517,7 +549,7 @@ cudaError_t launch_coop(const OP &op, int64_t units, const Bufs &B, double tol, 
 cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                cudaStream_t s) {
     Bufs B;
-    B.b = a.b; B.x = a.x; B.r = w.r; B.z = w.z; B.q = w.q; B.p[0] = w.p0; B.p[1] = w.p1;
+    B.b = a.b; B.x = a.x; B.r = w.r; B.z = w.z; B.q = w.q; B.p0 = w.p0; B.p1 = w.p1;
     B.dinv = op.dinv; B.part = w.partials;
     if (op.dim == 3) {
         Op3D o{op};
@@ -526,7 +558,8 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
         return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, s);
     }
     Op2D o{op};
-    const int64_t units = (int64_t)((op.nx + kPcgThreads - 1) / kPcgThreads) * ((op.ny + kStripRows - 1) / kStripRows);
+    // at least 4 rows per block so the row halo stays a small overhead
+    const int64_t units = ((int64_t)((op.nx + kPcgThreads - 1) / kPcgThreads) * op.ny + 3) / 4;
     return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, s);
 }
 
@@ -534,8 +567,9 @@ cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ct
     // the row count may live on the device (extracted subsystem): the kernel
     // is sized for the capacity op.n and reads the actual count itself
     csr_dinv_kernel<<<152 * 4, 256, 0, s>>>(op, w.dinv);
+    note_launches(1);
     Bufs B;
-    B.b = a.b; B.x = a.x; B.r = w.r; B.z = w.z; B.q = w.q; B.p[0] = w.p0; B.p[1] = w.p1;
+    B.b = a.b; B.x = a.x; B.r = w.r; B.z = w.z; B.q = w.q; B.p0 = w.p0; B.p1 = w.p1;
     B.dinv = w.dinv; B.part = w.partials;
     OpCsr o{op, op.n};
     const int64_t units = (op.n + kPcgThreads - 1) / kPcgThreads;
@@ -546,17 +580,20 @@ cudaError_t launch_dinv_stencil(int64_t n, const double *D, double *dinv, float 
                                 const double *Ty, const double *Tz, float *Tx32, float *Ty32, float *Tz32,
                                 float *dinv32, cudaStream_t s) {
     dinv_stencil_kernel<<<152 * 8, 256, 0, s>>>(n, D, dinv, D32, Tx, Ty, Tz, Tx32, Ty32, Tz32, dinv32);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_check_stencil(const Stencil &op, int *bad, cudaStream_t s) {
     check_stencil_kernel<<<152 * 8, 256, 0, s>>>(op, bad);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_check_csr(int32_t n, const int32_t *rp, const int32_t *ci, const double *av, int *bad,
                              cudaStream_t s) {
     check_csr_kernel<<<152 * 8, 256, 0, s>>>(n, rp, ci, av, bad);
+    note_launches(1);
     return cudaGetLastError();
 }
 
