@@ -218,6 +218,42 @@ LC_EXPORT int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double
 LC_EXPORT int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const double *b, double *x,
                                const lc_params *p, lc_stats *stats, void *stream);
 
+/* ---- marking without device allocation ------------------------------------
+ *
+ * For callers that cannot call cudaMalloc -- code that runs inside another
+ * framework's memory pool or under a fixed memory budget, or a service that
+ * must not allocate after start-up, and so cannot create an lc_op (whose
+ * workspaces are allocated at creation).  The paper has no counterpart: this
+ * is a deployment variant of lc_mark_residual.
+ *
+ * Same results, bit for bit, as lc_mark_residual on the stencil operator
+ * (D, Tx, Ty, Tz, shape as in lc_op_create_stencil), but it allocates no
+ * device memory: its scratch (control block, sum-of-squares tree partials,
+ * second mask buffer of multi-pass expansion) is one fixed array of about
+ * 4.3 MB compiled into the library, held by every device that loads the
+ * library until the process exits.  The caller passes every input and
+ * output: r0[N] is required (the residual is written there).
+ *   - N = nx*ny*nz must not exceed LC_NOALLOC_MAX_CELLS: larger grids return
+ *     LC_ERR_TOO_LARGE before any GPU work.
+ *   - Null pointers, bad shapes or parameters return LC_ERR_INVALID_ARG; a
+ *     failing CUDA call returns LC_ERR_CUDA.  There is no context, so no
+ *     message is recorded.
+ *   - The operator is not validated: interior face conductances must be > 0
+ *     (the dilation uses the grid adjacency).
+ *   - The first call on a device looks up the device address of the scratch
+ *     array (with that device current); make that first call before any
+ *     stream capture.
+ *   - All calls share the one array, which keeps the previous call's
+ *     contents; each call clears what must start at zero.  Calls that
+ *     overlap on the GPU (other streams, other host threads) race on it and
+ *     must be serialised by the caller. */
+#define LC_NOALLOC_MAX_CELLS 4194304
+LC_EXPORT int lc_mark_residual_stencil_noalloc(int32_t dim, const int32_t shape[3], const double *D,
+                                               const double *Tx, const double *Ty, const double *Tz,
+                                               const double *b, const double *x0, const lc_mark_params *p,
+                                               uint8_t *mask, double *r0, int32_t *K_dev, double *tau_dev,
+                                               void *stream);
+
 /* ---- diagnostics ---------------------------------------------------------- */
 
 LC_EXPORT const char *lc_error_string(int code);

@@ -282,3 +282,32 @@ def default_params(mark_mode=MARK_RESIDUAL, thr_mode=THR_REL_MAX, thr_param=1e-3
     g = SolveParams(tol, max_iter, precision, inner_tol, max_outer)
     l = SolveParams(tol if tol_local is None else tol_local, max_iter, precision, inner_tol, max_outer)
     return Params(mark_mode, MarkParams(thr_mode, thr_param, exp_mode, exp_rounds), alpha, grad_layers, g, l, 0)
+
+
+LC_NOALLOC_MAX_CELLS = 4194304
+
+
+def mark_residual_stencil_noalloc(shape, D, Tx, Ty, Tz, b, x0, params: MarkParams, mask, r0, K, tau=None,
+                                  stream=None) -> int:
+    """lc_mark_residual_stencil_noalloc: residual marking for callers that
+    cannot allocate device memory (no context, no operator).  Scratch lives in
+    a fixed device array inside the library, so grids are limited to
+    LC_NOALLOC_MAX_CELLS cells and calls must not overlap on the GPU.
+    Raises LcError on a non-zero return code."""
+    L = lib()
+    f = L.lc_mark_residual_stencil_noalloc
+    vp = C.c_void_p
+    f.argtypes = [C.c_int32, C.POINTER(C.c_int32), vp, vp, vp, vp, vp, vp, C.POINTER(MarkParams), vp, vp, vp, vp,
+                  vp]
+    nx, ny, nz = (tuple(shape) + (1,))[:3]
+    dim = 3 if Tz is not None else 2
+    sh = (C.c_int32 * 3)(nx, ny, nz)
+    rc = f(dim, sh, _ptr(D, torch.float64, "D"), _ptr(Tx, torch.float64, "Tx"), _ptr(Ty, torch.float64, "Ty"),
+           _ptr(Tz, torch.float64, "Tz"), _ptr(b, torch.float64, "b"), _ptr(x0, torch.float64, "x0"),
+           C.byref(params), _ptr(mask, torch.uint8, "mask"), _ptr(r0, torch.float64, "r0"),
+           _ptr(K, torch.int32, "K"), _ptr(tau, torch.float64, "tau"), _stream(stream))
+    if rc:
+        extra = f" (grid of {nx * ny * nz} cells exceeds LC_NOALLOC_MAX_CELLS = {LC_NOALLOC_MAX_CELLS})" \
+            if rc == LC_ERR_TOO_LARGE else ""
+        raise LcError(rc, L.lc_error_string(rc).decode() + extra)
+    return rc
