@@ -218,6 +218,19 @@ LC_EXPORT int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double
 LC_EXPORT int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const double *b, double *x,
                                const lc_params *p, lc_stats *stats, void *stream);
 
+/* ---- kernel tuning ----------------------------------------------------------
+ *
+ * Launch-shape knobs of an operator's kernels, for the autotuner; not part
+ * of the method (the paper has no counterpart).  Results do not depend on
+ * them beyond the rounding order of the Krylov solve's reductions.
+ *   "pcg_minblocks" 1..4 (default 3): register budget of the structured-grid
+ *       PCG kernel, as the number of 256-thread blocks that must fit on an SM.
+ *   "pcg_grid_cap"  0..4096 (default 0 = all that fit): blocks of the global
+ *       PCG launch.
+ * Unknown keys or out-of-range values return LC_ERR_INVALID_ARG. */
+LC_EXPORT int lc_op_set_tuning(lc_op *op, const char *key, int32_t value);
+LC_EXPORT int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value);
+
 /* ---- marking without device allocation ------------------------------------
  *
  * For callers that cannot call cudaMalloc -- code that runs inside another

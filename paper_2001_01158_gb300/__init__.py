@@ -107,6 +107,8 @@ def lib():
     L.lc_last_error.restype = C.c_char_p
     L.lc_kernel_launch_count.argtypes = []
     L.lc_kernel_launch_count.restype = C.c_int64
+    L.lc_op_set_tuning.argtypes = [vp, C.c_char_p, i32]
+    L.lc_op_get_tuning.argtypes = [vp, C.c_char_p, C.POINTER(i32)]
     _lib = L
     return L
 
@@ -154,6 +156,15 @@ class Context:
 class _Operator:
     n: int
     nnz: int
+
+    def set_tuning(self, key: str, value: int):
+        """lc_op_set_tuning (launch-shape knobs for the autotuner)."""
+        return self.ctx.check(lib().lc_op_set_tuning(self.h, key.encode(), int(value)))
+
+    def get_tuning(self, key: str) -> int:
+        v = C.c_int32()
+        self.ctx.check(lib().lc_op_get_tuning(self.h, key.encode(), C.byref(v)))
+        return v.value
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

@@ -45,6 +45,9 @@ struct lc_op {
     lc_subsys sub{};                 // internal subsystem buffers
     lc::PcgWork pw{};
     cudaEvent_t ev[6] = {};
+    // tuning knobs (lc_op_set_tuning)
+    int pcg_minblocks = 3;   // register budget of the structured-grid PCG kernel
+    int pcg_grid_cap = 0;    // blocks of the global PCG launch (0: as many as fit)
 };
 
 namespace {
@@ -284,15 +287,15 @@ int check_solve_params(lc_ctx *ctx, const lc_solve_params *p) {
 
 int pcg_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_solve_params *p, lc::Ctrl *ctrl,
              bool local, cudaStream_t s) {
-    lc::PcgArgs a{b, x, p->tol, p->max_iter, 3};
+    lc::PcgArgs a{b, x, p->tol, p->max_iter, 3, op->pcg_minblocks};
     lc::PcgWork w = op->pw;
     LC_CUDA(ctx, cudaMemsetAsync(&ctrl->status, 0, sizeof(int32_t), s));
     if (local) {
         LC_CUDA(ctx, lc::launch_pcg_csr(sub_csr(op), a, w, ctrl, ctx->sms * 2, s));
     } else if (op->kind == 0) {
-        LC_CUDA(ctx, lc::launch_pcg_stencil(op->st, a, w, ctrl, 0, s));
+        LC_CUDA(ctx, lc::launch_pcg_stencil(op->st, a, w, ctrl, op->pcg_grid_cap, s));
     } else {
-        LC_CUDA(ctx, lc::launch_pcg_csr(op->csr, a, w, ctrl, 0, s));
+        LC_CUDA(ctx, lc::launch_pcg_csr(op->csr, a, w, ctrl, op->pcg_grid_cap, s));
     }
     return LC_OK;
 }
@@ -331,6 +334,28 @@ const char *lc_error_string(int code) {
 const char *lc_last_error(const lc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int64_t lc_kernel_launch_count(void) { return (int64_t)lc::g_launches.load(std::memory_order_relaxed); }
+
+int lc_op_set_tuning(lc_op *op, const char *key, int32_t value) {
+    if (!op || !key) return LC_ERR_INVALID_ARG;
+    if (!strcmp(key, "pcg_minblocks")) {
+        if (value < 1 || value > 4) return fail(op->ctx, LC_ERR_INVALID_ARG, "pcg_minblocks must be 1..4");
+        op->pcg_minblocks = value;
+        return LC_OK;
+    }
+    if (!strcmp(key, "pcg_grid_cap")) {
+        if (value < 0 || value > lc::kMaxGrid) return fail(op->ctx, LC_ERR_INVALID_ARG, "pcg_grid_cap out of range");
+        op->pcg_grid_cap = value;
+        return LC_OK;
+    }
+    return fail(op->ctx, LC_ERR_INVALID_ARG, "unknown tuning key '%s'", key);
+}
+
+int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value) {
+    if (!op || !key || !value) return LC_ERR_INVALID_ARG;
+    if (!strcmp(key, "pcg_minblocks")) { *value = op->pcg_minblocks; return LC_OK; }
+    if (!strcmp(key, "pcg_grid_cap")) { *value = op->pcg_grid_cap; return LC_OK; }
+    return LC_ERR_INVALID_ARG;
+}
 
 int lc_ctx_create(lc_ctx **out, int device) {
     if (!out) return LC_ERR_INVALID_ARG;

@@ -265,6 +265,7 @@ struct PcgArgs {
     double tol;
     int32_t maxit;
     int32_t max_restarts;
+    int32_t minblocks;    // register budget of the structured-grid kernel (tuning)
 };
 cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                cudaStream_t s);

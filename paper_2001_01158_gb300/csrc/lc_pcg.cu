@@ -158,6 +158,175 @@ struct Op2D {
     __device__ void resolve() {}
 };
 
+// 2D, warp-independent: the grid is cut into column strips of 32*CPL cells,
+// one lane owning CPL adjacent columns (CPL = 2 when nx is even, so that
+// rows start 16-byte aligned and loads/stores are double2).  The strip-major
+// list of (strip, row) items is split evenly over all warps of the grid and
+// every warp marches down its own rows: p of the rows above and below in
+// registers, x-neighbours through warp shuffles, the one-cell halo at either
+// end of the strip recomputed by lanes 0 and 31.  No block barrier, no shared
+// memory.
+template <int CPL>
+struct Op2DW {
+    Stencil s;
+    static constexpr int kSW = 32 * CPL;
+    __device__ __forceinline__ int strips() const { return (s.nx + kSW - 1) / kSW; }
+    template <class F>
+    __device__ __forceinline__ void each_segment(F f) const {
+        const int wpb = blockDim.x >> 5;
+        const int64_t gw = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5);
+        const int64_t nw = (int64_t)gridDim.x * wpb;
+        const int64_t items = (int64_t)strips() * s.ny;
+        const int64_t lo = items * gw / nw, hi = items * (gw + 1) / nw;
+        if (lo >= hi) return;
+        const int st0 = (int)(lo / s.ny), st1 = (int)((hi - 1) / s.ny);
+        for (int st = st0; st <= st1; ++st) {
+            const int y0 = st == st0 ? (int)(lo % s.ny) : 0;
+            const int y1 = st == st1 ? (int)((hi - 1) % s.ny) + 1 : s.ny;
+            f(st * kSW, y0, y1);
+        }
+    }
+    __device__ __forceinline__ double pnew1(const Bufs &B, const double *pold, bool first, double beta,
+                                            int64_t i) const {
+        const double zi = ldcg(B.z + i);
+        return first ? zi : fma(beta, ldcg(pold + i), zi);
+    }
+    // p of the lane's CPL cells starting at i (i even when CPL == 2)
+    __device__ __forceinline__ void pnew(const Bufs &B, const double *pold, bool first, double beta, int64_t i,
+                                        double (&p)[CPL]) const {
+        if (CPL == 2) {
+            const double2 z2 = ldcg(reinterpret_cast<const double2 *>(B.z + i));
+            if (first) { p[0] = z2.x; p[CPL - 1] = z2.y; }
+            else {
+                const double2 o2 = ldcg(reinterpret_cast<const double2 *>(pold + i));
+                p[0] = fma(beta, o2.x, z2.x);
+                p[CPL - 1] = fma(beta, o2.y, z2.y);
+            }
+        } else {
+            p[0] = pnew1(B, pold, first, beta, i);
+        }
+    }
+    __device__ __forceinline__ void load2(const double *a, int64_t i, double (&v)[CPL]) const {
+        if (CPL == 2) {
+            const double2 t = *reinterpret_cast<const double2 *>(a + i);
+            v[0] = t.x; v[CPL - 1] = t.y;
+        } else {
+            v[0] = a[i];
+        }
+    }
+    __device__ void setup_block(const Bufs &B, double &bb, double &rz, double &rr) const {
+        const int lane = threadIdx.x & 31;
+        each_segment([&](int x0, int y0, int y1) {
+            for (int y = y0; y < y1; ++y) {
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) {
+                    const int xx = x0 + CPL * lane + k;
+                    if (xx >= s.nx) continue;
+                    const int64_t i = (int64_t)y * s.nx + xx;
+                    double ax = s.D[i] * ldcg(B.x + i);
+                    if (y > 0) ax = fma(-s.Ty[i - s.nx], ldcg(B.x + i - s.nx), ax);
+                    if (xx > 0) ax = fma(-s.Tx[i - 1], ldcg(B.x + i - 1), ax);
+                    if (xx + 1 < s.nx) ax = fma(-s.Tx[i], ldcg(B.x + i + 1), ax);
+                    if (y + 1 < s.ny) ax = fma(-s.Ty[i], ldcg(B.x + i + s.nx), ax);
+                    const double bi = B.b[i];
+                    const double ri = bi - ax;
+                    const double zi = s.dinv[i] * ri;
+                    B.r[i] = ri;
+                    B.z[i] = zi;
+                    bb = fma(bi, bi, bb);
+                    rz = fma(ri, zi, rz);
+                    rr = fma(ri, ri, rr);
+                }
+            }
+        });
+    }
+    __device__ void phaseA_block(const Bufs &B, const double *pold, double *pout, bool first, double beta,
+                                 double &pq, double *) const {
+        const int lane = threadIdx.x & 31;
+        each_segment([&](int x0, int y0, int y1) {
+            const int xa = x0 + CPL * lane;          // first column of this lane
+            const bool act = xa < s.nx;               // CPL == 2: nx even, so xa+1 < nx too
+            // halo column of the strip handled by lane 0 (west) / lane 31 (east)
+            const int hx = lane == 0 ? x0 - 1 : x0 + kSW;
+            const bool hact = (lane == 0 && x0 > 0) || (lane == 31 && x0 + kSW < s.nx);
+            double pm[CPL], pc[CPL], pn[CPL], tym[CPL];
+#pragma unroll
+            for (int k = 0; k < CPL; ++k) { pm[k] = 0.0; pc[k] = 0.0; tym[k] = 0.0; }
+            if (act) {
+                const int64_t i0 = (int64_t)y0 * s.nx + xa;
+                pnew(B, pold, first, beta, i0, pc);
+                if (y0 > 0) {
+                    pnew(B, pold, first, beta, i0 - s.nx, pm);
+                    load2(s.Ty, i0 - s.nx, tym);
+                }
+            }
+            for (int y = y0; y < y1; ++y) {
+                const int64_t i = (int64_t)y * s.nx + xa;
+                double d[CPL], tx[CPL], typ[CPL];
+                double txw0 = 0.0, ph = 0.0;
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) { pn[k] = 0.0; d[k] = 0.0; tx[k] = 0.0; typ[k] = 0.0; }
+                if (act) {
+                    if (y + 1 < s.ny) { pnew(B, pold, first, beta, i + s.nx, pn); load2(s.Ty, i, typ); }
+                    load2(s.D, i, d);
+                    load2(s.Tx, i, tx);
+                    if (lane == 0 && x0 > 0) txw0 = s.Tx[i - 1];
+                }
+                if (hact) ph = pnew1(B, pold, first, beta, (int64_t)y * s.nx + hx);
+                // face conductances to the west / east of each cell
+                const double tx_last_up = __shfl_up_sync(kFull, tx[CPL - 1], 1);
+                const double pc_last_up = __shfl_up_sync(kFull, pc[CPL - 1], 1);
+                const double pc_first_dn = __shfl_down_sync(kFull, pc[0], 1);
+                if (!act) continue;
+                double txw[CPL], txe[CPL], pw[CPL], pe[CPL];
+                txw[0] = lane == 0 ? txw0 : tx_last_up;
+                pw[0] = lane == 0 ? ph : pc_last_up;
+#pragma unroll
+                for (int k = 1; k < CPL; ++k) { txw[k] = tx[k - 1]; pw[k] = pc[k - 1]; }
+#pragma unroll
+                for (int k = 0; k < CPL - 1; ++k) { txe[k] = tx[k]; pe[k] = pc[k + 1]; }
+                const bool last_col = xa + CPL >= s.nx;   // the lane's last cell is the grid's last column
+                txe[CPL - 1] = last_col ? 0.0 : tx[CPL - 1];
+                pe[CPL - 1] = lane == 31 ? ph : pc_first_dn;
+                double q[CPL];
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) {
+                    double qi = d[k] * pc[k];
+                    qi = fma(-tym[k], pm[k], qi);
+                    qi = fma(-txw[k], pw[k], qi);
+                    qi = fma(-txe[k], pe[k], qi);
+                    qi = fma(-typ[k], pn[k], qi);
+                    q[k] = qi;
+                    pq = fma(pc[k], qi, pq);
+                }
+                if (CPL == 2) {
+                    *reinterpret_cast<double2 *>(pout + i) = make_double2(pc[0], pc[CPL - 1]);
+                    *reinterpret_cast<double2 *>(B.q + i) = make_double2(q[0], q[CPL - 1]);
+                } else {
+                    pout[i] = pc[0];
+                    B.q[i] = q[0];
+                }
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) { tym[k] = typ[k]; pm[k] = pc[k]; pc[k] = pn[k]; }
+            }
+        });
+    }
+    template <class F>
+    __device__ __forceinline__ void each_cell(F f) const {
+        const int lane = threadIdx.x & 31;
+        each_segment([&](int x0, int y0, int y1) {
+            const int xa = x0 + CPL * lane;
+            if (xa >= s.nx) return;
+#pragma unroll 2
+            for (int y = y0; y < y1; ++y)
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) f((int64_t)y * s.nx + xa + k);
+        });
+    }
+    static constexpr int kSmem = 1;
+    __device__ void resolve() {}
+};
+
 struct Op3D {
     Stencil s;
     __device__ int64_t units() const {
@@ -349,8 +518,8 @@ __device__ bool setup_phase(const OP &op, const Bufs &B, double *red, double &bb
     return true;
 }
 
-template <class OP>
-__global__ void __launch_bounds__(kPcgThreads) pcg_kernel(OP op, Bufs B, double tol, int maxit, int max_restarts,
+template <class OP, int MINB>
+__global__ void __launch_bounds__(kPcgThreads, MINB) pcg_kernel(OP op, Bufs B, double tol, int maxit, int max_restarts,
                                                           Ctrl *ctrl) {
     __shared__ double red[128];
     __shared__ double sm[OP::kSmem];
@@ -527,10 +696,23 @@ int pcg_grid(const void *kernel, int64_t units, int cap) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// minblocks = the register budget asked of the compiler (blocks of 256
+// threads that must fit on one SM): 1 = unconstrained, 2..4 = at most
+// 128 / 85 / 64 registers per thread.
+template <class OP>
+const void *pcg_kernel_for(int minblocks) {
+    switch (minblocks) {
+        case 2: return (const void *)pcg_kernel<OP, 2>;
+        case 3: return (const void *)pcg_kernel<OP, 3>;
+        case 4: return (const void *)pcg_kernel<OP, 4>;
+        default: return (const void *)pcg_kernel<OP, 1>;
+    }
+}
+
 template <class OP>
 cudaError_t launch_coop(const OP &op, int64_t units, const Bufs &B, double tol, int maxit, int max_restarts,
-                        Ctrl *ctrl, int cap, cudaStream_t s) {
-    const void *k = (const void *)pcg_kernel<OP>;
+                        Ctrl *ctrl, int cap, int minblocks, cudaStream_t s) {
+    const void *k = pcg_kernel_for<OP>(minblocks);
     const int grid = pcg_grid<OP>(k, units, cap);
     reset_ctrl_kernel<<<1, 1, 0, s>>>(ctrl);
     note_launches(1);
@@ -555,12 +737,21 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
         Op3D o{op};
         const int64_t units = (int64_t)((op.nx + kTileX - 1) / kTileX) * ((op.ny + kTileY - 1) / kTileY) *
                               ((op.nz + kTileZ - 1) / kTileZ);
-        return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, s);
+        return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, 1, s);
     }
-    Op2D o{op};
-    // at least 4 rows per block so the row halo stays a small overhead
-    const int64_t units = ((int64_t)((op.nx + kPcgThreads - 1) / kPcgThreads) * op.ny + 3) / 4;
-    return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, s);
+    // two cells per lane (16-byte vectors) when every row starts 16-byte aligned
+    auto al16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    const bool vec = op.nx % 2 == 0 && al16(op.D) && al16(op.Tx) && al16(op.Ty);
+    const int warps_per_block = kPcgThreads / 32;
+    if (vec) {
+        Op2DW<2> o{op};
+        // at least 4 rows per warp so the recomputed halo rows stay a small overhead
+        const int64_t units = ((int64_t)((op.nx + 63) / 64) * op.ny + 4 * warps_per_block - 1) / (4 * warps_per_block);
+        return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, a.minblocks, s);
+    }
+    Op2DW<1> o{op};
+    const int64_t units = ((int64_t)((op.nx + 31) / 32) * op.ny + 4 * warps_per_block - 1) / (4 * warps_per_block);
+    return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, a.minblocks, s);
 }
 
 cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint, cudaStream_t s) {
@@ -573,7 +764,7 @@ cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ct
     B.dinv = w.dinv; B.part = w.partials;
     OpCsr o{op, op.n};
     const int64_t units = (op.n + kPcgThreads - 1) / kPcgThreads;
-    return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, s);
+    return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, 1, s);
 }
 
 cudaError_t launch_dinv_stencil(int64_t n, const double *D, double *dinv, float *D32, const double *Tx,
