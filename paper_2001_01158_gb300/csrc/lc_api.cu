@@ -118,6 +118,14 @@ void carve(lc_op *op, Carver &c) {
     op->pw.q = c.take<double>(n);
     op->pw.dinv = c.take<double>(n);
     op->pw.partials = c.take<double>((size_t)lc::kMaxGrid * 8);
+    op->pw.r32 = c.take<float>(n);
+    op->pw.z32 = c.take<float>(n);
+    op->pw.p032 = c.take<float>(n);
+    op->pw.p132 = c.take<float>(n);
+    op->pw.q32 = c.take<float>(n);
+    op->pw.x32 = c.take<float>(n);
+    op->pw.dinv32 = c.take<float>(n);
+    op->pw.val32 = c.take<float>(nnz);
     if (op->kind == 0) {
         op->dinv = c.take<double>(n);
         op->D32 = c.take<float>(n);
@@ -280,14 +288,19 @@ int check_solve_params(lc_ctx *ctx, const lc_solve_params *p) {
     if (!p) return fail(ctx, LC_ERR_INVALID_ARG, "null solve parameters");
     if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) return fail(ctx, LC_ERR_INVALID_ARG, "tol must be finite and >= 0");
     if (p->max_iter < 0) return fail(ctx, LC_ERR_INVALID_ARG, "max_iter < 0");
-    if (p->precision != LC_PREC_FP64)
-        return fail(ctx, LC_ERR_UNSUPPORTED, "precision %d not provided by this build", p->precision);
+    if (p->precision == LC_PREC_MIXED) {
+        if (!(p->inner_tol > 0.0 && p->inner_tol < 1.0))
+            return fail(ctx, LC_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
+        if (p->max_outer < 1) return fail(ctx, LC_ERR_INVALID_ARG, "max_outer must be >= 1");
+    } else if (p->precision != LC_PREC_FP64) {
+        return fail(ctx, LC_ERR_INVALID_ARG, "unknown precision %d", p->precision);
+    }
     return LC_OK;
 }
 
 int pcg_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_solve_params *p, lc::Ctrl *ctrl,
              bool local, cudaStream_t s) {
-    lc::PcgArgs a{b, x, p->tol, p->max_iter, 3, op->pcg_minblocks};
+    lc::PcgArgs a{b, x, p->tol, p->max_iter, 3, op->pcg_minblocks, p->precision, p->inner_tol, p->max_outer};
     lc::PcgWork w = op->pw;
     LC_CUDA(ctx, cudaMemsetAsync(&ctrl->status, 0, sizeof(int32_t), s));
     if (local) {
@@ -400,6 +413,7 @@ int lc_op_create_stencil(lc_ctx *ctx, lc_op **out, int32_t dim, const int32_t sh
     op->n = n;
     op->nnz = nnz;
     op->st.dim = dim;
+    op->pcg_minblocks = dim == 3 ? 4 : 3;   // measured best register budgets (2D strips / 3D tiles)
     op->st.nx = (int)nx; op->st.ny = (int)ny; op->st.nz = (int)nz;
     op->st.n = n;
     op->st.D = D; op->st.Tx = Tx; op->st.Ty = Ty; op->st.Tz = dim == 3 ? Tz : nullptr;

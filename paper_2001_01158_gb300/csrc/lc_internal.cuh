@@ -206,6 +206,7 @@ __device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned int nblocks) {
 template <typename T>
 __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 
+
 // ---------------------------------------------------------------- host side
 
 struct Launch {
@@ -255,9 +256,9 @@ cudaError_t launch_assemble(const int32_t *K_dev, const int32_t *l2g, const doub
 struct PcgWork {
     double *r, *z, *p0, *p1, *q;     // capacity n
     double *dinv;                    // CSR: per-row 1/a_ii (capacity n)
-    double *partials;                // kMaxGrid * 4
-    float *r32, *z32, *p032, *p132, *q32, *x32, *b32, *dinv32;   // mixed precision (capacity n)
-    double *xd;                      // mixed: FP64 scratch (capacity n)
+    double *partials;                // kMaxGrid * 8
+    float *r32, *z32, *p032, *p132, *q32, *x32, *dinv32;   // mixed precision (capacity n)
+    float *val32;                    // mixed precision, CSR: FP32 values (capacity nnz)
 };
 struct PcgArgs {
     const double *b;
@@ -266,6 +267,9 @@ struct PcgArgs {
     int32_t maxit;
     int32_t max_restarts;
     int32_t minblocks;    // register budget of the structured-grid kernel (tuning)
+    int32_t precision;    // LC_PREC_FP64 | LC_PREC_MIXED
+    double inner_tol;     // mixed: reduction asked of each FP32 inner solve
+    int32_t max_outer;    // mixed: refinement sweeps
 };
 cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                cudaStream_t s);

@@ -1,9 +1,11 @@
 // lc_pcg.cu -- Jacobi-preconditioned conjugate gradients as ONE persistent
-// cooperative kernel per solve (the Krylov solver of Alg 1, steps 5 and 11).
+// cooperative kernel per solve (the Krylov solver of Alg 1, steps 5 and 11),
+// in FP64, and FP32 inner solves inside FP64 iterative refinement.
 //
-// Per iteration two grid-wide phases, each closed by a bounded grid barrier
-// and a deterministic fixed-slot reduction (every block sums the same block
-// partials in the same order, so every block takes the same decisions):
+// Per CG iteration two grid-wide phases, each closed by a bounded grid
+// barrier and a deterministic fixed-slot reduction (every block sums the
+// same block partials in the same order, so every block takes the same
+// decisions):
 //
 //   phase A  p = z + beta p_old          (computed where it is needed, halos
 //            q = A p, partial p.q          included, so no extra barrier)
@@ -12,18 +14,22 @@
 //            partials r.z and r.r
 //
 // z is stored so that phase A reads one vector where it would read r and
-// dinv; the stopping test ||r||^2 <= tol^2 ||b||^2 is taken on the recurrence
-// residual, confirmed with the true residual b - A x, and the iteration
-// restarts from the true residual when that misses (at most max_restarts).
-// The test on the starting iterate happens in the set-up phase: a converged
-// start (Alg 1 step 8, the local solution x~ already good enough) costs one
-// residual pass and no iteration.
+// dinv.  FP64 solve: the stopping test ||r||^2 <= tol^2 ||b||^2 is taken on
+// the recurrence residual, confirmed with the true residual b - A x, and the
+// iteration restarts from the true residual when that misses (at most
+// max_restarts).  The test on the starting iterate happens in the set-up
+// phase: a converged start (Alg 1 step 8, the local solution x~ already good
+// enough) costs one residual pass and no iteration.
 //
-// Data movement per cell and iteration (2D, FP64): phase A reads z, p_old,
-// D, Tx, Ty and writes p, q (56 B); phase B reads x, p, r, q, dinv and
-// writes x, r, z (64 B): 120 B.  Structured operators march a column strip
-// (2D) or an xy tile (3D) through the grid so that every p is computed once
-// plus a thin halo; CSR rows recompute the p of their columns.
+// Mixed precision (iterative refinement): r = b - A x in FP64; stop if
+// ||r|| <= tol ||b||; else solve fl32(A) d = fl32(r/||r||) by FP32 Jacobi-PCG
+// from d = 0 until its residual fell by inner_tol (vectors and per-thread
+// sums in FP32, only the cross-block sums in FP64); x += ||r|| d in FP64;
+// repeat.  All of it in one launch.
+//
+// Data movement per cell and CG iteration, 2D: phase A reads z, p_old, D,
+// Tx, Ty and writes p, q; phase B reads x, p, r, q, dinv and writes x, r, z:
+// 120 B in FP64, 60 B in FP32 (3D: 128 B / 64 B).
 #include "lc_internal.cuh"
 
 namespace lc {
@@ -31,145 +37,83 @@ namespace lc {
 namespace {
 
 constexpr int kPcgThreads = 256;
-constexpr int kStripRows = 16;     // 2D: rows per unit
 constexpr int kTileX = 32, kTileY = 8, kTileZ = 16;   // 3D unit
 
-struct Bufs {
-    const double *b;
-    double *x, *r, *z, *q;
-    double *p0, *p1;
-    const double *dinv;
-    double *part;          // [6][kMaxGrid]
+// N consecutive values of type T moved as one vector access (N = 1, 2, 4;
+// 4 only for float): 16-byte accesses for double2 / float4.
+template <typename T, int N> struct VecType { using type = T; };
+template <> struct VecType<double, 2> { using type = double2; };
+template <> struct VecType<float, 2> { using type = float2; };
+template <> struct VecType<float, 4> { using type = float4; };
+
+template <typename T, int N>
+union VecU {
+    typename VecType<T, N>::type v;
+    T e[N];
 };
+
+template <typename T, int N>
+__device__ __forceinline__ void vld(const T *a, T (&out)[N]) {
+    VecU<T, N> u;
+    u.v = *reinterpret_cast<const typename VecType<T, N>::type *>(a);
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] = u.e[k];
+}
+template <typename T, int N>
+__device__ __forceinline__ void vld_cg(const T *a, T (&out)[N]) {
+    VecU<T, N> u;
+    u.v = __ldcg(reinterpret_cast<const typename VecType<T, N>::type *>(a));
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] = u.e[k];
+}
+template <typename T, int N>
+__device__ __forceinline__ void vst(T *a, const T (&in)[N]) {
+    VecU<T, N> u;
+#pragma unroll
+    for (int k = 0; k < N; ++k) u.e[k] = in[k];
+    *reinterpret_cast<typename VecType<T, N>::type *>(a) = u.v;
+}
+
+template <typename T>
+struct Vecs {
+    const T *b;
+    T *x, *r, *z, *q, *p0, *p1;
+    const T *dinv;
+};
+
+template <typename T>
+struct Coef {
+    const T *D, *Tx, *Ty, *Tz;
+};
+
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 
 // -------------------------------------------------------------- operators
 //
 // Every operator provides, for the calling block:
-//   setup_block     r = b - A x, z = dinv r over its cells; sums b.b, r.z, r.r
+//   setup_block     r = b - A x (and z = dinv r if z is given) over its cells;
+//                   sums b.b, r.z, r.r
 //   phaseA_block    p = z + beta p_old, q = A p over its cells; sums p.q
-//   each_cell(f)    f(i) for its cells (phase B), in the same cell-to-thread
-//                   mapping as phase A, so the p and q a thread stored are
-//                   the ones it reads back.
-
-// 2D: the grid is cut into column strips of kPcgThreads cells (one thread
-// per column); the strip-major list of (strip, row) pairs is split evenly
-// into contiguous ranges, one per block, and a block marches down its rows.
-// p of the row above and below lives in registers, the two x-neighbours come
-// from a shared-memory row (double-buffered: one barrier per row).
-struct Op2D {
-    Stencil s;
-    __device__ __forceinline__ int strips() const { return (s.nx + kPcgThreads - 1) / kPcgThreads; }
-    template <class F>
-    __device__ __forceinline__ void each_segment(F f) const {
-        const int64_t rs = (int64_t)strips() * s.ny;
-        const int64_t lo = rs * blockIdx.x / gridDim.x, hi = rs * (blockIdx.x + 1) / gridDim.x;
-        if (lo >= hi) return;
-        const int st0 = (int)(lo / s.ny), st1 = (int)((hi - 1) / s.ny);
-        for (int st = st0; st <= st1; ++st) {
-            const int y0 = st == st0 ? (int)(lo % s.ny) : 0;
-            const int y1 = st == st1 ? (int)((hi - 1) % s.ny) + 1 : s.ny;
-            f(st * kPcgThreads, y0, y1);
-        }
-    }
-    __device__ void setup_block(const Bufs &B, double &bb, double &rz, double &rr) const {
-        each_segment([&](int x0, int y0, int y1) {
-            const int xx = x0 + threadIdx.x;
-            if (xx >= s.nx) return;
-            for (int y = y0; y < y1; ++y) {
-                const int64_t i = (int64_t)y * s.nx + xx;
-                double ax = s.D[i] * ldcg(B.x + i);
-                if (y > 0) ax = fma(-s.Ty[i - s.nx], ldcg(B.x + i - s.nx), ax);
-                if (xx > 0) ax = fma(-s.Tx[i - 1], ldcg(B.x + i - 1), ax);
-                if (xx + 1 < s.nx) ax = fma(-s.Tx[i], ldcg(B.x + i + 1), ax);
-                if (y + 1 < s.ny) ax = fma(-s.Ty[i], ldcg(B.x + i + s.nx), ax);
-                const double bi = B.b[i];
-                const double ri = bi - ax;
-                const double zi = s.dinv[i] * ri;
-                B.r[i] = ri;
-                B.z[i] = zi;
-                bb = fma(bi, bi, bb);
-                rz = fma(ri, zi, rz);
-                rr = fma(ri, ri, rr);
-            }
-        });
-    }
-    __device__ __forceinline__ double pnew(const Bufs &B, const double *pold, bool first, double beta,
-                                           int64_t i) const {
-        const double zi = ldcg(B.z + i);
-        return first ? zi : fma(beta, ldcg(pold + i), zi);
-    }
-    __device__ void phaseA_block(const Bufs &B, const double *pold, double *pout, bool first, double beta,
-                                 double &pq, double *srow) const {
-        each_segment([&](int x0, int y0, int y1) {
-            const int xx = x0 + threadIdx.x;
-            const bool act = xx < s.nx;
-            const bool hw = threadIdx.x == 0 && x0 > 0;
-            const bool he = threadIdx.x == kPcgThreads - 1 && x0 + kPcgThreads < s.nx;
-            double pm = 0.0, pc = 0.0, tym = 0.0;
-            if (act) {
-                const int64_t i0 = (int64_t)y0 * s.nx + xx;
-                pc = pnew(B, pold, first, beta, i0);
-                if (y0 > 0) { pm = pnew(B, pold, first, beta, i0 - s.nx); tym = s.Ty[i0 - s.nx]; }
-            }
-            for (int y = y0; y < y1; ++y) {
-                const int64_t i = (int64_t)y * s.nx + xx;
-                // every load of this row first, then one barrier
-                double pn = 0.0, d = 0.0, txw = 0.0, txe = 0.0, typ = 0.0, halo = 0.0;
-                if (act) {
-                    if (y + 1 < s.ny) { pn = pnew(B, pold, first, beta, i + s.nx); typ = s.Ty[i]; }
-                    d = s.D[i];
-                    if (xx > 0) txw = s.Tx[i - 1];
-                    if (xx + 1 < s.nx) txe = s.Tx[i];
-                }
-                if (hw) halo = pnew(B, pold, first, beta, (int64_t)y * s.nx + x0 - 1);
-                if (he) halo = pnew(B, pold, first, beta, (int64_t)y * s.nx + x0 + kPcgThreads);
-                double *buf = srow + (y & 1) * (kPcgThreads + 2);
-                buf[threadIdx.x + 1] = pc;
-                if (threadIdx.x == 0) buf[0] = halo;
-                if (threadIdx.x == kPcgThreads - 1) buf[kPcgThreads + 1] = halo;
-                __syncthreads();
-                if (act) {
-                    double qi = d * pc;
-                    qi = fma(-tym, pm, qi);
-                    qi = fma(-txw, buf[threadIdx.x], qi);
-                    qi = fma(-txe, buf[threadIdx.x + 2], qi);
-                    qi = fma(-typ, pn, qi);
-                    pout[i] = pc;
-                    B.q[i] = qi;
-                    pq = fma(pc, qi, pq);
-                }
-                tym = typ;
-                pm = pc;
-                pc = pn;
-            }
-            __syncthreads();
-        });
-    }
-    template <class F>
-    __device__ __forceinline__ void each_cell(F f) const {
-        each_segment([&](int x0, int y0, int y1) {
-            const int xx = x0 + threadIdx.x;
-            if (xx >= s.nx) return;
-#pragma unroll 4
-            for (int y = y0; y < y1; ++y) f((int64_t)y * s.nx + xx);
-        });
-    }
-    static constexpr int kSmem = 2 * (kPcgThreads + 2);
-    __device__ void resolve() {}
-};
+//   each_cell(f)    f(i) for its cells, in the same cell-to-thread mapping as
+//                   phase A, so the p and q a thread stored are the ones it
+//                   reads back.
 
 // 2D, warp-independent: the grid is cut into column strips of 32*CPL cells,
-// one lane owning CPL adjacent columns (CPL = 2 when nx is even, so that
-// rows start 16-byte aligned and loads/stores are double2).  The strip-major
-// list of (strip, row) items is split evenly over all warps of the grid and
-// every warp marches down its own rows: p of the rows above and below in
-// registers, x-neighbours through warp shuffles, the one-cell halo at either
-// end of the strip recomputed by lanes 0 and 31.  No block barrier, no shared
-// memory.
-template <int CPL>
+// one lane owning CPL adjacent columns (CPL = 2 when rows start aligned, so
+// loads/stores are pairs).  The strip-major list of (strip, row) items is
+// split evenly over all warps of the grid and every warp marches down its own
+// rows: p of the rows above and below in registers, x-neighbours through warp
+// shuffles, the one-cell halo at either end of the strip recomputed by lanes
+// 0 and 31.  No block barrier, no shared memory.
+template <typename T, int CPL>
 struct Op2DW {
     Stencil s;
+    Coef<T> c;
     static constexpr int kSW = 32 * CPL;
+    static constexpr int kSmem = 1;
+    static constexpr bool kTunable = true;    // register budget selectable (pcg_minblocks)
+    __device__ void resolve() {}
     __device__ __forceinline__ int strips() const { return (s.nx + kSW - 1) / kSW; }
     template <class F>
     __device__ __forceinline__ void each_segment(F f) const {
@@ -186,149 +130,129 @@ struct Op2DW {
             f(st * kSW, y0, y1);
         }
     }
-    __device__ __forceinline__ double pnew1(const Bufs &B, const double *pold, bool first, double beta,
-                                            int64_t i) const {
-        const double zi = ldcg(B.z + i);
-        return first ? zi : fma(beta, ldcg(pold + i), zi);
-    }
-    // p of the lane's CPL cells starting at i (i even when CPL == 2)
-    __device__ __forceinline__ void pnew(const Bufs &B, const double *pold, bool first, double beta, int64_t i,
-                                        double (&p)[CPL]) const {
-        if (CPL == 2) {
-            const double2 z2 = ldcg(reinterpret_cast<const double2 *>(B.z + i));
-            if (first) { p[0] = z2.x; p[CPL - 1] = z2.y; }
-            else {
-                const double2 o2 = ldcg(reinterpret_cast<const double2 *>(pold + i));
-                p[0] = fma(beta, o2.x, z2.x);
-                p[CPL - 1] = fma(beta, o2.y, z2.y);
-            }
-        } else {
-            p[0] = pnew1(B, pold, first, beta, i);
-        }
-    }
-    __device__ __forceinline__ void load2(const double *a, int64_t i, double (&v)[CPL]) const {
-        if (CPL == 2) {
-            const double2 t = *reinterpret_cast<const double2 *>(a + i);
-            v[0] = t.x; v[CPL - 1] = t.y;
-        } else {
-            v[0] = a[i];
-        }
-    }
-    __device__ void setup_block(const Bufs &B, double &bb, double &rz, double &rr) const {
+    template <class F>
+    __device__ __forceinline__ void each_cell(F f) const {
         const int lane = threadIdx.x & 31;
         each_segment([&](int x0, int y0, int y1) {
-            for (int y = y0; y < y1; ++y) {
+            const int xa = x0 + CPL * lane;
+#pragma unroll 2
+            for (int y = y0; y < y1; ++y)
 #pragma unroll
-                for (int k = 0; k < CPL; ++k) {
-                    const int xx = x0 + CPL * lane + k;
-                    if (xx >= s.nx) continue;
-                    const int64_t i = (int64_t)y * s.nx + xx;
-                    double ax = s.D[i] * ldcg(B.x + i);
-                    if (y > 0) ax = fma(-s.Ty[i - s.nx], ldcg(B.x + i - s.nx), ax);
-                    if (xx > 0) ax = fma(-s.Tx[i - 1], ldcg(B.x + i - 1), ax);
-                    if (xx + 1 < s.nx) ax = fma(-s.Tx[i], ldcg(B.x + i + 1), ax);
-                    if (y + 1 < s.ny) ax = fma(-s.Ty[i], ldcg(B.x + i + s.nx), ax);
-                    const double bi = B.b[i];
-                    const double ri = bi - ax;
-                    const double zi = s.dinv[i] * ri;
-                    B.r[i] = ri;
-                    B.z[i] = zi;
-                    bb = fma(bi, bi, bb);
-                    rz = fma(ri, zi, rz);
-                    rr = fma(ri, ri, rr);
-                }
+                for (int k = 0; k < CPL; ++k)
+                    if (xa + k < s.nx) f((int64_t)y * s.nx + xa + k);
+        });
+    }
+    __device__ void setup_block(const Vecs<T> &V, T &bb, T &rz, T &rr) const {
+        each_cell([&](int64_t i) {
+            const int xx = (int)(i % s.nx), y = (int)(i / s.nx);
+            T ax = c.D[i] * ldcg(V.x + i);
+            if (y > 0) ax = fmaT(-c.Ty[i - s.nx], ldcg(V.x + i - s.nx), ax);
+            if (xx > 0) ax = fmaT(-c.Tx[i - 1], ldcg(V.x + i - 1), ax);
+            if (xx + 1 < s.nx) ax = fmaT(-c.Tx[i], ldcg(V.x + i + 1), ax);
+            if (y + 1 < s.ny) ax = fmaT(-c.Ty[i], ldcg(V.x + i + s.nx), ax);
+            const T bi = V.b[i];
+            const T ri = bi - ax;
+            V.r[i] = ri;
+            bb = fmaT(bi, bi, bb);
+            rr = fmaT(ri, ri, rr);
+            if (V.z) {
+                const T zi = V.dinv[i] * ri;
+                V.z[i] = zi;
+                rz = fmaT(ri, zi, rz);
             }
         });
     }
-    __device__ void phaseA_block(const Bufs &B, const double *pold, double *pout, bool first, double beta,
-                                 double &pq, double *) const {
+    __device__ __forceinline__ T pnew1(const Vecs<T> &V, const T *pold, bool first, T beta, int64_t i) const {
+        const T zi = ldcg(V.z + i);
+        return first ? zi : fmaT(beta, ldcg(pold + i), zi);
+    }
+    __device__ __forceinline__ void pnew(const Vecs<T> &V, const T *pold, bool first, T beta, int64_t i,
+                                        T (&p)[CPL]) const {
+        vld_cg<T, CPL>(V.z + i, p);
+        if (!first) {
+            T o[CPL];
+            vld_cg<T, CPL>(pold + i, o);
+#pragma unroll
+            for (int k = 0; k < CPL; ++k) p[k] = fmaT(beta, o[k], p[k]);
+        }
+    }
+    __device__ __forceinline__ void load(const T *a, int64_t i, T (&v)[CPL]) const { vld<T, CPL>(a + i, v); }
+    __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *) const {
         const int lane = threadIdx.x & 31;
         each_segment([&](int x0, int y0, int y1) {
             const int xa = x0 + CPL * lane;          // first column of this lane
-            const bool act = xa < s.nx;               // CPL == 2: nx even, so xa+1 < nx too
-            // halo column of the strip handled by lane 0 (west) / lane 31 (east)
+            const bool act = xa < s.nx;               // nx is a multiple of CPL: all CPL cells valid
             const int hx = lane == 0 ? x0 - 1 : x0 + kSW;
             const bool hact = (lane == 0 && x0 > 0) || (lane == 31 && x0 + kSW < s.nx);
-            double pm[CPL], pc[CPL], pn[CPL], tym[CPL];
+            T pm[CPL], pc[CPL], pn[CPL], tym[CPL];
 #pragma unroll
-            for (int k = 0; k < CPL; ++k) { pm[k] = 0.0; pc[k] = 0.0; tym[k] = 0.0; }
+            for (int k = 0; k < CPL; ++k) { pm[k] = T(0); pc[k] = T(0); tym[k] = T(0); }
             if (act) {
                 const int64_t i0 = (int64_t)y0 * s.nx + xa;
-                pnew(B, pold, first, beta, i0, pc);
+                pnew(V, pold, first, beta, i0, pc);
                 if (y0 > 0) {
-                    pnew(B, pold, first, beta, i0 - s.nx, pm);
-                    load2(s.Ty, i0 - s.nx, tym);
+                    pnew(V, pold, first, beta, i0 - s.nx, pm);
+                    load(c.Ty, i0 - s.nx, tym);
                 }
             }
             for (int y = y0; y < y1; ++y) {
                 const int64_t i = (int64_t)y * s.nx + xa;
-                double d[CPL], tx[CPL], typ[CPL];
-                double txw0 = 0.0, ph = 0.0;
+                T d[CPL], tx[CPL], typ[CPL];
+                T txw0 = T(0), ph = T(0);
 #pragma unroll
-                for (int k = 0; k < CPL; ++k) { pn[k] = 0.0; d[k] = 0.0; tx[k] = 0.0; typ[k] = 0.0; }
+                for (int k = 0; k < CPL; ++k) { pn[k] = T(0); d[k] = T(0); tx[k] = T(0); typ[k] = T(0); }
                 if (act) {
-                    if (y + 1 < s.ny) { pnew(B, pold, first, beta, i + s.nx, pn); load2(s.Ty, i, typ); }
-                    load2(s.D, i, d);
-                    load2(s.Tx, i, tx);
-                    if (lane == 0 && x0 > 0) txw0 = s.Tx[i - 1];
+                    if (y + 1 < s.ny) { pnew(V, pold, first, beta, i + s.nx, pn); load(c.Ty, i, typ); }
+                    load(c.D, i, d);
+                    load(c.Tx, i, tx);
+                    if (lane == 0 && x0 > 0) txw0 = c.Tx[i - 1];
                 }
-                if (hact) ph = pnew1(B, pold, first, beta, (int64_t)y * s.nx + hx);
-                // face conductances to the west / east of each cell
-                const double tx_last_up = __shfl_up_sync(kFull, tx[CPL - 1], 1);
-                const double pc_last_up = __shfl_up_sync(kFull, pc[CPL - 1], 1);
-                const double pc_first_dn = __shfl_down_sync(kFull, pc[0], 1);
+                if (hact) ph = pnew1(V, pold, first, beta, (int64_t)y * s.nx + hx);
+                const T tx_last_up = __shfl_up_sync(kFull, tx[CPL - 1], 1);
+                const T pc_last_up = __shfl_up_sync(kFull, pc[CPL - 1], 1);
+                const T pc_first_dn = __shfl_down_sync(kFull, pc[0], 1);
                 if (!act) continue;
-                double txw[CPL], txe[CPL], pw[CPL], pe[CPL];
+                T txw[CPL], txe[CPL], pw[CPL], pe[CPL];
                 txw[0] = lane == 0 ? txw0 : tx_last_up;
                 pw[0] = lane == 0 ? ph : pc_last_up;
 #pragma unroll
                 for (int k = 1; k < CPL; ++k) { txw[k] = tx[k - 1]; pw[k] = pc[k - 1]; }
 #pragma unroll
                 for (int k = 0; k < CPL - 1; ++k) { txe[k] = tx[k]; pe[k] = pc[k + 1]; }
-                const bool last_col = xa + CPL >= s.nx;   // the lane's last cell is the grid's last column
-                txe[CPL - 1] = last_col ? 0.0 : tx[CPL - 1];
+                const bool last_col = xa + CPL >= s.nx;
+                txe[CPL - 1] = last_col ? T(0) : tx[CPL - 1];
                 pe[CPL - 1] = lane == 31 ? ph : pc_first_dn;
-                double q[CPL];
+                T q[CPL];
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
-                    double qi = d[k] * pc[k];
-                    qi = fma(-tym[k], pm[k], qi);
-                    qi = fma(-txw[k], pw[k], qi);
-                    qi = fma(-txe[k], pe[k], qi);
-                    qi = fma(-typ[k], pn[k], qi);
+                    T qi = d[k] * pc[k];
+                    qi = fmaT(-tym[k], pm[k], qi);
+                    qi = fmaT(-txw[k], pw[k], qi);
+                    qi = fmaT(-txe[k], pe[k], qi);
+                    qi = fmaT(-typ[k], pn[k], qi);
                     q[k] = qi;
-                    pq = fma(pc[k], qi, pq);
+                    pq = fmaT(pc[k], qi, pq);
                 }
-                if (CPL == 2) {
-                    *reinterpret_cast<double2 *>(pout + i) = make_double2(pc[0], pc[CPL - 1]);
-                    *reinterpret_cast<double2 *>(B.q + i) = make_double2(q[0], q[CPL - 1]);
-                } else {
-                    pout[i] = pc[0];
-                    B.q[i] = q[0];
-                }
+                vst<T, CPL>(pout + i, pc);
+                vst<T, CPL>(V.q + i, q);
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) { tym[k] = typ[k]; pm[k] = pc[k]; pc[k] = pn[k]; }
             }
         });
     }
-    template <class F>
-    __device__ __forceinline__ void each_cell(F f) const {
-        const int lane = threadIdx.x & 31;
-        each_segment([&](int x0, int y0, int y1) {
-            const int xa = x0 + CPL * lane;
-            if (xa >= s.nx) return;
-#pragma unroll 2
-            for (int y = y0; y < y1; ++y)
-#pragma unroll
-                for (int k = 0; k < CPL; ++k) f((int64_t)y * s.nx + xa + k);
-        });
-    }
-    static constexpr int kSmem = 1;
-    __device__ void resolve() {}
 };
 
+// 3D: units of kTileX x kTileY columns marching kTileZ planes; p of each
+// plane (tile + one-cell xy halo) built once into shared memory (four
+// rotating planes: one barrier per plane), z-neighbours from the planes
+// above and below.
+template <typename T>
 struct Op3D {
     Stencil s;
+    Coef<T> c;
+    static constexpr int kSmem = 2 * (kTileX + 2) * (kTileY + 2);
+    static constexpr bool kTunable = true;
+    __device__ void resolve() {}
     __device__ int64_t units() const {
         const int64_t tx = (s.nx + kTileX - 1) / kTileX, ty = (s.ny + kTileY - 1) / kTileY;
         const int64_t tz = (s.nz + kTileZ - 1) / kTileZ;
@@ -355,51 +279,57 @@ struct Op3D {
         const int64_t nu = units();
         for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) for_cells(u, f);
     }
-    __device__ void setup_block(const Bufs &B, double &bb, double &rz, double &rr) const {
+    __device__ void setup_block(const Vecs<T> &V, T &bb, T &rz, T &rr) const {
         const int64_t sxy = (int64_t)s.nx * s.ny;
         each_cell([&](int64_t i) {
             const int xx = (int)(i % s.nx), yy = (int)((i / s.nx) % s.ny), zz = (int)(i / sxy);
-            double ax = s.D[i] * ldcg(B.x + i);
-            if (zz > 0) ax = fma(-s.Tz[i - sxy], ldcg(B.x + i - sxy), ax);
-            if (yy > 0) ax = fma(-s.Ty[i - s.nx], ldcg(B.x + i - s.nx), ax);
-            if (xx > 0) ax = fma(-s.Tx[i - 1], ldcg(B.x + i - 1), ax);
-            if (xx + 1 < s.nx) ax = fma(-s.Tx[i], ldcg(B.x + i + 1), ax);
-            if (yy + 1 < s.ny) ax = fma(-s.Ty[i], ldcg(B.x + i + s.nx), ax);
-            if (zz + 1 < s.nz) ax = fma(-s.Tz[i], ldcg(B.x + i + sxy), ax);
-            const double bi = B.b[i];
-            const double ri = bi - ax;
-            const double zi = s.dinv[i] * ri;
-            B.r[i] = ri;
-            B.z[i] = zi;
-            bb = fma(bi, bi, bb);
-            rz = fma(ri, zi, rz);
-            rr = fma(ri, ri, rr);
+            T ax = c.D[i] * ldcg(V.x + i);
+            if (zz > 0) ax = fmaT(-c.Tz[i - sxy], ldcg(V.x + i - sxy), ax);
+            if (yy > 0) ax = fmaT(-c.Ty[i - s.nx], ldcg(V.x + i - s.nx), ax);
+            if (xx > 0) ax = fmaT(-c.Tx[i - 1], ldcg(V.x + i - 1), ax);
+            if (xx + 1 < s.nx) ax = fmaT(-c.Tx[i], ldcg(V.x + i + 1), ax);
+            if (yy + 1 < s.ny) ax = fmaT(-c.Ty[i], ldcg(V.x + i + s.nx), ax);
+            if (zz + 1 < s.nz) ax = fmaT(-c.Tz[i], ldcg(V.x + i + sxy), ax);
+            const T bi = V.b[i];
+            const T ri = bi - ax;
+            V.r[i] = ri;
+            bb = fmaT(bi, bi, bb);
+            rr = fmaT(ri, ri, rr);
+            if (V.z) {
+                const T zi = V.dinv[i] * ri;
+                V.z[i] = zi;
+                rz = fmaT(ri, zi, rz);
+            }
         });
     }
-    // p of plane z (tile + 1-cell xy halo) into a (kTileY+2) x (kTileX+2) buffer
-    __device__ void build_plane(const Bufs &B, const double *pold, bool first, double beta, int x0, int y0, int z,
-                                double *pl) const {
-        const int64_t sxy = (int64_t)s.nx * s.ny;
-        constexpr int ex = kTileX + 2, ey = kTileY + 2;
-        for (int k = threadIdx.x; k < ex * ey; k += kPcgThreads) {
-            const int gx = x0 - 1 + (k % ex), gy = y0 - 1 + (k / ex);
-            double v = 0.0;
-            if (z >= 0 && z < s.nz && gx >= 0 && gx < s.nx && gy >= 0 && gy < s.ny) {
-                const int64_t i = gx + (int64_t)s.nx * gy + sxy * z;
-                const double zi = ldcg(B.z + i);
-                v = first ? zi : fma(beta, ldcg(pold + i), zi);
-            }
-            pl[k] = v;
-        }
+    // p at global cell (gx, gy, z), 0 outside the grid
+    __device__ __forceinline__ T pat(const Vecs<T> &V, const T *pold, bool first, T beta, int gx, int gy,
+                                     int z) const {
+        if (z < 0 || z >= s.nz || gx < 0 || gx >= s.nx || gy < 0 || gy >= s.ny) return T(0);
+        const int64_t i = gx + (int64_t)s.nx * gy + (int64_t)s.nx * s.ny * z;
+        const T zi = ldcg(V.z + i);
+        return first ? zi : fmaT(beta, ldcg(pold + i), zi);
     }
-    __device__ void phaseA_block(const Bufs &B, const double *pold, double *pout, bool first, double beta,
-                                 double &pq, double *sm) const {
+    __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *sm) const {
         const int64_t nu = units();
-        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) phaseA_unit(u, B, pold, pout, first, beta, pq, sm);
+        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) phaseA_unit(u, V, pold, pout, first, beta, pq, sm);
     }
-    __device__ void phaseA_unit(int64_t u, const Bufs &B, const double *pold, double *pout, bool first, double beta,
-                                double &pq, double *sm) const {
-        constexpr int ex = kTileX + 2, ey = kTileY + 2, pls = ex * ey;
+    // 2.5D march: thread (lx, ly) owns column (x, y) and keeps p at z-1, z,
+    // z+1 in registers; the first kHalo threads own one cell of the plane's
+    // halo ring each.  Per plane: issue the loads of plane z+1 (own column
+    // and halo) and the coefficients of plane z, publish plane z to shared
+    // memory, one barrier, form q at plane z.  Two plane buffers alternate.
+    static constexpr int kEx = kTileX + 2, kEy = kTileY + 2, kPls = kEx * kEy;
+    static constexpr int kHalo = kPls - kTileX * kTileY;   // 84 ring cells
+    __device__ __forceinline__ void halo_cell(int k, int &hx, int &hy) const {
+        // ring of the (kTileX+2) x (kTileY+2) plane: bottom row, top row, left and right columns
+        if (k < kEx) { hx = k; hy = 0; }
+        else if (k < 2 * kEx) { hx = k - kEx; hy = kEy - 1; }
+        else if (k < 2 * kEx + kTileY) { hx = 0; hy = 1 + (k - 2 * kEx); }
+        else { hx = kEx - 1; hy = 1 + (k - 2 * kEx - kTileY); }
+    }
+    __device__ void phaseA_unit(int64_t u, const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq,
+                                T *sm) const {
         int x0, y0, z0;
         origin(u, x0, y0, z0);
         const int lx = threadIdx.x % kTileX, ly = threadIdx.x / kTileX;
@@ -407,135 +337,212 @@ struct Op3D {
         const bool act = xx < s.nx && yy < s.ny;
         const int z1 = min(z0 + kTileZ, s.nz);
         const int64_t sxy = (int64_t)s.nx * s.ny;
-        // planes z0-1 and z0 first
-        build_plane(B, pold, first, beta, x0, y0, z0 - 1, sm + ((z0 + 3) & 3) * pls);
-        build_plane(B, pold, first, beta, x0, y0, z0, sm + (z0 & 3) * pls);
-        const int c = (ly + 1) * ex + (lx + 1);
+        const bool has_h = threadIdx.x < kHalo;
+        int hx = 0, hy = 0;
+        if (has_h) halo_cell(threadIdx.x, hx, hy);
+        const int ghx = x0 - 1 + hx, ghy = y0 - 1 + hy;
+        const int cc = (ly + 1) * kEx + (lx + 1);
+        T pm = T(0), pc = T(0), ph = T(0);
+        if (act) { pm = pat(V, pold, first, beta, xx, yy, z0 - 1); pc = pat(V, pold, first, beta, xx, yy, z0); }
+        if (has_h) ph = pat(V, pold, first, beta, ghx, ghy, z0);
         for (int z = z0; z < z1; ++z) {
-            build_plane(B, pold, first, beta, x0, y0, z + 1, sm + ((z + 1) & 3) * pls);
+            const int64_t i = xx + (int64_t)s.nx * yy + sxy * z;
+            // loads of plane z+1 and coefficients of plane z, before the barrier
+            T pn = T(0), phn = T(0), d = T(0), tzm = T(0), tym = T(0), txm = T(0), txp = T(0), typ = T(0), tzp = T(0);
+            if (act) {
+                pn = pat(V, pold, first, beta, xx, yy, z + 1);
+                d = c.D[i];
+                if (z > 0) tzm = c.Tz[i - sxy];
+                if (yy > 0) tym = c.Ty[i - s.nx];
+                if (xx > 0) txm = c.Tx[i - 1];
+                if (xx + 1 < s.nx) txp = c.Tx[i];
+                if (yy + 1 < s.ny) typ = c.Ty[i];
+                if (z + 1 < s.nz) tzp = c.Tz[i];
+            }
+            if (has_h) phn = pat(V, pold, first, beta, ghx, ghy, z + 1);
+            T *pl = sm + (z & 1) * kPls;
+            pl[cc] = pc;
+            if (has_h) pl[hy * kEx + hx] = ph;
             __syncthreads();
             if (act) {
-                const double *pc = sm + (z & 3) * pls;
-                const double pmz = sm[((z + 3) & 3) * pls + c];
-                const double ppz = sm[((z + 1) & 3) * pls + c];
-                const int64_t i = xx + (int64_t)s.nx * yy + sxy * z;
-                const double p0 = pc[c];
-                double qi = s.D[i] * p0;
-                if (z > 0) qi = fma(-s.Tz[i - sxy], pmz, qi);
-                if (yy > 0) qi = fma(-s.Ty[i - s.nx], pc[c - ex], qi);
-                if (xx > 0) qi = fma(-s.Tx[i - 1], pc[c - 1], qi);
-                if (xx + 1 < s.nx) qi = fma(-s.Tx[i], pc[c + 1], qi);
-                if (yy + 1 < s.ny) qi = fma(-s.Ty[i], pc[c + ex], qi);
-                if (z + 1 < s.nz) qi = fma(-s.Tz[i], ppz, qi);
-                pout[i] = p0;
-                B.q[i] = qi;
-                pq = fma(p0, qi, pq);
+                T qi = d * pc;
+                qi = fmaT(-tzm, pm, qi);
+                qi = fmaT(-tym, pl[cc - kEx], qi);
+                qi = fmaT(-txm, pl[cc - 1], qi);
+                qi = fmaT(-txp, pl[cc + 1], qi);
+                qi = fmaT(-typ, pl[cc + kEx], qi);
+                qi = fmaT(-tzp, pn, qi);
+                pout[i] = pc;
+                V.q[i] = qi;
+                pq = fmaT(pc, qi, pq);
             }
+            pm = pc;
+            pc = pn;
+            ph = phn;
         }
         __syncthreads();
     }
-    static constexpr int kSmem = 4 * (kTileX + 2) * (kTileY + 2);
-    __device__ void resolve() {}
 };
 
+// CSR: one row per thread; the p of every referenced column is recomputed
+// from z and p_old (rows are independent, no shared memory).
+template <typename T>
 struct OpCsr {
-    Csr c;
+    Csr cs;
+    const T *av;
     int32_t n;   // resolved at kernel start (device-side count of an extracted subsystem)
-    __device__ void resolve() { if (c.n_dev) n = *c.n_dev; }
-    __device__ int64_t units() const { return (n + kPcgThreads - 1) / kPcgThreads; }
+    static constexpr int kSmem = 1;
+    static constexpr bool kTunable = false;
+    __device__ void resolve() { if (cs.n_dev) n = *cs.n_dev; }
     template <class F>
     __device__ __forceinline__ void each_cell(F f) const {
         for (int64_t i = blockIdx.x * (int64_t)kPcgThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kPcgThreads)
             f(i);
     }
-    __device__ void setup_block(const Bufs &B, double &bb, double &rz, double &rr) const {
+    __device__ void setup_block(const Vecs<T> &V, T &bb, T &rz, T &rr) const {
         each_cell([&](int64_t i) {
-            double ax = 0.0;
-            const int32_t e1 = c.rp[i + 1];
-            for (int32_t e = c.rp[i]; e < e1; ++e) ax = fma(c.av[e], ldcg(B.x + c.ci[e]), ax);
-            const double bi = B.b[i];
-            const double ri = bi - ax;
-            const double zi = B.dinv[i] * ri;
-            B.r[i] = ri;
-            B.z[i] = zi;
-            bb = fma(bi, bi, bb);
-            rz = fma(ri, zi, rz);
-            rr = fma(ri, ri, rr);
+            T ax = T(0);
+            const int32_t e1 = cs.rp[i + 1];
+            for (int32_t e = cs.rp[i]; e < e1; ++e) ax = fmaT(av[e], ldcg(V.x + cs.ci[e]), ax);
+            const T bi = V.b[i];
+            const T ri = bi - ax;
+            V.r[i] = ri;
+            bb = fmaT(bi, bi, bb);
+            rr = fmaT(ri, ri, rr);
+            if (V.z) {
+                const T zi = V.dinv[i] * ri;
+                V.z[i] = zi;
+                rz = fmaT(ri, zi, rz);
+            }
         });
     }
-    __device__ void phaseA_block(const Bufs &B, const double *pold, double *pout, bool first, double beta,
-                                 double &pq, double *) const {
+    __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *) const {
         each_cell([&](int64_t i) {
-            double qi = 0.0, pi = 0.0;
-            const int32_t e1 = c.rp[i + 1];
-            for (int32_t e = c.rp[i]; e < e1; ++e) {
-                const int32_t j = c.ci[e];
-                const double zj = ldcg(B.z + j);
-                const double pj = first ? zj : fma(beta, ldcg(pold + j), zj);
+            T qi = T(0), pi = T(0);
+            const int32_t e1 = cs.rp[i + 1];
+            for (int32_t e = cs.rp[i]; e < e1; ++e) {
+                const int32_t j = cs.ci[e];
+                const T zj = ldcg(V.z + j);
+                const T pj = first ? zj : fmaT(beta, ldcg(pold + j), zj);
                 if (j == i) pi = pj;
-                qi = fma(c.av[e], pj, qi);
+                qi = fmaT(av[e], pj, qi);
             }
             pout[i] = pi;
-            B.q[i] = qi;
-            pq = fma(pi, qi, pq);
+            V.q[i] = qi;
+            pq = fmaT(pi, qi, pq);
         });
     }
-    static constexpr int kSmem = 1;
 };
 
-// -------------------------------------------------------------- kernel
+// -------------------------------------------------------------- building blocks
 
-// Deterministic grid-wide sum of slot `k` of the block partials: every block
-// computes the same value in the same order.
-__device__ __forceinline__ double grid_reduce(const double *part, int k, unsigned nb, double *bcast) {
-    if (threadIdx.x < 32) {
-        double v = 0.0;
-        for (unsigned b = threadIdx.x; b < nb; b += 32) v += ldcg(part + (size_t)k * kMaxGrid + b);
-        v = warp_sum(v);
-        if (threadIdx.x == 0) *bcast = v;
-    }
-    __syncthreads();
-    const double r = *bcast;
-    __syncthreads();
-    return r;
-}
-
-template <class OP>
-__device__ bool setup_phase(const OP &op, const Bufs &B, double *red, double &bb, double &rz, double &rr,
-                            Ctrl *ctrl) {
-    double acc[3] = {0.0, 0.0, 0.0};
-    op.setup_block(B, acc[0], acc[1], acc[2]);
-    block_sum<3>(acc, red);
-    if (threadIdx.x == 0) {
-        B.part[0 * kMaxGrid + blockIdx.x] = acc[0];
-        B.part[1 * kMaxGrid + blockIdx.x] = acc[1];
-        B.part[2 * kMaxGrid + blockIdx.x] = acc[2];
-    }
+// Block sums of NV thread values into partial slots `slot0..`, barrier, and
+// the grid-wide sums (identical in every block).  False if a wait timed out.
+template <int NV, typename T>
+__device__ __forceinline__ bool grid_sums(T (&v)[NV], int slot0, double *part, double *red, Ctrl *ctrl,
+                                          double (&out)[NV]) {
+    T tmp[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tmp[k] = v[k];
+    block_sum<NV, T>(tmp, reinterpret_cast<T *>(red));
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[(size_t)(slot0 + k) * kMaxGrid + blockIdx.x] = (double)tmp[k];
     if (!grid_sync(ctrl, gridDim.x)) return false;
-    bb = grid_reduce(B.part, 0, gridDim.x, red + 96);
-    rz = grid_reduce(B.part, 1, gridDim.x, red + 96);
-    rr = grid_reduce(B.part, 2, gridDim.x, red + 96);
+    // every thread loads its few block partials at once (one L2 round trip),
+    // then a fixed-order block sum: the same totals in every block
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += ldcg(part + (size_t)(slot0 + k) * kMaxGrid + b);
+    block_sum<NV, double>(acc, red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[96 + k] = acc[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = red[96 + k];
+    __syncthreads();
     return true;
 }
 
+// r = b - A x (z = dinv r if V.z), with the grid sums of b.b, r.z, r.r.
+template <class OP, typename T>
+__device__ bool residual_phase(const OP &op, const Vecs<T> &V, double *part, double *red, Ctrl *ctrl, double &bb,
+                               double &rz, double &rr) {
+    T acc[3] = {T(0), T(0), T(0)};
+    op.setup_block(V, acc[0], acc[1], acc[2]);
+    double out[3];
+    if (!grid_sums<3, T>(acc, 0, part, red, ctrl, out)) return false;
+    bb = out[0];
+    rz = out[1];
+    rr = out[2];
+    return true;
+}
+
+// CG iterations from the current r, z (first phase with p = z).  Stops when
+// r.r <= stop on the recurrence residual, at maxit, or on breakdown.
+// Returns 1 converged, 0 iteration limit, -1 breakdown, -2 wait timed out.
+template <class OP, typename T>
+__device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, double *red, T *sm, Ctrl *ctrl,
+                             double rz, double stop, int maxit, int &it, int &pin) {
+    bool first = true;
+    double beta = 0.0;
+    while (true) {
+        T pq = T(0);
+        const T *pold = pin ? V.p1 : V.p0;
+        T *pout = pin ? V.p0 : V.p1;
+        op.phaseA_block(V, pold, pout, first, (T)beta, pq, sm);
+        T a1[1] = {pq};
+        double o1[1];
+        if (!grid_sums<1, T>(a1, 3, part, red, ctrl, o1)) return -2;
+        const double pqs = o1[0];
+        if (!(pqs > 0.0) || !isfinite(pqs)) return -1;
+        const T alpha = (T)(rz / pqs);
+        pin ^= 1;
+        const T *p = pout;
+        T acc[2] = {T(0), T(0)};
+        op.each_cell([&](int64_t i) {
+            const T pi = p[i], qi = V.q[i];
+            V.x[i] = fmaT(alpha, pi, V.x[i]);
+            const T ri = fmaT(-alpha, qi, V.r[i]);
+            const T zi = V.dinv[i] * ri;
+            V.r[i] = ri;
+            V.z[i] = zi;
+            acc[0] = fmaT(ri, zi, acc[0]);
+            acc[1] = fmaT(ri, ri, acc[1]);
+        });
+        double o2[2];
+        if (!grid_sums<2, T>(acc, 4, part, red, ctrl, o2)) return -2;
+        ++it;
+        if (o2[1] <= stop) return 1;
+        if (it >= maxit) return 0;
+        beta = o2[0] / rz;
+        rz = o2[0];
+        first = false;
+    }
+}
+
+// -------------------------------------------------------------- kernels
+
 template <class OP, int MINB>
-__global__ void __launch_bounds__(kPcgThreads, MINB) pcg_kernel(OP op, Bufs B, double tol, int maxit, int max_restarts,
-                                                          Ctrl *ctrl) {
+__global__ void __launch_bounds__(kPcgThreads, MINB) pcg_kernel(OP op, Vecs<double> V, double *part, double tol,
+                                                                int maxit, int max_restarts, Ctrl *ctrl) {
     __shared__ double red[128];
     __shared__ double sm[OP::kSmem];
     op.resolve();
     double bb, rz, rr;
-    if (!setup_phase(op, B, red, bb, rz, rr, ctrl)) return;
+    if (!residual_phase(op, V, part, red, ctrl, bb, rz, rr)) return;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const double stop = (tol * tol) * bb;
     if (lead) {
         ctrl->bnorm2 = bb;
         ctrl->relres0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-        ctrl->iters = 0;
-        ctrl->restarts = 0;
     }
     if (bb == 0.0) {   // A x = 0: x = 0
-        op.each_cell([&](int64_t i) { B.x[i] = 0.0; });
+        op.each_cell([&](int64_t i) { V.x[i] = 0.0; });
         if (lead) { ctrl->converged = 1; ctrl->early = 1; ctrl->relres = 0.0; }
         return;
     }
@@ -543,69 +550,21 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) pcg_kernel(OP op, Bufs B, d
         if (lead) { ctrl->converged = 1; ctrl->early = 1; ctrl->relres = sqrt(rr / bb); }
         return;
     }
-    int it = 0, restarts = 0, pin = 0;
-    bool first = true;
-    double beta = 0.0;
-    int result = 0;   // 1 converged, 0 not converged, -1 breakdown
+    int it = 0, restarts = 0, pin = 0, result;
     while (true) {
-        // ---- phase A
-        double pq = 0.0;
-        const double *pold = pin ? B.p1 : B.p0;
-        double *pout = pin ? B.p0 : B.p1;
-        op.phaseA_block(B, pold, pout, first, beta, pq, sm);
-        {
-            double a1[1] = {pq};
-            block_sum<1>(a1, red);
-            if (threadIdx.x == 0) B.part[3 * kMaxGrid + blockIdx.x] = a1[0];
-        }
-        if (!grid_sync(ctrl, gridDim.x)) return;
-        pq = grid_reduce(B.part, 3, gridDim.x, red + 96);
-        if (!(pq > 0.0) || !isfinite(pq)) { result = -1; break; }
-        const double alpha = rz / pq;
-        pin ^= 1;
-        const double *p = pout;
-        // ---- phase B
-        double acc[2] = {0.0, 0.0};
-        op.each_cell([&](int64_t i) {
-            const double pi = p[i], qi = B.q[i];
-            B.x[i] = fma(alpha, pi, B.x[i]);
-            const double ri = fma(-alpha, qi, B.r[i]);
-            const double zi = B.dinv[i] * ri;
-            B.r[i] = ri;
-            B.z[i] = zi;
-            acc[0] = fma(ri, zi, acc[0]);
-            acc[1] = fma(ri, ri, acc[1]);
-        });
-        block_sum<2>(acc, red);
-        if (threadIdx.x == 0) {
-            B.part[4 * kMaxGrid + blockIdx.x] = acc[0];
-            B.part[5 * kMaxGrid + blockIdx.x] = acc[1];
-        }
-        if (!grid_sync(ctrl, gridDim.x)) return;
-        const double rz_new = grid_reduce(B.part, 4, gridDim.x, red + 96);
-        rr = grid_reduce(B.part, 5, gridDim.x, red + 96);
-        ++it;
-        if (rr <= stop) {
-            // confirm with the true residual
-            double bb2;
-            if (!setup_phase(op, B, red, bb2, rz, rr, ctrl)) return;
-            if (rr <= stop) { result = 1; break; }
-            if (++restarts > max_restarts) { result = 0; break; }
-            first = true;
-            beta = 0.0;
-            if (it >= maxit) { result = 0; break; }
-            continue;
-        }
-        if (it >= maxit) { result = 0; break; }
-        beta = rz_new / rz;
-        rz = rz_new;
-        first = false;
+        result = cg_iterations(op, V, part, red, sm, ctrl, rz, stop, maxit, it, pin);
+        if (result == -2) return;
+        if (result != 1) break;
+        // converged on the recurrence residual: confirm with the true one
+        double bb2;
+        if (!residual_phase(op, V, part, red, ctrl, bb2, rz, rr)) return;
+        if (rr <= stop) break;
+        result = 0;
+        if (++restarts > max_restarts || it >= maxit) break;
     }
-    if (result == 0 && it >= maxit) {
-        // report the true residual of the last iterate
-        double bb2, rz2, rr2;
-        if (!setup_phase(op, B, red, bb2, rz2, rr2, ctrl)) return;
-        rr = rr2;
+    if (result == 0 && it >= maxit) {   // report the true residual of the last iterate
+        double bb2, rz2;
+        if (!residual_phase(op, V, part, red, ctrl, bb2, rz2, rr)) return;
     }
     if (lead) {
         ctrl->iters = it;
@@ -617,21 +576,98 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) pcg_kernel(OP op, Bufs B, d
     }
 }
 
-__global__ void csr_dinv_kernel(Csr c, double *dinv) {
+// Iterative refinement: FP64 residual and update around FP32 inner CG.
+template <class OPD, class OPF, int MINB>
+__global__ void __launch_bounds__(kPcgThreads, MINB) ir_kernel(OPD opd, OPF opf, Vecs<double> VD, Vecs<float> VF,
+                                                               double *part, double tol, double inner_tol,
+                                                               int maxit, int max_outer, Ctrl *ctrl) {
+    __shared__ double red[128];
+    __shared__ float sm[OPF::kSmem];
+    opd.resolve();
+    opf.resolve();
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    int it = 0, outer = 0, result = 0, pin = 0;
+    double bb = 0.0, rr = 0.0, stop = 0.0;
+    while (true) {
+        // FP64 residual r = b - A x (no z)
+        double bbo, rzo;
+        if (!residual_phase(opd, VD, part, red, ctrl, bbo, rzo, rr)) return;
+        if (outer == 0) {
+            bb = bbo;
+            stop = (tol * tol) * bb;
+            if (lead) {
+                ctrl->bnorm2 = bb;
+                ctrl->relres0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+            }
+            if (bb == 0.0) {
+                opd.each_cell([&](int64_t i) { VD.x[i] = 0.0; });
+                if (lead) { ctrl->converged = 1; ctrl->early = 1; ctrl->relres = 0.0; }
+                return;
+            }
+        }
+        if (rr <= stop) { result = 1; break; }
+        if (outer >= max_outer || it >= maxit) { result = 0; break; }
+        // inner problem: fl32(A) d = fl32(r / ||r||), d = 0
+        const double sc = sqrt(rr), inv = 1.0 / sc;
+        float acc[2] = {0.f, 0.f};
+        opf.each_cell([&](int64_t i) {
+            const float ri = (float)(ldcg(VD.r + i) * inv);
+            const float zi = VF.dinv[i] * ri;
+            VF.r[i] = ri;
+            VF.z[i] = zi;
+            VF.x[i] = 0.f;
+            acc[0] = fmaf(ri, zi, acc[0]);
+            acc[1] = fmaf(ri, ri, acc[1]);
+        });
+        double o[2];
+        if (!grid_sums<2, float>(acc, 6, part, red, ctrl, o)) return;
+        const double stop_in = (inner_tol * inner_tol) * o[1];
+        const int res = cg_iterations(opf, VF, part, red, sm, ctrl, o[0], stop_in, maxit, it, pin);
+        if (res == -2) return;
+        if (res == -1) { result = -1; break; }
+        // x += ||r|| d in FP64
+        opd.each_cell([&](int64_t i) { VD.x[i] = fma(sc, (double)ldcg(VF.x + i), VD.x[i]); });
+        ++outer;
+        if (!grid_sync(ctrl, gridDim.x)) return;
+    }
+    if (lead) {
+        ctrl->iters = it;
+        ctrl->restarts = outer;
+        ctrl->outer = outer;
+        ctrl->converged = result;
+        ctrl->early = (result == 1 && outer == 0) ? 1 : 0;
+        ctrl->relres = sqrt(rr / bb);
+        if (result == -1) atomicCAS(&ctrl->status, LC_OK, LC_ERR_BREAKDOWN);
+    }
+}
+
+// -------------------------------------------------------------- small kernels
+
+template <typename T>
+__global__ void csr_dinv_kernel(Csr c, const T *av, T *dinv) {
     const int32_t n = c.n_dev ? *c.n_dev : c.n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double d = 0.0;
+        T d = T(0);
         const int32_t e1 = c.rp[i + 1];
         for (int32_t e = c.rp[i]; e < e1; ++e)
-            if (c.ci[e] == i) d = c.av[e];
-        dinv[i] = 1.0 / d;
+            if (c.ci[e] == i) d = av[e];
+        dinv[i] = T(1) / d;
     }
+}
+
+// FP32 copy of the CSR values (of the first *n_dev rows, or all rows).
+__global__ void csr_to_f32_kernel(Csr c, float *av32) {
+    const int32_t n = c.n_dev ? *c.n_dev : c.n;
+    const int32_t nnz = c.rp[n];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        av32[e] = (float)c.av[e];
 }
 
 __global__ void reset_ctrl_kernel(Ctrl *ctrl) {
     ctrl->bar_count = 0;
     ctrl->iters = 0;
     ctrl->restarts = 0;
+    ctrl->outer = 0;
     ctrl->converged = 0;
     ctrl->early = 0;
 }
@@ -683,8 +719,9 @@ __global__ void check_csr_kernel(int32_t n, const int32_t *rp, const int32_t *ci
     }
 }
 
-template <class OP>
-int pcg_grid(const void *kernel, int64_t units, int cap) {
+// -------------------------------------------------------------- launch
+
+int coop_grid(const void *kernel, int64_t units, int cap) {
     int dev = 0, sms = 152, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -701,6 +738,7 @@ int pcg_grid(const void *kernel, int64_t units, int cap) {
 // 128 / 85 / 64 registers per thread.
 template <class OP>
 const void *pcg_kernel_for(int minblocks) {
+    if constexpr (!OP::kTunable) return (const void *)pcg_kernel<OP, 1>;
     switch (minblocks) {
         case 2: return (const void *)pcg_kernel<OP, 2>;
         case 3: return (const void *)pcg_kernel<OP, 3>;
@@ -708,63 +746,126 @@ const void *pcg_kernel_for(int minblocks) {
         default: return (const void *)pcg_kernel<OP, 1>;
     }
 }
+template <class OPD, class OPF>
+const void *ir_kernel_for(int minblocks) {
+    if constexpr (!OPD::kTunable) return (const void *)ir_kernel<OPD, OPF, 1>;
+    switch (minblocks) {
+        case 2: return (const void *)ir_kernel<OPD, OPF, 2>;
+        case 3: return (const void *)ir_kernel<OPD, OPF, 3>;
+        case 4: return (const void *)ir_kernel<OPD, OPF, 4>;
+        default: return (const void *)ir_kernel<OPD, OPF, 1>;
+    }
+}
 
-template <class OP>
-cudaError_t launch_coop(const OP &op, int64_t units, const Bufs &B, double tol, int maxit, int max_restarts,
-                        Ctrl *ctrl, int cap, int minblocks, cudaStream_t s) {
-    const void *k = pcg_kernel_for<OP>(minblocks);
-    const int grid = pcg_grid<OP>(k, units, cap);
+cudaError_t coop_launch(const void *k, int64_t units, int cap, void **args, Ctrl *ctrl, cudaStream_t s) {
+    const int grid = coop_grid(k, units, cap);
     reset_ctrl_kernel<<<1, 1, 0, s>>>(ctrl);
-    note_launches(1);
-    OP o = op;
-    Bufs b = B;
-    double t = tol;
-    int mi = maxit, mr = max_restarts;
-    Ctrl *c = ctrl;
-    void *args[] = {&o, &b, &t, &mi, &mr, &c};
-    note_launches(1);
+    note_launches(2);
     return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kPcgThreads), args, 0, s);
 }
+
+template <class OP>
+cudaError_t launch_pcg(const OP &op, int64_t units, const Vecs<double> &V, double *part, const PcgArgs &a,
+                       Ctrl *ctrl, int cap, int minblocks, cudaStream_t s) {
+    OP o = op;
+    Vecs<double> v = V;
+    double *pt = part;
+    double t = a.tol;
+    int mi = a.maxit, mr = a.max_restarts;
+    Ctrl *c = ctrl;
+    void *args[] = {&o, &v, &pt, &t, &mi, &mr, &c};
+    return coop_launch(pcg_kernel_for<OP>(minblocks), units, cap, args, ctrl, s);
+}
+
+template <class OPD, class OPF>
+cudaError_t launch_ir(const OPD &opd, const OPF &opf, int64_t units, const Vecs<double> &VD, const Vecs<float> &VF,
+                      double *part, const PcgArgs &a, Ctrl *ctrl, int cap, int minblocks, cudaStream_t s) {
+    OPD od = opd;
+    OPF of = opf;
+    Vecs<double> vd = VD;
+    Vecs<float> vf = VF;
+    double *pt = part;
+    double t = a.tol, ti = a.inner_tol;
+    int mi = a.maxit, mo = a.max_outer;
+    Ctrl *c = ctrl;
+    void *args[] = {&od, &of, &vd, &vf, &pt, &t, &ti, &mi, &mo, &c};
+    return coop_launch(ir_kernel_for<OPD, OPF>(minblocks), units, cap, args, ctrl, s);
+}
+
+Vecs<double> vecs64(const PcgArgs &a, const PcgWork &w, const double *dinv) {
+    Vecs<double> V;
+    V.b = a.b; V.x = a.x; V.r = w.r; V.z = w.z; V.q = w.q; V.p0 = w.p0; V.p1 = w.p1; V.dinv = dinv;
+    return V;
+}
+Vecs<float> vecs32(const PcgWork &w, const float *dinv32) {
+    Vecs<float> V;
+    V.b = nullptr; V.x = w.x32; V.r = w.r32; V.z = w.z32; V.q = w.q32; V.p0 = w.p032; V.p1 = w.p132; V.dinv = dinv32;
+    return V;
+}
+
+Coef<double> coef64(const Stencil &s) { return {s.D, s.Tx, s.Ty, s.Tz}; }
+Coef<float> coef32(const Stencil &s) { return {s.D32, s.Tx32, s.Ty32, s.Tz32}; }
 
 }  // namespace
 
 cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                cudaStream_t s) {
-    Bufs B;
-    B.b = a.b; B.x = a.x; B.r = w.r; B.z = w.z; B.q = w.q; B.p0 = w.p0; B.p1 = w.p1;
-    B.dinv = op.dinv; B.part = w.partials;
+    const bool mixed = a.precision == LC_PREC_MIXED;
+    Vecs<double> VD = vecs64(a, w, op.dinv);
+    if (mixed) VD.z = nullptr;   // the refinement residual needs no z
+    Vecs<float> VF = vecs32(w, op.dinv32);
     if (op.dim == 3) {
-        Op3D o{op};
         const int64_t units = (int64_t)((op.nx + kTileX - 1) / kTileX) * ((op.ny + kTileY - 1) / kTileY) *
                               ((op.nz + kTileZ - 1) / kTileZ);
-        return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, 1, s);
+        Op3D<double> od{op, coef64(op)};
+        if (!mixed) return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+        Op3D<float> of{op, coef32(op)};
+        return launch_ir(od, of, units, VD, VF, w.partials, a, ctrl, grid_hint, a.minblocks, s);
     }
-    // two cells per lane (16-byte vectors) when every row starts 16-byte aligned
+    // two cells per lane (paired loads) when every row starts 16-byte aligned
     auto al16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
     const bool vec = op.nx % 2 == 0 && al16(op.D) && al16(op.Tx) && al16(op.Ty);
-    const int warps_per_block = kPcgThreads / 32;
+    const int wpb = kPcgThreads / 32;
     if (vec) {
-        Op2DW<2> o{op};
         // at least 4 rows per warp so the recomputed halo rows stay a small overhead
-        const int64_t units = ((int64_t)((op.nx + 63) / 64) * op.ny + 4 * warps_per_block - 1) / (4 * warps_per_block);
-        return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, a.minblocks, s);
+        const int64_t units = ((int64_t)((op.nx + 63) / 64) * op.ny + 4 * wpb - 1) / (4 * wpb);
+        Op2DW<double, 2> od{op, coef64(op)};
+        if (!mixed) return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+        if (op.nx % 4 == 0) {   // FP32 copies are the library's own, 256-byte aligned: float4 lanes
+            Op2DW<float, 4> of{op, coef32(op)};
+            return launch_ir(od, of, units, VD, VF, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+        }
+        Op2DW<float, 2> of{op, coef32(op)};
+        return launch_ir(od, of, units, VD, VF, w.partials, a, ctrl, grid_hint, a.minblocks, s);
     }
-    Op2DW<1> o{op};
-    const int64_t units = ((int64_t)((op.nx + 31) / 32) * op.ny + 4 * warps_per_block - 1) / (4 * warps_per_block);
-    return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, a.minblocks, s);
+    const int64_t units = ((int64_t)((op.nx + 31) / 32) * op.ny + 4 * wpb - 1) / (4 * wpb);
+    Op2DW<double, 1> od{op, coef64(op)};
+    if (!mixed) return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+    Op2DW<float, 1> of{op, coef32(op)};
+    return launch_ir(od, of, units, VD, VF, w.partials, a, ctrl, grid_hint, a.minblocks, s);
 }
 
 cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint, cudaStream_t s) {
-    // the row count may live on the device (extracted subsystem): the kernel
-    // is sized for the capacity op.n and reads the actual count itself
-    csr_dinv_kernel<<<152 * 4, 256, 0, s>>>(op, w.dinv);
-    note_launches(1);
-    Bufs B;
-    B.b = a.b; B.x = a.x; B.r = w.r; B.z = w.z; B.q = w.q; B.p0 = w.p0; B.p1 = w.p1;
-    B.dinv = w.dinv; B.part = w.partials;
-    OpCsr o{op, op.n};
+    // the row count may live on the device (extracted subsystem): the kernels
+    // are sized for the capacity op.n and read the actual count themselves
     const int64_t units = (op.n + kPcgThreads - 1) / kPcgThreads;
-    return launch_coop(o, units, B, a.tol, a.maxit, a.max_restarts, ctrl, grid_hint, 1, s);
+    csr_dinv_kernel<double><<<152 * 4, 256, 0, s>>>(op, op.av, w.dinv);
+    note_launches(1);
+    Vecs<double> VD = vecs64(a, w, w.dinv);
+    OpCsr<double> od{op, op.av, op.n};
+    if (a.precision != LC_PREC_MIXED) return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, 1, s);
+    VD.z = nullptr;
+    const float *av32 = op.av32;
+    if (!av32) {   // per-solve FP32 copy of the values into the workspace
+        csr_to_f32_kernel<<<152 * 8, 256, 0, s>>>(op, w.val32);
+        note_launches(1);
+        av32 = w.val32;
+    }
+    csr_dinv_kernel<float><<<152 * 4, 256, 0, s>>>(op, av32, w.dinv32);
+    note_launches(1);
+    Vecs<float> VF = vecs32(w, w.dinv32);
+    OpCsr<float> of{op, av32, op.n};
+    return launch_ir(od, of, units, VD, VF, w.partials, a, ctrl, grid_hint, 1, s);
 }
 
 cudaError_t launch_dinv_stencil(int64_t n, const double *D, double *dinv, float *D32, const double *Tx,

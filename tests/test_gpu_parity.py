@@ -269,3 +269,54 @@ def test_nan_handling_matches_oracle(ctx):
     K = torch.zeros(1, dtype=torch.int32, device=DEV)
     lcg.mark_gradient(ctx, stencil_op(ctx, op), cu(x0), 0.1, 1, mask, K)
     assert np.array_equal(mask.cpu().numpy(), ref["mask"])
+
+
+# ---------------------------------------------------------------- mixed precision (FP32 inner, FP64 refinement)
+
+MIXED = [p for p in PROBLEMS if p[1].n >= 20]
+
+
+@pytest.mark.parametrize("name,op", MIXED, ids=[p[0] for p in MIXED])
+def test_mixed_precision_pcg_reaches_fp64_tolerance(ctx, name, op):
+    """FP32 inner CG inside FP64 refinement reaches the FP64 relative residual
+    of the plain FP64 solve; its error against the oracle's FP64 solution is
+    stated (and bounded loosely by the conditioning)."""
+    A, b, x0 = rhs_and_x0(op, 21)
+    tol = 1e-10
+    xr, st, _, _ = oracle.pcg(A, b, x0, tol=1e-13)
+    for gop in (stencil_op(ctx, op), csr_op(ctx, A)):
+        x = cu(x0)
+        stats = lcg.Stats()
+        lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(tol, 100000, lcg.PREC_MIXED, 1e-4, 30), stats)
+        xg = x.cpu().numpy()
+        rr = oracle.relres(A, b, xg)
+        assert rr <= tol, rr
+        assert stats.restarts >= 1 and stats.relres_final <= tol
+        err = np.linalg.norm(xg - xr) / np.linalg.norm(xr)
+        assert err <= 1e-7, err
+
+
+def test_mixed_precision_local_then_global(ctx):
+    d = gen.cfg1_heat2d(seed=9, n=96, radius=8)
+    A = oracle.from_stencil(d["op"])
+    xr, sr, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], tol=1e-8)
+    for gop in (stencil_op(ctx, d["op"]), csr_op(ctx, A)):
+        x = cu(d["x0"])
+        st = lcg.Stats()
+        lcg.solve_local_then_global(ctx, gop, cu(d["b"]), x, lcg.default_params(tol=1e-8, precision=lcg.PREC_MIXED,
+                                                                                 inner_tol=1e-4), st)
+        xg = x.cpu().numpy()
+        assert st.K == sr["K"]
+        assert oracle.relres(A, d["b"], xg) <= 1e-8
+        assert np.linalg.norm(xg - xr) <= 1e-6 * np.linalg.norm(xr)
+
+
+def test_mixed_precision_rejects_bad_parameters(ctx):
+    op = gen.random_stencil_2d(1, 16, 16)
+    gop = stencil_op(ctx, op)
+    x = cu(np.zeros(op.n))
+    for bad in [lcg.SolveParams(1e-8, 100, lcg.PREC_MIXED, 0.0, 10), lcg.SolveParams(1e-8, 100, lcg.PREC_MIXED, 1e-4, 0),
+                lcg.SolveParams(1e-8, 100, 7, 1e-4, 10)]:
+        with pytest.raises(lcg.LcError) as e:
+            lcg.pcg_solve(ctx, gop, cu(np.ones(op.n)), x, bad)
+        assert e.value.code == lcg.LC_ERR_INVALID_ARG
