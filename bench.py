@@ -48,6 +48,9 @@ WORKLOAD = ("2D 2048x2048 5-point FP64 diffusion, 64 rectangles k in [1,1e3], Ga
 # x, p, r, q, dinv in, x, r, z out).
 SETUP_BYTES = 64
 ITER_BYTES = 120
+DP_SETUP = 7
+DP_ITER = 12
+DP_PEAK_GOPS = 152 * 2 * 2.07   # FP64 FMA instructions per second, in G (nominal 1.25 TFLOP/s)
 
 
 def parse():
@@ -274,6 +277,9 @@ def run_gpu(args, rank, ws, local):
 
     prm_res = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8)
     prm_grad = lcg.default_params(lcg.MARK_GRADIENT, alpha=1e-3, grad_layers=2, tol=1e-8)
+    prm_mixed = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8,
+                                   precision=lcg.PREC_MIXED, inner_tol=1e-4)
+    prms = {"res": prm_res, "grad": prm_grad, "mixed": prm_mixed}
     work = torch.empty(N, dtype=torch.float64, device=dev)
 
     def system(k):
@@ -286,7 +292,7 @@ def run_gpu(args, rank, ws, local):
         if kind == "global":
             lcg.pcg_solve(ctx, gop, b, work, sp, stats)
         else:
-            lcg.solve_local_then_global(ctx, gop, b, work, prm_res if kind == "res" else prm_grad, stats)
+            lcg.solve_local_then_global(ctx, gop, b, work, prms[kind], stats)
 
     def timed_loop(kind, steps, warmup, clocks=None):
         st = lcg.Stats()
@@ -313,6 +319,12 @@ def run_gpu(args, rank, ws, local):
     clocks = cs.summary()
     ms_glob, per_glob, _ = timed_loop("global", args.steps, args.warmup)
     ms_grad, per_grad, _ = timed_loop("grad", args.steps, args.warmup)
+    ms_mixed, per_mixed, _ = timed_loop("mixed", args.steps, args.warmup)
+    # error of the mixed-precision result against the FP64 reference state
+    solve("mixed", 0, lcg.Stats())
+    torch.cuda.synchronize(dev)
+    x_ref = xs[1]
+    mixed_err = float(torch.linalg.norm(work - x_ref) / torch.linalg.norm(x_ref))
 
     # roofline of the dominant kernel: the global PCG launch inside Alg 1,
     # timed by CUDA events the library records on the launching stream
@@ -330,6 +342,13 @@ def run_gpu(args, rank, ws, local):
     if tr is not None:
         bpc_iter, bpc_setup = tr
         traffic = float(N * (bpc_iter * mean_it + (bpc_setup if math.isfinite(bpc_setup) else SETUP_BYTES) * 2))
+    # the same kernel seen from FP64 issue: 12 FP64 instructions per cell and
+    # iteration (phase A: 1 for p, 1 mul + 4 fma for q, 1 for p.q; phase B: x,
+    # r, z, r.z, r.r), 7 per cell and residual pass; peak = 152 SMs x 2 FP64
+    # FMA/clk x 2.07 GHz (the nominal 1.25 TFLOP/s)
+    dp = sum(N * (DP_SETUP * (1 + (0 if s["early_exit"] else 1 + s["restarts"])) + DP_ITER * s["it_global"])
+             for s in per_res)
+    dp_achieved = dp / t_pcg / 1e9 if t_pcg > 0 else 0.0
     # GB/s of the plain global PCG (the "SpMV HBM GB/s" half of the metric)
     byts_g = sum(pcg_bytes(s) for s in per_glob)
     t_g = sum(s["t_global_ms"] for s in per_glob) * 1e-3
@@ -369,8 +388,13 @@ def run_gpu(args, rank, ws, local):
                    "systems": nsys, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (operator + 20 resident systems + PCG vectors > 1 GB)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "pcg_kernel<Op2D> (global Jacobi-PCG)",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "pcg_kernel<Op2DW<double,2>> (global Jacobi-PCG, FP64)",
                      "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_cell_iter": ITER_BYTES},
+        "roofline_fp64_issue": {"bound": "alu", "achieved": dp_achieved, "peak": DP_PEAK_GOPS,
+                                "unit": "G FP64 instr/s", "frac": dp_achieved / DP_PEAK_GOPS,
+                                "alg_fp64_instr_per_cell_iter": DP_ITER,
+                                "note": "same kernel; ncu shows the FP64 pipe ~76% busy at ~49% DRAM throughput"},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": e2e_ms / total_sys, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * N,
@@ -391,7 +415,14 @@ def run_gpu(args, rank, ws, local):
             "it_local": statistics.mean(s["it_local"] for s in per_grad),
             "it_global": statistics.mean(s["it_global"] for s in per_grad),
             "relres_max": max(s["relres_final"] for s in per_grad)},
+        "local_first_mixed_precision": {
+            "value": ms_mixed / total_sys, "inner_tol": 1e-4,
+            "inner_iterations": statistics.mean(s["it_global"] for s in per_mixed),
+            "refinement_sweeps": statistics.mean(s["restarts"] for s in per_mixed),
+            "relres_max": max(s["relres_final"] for s in per_mixed),
+            "err_vs_fp64_reference": mixed_err},
         "speedup_vs_global_pcg": ms_glob / ms_res,
+        "speedup_mixed_vs_global_pcg": ms_glob / ms_mixed,
     }
     if rank == 0 and not args.no_cpu_baseline:
         from oracle.build import build_oracle

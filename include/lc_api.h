@@ -218,6 +218,40 @@ LC_EXPORT int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double
 LC_EXPORT int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const double *b, double *x,
                                const lc_params *p, lc_stats *stats, void *stream);
 
+/* ---- operators from conductivity, and the adjoint -----------------------------
+ *
+ * 2D backward-Euler diffusion on an nx x ny grid (grid units):
+ *   A(k) = I/dt + sum_faces T_f (e_P - e_N)(e_P - e_N)^T + sum_{boundary faces} 2 k_P e_P e_P^T,
+ *   T_f = 2 k_P k_N / (k_P + k_N)  (harmonic face conductance; homogeneous
+ *   Dirichlet ghost half a cell outside each boundary face),
+ * the operator family of the paper's time-stepped diffusion systems (Sec. 3).
+ * These calls make the solve differentiable: for a loss L(x), x = A(k)^-1 b,
+ * the adjoint lambda = A^-T dL/dx (A is symmetric, so any solve of this
+ * library computes it) gives dL/db = lambda and dL/dk per cell (below). */
+
+/* D, Tx, Ty (device, N = nx*ny each, stencil layout of lc_op_create_stencil)
+ * from per-cell conductivities k[N] > 0 and dt > 0.  Per cell, in this
+ * order: T = ((2 kP) kE) / (kP + kE) for each interior face; D = 1/dt + east
+ * + west + north + south face conductances + 2 kP for each boundary face
+ * (west, east, south, north).  Tx/Ty on the last column/row are set to 0. */
+LC_EXPORT int lc_assemble_diffusion_2d(lc_ctx *ctx, const int32_t shape[2], const double *k, double dt, double *D,
+                                       double *Tx, double *Ty, void *stream);
+
+/* Recompute an operator's derived data (1/D and the FP32 copies used by
+ * LC_PREC_MIXED) after its coefficient arrays were changed in place, e.g.
+ * by lc_assemble_diffusion_2d.  Stream-ordered; the new coefficients are not
+ * re-validated (they must keep D > 0 and interior faces > 0).  No-op for CSR
+ * operators (their derived data is formed per solve). */
+LC_EXPORT int lc_op_refresh(lc_op *op, void *stream);
+
+/* dk[c] = dL/dk_c = - sum_{interior faces (c,N)} 2 k_N^2/(k_c+k_N)^2 (lam_c - lam_N)(x_c - x_N)
+ *                   - sum_{boundary faces of c} 2 lam_c x_c
+ * for the operator of lc_assemble_diffusion_2d, given the state x and the
+ * adjoint lam (A lam = dL/dx).  Derived from dL/dk = -lam^T (dA/dk) x.  All
+ * arrays device, N values. */
+LC_EXPORT int lc_adjoint_grad_k_2d(lc_ctx *ctx, const int32_t shape[2], const double *k, const double *x,
+                                   const double *lam, double *dk, void *stream);
+
 /* ---- kernel tuning ----------------------------------------------------------
  *
  * Launch-shape knobs of an operator's kernels, for the autotuner; not part

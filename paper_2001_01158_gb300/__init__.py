@@ -109,6 +109,9 @@ def lib():
     L.lc_kernel_launch_count.restype = C.c_int64
     L.lc_op_set_tuning.argtypes = [vp, C.c_char_p, i32]
     L.lc_op_get_tuning.argtypes = [vp, C.c_char_p, C.POINTER(i32)]
+    L.lc_assemble_diffusion_2d.argtypes = [vp, C.POINTER(i32), vp, d, vp, vp, vp, vp]
+    L.lc_op_refresh.argtypes = [vp, vp]
+    L.lc_adjoint_grad_k_2d.argtypes = [vp, C.POINTER(i32), vp, vp, vp, vp, vp]
     _lib = L
     return L
 

@@ -304,7 +304,8 @@ int pcg_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_
     lc::PcgWork w = op->pw;
     LC_CUDA(ctx, cudaMemsetAsync(&ctrl->status, 0, sizeof(int32_t), s));
     if (local) {
-        LC_CUDA(ctx, lc::launch_pcg_csr(sub_csr(op), a, w, ctrl, ctx->sms * 2, s));
+        // one block per SM: the local system is small and its barriers dominate
+        LC_CUDA(ctx, lc::launch_pcg_csr(sub_csr(op), a, w, ctrl, ctx->sms, s));
     } else if (op->kind == 0) {
         LC_CUDA(ctx, lc::launch_pcg_stencil(op->st, a, w, ctrl, op->pcg_grid_cap, s));
     } else {
@@ -347,6 +348,38 @@ const char *lc_error_string(int code) {
 const char *lc_last_error(const lc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int64_t lc_kernel_launch_count(void) { return (int64_t)lc::g_launches.load(std::memory_order_relaxed); }
+
+int lc_assemble_diffusion_2d(lc_ctx *ctx, const int32_t shape[2], const double *k, double dt, double *D,
+                             double *Tx, double *Ty, void *stream) {
+    if (!ctx) return LC_ERR_INVALID_ARG;
+    if (!shape || !k || !D || !Tx || !Ty) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    if (shape[0] <= 0 || shape[1] <= 0) return fail(ctx, LC_ERR_INVALID_ARG, "shape must be positive");
+    if ((int64_t)shape[0] * shape[1] >= (int64_t)INT32_MAX) return fail(ctx, LC_ERR_TOO_LARGE, "N does not fit int32");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, LC_ERR_INVALID_ARG, "dt must be finite and > 0");
+    LC_CUDA(ctx, cudaSetDevice(ctx->device));
+    LC_CUDA(ctx, lc::launch_assemble_2d(shape[0], shape[1], k, dt, D, Tx, Ty, (cudaStream_t)stream));
+    return LC_OK;
+}
+
+int lc_op_refresh(lc_op *op, void *stream) {
+    if (!op) return LC_ERR_INVALID_ARG;
+    if (op->kind != 0) return LC_OK;
+    LC_CUDA(op->ctx, cudaSetDevice(op->ctx->device));
+    LC_CUDA(op->ctx, lc::launch_dinv_stencil(op->n, op->st.D, op->dinv, op->D32, op->st.Tx, op->st.Ty, op->st.Tz,
+                                             op->Tx32, op->Ty32, op->Tz32, op->dinv32, (cudaStream_t)stream));
+    return LC_OK;
+}
+
+int lc_adjoint_grad_k_2d(lc_ctx *ctx, const int32_t shape[2], const double *k, const double *x, const double *lam,
+                         double *dk, void *stream) {
+    if (!ctx) return LC_ERR_INVALID_ARG;
+    if (!shape || !k || !x || !lam || !dk) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    if (shape[0] <= 0 || shape[1] <= 0) return fail(ctx, LC_ERR_INVALID_ARG, "shape must be positive");
+    if ((int64_t)shape[0] * shape[1] >= (int64_t)INT32_MAX) return fail(ctx, LC_ERR_TOO_LARGE, "N does not fit int32");
+    LC_CUDA(ctx, cudaSetDevice(ctx->device));
+    LC_CUDA(ctx, lc::launch_adjoint_grad_k_2d(shape[0], shape[1], k, x, lam, dk, (cudaStream_t)stream));
+    return LC_OK;
+}
 
 int lc_op_set_tuning(lc_op *op, const char *key, int32_t value) {
     if (!op || !key) return LC_ERR_INVALID_ARG;

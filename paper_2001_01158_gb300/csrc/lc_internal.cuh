@@ -216,6 +216,12 @@ struct Launch {
 // Accounting of kernel launches (lc_kernel_launch_count).
 void note_launches(int n);
 
+// Operator assembly and adjoint gradient (lc_adjoint.cu)
+cudaError_t launch_assemble_2d(int nx, int ny, const double *k, double dt, double *D, double *Tx, double *Ty,
+                               cudaStream_t s);
+cudaError_t launch_adjoint_grad_k_2d(int nx, int ny, const double *k, const double *x, const double *lam, double *dk,
+                                     cudaStream_t s);
+
 // Launchers (one translation unit each).  All return cudaError_t of the
 // last launch; argument validation happens in lc_api.cu.
 cudaError_t launch_residual_stencil(const Stencil &op, const double *b, const double *x, double *r,

@@ -1,0 +1,101 @@
+"""The differentiable solve: operator assembly from conductivity, and the
+adjoint gradients dL/dk, dL/db through torch.autograd, against central
+finite differences (32x32) and against the oracle's FP64 gradient (1024^2).
+The oracle side computes its own states and adjoints with its own solver."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_2001_01158_gb300 as lcg
+from paper_2001_01158_gb300.autograd import diffusion_solve
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+
+
+def cu(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+@pytest.mark.parametrize("ny,nx,dt", [(32, 32, 1.0), (7, 40, 0.5), (1, 9, 2.0), (33, 1, 1.0), (64, 96, 0.25)])
+def test_assembly_matches_generator_bit_for_bit(ny, nx, dt):
+    lcg.build()
+    ctx = lcg.Context(0)
+    k = np.exp(np.random.default_rng(ny * nx).uniform(-2, 3, (ny, nx)))
+    ref = gen.operator_2d(k, dt)
+    D, Tx, Ty = (torch.empty(nx * ny, dtype=torch.float64, device=DEV) for _ in range(3))
+    import ctypes as C
+    sh = (C.c_int32 * 2)(nx, ny)
+    ctx.check(lcg.lib().lc_assemble_diffusion_2d(ctx.h, sh, C.c_void_p(cu(k).data_ptr()), dt,
+                                                 C.c_void_p(D.data_ptr()), C.c_void_p(Tx.data_ptr()),
+                                                 C.c_void_p(Ty.data_ptr()), None))
+    torch.cuda.synchronize()
+    for got, want in ((D, ref.D), (Tx, ref.Tx), (Ty, ref.Ty)):
+        assert np.array_equal(got.cpu().numpy().view(np.int64), np.ascontiguousarray(want).view(np.int64))
+
+
+def _loss(k, b, xt, params):
+    x = diffusion_solve(k, b, None, params)
+    return ((x - xt) ** 2).sum()
+
+
+def test_adjoint_gradient_matches_central_differences():
+    lcg.build()
+    d = gen.cfg5_adjoint(seed=1, n=32)
+    params = lcg.default_params(tol=1e-13)
+    k = cu(d["k"]).requires_grad_(True)
+    b = cu(d["b"].reshape(32, 32)).requires_grad_(True)
+    with torch.no_grad():
+        xt = diffusion_solve(cu(d["k_target"]), b.detach(), None, params)
+    L = _loss(k, b, xt, params)
+    L.backward()
+    dk, db = k.grad.detach().clone(), b.grad.detach().clone()
+    rng = np.random.default_rng(0)
+    cells = [(0, 0), (31, 31), (0, 17), (15, 16)] + [tuple(c) for c in rng.integers(0, 32, (4, 2))]
+    with torch.no_grad():
+        for (iy, ix) in cells:
+            h = 1e-5 * float(k[iy, ix])
+            kp, km = k.detach().clone(), k.detach().clone()
+            kp[iy, ix] += h
+            km[iy, ix] -= h
+            fd = (float(_loss(kp, b.detach(), xt, params)) - float(_loss(km, b.detach(), xt, params))) / (2 * h)
+            assert float(dk[iy, ix]) == pytest.approx(fd, rel=2e-5, abs=1e-10)
+        for (iy, ix) in cells[:3]:
+            h = 1e-5
+            bp, bm = b.detach().clone(), b.detach().clone()
+            bp[iy, ix] += h
+            bm[iy, ix] -= h
+            fd = (float(_loss(k.detach(), bp, xt, params)) - float(_loss(k.detach(), bm, xt, params))) / (2 * h)
+            assert float(db[iy, ix]) == pytest.approx(fd, rel=2e-5, abs=1e-10)
+
+
+def test_adjoint_gradient_matches_oracle_at_1024():
+    lcg.build()
+    n = 1024
+    d = gen.cfg5_adjoint(seed=0, n=n)
+    tol = 1e-12
+    # oracle: its own operator, states, adjoint and gradient (plain FP64 CPU)
+    A = oracle.from_stencil(gen.operator_2d(d["k"], d["dt"]))
+    At = oracle.from_stencil(gen.operator_2d(d["k_target"], d["dt"]))
+    z = np.zeros(n * n)
+    x_o, st1, _, _ = oracle.pcg(A, d["b"], z, tol=tol)
+    xt_o, st2, _, _ = oracle.pcg(At, d["b"], z, tol=tol)
+    lam_o, st3, _, _ = oracle.pcg(A, 2.0 * (x_o - xt_o), z, tol=tol)
+    assert st1 == st2 == st3 == oracle.OK
+    dk_o = oracle.adjoint_grad_k_2d(n, n, d["k"].ravel(), x_o, lam_o)
+    # GPU through autograd
+    params = lcg.default_params(tol=tol)
+    k = cu(d["k"]).requires_grad_(True)
+    b = cu(d["b"].reshape(n, n)).requires_grad_(True)
+    with torch.no_grad():
+        xt = diffusion_solve(cu(d["k_target"]), b.detach(), None, params)
+    L = _loss(k, b, xt, params)
+    L.backward()
+    dk = k.grad.detach().cpu().numpy().ravel()
+    db = b.grad.detach().cpu().numpy().ravel()
+    assert np.linalg.norm(dk - dk_o) <= 1e-6 * np.linalg.norm(dk_o)
+    assert np.linalg.norm(db - lam_o) <= 1e-6 * np.linalg.norm(lam_o)
+    assert float(L.detach()) == pytest.approx(float(((x_o - xt_o) ** 2).sum()), rel=1e-8)
