@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--impl", choices=["lc", "reference"], default="lc")
     ap.add_argument("--n", type=int, default=2048, help="grid side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched workload")
     return ap.parse_args()
 
 
@@ -424,6 +425,8 @@ def run_gpu(args, rank, ws, local):
         "speedup_vs_global_pcg": ms_glob / ms_res,
         "speedup_mixed_vs_global_pcg": ms_glob / ms_mixed,
     }
+    if not args.no_batched:
+        res["batched_512"] = run_batched(args, rank, dev, ws)
     if rank == 0 and not args.no_cpu_baseline:
         from oracle.build import build_oracle
         build_oracle()
@@ -431,6 +434,71 @@ def run_gpu(args, rank, ws, local):
         res["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(res), flush=True)
+
+
+def run_batched(args, rank, dev, ws):
+    """512 independent 2D systems (sides log-uniform in [64, 512], local
+    sources covering 1-30 % of cells): all of Alg 1 in one autotuned,
+    graph-captured launch (FP32 inner CG, FP64 refinement, relres 1e-8),
+    against the same systems solved one after another by global FP64 PCG."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2001_01158_gb300 as lcg
+    from paper_2001_01158_gb300.autotune import tune_batch
+
+    items = gen.cfg4_batch(seed=rank)
+    T = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)  # noqa: E731
+    ctx = lcg.Context(dev.index)
+    systems = [(d["op"].shape[0], d["op"].shape[1], T(d["op"].D), T(d["op"].Tx), T(d["op"].Ty)) for d in items]
+    batch = lcg.Batch(ctx, systems)
+    b = T(np.concatenate([d["b"] for d in items]))
+    x0 = T(np.concatenate([d["x0"] for d in items]))
+    prm = lcg.batch_params(beta=1e-3, layers=2, tol=1e-8, inner_tol=1e-4)
+    cfg = tune_batch(batch, b, x0, prm)
+    x = x0.clone()
+    batch.capture(b, x, prm)
+    reps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        x.copy_(x0)
+        batch.replay()
+    torch.cuda.synchronize(dev)
+    ts = []
+    for _ in range(reps):
+        x.copy_(x0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        batch.replay()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ts.append(e0.elapsed_time(e1))
+    st = batch.stats()
+    ms_batched = statistics.median(ts)
+    # the same systems, one at a time, by the global FP64 PCG
+    sp = lcg.SolveParams(1e-8, 200000, lcg.PREC_FP64, 0.0, 0)
+    ops = [lcg.StencilOperator(ctx, (s[0], s[1], 1), s[2], s[3], s[4]) for s in systems]
+    xs = [T(d["x0"]) for d in items]
+    bs = [T(d["b"]) for d in items]
+    for op_, b_, x_ in zip(ops[:8], bs[:8], xs[:8]):   # warm-up
+        lcg.pcg_solve(ctx, op_, b_, x_.clone(), sp)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for op_, b_, x_ in zip(ops, bs, xs):
+        lcg.pcg_solve(ctx, op_, b_, x_, sp)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms_seq = e0.elapsed_time(e1)
+    cells = batch.cells
+    return {"systems": batch.nsys, "cells": cells, "ms_per_batch": ms_batched,
+            "ms_per_system": ms_batched / batch.nsys, "cells_per_s": cells / (ms_batched * 1e-3),
+            "sequential_global_fp64_ms": ms_seq, "speedup_vs_sequential_global_fp64": ms_seq / ms_batched,
+            "eta_mean": statistics.mean(s["eta"] for s in st),
+            "relres_max": max(s["relres_final"] for s in st), "all_converged": all(s["status"] == 0 for s in st),
+            "inner_iterations_mean": statistics.mean(s["it_global"] for s in st),
+            "autotuned": {"block": cfg["block"], "ctas_per_sm": cfg["ctas_per_sm"]},
+            "launch": "one persistent kernel, CUDA-graph replay"}
 
 
 def main():

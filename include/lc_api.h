@@ -218,6 +218,55 @@ LC_EXPORT int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double
 LC_EXPORT int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const double *b, double *x,
                                const lc_params *p, lc_stats *stats, void *stream);
 
+/* ---- many independent systems in one launch -----------------------------------
+ *
+ * Alg 1 on a batch of independent 2D 5-point systems of uneven sizes (each
+ * system its own nx x ny grid), all solved by ONE persistent kernel launch in
+ * which each CTA takes systems from a device work queue (largest first) and
+ * runs the whole method on one system with block-level synchronisation:
+ * residual marking (relative threshold, layer dilation), extraction,
+ * local solve and the check/global solve, both as FP32 Jacobi-CG inside
+ * FP64 iterative refinement.  The launch can be captured once into a CUDA
+ * graph and replayed.  Masks and subsystems are bit-identical to
+ * lc_mark_residual / lc_extract on each system; the solves reach the FP64
+ * relative residual `global.tol`. */
+typedef struct lc_batch lc_batch;
+
+/* nx[nsys], ny[nsys] are HOST arrays; D, Tx, Ty are DEVICE arrays holding
+ * the systems' stencil coefficients concatenated in system order (system s
+ * occupies cells [sum_{t<s} nx_t ny_t, ...) in the layout of
+ * lc_op_create_stencil).  Allocates the batch's workspace (about 160 bytes
+ * per cell) and FP32 copies of the coefficients; synchronises the device.
+ * The caller keeps D, Tx, Ty alive and unchanged while the batch is used. */
+LC_EXPORT int lc_batch_create(lc_ctx *ctx, lc_batch **batch, int32_t nsys, const int32_t *nx, const int32_t *ny,
+                              const double *D, const double *Tx, const double *Ty);
+LC_EXPORT int lc_batch_destroy(lc_batch *batch);
+
+/* Enqueue one batched solve: b (device, concatenated) and x (device; in x0,
+ * out x).  p must ask for residual marking with LC_THR_REL_MAX, LC_EXP_NONE
+ * or LC_EXP_DILATE, and LC_PREC_MIXED for both solves (otherwise
+ * LC_ERR_UNSUPPORTED); global.max_iter caps each inner FP32 solve,
+ * global.max_outer the refinement sweeps, local.tol is relative to the
+ * subsystem's right-hand side. */
+LC_EXPORT int lc_batch_solve(lc_ctx *ctx, lc_batch *batch, const double *b, double *x, const lc_params *p,
+                             void *stream);
+
+/* Capture the same work (for these b, x and p) into a CUDA graph held by the
+ * batch, on a stream of the library's own; lc_batch_replay launches it on
+ * `stream`.  A new capture replaces the previous graph. */
+LC_EXPORT int lc_batch_capture(lc_ctx *ctx, lc_batch *batch, const double *b, double *x, const lc_params *p);
+LC_EXPORT int lc_batch_replay(lc_batch *batch, void *stream);
+
+/* Waits for `stream`, then fills per_system[nsys] (host): status, n, K, nnzB,
+ * it_local, it_global (FP32 inner iterations), restarts (= refinement sweeps
+ * of the global solve), early_exit, tau, eta, relres_tilde, relres_final.
+ * Returns the first non-OK system status, else LC_OK. */
+LC_EXPORT int lc_batch_stats(lc_batch *batch, lc_stats *per_system, void *stream);
+
+/* Launch-shape knobs (for the autotuner): "block" = 256 | 512 | 1024 threads
+ * per CTA (default 512); "ctas_per_sm" = 0 (as many as fit) .. 32. */
+LC_EXPORT int lc_batch_set_tuning(lc_batch *batch, const char *key, int32_t value);
+
 /* ---- operators from conductivity, and the adjoint -----------------------------
  *
  * 2D backward-Euler diffusion on an nx x ny grid (grid units):

@@ -325,3 +325,76 @@ def mark_residual_stencil_noalloc(shape, D, Tx, Ty, Tz, b, x0, params: MarkParam
             if rc == LC_ERR_TOO_LARGE else ""
         raise LcError(rc, L.lc_error_string(rc).decode() + extra)
     return rc
+
+
+class Batch:
+    """lc_batch: many independent 2D systems solved by Alg 1 in one launch.
+
+    `systems` is a list of (nx, ny, D, Tx, Ty) with device FP64 arrays; they
+    are concatenated into one set of coefficient arrays owned by this object."""
+
+    def __init__(self, ctx: Context, systems):
+        L = lib()
+        vp, i32 = C.c_void_p, C.c_int32
+        L.lc_batch_create.argtypes = [vp, C.POINTER(vp), i32, C.POINTER(i32), C.POINTER(i32), vp, vp, vp]
+        L.lc_batch_destroy.argtypes = [vp]
+        L.lc_batch_solve.argtypes = [vp, vp, vp, vp, C.POINTER(Params), vp]
+        L.lc_batch_capture.argtypes = [vp, vp, vp, vp, C.POINTER(Params)]
+        L.lc_batch_replay.argtypes = [vp, vp]
+        L.lc_batch_stats.argtypes = [vp, C.POINTER(Stats), vp]
+        L.lc_batch_set_tuning.argtypes = [vp, C.c_char_p, i32]
+        self.ctx = ctx
+        self.nx = [int(s[0]) for s in systems]
+        self.ny = [int(s[1]) for s in systems]
+        self.sizes = [a * b for a, b in zip(self.nx, self.ny)]
+        self.offsets = [0]
+        for n in self.sizes:
+            self.offsets.append(self.offsets[-1] + n)
+        self.cells = self.offsets[-1]
+        self.D = torch.cat([s[2].reshape(-1) for s in systems]).contiguous()
+        self.Tx = torch.cat([s[3].reshape(-1) for s in systems]).contiguous()
+        self.Ty = torch.cat([s[4].reshape(-1) for s in systems]).contiguous()
+        torch.cuda.current_stream().synchronize()
+        nsys = len(systems)
+        h = C.c_void_p()
+        ctx.check(L.lc_batch_create(ctx.h, C.byref(h), nsys, (i32 * nsys)(*self.nx), (i32 * nsys)(*self.ny),
+                                    _ptr(self.D, torch.float64, "D"), _ptr(self.Tx, torch.float64, "Tx"),
+                                    _ptr(self.Ty, torch.float64, "Ty")))
+        self.h = h
+        self.nsys = nsys
+
+    def solve(self, b, x, params: Params, stream=None):
+        return self.ctx.check(lib().lc_batch_solve(self.ctx.h, self.h, _ptr(b, torch.float64, "b"),
+                                                   _ptr(x, torch.float64, "x"), C.byref(params), _stream(stream)))
+
+    def capture(self, b, x, params: Params):
+        """Capture the batched solve for these b, x, params into a CUDA graph."""
+        self._captured = (b, x)
+        return self.ctx.check(lib().lc_batch_capture(self.ctx.h, self.h, _ptr(b, torch.float64, "b"),
+                                                     _ptr(x, torch.float64, "x"), C.byref(params)))
+
+    def replay(self, stream=None):
+        return self.ctx.check(lib().lc_batch_replay(self.h, _stream(stream)))
+
+    def stats(self, stream=None, allow_not_converged=False):
+        st = (Stats * self.nsys)()
+        allow = (LC_ERR_NOT_CONVERGED, LC_ERR_BREAKDOWN) if allow_not_converged else ()
+        self.ctx.check(lib().lc_batch_stats(self.h, st, _stream(stream)), allow)
+        return [s.as_dict() for s in st]
+
+    def set_tuning(self, key: str, value: int):
+        return self.ctx.check(lib().lc_batch_set_tuning(self.h, key.encode(), int(value)))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.lc_batch_destroy(self.h)
+            self.h = None
+
+
+def batch_params(beta=1e-3, layers=2, tol=1e-8, tol_local=None, inner_tol=1e-4, max_outer=30,
+                 max_inner=20000) -> Params:
+    """Parameters accepted by the batched solve (relative threshold, layer
+    dilation, mixed precision)."""
+    return default_params(MARK_RESIDUAL, THR_REL_MAX, beta, EXP_DILATE if layers else EXP_NONE, layers, tol=tol,
+                          tol_local=tol_local, max_iter=max_inner, precision=PREC_MIXED, inner_tol=inner_tol,
+                          max_outer=max_outer)

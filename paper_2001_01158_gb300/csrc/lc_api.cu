@@ -8,8 +8,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
+#include <vector>
 
 #include <atomic>
 
@@ -379,6 +381,254 @@ int lc_adjoint_grad_k_2d(lc_ctx *ctx, const int32_t shape[2], const double *k, c
     LC_CUDA(ctx, cudaSetDevice(ctx->device));
     LC_CUDA(ctx, lc::launch_adjoint_grad_k_2d(shape[0], shape[1], k, x, lam, dk, (cudaStream_t)stream));
     return LC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batched Alg 1
+
+struct lc_batch {
+    lc_ctx *ctx = nullptr;
+    int32_t nsys = 0;
+    int64_t cells = 0;
+    void *arena = nullptr;
+    lc::BatchLaunch L{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int32_t> nx, ny;
+};
+
+namespace {
+
+void batch_carve(lc_batch *bt, Carver &c) {
+    const size_t T = (size_t)bt->cells, S = (size_t)bt->nsys;
+    lc::BatchView &v = bt->L.v;
+    v.nx = c.take<int32_t>(S);
+    v.ny = c.take<int32_t>(S);
+    v.off = c.take<int64_t>(S);
+    v.order = c.take<int32_t>(S);
+    v.next = c.take<int32_t>(1);
+    v.stat_i = c.take<int32_t>(8 * S);
+    v.stat_d = c.take<double>(4 * S);
+    v.D32 = c.take<float>(T);
+    v.Tx32 = c.take<float>(T);
+    v.Ty32 = c.take<float>(T);
+    v.dinv32 = c.take<float>(T);
+    v.r = c.take<double>(T);
+    v.m0 = c.take<uint8_t>(T);
+    v.m1 = c.take<uint8_t>(T);
+    v.g2l = c.take<int32_t>(T);
+    v.l2g = c.take<int32_t>(T);
+    v.rowptr = c.take<int32_t>(T + S);
+    v.col = c.take<int32_t>(5 * T);
+    v.val = c.take<double>(5 * T);
+    v.val32 = c.take<float>(5 * T);
+    v.rhs = c.take<double>(T);
+    v.xl = c.take<double>(T);
+    v.dl32 = c.take<float>(T);
+    v.r32 = c.take<float>(T);
+    v.z32 = c.take<float>(T);
+    v.p32 = c.take<float>(T);
+    v.q32 = c.take<float>(T);
+    v.d32 = c.take<float>(T);
+}
+
+int batch_params(lc_ctx *ctx, const lc_params *p, lc::BatchParams &bp) {
+    if (!p) return fail(ctx, LC_ERR_INVALID_ARG, "null parameters");
+    if (p->mark_mode != LC_MARK_RESIDUAL || p->mark.thr_mode != LC_THR_REL_MAX ||
+        (p->mark.exp_mode != LC_EXP_NONE && p->mark.exp_mode != LC_EXP_DILATE) ||
+        p->global.precision != LC_PREC_MIXED || p->local.precision != LC_PREC_MIXED || p->gs_sweeps != 0)
+        return fail(ctx, LC_ERR_UNSUPPORTED,
+                    "batched solve: residual marking with the relative threshold and dilation, mixed precision");
+    if (!(p->mark.thr_param >= 0.0) || !std::isfinite(p->mark.thr_param) || p->mark.exp_rounds < 0 ||
+        p->mark.exp_rounds > lc::kMaxExpRounds)
+        return fail(ctx, LC_ERR_INVALID_ARG, "bad marking parameters");
+    int rc;
+    if ((rc = check_solve_params(ctx, &p->global)) || (rc = check_solve_params(ctx, &p->local))) return rc;
+    bp.beta = p->mark.thr_param == 0.0 ? 0.0 : p->mark.thr_param;
+    bp.layers = p->mark.exp_mode == LC_EXP_DILATE ? p->mark.exp_rounds : 0;
+    bp.tol = p->global.tol;
+    bp.tol_local = p->local.tol;
+    bp.inner_tol = p->global.inner_tol;
+    bp.max_outer = p->global.max_outer;
+    bp.max_inner = p->global.max_iter;
+    return LC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lc_batch_create(lc_ctx *ctx, lc_batch **out, int32_t nsys, const int32_t *nx, const int32_t *ny, const double *D,
+                    const double *Tx, const double *Ty) {
+    if (!ctx || !out) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nsys <= 0 || !nx || !ny || !D || !Tx || !Ty) return fail(ctx, LC_ERR_INVALID_ARG, "bad batch description");
+    int64_t cells = 0;
+    std::vector<int64_t> off(nsys);
+    for (int32_t s = 0; s < nsys; ++s) {
+        if (nx[s] <= 0 || ny[s] <= 0) return fail(ctx, LC_ERR_INVALID_ARG, "system %d has a non-positive shape", s);
+        off[s] = cells;
+        cells += (int64_t)nx[s] * ny[s];
+    }
+    if (5 * cells + nsys >= (int64_t)INT32_MAX || (int64_t)nx[0] * ny[0] >= (int64_t)INT32_MAX)
+        return fail(ctx, LC_ERR_TOO_LARGE, "batch of %lld cells exceeds int32 indexing", (long long)cells);
+    LC_CUDA(ctx, cudaSetDevice(ctx->device));
+    lc_batch *bt = new (std::nothrow) lc_batch;
+    if (!bt) return LC_ERR_NO_MEMORY;
+    bt->ctx = ctx;
+    bt->nsys = nsys;
+    bt->cells = cells;
+    bt->nx.assign(nx, nx + nsys);
+    bt->ny.assign(ny, ny + nsys);
+    Carver probe;
+    batch_carve(bt, probe);
+    if (cudaMalloc(&bt->arena, probe.off) != cudaSuccess) {
+        cudaGetLastError();
+        delete bt;
+        return fail(ctx, LC_ERR_NO_MEMORY, "batch workspace of %zu bytes", probe.off);
+    }
+    Carver real;
+    real.base = static_cast<char *>(bt->arena);
+    batch_carve(bt, real);
+    lc::BatchView &v = bt->L.v;
+    v.nsys = nsys;
+    v.D = D; v.Tx = Tx; v.Ty = Ty;
+    std::vector<int32_t> order(nsys);
+    for (int32_t s = 0; s < nsys; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return (int64_t)nx[a] * ny[a] > (int64_t)nx[b] * ny[b];
+    });
+    cudaError_t e = cudaMemcpy(const_cast<int32_t *>(v.nx), nx, sizeof(int32_t) * nsys, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(const_cast<int32_t *>(v.ny), ny, sizeof(int32_t) * nsys, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(const_cast<int64_t *>(v.off), off.data(), sizeof(int64_t) * nsys, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(const_cast<int32_t *>(v.order), order.data(), sizeof(int32_t) * nsys, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = lc::launch_batch_f32(cells, D, Tx, Ty, const_cast<float *>(v.D32), const_cast<float *>(v.Tx32),
+                                 const_cast<float *>(v.Ty32), const_cast<float *>(v.dinv32), 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(ctx, e, "batch set-up");
+        lc_batch_destroy(bt);
+        return rc;
+    }
+    bt->L.block = 512;
+    bt->L.ctas_per_sm = 0;
+    *out = bt;
+    return LC_OK;
+}
+
+int lc_batch_destroy(lc_batch *bt) {
+    if (!bt) return LC_OK;
+    if (bt->ctx) cudaSetDevice(bt->ctx->device);
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    if (bt->arena) cudaFree(bt->arena);
+    delete bt;
+    return LC_OK;
+}
+
+static int batch_enqueue(lc_batch *bt, cudaStream_t s) {
+    lc_ctx *ctx = bt->ctx;
+    LC_CUDA(ctx, cudaMemsetAsync(bt->L.v.next, 0, sizeof(int32_t), s));
+    LC_CUDA(ctx, lc::launch_batched(&bt->L, ctx->sms, s));
+    return LC_OK;
+}
+
+int lc_batch_solve(lc_ctx *ctx, lc_batch *bt, const double *b, double *x, const lc_params *p, void *stream) {
+    if (!ctx || !bt || bt->ctx != ctx) return LC_ERR_INVALID_ARG;
+    if (!b || !x) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    int rc;
+    if ((rc = batch_params(ctx, p, bt->L.p))) return rc;
+    LC_CUDA(ctx, cudaSetDevice(ctx->device));
+    bt->L.v.b = b;
+    bt->L.v.x = x;
+    return batch_enqueue(bt, (cudaStream_t)stream);
+}
+
+int lc_batch_capture(lc_ctx *ctx, lc_batch *bt, const double *b, double *x, const lc_params *p) {
+    if (!ctx || !bt || bt->ctx != ctx) return LC_ERR_INVALID_ARG;
+    if (!b || !x) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    int rc;
+    if ((rc = batch_params(ctx, p, bt->L.p))) return rc;
+    LC_CUDA(ctx, cudaSetDevice(ctx->device));
+    bt->L.v.b = b;
+    bt->L.v.x = x;
+    if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
+    if (bt->graph) { cudaGraphDestroy(bt->graph); bt->graph = nullptr; }
+    cudaStream_t cs;
+    LC_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = batch_enqueue(bt, cs);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (!rc && e2 == cudaSuccess) {
+            bt->graph = g;
+            e = cudaGraphInstantiate(&bt->exec, g, 0);
+        } else {
+            e = e2;
+            if (g) cudaGraphDestroy(g);
+        }
+    }
+    cudaStreamDestroy(cs);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch graph capture");
+    return LC_OK;
+}
+
+int lc_batch_replay(lc_batch *bt, void *stream) {
+    if (!bt) return LC_ERR_INVALID_ARG;
+    if (!bt->exec) return fail(bt->ctx, LC_ERR_INVALID_ARG, "no captured graph (call lc_batch_capture first)");
+    LC_CUDA(bt->ctx, cudaSetDevice(bt->ctx->device));
+    LC_CUDA(bt->ctx, cudaGraphLaunch(bt->exec, (cudaStream_t)stream));
+    lc::note_launches(1);
+    return LC_OK;
+}
+
+int lc_batch_stats(lc_batch *bt, lc_stats *per_system, void *stream) {
+    if (!bt || !per_system) return LC_ERR_INVALID_ARG;
+    LC_CUDA(bt->ctx, cudaSetDevice(bt->ctx->device));
+    LC_CUDA(bt->ctx, cudaStreamSynchronize((cudaStream_t)stream));
+    std::vector<int32_t> si(8 * (size_t)bt->nsys);
+    std::vector<double> sd(4 * (size_t)bt->nsys);
+    LC_CUDA(bt->ctx, cudaMemcpy(si.data(), bt->L.v.stat_i, sizeof(int32_t) * si.size(), cudaMemcpyDeviceToHost));
+    LC_CUDA(bt->ctx, cudaMemcpy(sd.data(), bt->L.v.stat_d, sizeof(double) * sd.size(), cudaMemcpyDeviceToHost));
+    int worst = LC_OK;
+    for (int32_t s = 0; s < bt->nsys; ++s) {
+        lc_stats &st = per_system[s];
+        memset(&st, 0, sizeof st);
+        st.status = si[8 * s + 0];
+        st.n = bt->nx[s] * bt->ny[s];
+        st.K = si[8 * s + 1];
+        st.nnzB = si[8 * s + 2];
+        st.it_local = si[8 * s + 3];
+        st.it_global = si[8 * s + 4];
+        st.restarts = si[8 * s + 6];
+        st.early_exit = si[8 * s + 7];
+        st.tau = sd[4 * s + 0];
+        st.relres_tilde = sd[4 * s + 1];
+        st.relres_final = sd[4 * s + 2];
+        st.eta = st.n ? (double)st.K / st.n : 0.0;
+        if (st.status != LC_OK && worst == LC_OK) worst = st.status;
+    }
+    return worst;
+}
+
+int lc_batch_set_tuning(lc_batch *bt, const char *key, int32_t value) {
+    if (!bt || !key) return LC_ERR_INVALID_ARG;
+    if (!strcmp(key, "block")) {
+        if (value != 256 && value != 512 && value != 1024)
+            return fail(bt->ctx, LC_ERR_INVALID_ARG, "block must be 256, 512 or 1024");
+        bt->L.block = value;
+        return LC_OK;
+    }
+    if (!strcmp(key, "ctas_per_sm")) {
+        if (value < 0 || value > 32) return fail(bt->ctx, LC_ERR_INVALID_ARG, "ctas_per_sm must be 0..32");
+        bt->L.ctas_per_sm = value;
+        return LC_OK;
+    }
+    return fail(bt->ctx, LC_ERR_INVALID_ARG, "unknown tuning key '%s'", key);
 }
 
 int lc_op_set_tuning(lc_op *op, const char *key, int32_t value) {

@@ -216,6 +216,50 @@ struct Launch {
 // Accounting of kernel launches (lc_kernel_launch_count).
 void note_launches(int n);
 
+// Batched Alg 1 (lc_batched.cu): many independent 2D systems in one launch
+struct BatchView {
+    int nsys;
+    const int32_t *nx, *ny;
+    const int64_t *off;        // cell offset of each system
+    const int32_t *order;      // processing order (largest first)
+    const double *D, *Tx, *Ty; // FP64 operator (caller's, concatenated)
+    const float *D32, *Tx32, *Ty32, *dinv32;   // FP32 copies (library's)
+    const double *b;
+    double *x;
+    // workspace, concatenated like the cells (capacities: cells, 5 x cells for B)
+    double *r;                 // FP64 residual
+    uint8_t *m0, *m1;          // masks
+    int32_t *g2l, *l2g, *rowptr;   // rowptr: cells + nsys (offset off[s] + s)
+    int32_t *col;              // 5 x cells (offset 5 off[s])
+    double *val;
+    float *val32;
+    double *rhs, *xl;
+    float *dl32;               // 1/diag(B) in FP32
+    float *r32, *z32, *p32, *q32, *d32;
+    int32_t *next;             // work-queue counter
+    int32_t *stat_i;           // [nsys][8]: status, K, nnzB, it_local, it_global, outer_local, outer_global, early
+    double *stat_d;            // [nsys][4]: tau, relres_tilde, relres_final, bnorm
+};
+
+struct BatchParams {
+    double beta;
+    int layers;
+    double tol, tol_local, inner_tol;
+    int max_outer, max_inner;
+};
+
+struct BatchLaunch {
+    BatchView v;
+    BatchParams p;
+    int block;       // 256, 512 or 1024
+    int ctas_per_sm; // 0 = as many as fit
+};
+
+cudaError_t launch_batched(const void *launch_desc, int sms, cudaStream_t s);
+cudaError_t launch_batch_f32(int64_t n, const double *D, const double *Tx, const double *Ty, float *D32, float *Tx32,
+                             float *Ty32, float *dinv32, cudaStream_t s);
+int batched_occupancy(int block);
+
 // Operator assembly and adjoint gradient (lc_adjoint.cu)
 cudaError_t launch_assemble_2d(int nx, int ny, const double *k, double dt, double *D, double *Tx, double *Ty,
                                cudaStream_t s);

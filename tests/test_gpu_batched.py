@@ -1,0 +1,112 @@
+"""Batched Alg 1 (many uneven systems in one launch, CUDA graph, autotuner)
+against the oracle, system by system: the local domain's size K and nnz(B)
+equal the oracle's (the marking and extraction are bit-identical), each
+solution reaches the FP64 relative residual, and its error against the
+oracle's FP64 solution is stated and bounded."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_2001_01158_gb300 as lcg
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+
+
+def cu(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def make_batch(seed, sides):
+    rng = np.random.default_rng(seed)
+    items = []
+    for k, (nx, ny) in enumerate(sides):
+        d = gen.cfg1_heat2d(seed=int(rng.integers(1 << 30)), n=max(nx, ny), radius=max(1.0, 0.15 * min(nx, ny)))
+        if (nx, ny) != (d["op"].shape[0], d["op"].shape[1]):
+            # rectangular system: random operator, local source
+            op = gen.random_stencil_2d(int(rng.integers(1 << 30)), nx, ny)
+            x0 = 1.0 + 0.1 * rng.standard_normal(op.n)
+            src = np.zeros(op.n)
+            src[rng.choice(op.n, size=max(1, op.n // 30), replace=False)] = 1.0
+            d = {"op": op, "x0": x0, "b": gen.stencil_matvec(op, x0) + src}
+        items.append(d)
+    return items
+
+
+SIDES = [(64, 64), (8, 8), (1, 50), (37, 1), (129, 70), (200, 200), (33, 17), (96, 96), (5, 300), (150, 149),
+         (64, 65), (17, 33), (2, 2), (100, 3)]
+
+
+@pytest.fixture(scope="module")
+def setup():
+    lcg.build()
+    ctx = lcg.Context(0)
+    items = make_batch(7, SIDES)
+    systems = [(d["op"].shape[0], d["op"].shape[1], cu(d["op"].D), cu(d["op"].Tx), cu(d["op"].Ty)) for d in items]
+    batch = lcg.Batch(ctx, systems)
+    b = cu(np.concatenate([d["b"] for d in items]))
+    x0 = cu(np.concatenate([d["x0"] for d in items]))
+    return ctx, items, batch, b, x0
+
+
+@pytest.mark.parametrize("block", [256, 512, 1024])
+def test_batched_matches_oracle_per_system(setup, block):
+    ctx, items, batch, b, x0 = setup
+    tol = 1e-8
+    prm = lcg.batch_params(beta=1e-3, layers=2, tol=tol, inner_tol=1e-4)
+    batch.set_tuning("block", block)
+    x = x0.clone()
+    batch.solve(b, x, prm)
+    st = batch.stats()
+    xs = x.cpu().numpy()
+    for s, d in enumerate(items):
+        A = oracle.from_stencil(d["op"])
+        m = oracle.mark_residual(A, d["b"], d["x0"], oracle.THR_REL_MAX, 1e-3, oracle.EXP_DILATE, 2)
+        ex = oracle.extract(A, m["mask"], d["b"], d["x0"])
+        assert st[s]["K"] == m["K"] and st[s]["nnzB"] == len(ex["B"].col), s
+        assert st[s]["tau"] == m["tau"]
+        xg = xs[batch.offsets[s]:batch.offsets[s + 1]]
+        assert oracle.relres(A, d["b"], xg) <= tol, s
+        xr, _, _, _ = oracle.pcg(A, d["b"], d["x0"], tol=1e-13)
+        assert np.linalg.norm(xg - xr) <= 1e-6 * np.linalg.norm(xr), s
+
+
+def test_graph_replay_equals_direct_launch(setup):
+    ctx, items, batch, b, x0 = setup
+    prm = lcg.batch_params()
+    batch.set_tuning("block", 512)
+    x1 = x0.clone()
+    batch.solve(b, x1, prm)
+    torch.cuda.synchronize()
+    x2 = x0.clone()
+    batch.capture(b, x2, prm)
+    for _ in range(2):   # replays start from whatever x holds: reset it each time
+        x2.copy_(x0)
+        batch.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2)
+    assert all(s["status"] == 0 for s in batch.stats())
+
+
+def test_autotuner_picks_a_configuration(setup, tmp_path, monkeypatch):
+    from paper_2001_01158_gb300 import autotune
+    ctx, items, batch, b, x0 = setup
+    monkeypatch.setenv("LC_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    cfg = autotune.tune_batch(batch, b, x0, lcg.batch_params())
+    assert cfg["block"] in (256, 512, 1024) and len(cfg["candidates"]) == 9
+    again = autotune.tune_batch(batch, b, x0, lcg.batch_params())   # from the cache
+    assert again["block"] == cfg["block"] and again["ctas_per_sm"] == cfg["ctas_per_sm"]
+
+
+def test_batched_rejects_unsupported_parameters(setup):
+    ctx, items, batch, b, x0 = setup
+    x = x0.clone()
+    for p in [lcg.default_params(precision=lcg.PREC_FP64),
+              lcg.default_params(lcg.MARK_GRADIENT, precision=lcg.PREC_MIXED),
+              lcg.default_params(thr_mode=lcg.THR_EPS_NORMB, precision=lcg.PREC_MIXED)]:
+        with pytest.raises(lcg.LcError) as e:
+            batch.solve(b, x, p)
+        assert e.value.code == lcg.LC_ERR_UNSUPPORTED
