@@ -42,14 +42,21 @@ WORKLOAD = ("2D 2048x2048 5-point FP64 diffusion, 64 rectangles k in [1,1e3], Ga
             "8 cells/step, 20 backward-Euler steps; Alg 1 with residual marking (1e-3 max|r|, 2 layers), "
             "Jacobi-PCG to relres 1e-8")
 
-# Bytes the global PCG kernel must move per cell (2D FP64): set-up / true
-# residual pass reads b, x, D, Tx, Ty, dinv and writes r, z (64 B); each
-# iteration moves 120 B (phase A: z, p_old, D, Tx, Ty in, p, q out; phase B:
-# x, p, r, q, dinv in, x, r, z out).
+# Algorithmic bytes of a Jacobi-PCG iteration on the 2D FP64 operator, per
+# cell: set-up / true residual pass reads b, x, D, Tx, Ty, dinv and writes r, z
+# (64 B); each iteration moves 120 B (phase A: z, p_old, D, Tx, Ty in, p, q
+# out; phase B: x, p, r, q, dinv in, x, r, z out).  The kernel iterates on
+# the symmetrically scaled system D^-1/2 A D^-1/2 (unit diagonal: no D, no
+# dinv, z = r) and moves 100 B per cell and iteration (phase A: r, p_old, Tx,
+# Ty in, p, q out; phase B: x, p, r, q in, fl32(D) for the FP32 stopping norm,
+# x, r out); the roofline reports the algorithmic figure.
 SETUP_BYTES = 64
 ITER_BYTES = 120
-DP_SETUP = 7
-DP_ITER = 12
+IMPL_ITER_BYTES = 100
+# FP64 instructions the scaled kernel issues per cell: 9 per iteration (phase
+# A: 1 for p, 4 fma for q, 1 for p.q; phase B: x, r, r.r), 10 per residual pass
+DP_SETUP = 10
+DP_ITER = 9
 DP_PEAK_GOPS = 152 * 2 * 2.07   # FP64 FMA instructions per second, in G (nominal 1.25 TFLOP/s)
 
 
@@ -343,10 +350,8 @@ def run_gpu(args, rank, ws, local):
     if tr is not None:
         bpc_iter, bpc_setup = tr
         traffic = float(N * (bpc_iter * mean_it + (bpc_setup if math.isfinite(bpc_setup) else SETUP_BYTES) * 2))
-    # the same kernel seen from FP64 issue: 12 FP64 instructions per cell and
-    # iteration (phase A: 1 for p, 1 mul + 4 fma for q, 1 for p.q; phase B: x,
-    # r, z, r.z, r.r), 7 per cell and residual pass; peak = 152 SMs x 2 FP64
-    # FMA/clk x 2.07 GHz (the nominal 1.25 TFLOP/s)
+    # the same kernel seen from FP64 issue (DP_ITER, DP_SETUP); peak = 152 SMs
+    # x 2 FP64 FMA/clk x 2.07 GHz (the nominal 1.25 TFLOP/s)
     dp = sum(N * (DP_SETUP * (1 + (0 if s["early_exit"] else 1 + s["restarts"])) + DP_ITER * s["it_global"])
              for s in per_res)
     dp_achieved = dp / t_pcg / 1e9 if t_pcg > 0 else 0.0
@@ -390,12 +395,13 @@ def run_gpu(args, rank, ws, local):
                    "l2": "inputs larger than L2 (operator + 20 resident systems + PCG vectors > 1 GB)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "pcg_kernel<Op2DW<double,2>> (global Jacobi-PCG, FP64)",
-                     "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_cell_iter": ITER_BYTES},
+                     "kernel": "pcg_kernel<Op2DW<double,2,true>> (global Jacobi-PCG on D^-1/2 A D^-1/2, FP64)",
+                     "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_cell_iter": ITER_BYTES,
+                     "impl_bytes_per_cell_iter": IMPL_ITER_BYTES},
         "roofline_fp64_issue": {"bound": "alu", "achieved": dp_achieved, "peak": DP_PEAK_GOPS,
                                 "unit": "G FP64 instr/s", "frac": dp_achieved / DP_PEAK_GOPS,
                                 "alg_fp64_instr_per_cell_iter": DP_ITER,
-                                "note": "same kernel; ncu shows the FP64 pipe ~76% busy at ~49% DRAM throughput"},
+                                "note": "same kernel; ncu shows the FP64 pipe ~75% busy at ~50% DRAM throughput"},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": e2e_ms / total_sys, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * N,

@@ -310,6 +310,13 @@ LC_EXPORT int lc_adjoint_grad_k_2d(lc_ctx *ctx, const int32_t shape[2], const do
  *       PCG kernel, as the number of 256-thread blocks that must fit on an SM.
  *   "pcg_grid_cap"  0..4096 (default 0 = all that fit): blocks of the global
  *       PCG launch.
+ *   "pcg_scaled"    0 or 1 (default 1): 2-D FP64 solves iterate on the
+ *       symmetrically scaled system D^-1/2 A D^-1/2 (unit diagonal, so the
+ *       Jacobi preconditioner becomes the identity) and map back, which is
+ *       the same preconditioned iteration in exact arithmetic with fewer
+ *       FP64 instructions and bytes per iteration.  0 iterates on A with the
+ *       explicit Jacobi preconditioner.  The stopping test is the same in
+ *       both: ||b - A x||_2 / ||b||_2 <= tol on the unscaled system.
  * Unknown keys or out-of-range values return LC_ERR_INVALID_ARG. */
 LC_EXPORT int lc_op_set_tuning(lc_op *op, const char *key, int32_t value);
 LC_EXPORT int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value);

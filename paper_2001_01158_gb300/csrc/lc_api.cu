@@ -50,6 +50,10 @@ struct lc_op {
     // tuning knobs (lc_op_set_tuning)
     int pcg_minblocks = 3;   // register budget of the structured-grid PCG kernel
     int pcg_grid_cap = 0;    // blocks of the global PCG launch (0: as many as fit)
+    int pcg_scaled = 1;      // 2D FP64: iterate on D^-1/2 A D^-1/2 (fewer FP64 instructions)
+    double *sc = nullptr, *sq = nullptr, *Txh = nullptr, *Tyh = nullptr;
+    float *dn32 = nullptr;
+    int *dexp = nullptr;
 };
 
 namespace {
@@ -135,6 +139,14 @@ void carve(lc_op *op, Carver &c) {
         op->Ty32 = c.take<float>(n);
         op->Tz32 = op->st.dim == 3 ? c.take<float>(n) : nullptr;
         op->dinv32 = c.take<float>(n);
+        if (op->st.dim == 2) {
+            op->sc = c.take<double>(n);
+            op->sq = c.take<double>(n);
+            op->Txh = c.take<double>(n);
+            op->Tyh = c.take<double>(n);
+            op->dn32 = c.take<float>(n);
+            op->dexp = c.take<int>(1);
+        }
     }
 }
 
@@ -302,7 +314,8 @@ int check_solve_params(lc_ctx *ctx, const lc_solve_params *p) {
 
 int pcg_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_solve_params *p, lc::Ctrl *ctrl,
              bool local, cudaStream_t s) {
-    lc::PcgArgs a{b, x, p->tol, p->max_iter, 3, op->pcg_minblocks, p->precision, p->inner_tol, p->max_outer};
+    lc::PcgArgs a{b,           x,           p->tol,        p->max_iter,  3,
+                  op->pcg_minblocks, p->precision, p->inner_tol, p->max_outer, op->pcg_scaled};
     lc::PcgWork w = op->pw;
     LC_CUDA(ctx, cudaMemsetAsync(&ctrl->status, 0, sizeof(int32_t), s));
     if (local) {
@@ -369,6 +382,9 @@ int lc_op_refresh(lc_op *op, void *stream) {
     LC_CUDA(op->ctx, cudaSetDevice(op->ctx->device));
     LC_CUDA(op->ctx, lc::launch_dinv_stencil(op->n, op->st.D, op->dinv, op->D32, op->st.Tx, op->st.Ty, op->st.Tz,
                                              op->Tx32, op->Ty32, op->Tz32, op->dinv32, (cudaStream_t)stream));
+    if (op->st.sc)
+        LC_CUDA(op->ctx, lc::launch_scaling_2d(op->st, op->sc, op->sq, op->Txh, op->Tyh, op->dn32, op->dexp,
+                                               (cudaStream_t)stream));
     return LC_OK;
 }
 
@@ -643,6 +659,11 @@ int lc_op_set_tuning(lc_op *op, const char *key, int32_t value) {
         op->pcg_grid_cap = value;
         return LC_OK;
     }
+    if (!strcmp(key, "pcg_scaled")) {
+        if (value < 0 || value > 1) return fail(op->ctx, LC_ERR_INVALID_ARG, "pcg_scaled must be 0 or 1");
+        op->pcg_scaled = value;
+        return LC_OK;
+    }
     return fail(op->ctx, LC_ERR_INVALID_ARG, "unknown tuning key '%s'", key);
 }
 
@@ -650,6 +671,7 @@ int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value) {
     if (!op || !key || !value) return LC_ERR_INVALID_ARG;
     if (!strcmp(key, "pcg_minblocks")) { *value = op->pcg_minblocks; return LC_OK; }
     if (!strcmp(key, "pcg_grid_cap")) { *value = op->pcg_grid_cap; return LC_OK; }
+    if (!strcmp(key, "pcg_scaled")) { *value = op->pcg_scaled; return LC_OK; }
     return LC_ERR_INVALID_ARG;
 }
 
@@ -705,12 +727,16 @@ int lc_op_create_stencil(lc_ctx *ctx, lc_op **out, int32_t dim, const int32_t sh
     op->st.dinv = op->dinv;
     op->st.D32 = op->D32; op->st.Tx32 = op->Tx32; op->st.Ty32 = op->Ty32; op->st.Tz32 = op->Tz32;
     op->st.dinv32 = op->dinv32;
+    op->st.sc = op->sc; op->st.sq = op->sq; op->st.Txh = op->Txh; op->st.Tyh = op->Tyh;
+    op->st.dn32 = op->dn32; op->st.dexp = op->dexp;
     int *bad = reinterpret_cast<int *>(&op->ctrl->K);
     cudaError_t e = cudaMemset(bad, 0, sizeof(int));
     if (e == cudaSuccess) e = lc::launch_check_stencil(op->st, bad, 0);
     if (e == cudaSuccess)
         e = lc::launch_dinv_stencil(n, D, op->dinv, op->D32, Tx, Ty, op->st.Tz, op->Tx32, op->Ty32, op->Tz32,
                                     op->dinv32, 0);
+    if (e == cudaSuccess && dim == 2)
+        e = lc::launch_scaling_2d(op->st, op->sc, op->sq, op->Txh, op->Tyh, op->dn32, op->dexp, 0);
     int hbad = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "stencil set-up"); lc_op_destroy(op); return rc; }

@@ -33,6 +33,13 @@ struct Stencil {
     const double *dinv;
     // FP32 copies for the mixed-precision inner solve (fl32 of the above)
     const float *D32, *Tx32, *Ty32, *Tz32, *dinv32;
+    // symmetric Jacobi scaling S = D^-1/2 (FP64 solve): S^-1 = D^1/2 and the
+    // scaled face conductances T_f / sqrt(D_P D_N) of S A S (unit diagonal);
+    // dn32 = fl32(D 2^-2h), h = floor(e/2), e the largest binary exponent of
+    // D, stored biased (+1023) in *dexp
+    const double *sc, *sq, *Txh, *Tyh;
+    const float *dn32;
+    const int *dexp;
 };
 
 // CSR operator; rows ascending, diagonal present.  `n_dev`, if not null,
@@ -320,6 +327,7 @@ struct PcgArgs {
     int32_t precision;    // LC_PREC_FP64 | LC_PREC_MIXED
     double inner_tol;     // mixed: reduction asked of each FP32 inner solve
     int32_t max_outer;    // mixed: refinement sweeps
+    int32_t scaled;       // FP64 2D: iterate on the symmetrically scaled system (tuning)
 };
 cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                cudaStream_t s);
@@ -329,6 +337,10 @@ cudaError_t launch_dinv_stencil(int64_t n, const double *D, double *dinv, float 
                                 const double *Ty, const double *Tz, float *Tx32, float *Ty32, float *Tz32,
                                 float *dinv32, cudaStream_t s);
 cudaError_t launch_check_stencil(const Stencil &op, int *bad, cudaStream_t s);
+// 2D: sc = D^-1/2, sq = D^1/2, Txh/Tyh = T / sqrt(D_P D_N) (0 on the last
+// column/row), dn32 and dexp as described in Stencil; two launches
+cudaError_t launch_scaling_2d(const Stencil &st, double *sc, double *sq, double *Txh, double *Tyh, float *dn32,
+                              int *dexp, cudaStream_t s);
 cudaError_t launch_check_csr(int32_t n, const int32_t *rp, const int32_t *ci, const double *av, int *bad,
                              cudaStream_t s);
 

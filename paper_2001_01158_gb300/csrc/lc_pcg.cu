@@ -27,9 +27,20 @@
 // sums in FP32, only the cross-block sums in FP64); x += ||r|| d in FP64;
 // repeat.  All of it in one launch.
 //
+// 2D FP64 solves (by default) iterate on the symmetrically scaled system
+// S A S x^ = S b, S = D^-1/2, x = S x^: its diagonal is 1, so the Jacobi
+// preconditioner is the identity, z = r^, and no D or dinv is read in the
+// loop -- the same preconditioned iteration in exact arithmetic (the
+// Jacobi-PCG iterates x_k are S times the scaled iterates), with 9 instead
+// of 12 FP64 instructions per cell.  Its stopping norm ||r||^2 = sum D r^^2
+// is summed in FP32 from the bits of r^ (no FP64 instruction) and confirmed
+// in FP64 by the true-residual pass like every other convergence.
+//
 // Data movement per cell and CG iteration, 2D: phase A reads z, p_old, D,
 // Tx, Ty and writes p, q; phase B reads x, p, r, q, dinv and writes x, r, z:
-// 120 B in FP64, 60 B in FP32 (3D: 128 B / 64 B).
+// 120 B in FP64, 60 B in FP32 (3D: 128 B / 64 B); scaled 2D FP64: phase A
+// reads r^, p_old, Tx^, Ty^ and writes p, q, phase B reads x^, p, r^, q and
+// fl32(D), writes x^, r^: 100 B.
 #include "lc_internal.cuh"
 
 namespace lc {
@@ -79,7 +90,21 @@ struct Vecs {
     const T *b;
     T *x, *r, *z, *q, *p0, *p1;
     const T *dinv;
+    T *xu;   // scaled solves: the caller's x (x holds x^ = D^1/2 x in a workspace)
 };
+
+// A float within 2^-23 (relative) of |v| * 2^-nscale, built from the bits of
+// v with integer instructions only (no FP64 instruction): enough for a
+// stopping norm, which is confirmed in FP64 afterwards.  nscale moves the
+// values the norm sums into FP32's range; below that range it gives 0, above
+// it (or for NaN) +inf.
+__device__ __forceinline__ float approx_abs_f32(double v, int nscale) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023 + 127 - nscale;
+    if (e <= 0) return 0.0f;
+    if (e >= 255) return __int_as_float(0x7f800000);
+    return __uint_as_float(((unsigned)e << 23) | (unsigned)((bits >> 29) & 0x7fffff));
+}
 
 template <typename T>
 struct Coef {
@@ -88,6 +113,22 @@ struct Coef {
 
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+
+// Phase B of a Jacobi-PCG iteration over the operator's cells:
+// x += alpha p, r -= alpha q, z = dinv r; sums r.z and r.r.
+template <class OP, typename T>
+__device__ __forceinline__ void phaseB_generic(const OP &op, const Vecs<T> &V, const T *p, T alpha, T (&acc)[2]) {
+    op.each_cell([&](int64_t i) {
+        const T pi = p[i], qi = V.q[i];
+        V.x[i] = fmaT(alpha, pi, V.x[i]);
+        const T ri = fmaT(-alpha, qi, V.r[i]);
+        const T zi = V.dinv[i] * ri;
+        V.r[i] = ri;
+        V.z[i] = zi;
+        acc[0] = fmaT(ri, zi, acc[0]);
+        acc[1] = fmaT(ri, ri, acc[1]);
+    });
+}
 
 // -------------------------------------------------------------- operators
 //
@@ -106,14 +147,79 @@ __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a
 // rows: p of the rows above and below in registers, x-neighbours through warp
 // shuffles, the one-cell halo at either end of the strip recomputed by lanes
 // 0 and 31.  No block barrier, no shared memory.
-template <typename T, int CPL>
+//
+// UNIT = the symmetrically scaled system S A S x^ = S b, S = D^-1/2, x = S x^
+// (Jacobi-PCG on A in exact arithmetic): unit diagonal, z = r^ (no multiply,
+// no separate vector), r.z = r^.r^; the stopping norm ||r||^2 = sum D r^^2
+// is accumulated in FP32 from approx_abs_f32 and confirmed in FP64 by the
+// true-residual pass.  c holds D (for that pass) and the scaled faces.
+template <typename T, int CPL, bool UNIT = false>
 struct Op2DW {
     Stencil s;
     Coef<T> c;
+    const double *sc = nullptr, *sq = nullptr;   // UNIT: D^-1/2, D^1/2
+    const float *d32 = nullptr;                  // UNIT: fl32(D 2^-2h) for the stopping norm
+    const int *dexp = nullptr;                   // UNIT: h = (*dexp - 1023) >> 1
     static constexpr int kSW = 32 * CPL;
     static constexpr int kSmem = 1;
     static constexpr bool kTunable = true;    // register budget selectable (pcg_minblocks)
+    static constexpr bool kScaled = UNIT;
     __device__ void resolve() {}
+    __device__ int dn_shift() const { return UNIT ? (*dexp - 1023) >> 1 : 0; }
+    __device__ void prologue(const Vecs<T> &V) const {
+        if (UNIT) each_cell([&](int64_t i) { V.x[i] = V.xu[i] * sq[i]; });
+    }
+    __device__ void epilogue(const Vecs<T> &V) const {
+        if (UNIT) each_cell([&](int64_t i) { V.xu[i] = V.x[i] * sc[i]; });
+    }
+    __device__ void zero_solution(const Vecs<T> &V) const {
+        each_cell([&](int64_t i) { (UNIT ? V.xu : V.x)[i] = T(0); });
+    }
+    // rows of CPL-wide vector loads and stores (nx is a multiple of CPL)
+    __device__ void phaseB_block(const Vecs<T> &V, const T *p, T alpha, T (&acc)[2], int nscale) const {
+        const int lane = threadIdx.x & 31;
+        float rrf = 0.f;
+        each_segment([&](int x0, int y0, int y1) {
+            const int xa = x0 + CPL * lane;
+            if (xa >= s.nx) return;
+#pragma unroll 2
+            for (int y = y0; y < y1; ++y) {
+                const int64_t i = (int64_t)y * s.nx + xa;
+                T pv[CPL], qv[CPL], xv[CPL], rv[CPL];
+                vld<T, CPL>(p + i, pv);
+                vld<T, CPL>(V.q + i, qv);
+                vld<T, CPL>(V.x + i, xv);
+                vld<T, CPL>(V.r + i, rv);
+                if (UNIT) {
+                    float dv[CPL];
+                    vld<float, CPL>(d32 + i, dv);
+#pragma unroll
+                    for (int k = 0; k < CPL; ++k) {
+                        xv[k] = fmaT(alpha, pv[k], xv[k]);
+                        rv[k] = fmaT(-alpha, qv[k], rv[k]);
+                        acc[0] = fmaT(rv[k], rv[k], acc[0]);
+                        const float f = approx_abs_f32((double)rv[k], nscale);
+                        rrf = fmaf(dv[k] * f, f, rrf);
+                    }
+                } else {
+                    T dv[CPL], zv[CPL];
+                    vld<T, CPL>(V.dinv + i, dv);
+#pragma unroll
+                    for (int k = 0; k < CPL; ++k) {
+                        xv[k] = fmaT(alpha, pv[k], xv[k]);
+                        rv[k] = fmaT(-alpha, qv[k], rv[k]);
+                        zv[k] = dv[k] * rv[k];
+                        acc[0] = fmaT(rv[k], zv[k], acc[0]);
+                        acc[1] = fmaT(rv[k], rv[k], acc[1]);
+                    }
+                    vst<T, CPL>(V.z + i, zv);
+                }
+                vst<T, CPL>(V.x + i, xv);
+                vst<T, CPL>(V.r + i, rv);
+            }
+        });
+        if (UNIT) acc[1] = (T)rrf;
+    }
     __device__ __forceinline__ int strips() const { return (s.nx + kSW - 1) / kSW; }
     template <class F>
     __device__ __forceinline__ void each_segment(F f) const {
@@ -145,15 +251,22 @@ struct Op2DW {
     __device__ void setup_block(const Vecs<T> &V, T &bb, T &rz, T &rr) const {
         each_cell([&](int64_t i) {
             const int xx = (int)(i % s.nx), y = (int)(i / s.nx);
-            T ax = c.D[i] * ldcg(V.x + i);
+            T ax = UNIT ? ldcg(V.x + i) : c.D[i] * ldcg(V.x + i);
             if (y > 0) ax = fmaT(-c.Ty[i - s.nx], ldcg(V.x + i - s.nx), ax);
             if (xx > 0) ax = fmaT(-c.Tx[i - 1], ldcg(V.x + i - 1), ax);
             if (xx + 1 < s.nx) ax = fmaT(-c.Tx[i], ldcg(V.x + i + 1), ax);
             if (y + 1 < s.ny) ax = fmaT(-c.Ty[i], ldcg(V.x + i + s.nx), ax);
             const T bi = V.b[i];
+            bb = fmaT(bi, bi, bb);
+            if (UNIT) {   // r^ = S b - A^ x^;  ||r||^2 = sum D r^^2
+                const T ri = (T)sc[i] * bi - ax;
+                V.r[i] = ri;
+                rz = fmaT(ri, ri, rz);
+                rr = fmaT(c.D[i] * ri, ri, rr);
+                return;
+            }
             const T ri = bi - ax;
             V.r[i] = ri;
-            bb = fmaT(bi, bi, bb);
             rr = fmaT(ri, ri, rr);
             if (V.z) {
                 const T zi = V.dinv[i] * ri;
@@ -203,7 +316,7 @@ struct Op2DW {
                 for (int k = 0; k < CPL; ++k) { pn[k] = T(0); d[k] = T(0); tx[k] = T(0); typ[k] = T(0); }
                 if (act) {
                     if (y + 1 < s.ny) { pnew(V, pold, first, beta, i + s.nx, pn); load(c.Ty, i, typ); }
-                    load(c.D, i, d);
+                    if (!UNIT) load(c.D, i, d);
                     load(c.Tx, i, tx);
                     if (lane == 0 && x0 > 0) txw0 = c.Tx[i - 1];
                 }
@@ -225,7 +338,7 @@ struct Op2DW {
                 T q[CPL];
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
-                    T qi = d[k] * pc[k];
+                    T qi = UNIT ? pc[k] : d[k] * pc[k];
                     qi = fmaT(-tym[k], pm[k], qi);
                     qi = fmaT(-txw[k], pw[k], qi);
                     qi = fmaT(-txe[k], pe[k], qi);
@@ -252,7 +365,14 @@ struct Op3D {
     Coef<T> c;
     static constexpr int kSmem = 2 * (kTileX + 2) * (kTileY + 2);
     static constexpr bool kTunable = true;
+    static constexpr bool kScaled = false;
     __device__ void resolve() {}
+    __device__ void prologue(const Vecs<T> &) const {}
+    __device__ void epilogue(const Vecs<T> &) const {}
+    __device__ void zero_solution(const Vecs<T> &V) const { each_cell([&](int64_t i) { V.x[i] = T(0); }); }
+    __device__ void phaseB_block(const Vecs<T> &V, const T *p, T alpha, T (&acc)[2], int) const {
+        phaseB_generic(*this, V, p, alpha, acc);
+    }
     __device__ int64_t units() const {
         const int64_t tx = (s.nx + kTileX - 1) / kTileX, ty = (s.ny + kTileY - 1) / kTileY;
         const int64_t tz = (s.nz + kTileZ - 1) / kTileZ;
@@ -393,7 +513,14 @@ struct OpCsr {
     int32_t n;   // resolved at kernel start (device-side count of an extracted subsystem)
     static constexpr int kSmem = 1;
     static constexpr bool kTunable = false;
+    static constexpr bool kScaled = false;
     __device__ void resolve() { if (cs.n_dev) n = *cs.n_dev; }
+    __device__ void prologue(const Vecs<T> &) const {}
+    __device__ void epilogue(const Vecs<T> &) const {}
+    __device__ void zero_solution(const Vecs<T> &V) const { each_cell([&](int64_t i) { V.x[i] = T(0); }); }
+    __device__ void phaseB_block(const Vecs<T> &V, const T *p, T alpha, T (&acc)[2], int) const {
+        phaseB_generic(*this, V, p, alpha, acc);
+    }
     template <class F>
     __device__ __forceinline__ void each_cell(F f) const {
         for (int64_t i = blockIdx.x * (int64_t)kPcgThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kPcgThreads)
@@ -487,7 +614,7 @@ __device__ bool residual_phase(const OP &op, const Vecs<T> &V, double *part, dou
 // Returns 1 converged, 0 iteration limit, -1 breakdown, -2 wait timed out.
 template <class OP, typename T>
 __device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, double *red, T *sm, Ctrl *ctrl,
-                             double rz, double stop, int maxit, int &it, int &pin) {
+                             double rz, double stop, int maxit, int &it, int &pin, int nscale = 0) {
     bool first = true;
     double beta = 0.0;
     while (true) {
@@ -504,16 +631,7 @@ __device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, doubl
         pin ^= 1;
         const T *p = pout;
         T acc[2] = {T(0), T(0)};
-        op.each_cell([&](int64_t i) {
-            const T pi = p[i], qi = V.q[i];
-            V.x[i] = fmaT(alpha, pi, V.x[i]);
-            const T ri = fmaT(-alpha, qi, V.r[i]);
-            const T zi = V.dinv[i] * ri;
-            V.r[i] = ri;
-            V.z[i] = zi;
-            acc[0] = fmaT(ri, zi, acc[0]);
-            acc[1] = fmaT(ri, ri, acc[1]);
-        });
+        op.phaseB_block(V, p, alpha, acc, nscale);
         double o2[2];
         if (!grid_sums<2, T>(acc, 4, part, red, ctrl, o2)) return -2;
         ++it;
@@ -533,6 +651,10 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) pcg_kernel(OP op, Vecs<doub
     __shared__ double red[128];
     __shared__ double sm[OP::kSmem];
     op.resolve();
+    if (OP::kScaled) {   // x^ = D^1/2 x into the workspace (the caller's x stays untouched until the end)
+        op.prologue(V);
+        if (!grid_sync(ctrl, gridDim.x)) return;
+    }
     double bb, rz, rr;
     if (!residual_phase(op, V, part, red, ctrl, bb, rz, rr)) return;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -542,17 +664,26 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) pcg_kernel(OP op, Vecs<doub
         ctrl->relres0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
     }
     if (bb == 0.0) {   // A x = 0: x = 0
-        op.each_cell([&](int64_t i) { V.x[i] = 0.0; });
+        op.zero_solution(V);
         if (lead) { ctrl->converged = 1; ctrl->early = 1; ctrl->relres = 0.0; }
         return;
     }
-    if (rr <= stop) {
+    if (rr <= stop) {   // the starting iterate is returned as it is
         if (lead) { ctrl->converged = 1; ctrl->early = 1; ctrl->relres = sqrt(rr / bb); }
         return;
     }
+    // scaled solves sum the stopping norm sum D r^^2 in FP32, relative to
+    // 2^(2 e) ~ b.b: D 2^-2h times (|r^| 2^-(e-h))^2
+    int nscale = 0;
+    double stop_rec = stop;
+    if constexpr (OP::kScaled) {
+        const int e = (((int)((__double_as_longlong(bb) >> 52) & 0x7ff)) - 1023) >> 1;
+        nscale = e - op.dn_shift();
+        stop_rec = ldexp(stop, -2 * e);
+    }
     int it = 0, restarts = 0, pin = 0, result;
     while (true) {
-        result = cg_iterations(op, V, part, red, sm, ctrl, rz, stop, maxit, it, pin);
+        result = cg_iterations(op, V, part, red, sm, ctrl, rz, stop_rec, maxit, it, pin, nscale);
         if (result == -2) return;
         if (result != 1) break;
         // converged on the recurrence residual: confirm with the true one
@@ -566,6 +697,7 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) pcg_kernel(OP op, Vecs<doub
         double bb2, rz2;
         if (!residual_phase(op, V, part, red, ctrl, bb2, rz2, rr)) return;
     }
+    op.epilogue(V);   // scaled solves: x = D^-1/2 x^
     if (lead) {
         ctrl->iters = it;
         ctrl->restarts = restarts;
@@ -795,11 +927,13 @@ cudaError_t launch_ir(const OPD &opd, const OPF &opf, int64_t units, const Vecs<
 Vecs<double> vecs64(const PcgArgs &a, const PcgWork &w, const double *dinv) {
     Vecs<double> V;
     V.b = a.b; V.x = a.x; V.r = w.r; V.z = w.z; V.q = w.q; V.p0 = w.p0; V.p1 = w.p1; V.dinv = dinv;
+    V.xu = nullptr;
     return V;
 }
 Vecs<float> vecs32(const PcgWork &w, const float *dinv32) {
     Vecs<float> V;
     V.b = nullptr; V.x = w.x32; V.r = w.r32; V.z = w.z32; V.q = w.q32; V.p0 = w.p032; V.p1 = w.p132; V.dinv = dinv32;
+    V.xu = nullptr;
     return V;
 }
 
@@ -830,6 +964,17 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
         // at least 4 rows per warp so the recomputed halo rows stay a small overhead
         const int64_t units = ((int64_t)((op.nx + 63) / 64) * op.ny + 4 * wpb - 1) / (4 * wpb);
         Op2DW<double, 2> od{op, coef64(op)};
+        if (!mixed && a.scaled && op.sc) {
+            // the symmetrically scaled system: x^ in the z workspace, z = r^
+            Op2DW<double, 2, true> os{op, Coef<double>{op.D, op.Txh, op.Tyh, nullptr}, op.sc, op.sq, op.dn32,
+                                      op.dexp};
+            Vecs<double> VS = VD;
+            VS.x = w.z;
+            VS.z = w.r;
+            VS.dinv = nullptr;
+            VS.xu = a.x;
+            return launch_pcg(os, units, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+        }
         if (!mixed) return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);
         if (op.nx % 4 == 0) {   // FP32 copies are the library's own, 256-byte aligned: float4 lanes
             Op2DW<float, 4> of{op, coef32(op)};
@@ -873,6 +1018,43 @@ cudaError_t launch_dinv_stencil(int64_t n, const double *D, double *dinv, float 
                                 float *dinv32, cudaStream_t s) {
     dinv_stencil_kernel<<<152 * 8, 256, 0, s>>>(n, D, dinv, D32, Tx, Ty, Tz, Tx32, Ty32, Tz32, dinv32);
     note_launches(1);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void max_exponent_kernel(int64_t n, const double *__restrict__ D, int *dexp) {
+    int m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (int)((__double_as_longlong(D[i]) >> 52) & 0x7ff));
+    m = __reduce_max_sync(0xffffffffu, (unsigned)m);
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(dexp, m);
+}
+
+__global__ void scaling_2d_kernel(int nx, int ny, const double *__restrict__ D, const double *__restrict__ Tx,
+                                  const double *__restrict__ Ty, double *sc, double *sq, double *Txh, double *Tyh,
+                                  float *dn32, const int *dexp) {
+    const int64_t n = (int64_t)nx * ny;
+    const int h = (*dexp - 1023) >> 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)(i / nx);
+        const double r = sqrt(D[i]);
+        const double s = 1.0 / r;
+        sc[i] = s;
+        sq[i] = r;
+        Txh[i] = x + 1 < nx ? Tx[i] * s * (1.0 / sqrt(D[i + 1])) : 0.0;
+        Tyh[i] = y + 1 < ny ? Ty[i] * s * (1.0 / sqrt(D[i + nx])) : 0.0;
+        dn32[i] = (float)ldexp(D[i], -2 * h);
+    }
+}
+}  // namespace
+
+cudaError_t launch_scaling_2d(const Stencil &st, double *sc, double *sq, double *Txh, double *Tyh, float *dn32,
+                              int *dexp, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(dexp, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    max_exponent_kernel<<<152 * 4, 256, 0, s>>>(st.n, st.D, dexp);
+    scaling_2d_kernel<<<152 * 8, 256, 0, s>>>(st.nx, st.ny, st.D, st.Tx, st.Ty, sc, sq, Txh, Tyh, dn32, dexp);
+    note_launches(2);
     return cudaGetLastError();
 }
 

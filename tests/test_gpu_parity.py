@@ -178,6 +178,61 @@ def test_pcg_matches_oracle(ctx, name, op):
         assert stats.relres_final <= tol
 
 
+SCALED_SHAPES = [(64, 16), (130, 37), (300, 260), (2, 50)]
+
+
+@pytest.mark.parametrize("nx,ny", SCALED_SHAPES)
+@pytest.mark.parametrize("scaled", [0, 1])
+def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled):
+    """The 2-D FP64 solve on D^-1/2 A D^-1/2 (pcg_scaled = 1) and on A with the
+    explicit Jacobi preconditioner (0) are the same Jacobi-PCG iteration in
+    exact arithmetic: both match the oracle's iteration count within one and
+    its solution within 1e-9."""
+    op = gen.random_stencil_2d(nx + 7 * ny, nx, ny)
+    A, b, x0 = rhs_and_x0(op, 13)
+    tol = 1e-9
+    xr, st, it_ref, _ = oracle.pcg(A, b, x0, tol=tol)
+    assert st == oracle.OK
+    gop = stencil_op(ctx, op)
+    gop.set_tuning("pcg_scaled", scaled)
+    assert gop.get_tuning("pcg_scaled") == scaled
+    x = cu(x0)
+    stats = lcg.Stats()
+    lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(tol, 100000, lcg.PREC_FP64, 0.0, 0), stats)
+    xg = x.cpu().numpy()
+    assert oracle.relres(A, b, xg) <= tol
+    assert stats.relres_final <= tol
+    assert abs(stats.it_global - it_ref) <= 1
+    assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
+
+
+@pytest.mark.parametrize("cscale,bscale", [(1e25, 1e35), (1e-25, 1e-30), (1.0, 1e-140), (1e5, 1e150),
+                                            (1e45, 1e50), (1e-45, 1e-40)])
+def test_pcg_scaled_extreme_magnitudes(ctx, cscale, bscale):
+    """The scaled solve sums its stopping norm in FP32 with exponents shifted
+    by ||b|| and max D, so coefficients and right-hand sides far outside
+    FP32's range still stop at the FP64 tolerance (the oracle's iteration
+    count within one)."""
+    op0 = gen.random_stencil_2d(77, 96, 40)
+    op = gen.Stencil(op0.shape, op0.D * cscale, op0.Tx * cscale, op0.Ty * cscale, None, op0.meta)
+    A = oracle.from_stencil(op)
+    rng = np.random.default_rng(3)
+    b = rng.uniform(0.5, 1.5, op.n) * bscale
+    x0 = np.zeros(op.n)
+    tol = 1e-8
+    xr, st, it_ref, _ = oracle.pcg(A, b, x0, tol=tol)
+    assert st == oracle.OK
+    gop = stencil_op(ctx, op)
+    assert gop.get_tuning("pcg_scaled") == 1
+    x = cu(x0)
+    stats = lcg.Stats()
+    lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(tol, 100000, lcg.PREC_FP64, 0.0, 0), stats)
+    xg = x.cpu().numpy()
+    assert oracle.relres(A, b, xg) <= tol
+    assert abs(stats.it_global - it_ref) <= 1
+    assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
+
+
 def test_pcg_edge_cases(ctx):
     op = gen.random_stencil_2d(1, 33, 21)
     A = oracle.from_stencil(op)
