@@ -168,8 +168,13 @@ def measured_peaks():
 
 
 def source_digest() -> str:
-    with open(os.path.join(ROOT, "paper_2001_01158_gb300", "csrc", "lc_pcg.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Digest of the global PCG kernel's sources (the kernel file and the
+    shared header with its barrier and reductions)."""
+    h = hashlib.sha256()
+    for name in ("lc_pcg.cu", "lc_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2001_01158_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic_per_cell_iter():
@@ -184,7 +189,7 @@ def ncu_traffic_per_cell_iter():
             if "=" in ln and not ln.lstrip().startswith("#"):
                 k, v = ln.split("=", 1)
                 vals[k.strip()] = v.strip()
-    if vals.get("lc_pcg_cu_sha256_16") != source_digest():
+    if vals.get("pcg_sources_sha256_16") != source_digest():
         return None
     try:
         return float(vals["dram_bytes_per_cell_iter"]), float(vals.get("dram_bytes_per_cell_setup", "nan"))

@@ -317,6 +317,16 @@ LC_EXPORT int lc_adjoint_grad_k_2d(lc_ctx *ctx, const int32_t shape[2], const do
  *       FP64 instructions and bytes per iteration.  0 iterates on A with the
  *       explicit Jacobi preconditioner.  The stopping test is the same in
  *       both: ||b - A x||_2 / ||b||_2 <= tol on the unscaled system.
+ *   "local_cluster_rows" >= 0 (default 8192): the FP64 local solve of
+ *       lc_solve_local_then_global runs on one thread-block cluster, its
+ *       vectors in distributed shared memory, when the subsystem has at most
+ *       this many rows and they fit the cluster (about 76,000 rows on a
+ *       GB300); larger subsystems, mixed precision, or 0 use the grid-wide
+ *       kernel.  Same iteration, different rounding order of the dot
+ *       products.  (16 SMs' FP64 throughput makes the cluster slower than the
+ *       grid kernel above roughly 10,000 rows.)
+ *   "local_cluster_threads" 256, 512 or 1024 (default 256): threads per CTA
+ *       of that cluster.
  * Unknown keys or out-of-range values return LC_ERR_INVALID_ARG. */
 LC_EXPORT int lc_op_set_tuning(lc_op *op, const char *key, int32_t value);
 LC_EXPORT int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value);

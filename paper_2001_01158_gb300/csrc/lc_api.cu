@@ -50,6 +50,10 @@ struct lc_op {
     // tuning knobs (lc_op_set_tuning)
     int pcg_minblocks = 3;   // register budget of the structured-grid PCG kernel
     int pcg_grid_cap = 0;    // blocks of the global PCG launch (0: as many as fit)
+    // local solves of up to this many rows on one thread-block cluster of
+    // 256-thread CTAs: measured faster than the grid kernel below ~8K rows
+    int local_cluster_rows = 8192;
+    int local_cluster_threads = 256;
     int pcg_scaled = 1;      // 2D FP64: iterate on D^-1/2 A D^-1/2 (fewer FP64 instructions)
     double *sc = nullptr, *sq = nullptr, *Txh = nullptr, *Tyh = nullptr;
     float *dn32 = nullptr;
@@ -319,8 +323,13 @@ int pcg_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_
     lc::PcgWork w = op->pw;
     LC_CUDA(ctx, cudaMemsetAsync(&ctrl->status, 0, sizeof(int32_t), s));
     if (local) {
-        // one block per SM: the local system is small and its barriers dominate
-        LC_CUDA(ctx, lc::launch_pcg_csr(sub_csr(op), a, w, ctrl, ctx->sms, s));
+        // the local system is small and its barriers dominate: one thread-block
+        // cluster when it fits (FP64), else one block per SM
+        const bool cl = op->local_cluster_rows > 0 && p->precision == LC_PREC_FP64 && lc::cluster_local_rows() > 0;
+        if (cl)
+            LC_CUDA(ctx, lc::launch_pcg_csr_cluster(sub_csr(op), a, op->local_cluster_rows, op->local_cluster_threads,
+                                                    ctrl, s));
+        LC_CUDA(ctx, lc::launch_pcg_csr(sub_csr(op), a, w, ctrl, ctx->sms, s, cl));
     } else if (op->kind == 0) {
         LC_CUDA(ctx, lc::launch_pcg_stencil(op->st, a, w, ctrl, op->pcg_grid_cap, s));
     } else {
@@ -664,6 +673,17 @@ int lc_op_set_tuning(lc_op *op, const char *key, int32_t value) {
         op->pcg_scaled = value;
         return LC_OK;
     }
+    if (!strcmp(key, "local_cluster_rows")) {
+        if (value < 0) return fail(op->ctx, LC_ERR_INVALID_ARG, "local_cluster_rows must be >= 0");
+        op->local_cluster_rows = value;
+        return LC_OK;
+    }
+    if (!strcmp(key, "local_cluster_threads")) {
+        if (value != 256 && value != 512 && value != 1024)
+            return fail(op->ctx, LC_ERR_INVALID_ARG, "local_cluster_threads must be 256, 512 or 1024");
+        op->local_cluster_threads = value;
+        return LC_OK;
+    }
     return fail(op->ctx, LC_ERR_INVALID_ARG, "unknown tuning key '%s'", key);
 }
 
@@ -672,6 +692,8 @@ int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value) {
     if (!strcmp(key, "pcg_minblocks")) { *value = op->pcg_minblocks; return LC_OK; }
     if (!strcmp(key, "pcg_grid_cap")) { *value = op->pcg_grid_cap; return LC_OK; }
     if (!strcmp(key, "pcg_scaled")) { *value = op->pcg_scaled; return LC_OK; }
+    if (!strcmp(key, "local_cluster_rows")) { *value = op->local_cluster_rows; return LC_OK; }
+    if (!strcmp(key, "local_cluster_threads")) { *value = op->local_cluster_threads; return LC_OK; }
     return LC_ERR_INVALID_ARG;
 }
 

@@ -56,10 +56,9 @@ struct Csr {
 // Device-resident control block of one operator (one per lc_op).
 struct Ctrl {
     // grid barrier
-    unsigned int bar_count;
-    unsigned int bar_gen;
+    unsigned long long bar_count;   // arrivals since the launch started (zeroed before it)
     int32_t status;                 // first error a kernel raised (LC_OK if none)
-    int32_t pad0;
+    int32_t done;                   // local solve: 1 if the cluster kernel solved the system
     // marking
     unsigned long long maxabs_bits; // max |r| (or max g) as bits, NaN excluded
     double tau;
@@ -176,33 +175,40 @@ __device__ __forceinline__ int block_isum(int v, int *sm) {
 // ---------------------------------------------------------------- grid barrier
 
 // Spin limit of every grid-wide wait: ~2 s at 2 GHz, after which the block
-// records LC_ERR_TIMEOUT in ctrl->status and returns false (so do all
-// blocks that wait after it); kernels then exit.  Co-residency of all
+// records LC_ERR_TIMEOUT in ctrl->status and returns false; the other blocks
+// stop at their own next wait, bounded the same way, and kernels exit.  Co-residency of all
 // blocks is guaranteed by the cooperative launch.
 constexpr long long kBarrierTimeoutCycles = 4000000000ll;
 
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Counting barrier: arrival k of a block (k = 0, 1, ...) takes the counter
+// from somewhere in [k n, (k+1) n) and the barrier opens when it reaches
+// (k+1) n, so the target follows from the value the arrival returns: one
+// atomic per block and arrival, no generation word, no reset between
+// barriers.  A block never sees the counter past its own target before it
+// arrives (no block passes barrier k before all arrived).
 __device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned int nblocks) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = &ctrl->bar_gen;
-        unsigned int g = *vgen;
-        __threadfence();
-        unsigned int arrived = atomicAdd(&ctrl->bar_count, 1u);
+        __threadfence();   // the block's writes (ordered by the barrier above) before the arrival
+        const unsigned long long old = atomicAdd(&ctrl->bar_count, 1ull);
+        const unsigned long long target = (old / nblocks + 1) * nblocks;
         int ok = 1;
-        if (arrived == nblocks - 1) {
-            ctrl->bar_count = 0;
-            __threadfence();
-            atomicAdd(&ctrl->bar_gen, 1u);
-        } else {
-            long long t0 = clock64();
-            while (*vgen == g) {
+        if (old + 1 < target) {
+            const long long t0 = clock64();
+            while (ld_acquire_u64(&ctrl->bar_count) < target) {
                 if (clock64() - t0 > kBarrierTimeoutCycles) { ok = 0; break; }
             }
         }
         __threadfence();
         if (!ok) atomicCAS(&ctrl->status, LC_OK, LC_ERR_TIMEOUT);
-        s_ok = ok && (*(volatile int32_t *)&ctrl->status == LC_OK);
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
@@ -331,8 +337,17 @@ struct PcgArgs {
 };
 cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                cudaStream_t s);
+// after_cluster: launched right after launch_pcg_csr_cluster on the same
+// ctrl -- no reset of ctrl, and the kernel returns at once if ctrl->done
 cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
-                           cudaStream_t s);
+                           cudaStream_t s, bool after_cluster = false);
+// FP64 Jacobi-PCG of a CSR system on one thread-block cluster (lc_cluster.cu),
+// when it has at most max_rows rows and they fit the cluster's shared memory
+// (cluster_local_rows(); 0 if the device cannot run the cluster); sets
+// ctrl->done
+int cluster_local_rows();
+cudaError_t launch_pcg_csr_cluster(const Csr &op, const PcgArgs &a, int max_rows, int threads, Ctrl *ctrl,
+                                   cudaStream_t s);
 cudaError_t launch_dinv_stencil(int64_t n, const double *D, double *dinv, float *D32, const double *Tx,
                                 const double *Ty, const double *Tz, float *Tx32, float *Ty32, float *Tz32,
                                 float *dinv32, cudaStream_t s);

@@ -164,6 +164,7 @@ struct Op2DW {
     static constexpr int kSmem = 1;
     static constexpr bool kTunable = true;    // register budget selectable (pcg_minblocks)
     static constexpr bool kScaled = UNIT;
+    __device__ bool skipped() const { return false; }
     __device__ void resolve() {}
     __device__ int dn_shift() const { return UNIT ? (*dexp - 1023) >> 1 : 0; }
     __device__ void prologue(const Vecs<T> &V) const {
@@ -366,6 +367,7 @@ struct Op3D {
     static constexpr int kSmem = 2 * (kTileX + 2) * (kTileY + 2);
     static constexpr bool kTunable = true;
     static constexpr bool kScaled = false;
+    __device__ bool skipped() const { return false; }
     __device__ void resolve() {}
     __device__ void prologue(const Vecs<T> &) const {}
     __device__ void epilogue(const Vecs<T> &) const {}
@@ -511,9 +513,11 @@ struct OpCsr {
     Csr cs;
     const T *av;
     int32_t n;   // resolved at kernel start (device-side count of an extracted subsystem)
+    const int32_t *done = nullptr;   // set: the cluster kernel may have solved the system already
     static constexpr int kSmem = 1;
     static constexpr bool kTunable = false;
     static constexpr bool kScaled = false;
+    __device__ bool skipped() const { return done && *done; }
     __device__ void resolve() { if (cs.n_dev) n = *cs.n_dev; }
     __device__ void prologue(const Vecs<T> &) const {}
     __device__ void epilogue(const Vecs<T> &) const {}
@@ -563,11 +567,20 @@ struct OpCsr {
 
 // -------------------------------------------------------------- building blocks
 
+struct NoPost {
+    __device__ void operator()(double *) const {}
+};
+
 // Block sums of NV thread values into partial slots `slot0..`, barrier, and
-// the grid-wide sums (identical in every block).  False if a wait timed out.
-template <int NV, typename T>
+// the grid-wide sums (identical in every block): warp 0 adds the block
+// partials lane-strided and reduces them in a fixed order.  Thread 0 then
+// runs post(t) on t[0..NV) = the totals, which may append ND derived scalars
+// t[NV..NV+ND) (the CG step lengths): FP64 divisions and tests run once per
+// block instead of once per thread -- FP64 issue is scarce.  Every thread
+// reads the totals and derived values back.  False if a wait timed out.
+template <int NV, int ND = 0, typename T, class Post = NoPost>
 __device__ __forceinline__ bool grid_sums(T (&v)[NV], int slot0, double *part, double *red, Ctrl *ctrl,
-                                          double (&out)[NV]) {
+                                          double (&out)[NV + ND], Post post = Post()) {
     T tmp[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) tmp[k] = v[k];
@@ -576,24 +589,33 @@ __device__ __forceinline__ bool grid_sums(T (&v)[NV], int slot0, double *part, d
 #pragma unroll
         for (int k = 0; k < NV; ++k) part[(size_t)(slot0 + k) * kMaxGrid + blockIdx.x] = (double)tmp[k];
     if (!grid_sync(ctrl, gridDim.x)) return false;
-    // every thread loads its few block partials at once (one L2 round trip),
-    // then a fixed-order block sum: the same totals in every block
-    double acc[NV];
+    if (threadIdx.x < 32) {
+        double acc[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] += ldcg(part + (size_t)(slot0 + k) * kMaxGrid + b);
-    block_sum<NV, double>(acc, red);
-    if (threadIdx.x == 0)
+            for (int k = 0; k < NV; ++k) acc[k] += ldcg(part + (size_t)(slot0 + k) * kMaxGrid + b);
 #pragma unroll
-        for (int k = 0; k < NV; ++k) red[96 + k] = acc[k];
+        for (int k = 0; k < NV; ++k) acc[k] = warp_sum(acc[k]);
+        if (threadIdx.x == 0) {
+            double t[NV + ND];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) t[k] = acc[k];
+            post(t);
+#pragma unroll
+            for (int k = 0; k < NV + ND; ++k) red[96 + k] = t[k];
+        }
+    }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NV; ++k) out[k] = red[96 + k];
+    for (int k = 0; k < NV + ND; ++k) out[k] = red[96 + k];
     __syncthreads();
     return true;
 }
+
+// A flag stored as a double by post(): tested with an integer compare.
+__device__ __forceinline__ bool flag_set(double f) { return __double_as_longlong(f) != 0; }
 
 // r = b - A x (z = dinv r if V.z), with the grid sums of b.b, r.z, r.r.
 template <class OP, typename T>
@@ -602,7 +624,7 @@ __device__ bool residual_phase(const OP &op, const Vecs<T> &V, double *part, dou
     T acc[3] = {T(0), T(0), T(0)};
     op.setup_block(V, acc[0], acc[1], acc[2]);
     double out[3];
-    if (!grid_sums<3, T>(acc, 0, part, red, ctrl, out)) return false;
+    if (!grid_sums<3, 0, T>(acc, 0, part, red, ctrl, out)) return false;
     bb = out[0];
     rz = out[1];
     rr = out[2];
@@ -623,21 +645,30 @@ __device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, doubl
         T *pout = pin ? V.p0 : V.p1;
         op.phaseA_block(V, pold, pout, first, (T)beta, pq, sm);
         T a1[1] = {pq};
-        double o1[1];
-        if (!grid_sums<1, T>(a1, 3, part, red, ctrl, o1)) return -2;
-        const double pqs = o1[0];
-        if (!(pqs > 0.0) || !isfinite(pqs)) return -1;
-        const T alpha = (T)(rz / pqs);
+        double o1[3];   // p.q, alpha, breakdown flag
+        const double rz_ = rz;
+        if (!grid_sums<1, 2, T>(a1, 3, part, red, ctrl, o1, [rz_](double *t) {
+                const bool ok = t[0] > 0.0 && isfinite(t[0]);
+                t[1] = ok ? rz_ / t[0] : 0.0;
+                t[2] = ok ? 0.0 : 1.0;
+            }))
+            return -2;
+        if (flag_set(o1[2])) return -1;
+        const T alpha = (T)o1[1];
         pin ^= 1;
         const T *p = pout;
         T acc[2] = {T(0), T(0)};
         op.phaseB_block(V, p, alpha, acc, nscale);
-        double o2[2];
-        if (!grid_sums<2, T>(acc, 4, part, red, ctrl, o2)) return -2;
+        double o2[4];   // r.z, stopping norm, converged flag, beta
+        if (!grid_sums<2, 2, T>(acc, 4, part, red, ctrl, o2, [rz_, stop](double *t) {
+                t[2] = t[1] <= stop ? 1.0 : 0.0;
+                t[3] = t[0] / rz_;
+            }))
+            return -2;
         ++it;
-        if (o2[1] <= stop) return 1;
+        if (flag_set(o2[2])) return 1;
         if (it >= maxit) return 0;
-        beta = o2[0] / rz;
+        beta = o2[3];
         rz = o2[0];
         first = false;
     }
@@ -650,6 +681,7 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) pcg_kernel(OP op, Vecs<doub
                                                                 int maxit, int max_restarts, Ctrl *ctrl) {
     __shared__ double red[128];
     __shared__ double sm[OP::kSmem];
+    if (op.skipped()) return;
     op.resolve();
     if (OP::kScaled) {   // x^ = D^1/2 x into the workspace (the caller's x stays untouched until the end)
         op.prologue(V);
@@ -752,7 +784,7 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) ir_kernel(OPD opd, OPF opf,
             acc[1] = fmaf(ri, ri, acc[1]);
         });
         double o[2];
-        if (!grid_sums<2, float>(acc, 6, part, red, ctrl, o)) return;
+        if (!grid_sums<2, 0, float>(acc, 6, part, red, ctrl, o)) return;
         const double stop_in = (inner_tol * inner_tol) * o[1];
         const int res = cg_iterations(opf, VF, part, red, sm, ctrl, o[0], stop_in, maxit, it, pin);
         if (res == -2) return;
@@ -889,16 +921,20 @@ const void *ir_kernel_for(int minblocks) {
     }
 }
 
-cudaError_t coop_launch(const void *k, int64_t units, int cap, void **args, Ctrl *ctrl, cudaStream_t s) {
+cudaError_t coop_launch(const void *k, int64_t units, int cap, void **args, Ctrl *ctrl, cudaStream_t s,
+                        bool reset = true) {
     const int grid = coop_grid(k, units, cap);
-    reset_ctrl_kernel<<<1, 1, 0, s>>>(ctrl);
-    note_launches(2);
+    if (reset) {
+        reset_ctrl_kernel<<<1, 1, 0, s>>>(ctrl);
+        note_launches(1);
+    }
+    note_launches(1);
     return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kPcgThreads), args, 0, s);
 }
 
 template <class OP>
 cudaError_t launch_pcg(const OP &op, int64_t units, const Vecs<double> &V, double *part, const PcgArgs &a,
-                       Ctrl *ctrl, int cap, int minblocks, cudaStream_t s) {
+                       Ctrl *ctrl, int cap, int minblocks, cudaStream_t s, bool reset = true) {
     OP o = op;
     Vecs<double> v = V;
     double *pt = part;
@@ -906,7 +942,7 @@ cudaError_t launch_pcg(const OP &op, int64_t units, const Vecs<double> &V, doubl
     int mi = a.maxit, mr = a.max_restarts;
     Ctrl *c = ctrl;
     void *args[] = {&o, &v, &pt, &t, &mi, &mr, &c};
-    return coop_launch(pcg_kernel_for<OP>(minblocks), units, cap, args, ctrl, s);
+    return coop_launch(pcg_kernel_for<OP>(minblocks), units, cap, args, ctrl, s, reset);
 }
 
 template <class OPD, class OPF>
@@ -990,7 +1026,8 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
     return launch_ir(od, of, units, VD, VF, w.partials, a, ctrl, grid_hint, a.minblocks, s);
 }
 
-cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint, cudaStream_t s) {
+cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint, cudaStream_t s,
+                           bool after_cluster) {
     // the row count may live on the device (extracted subsystem): the kernels
     // are sized for the capacity op.n and read the actual count themselves
     const int64_t units = (op.n + kPcgThreads - 1) / kPcgThreads;
@@ -998,6 +1035,10 @@ cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ct
     note_launches(1);
     Vecs<double> VD = vecs64(a, w, w.dinv);
     OpCsr<double> od{op, op.av, op.n};
+    if (after_cluster) {
+        od.done = &ctrl->done;
+        return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, 1, s, false);
+    }
     if (a.precision != LC_PREC_MIXED) return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, 1, s);
     VD.z = nullptr;
     const float *av32 = op.av32;

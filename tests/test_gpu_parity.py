@@ -293,6 +293,76 @@ def test_local_then_global_matches_oracle(ctx, mode, n):
         assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
 
 
+@pytest.mark.parametrize("n,radius,beta,rounds", [(96, 10, 1e-3, 2), (256, 40, 1e-3, 3), (384, 90, 1e-4, 4),
+                                                   (300, 150, 1e-6, 8)])
+@pytest.mark.parametrize("cluster,threads", [(1 << 30, 256), (1 << 30, 1024), (0, 256)])
+def test_local_solve_cluster_and_grid_match_oracle(ctx, n, radius, beta, rounds, cluster, threads):
+    """The local solve on one thread-block cluster (vectors in distributed
+    shared memory) and on the whole grid give the oracle's local iteration
+    count within one and the same Alg 1 result; subsystems from a few hundred
+    rows to more than the cluster holds (that one falls back to the grid
+    kernel)."""
+    d = gen.cfg1_heat2d(seed=n + radius, n=n, radius=radius)
+    A = oracle.from_stencil(d["op"])
+    tol = 1e-8
+    xr, sr, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], thr_mode=oracle.THR_REL_MAX, thr_param=beta,
+                                               exp_mode=oracle.EXP_DILATE, exp_rounds=rounds, tol=tol)
+    prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, beta, lcg.EXP_DILATE, rounds, tol=tol)
+    gop = stencil_op(ctx, d["op"])
+    gop.set_tuning("local_cluster_rows", cluster)
+    gop.set_tuning("local_cluster_threads", threads)
+    assert gop.get_tuning("local_cluster_rows") == cluster and gop.get_tuning("local_cluster_threads") == threads
+    x = cu(d["x0"])
+    st = lcg.Stats()
+    lcg.solve_local_then_global(ctx, gop, cu(d["b"]), x, prm, st)
+    xg = x.cpu().numpy()
+    assert st.K == sr["K"] and st.nnzB == sr["nnzB"] and st.K > 0
+    assert abs(st.it_local - sr["it_local"]) <= 1
+    assert st.relres_tilde == pytest.approx(sr["relres_tilde"], rel=1e-6)
+    assert oracle.relres(A, d["b"], xg) <= tol
+    assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
+
+
+def test_local_solve_cluster_edge_sizes(ctx):
+    """K = 0, 1, and a few rows (fewer rows than CTAs in the cluster): the
+    cluster kernel's empty and ragged partitions."""
+    op, A, b, x0, beta_for = edge_case_problem()
+    gop = stencil_op(ctx, op)
+    gop.set_tuning("local_cluster_rows", 1 << 30)
+    for k in (1, 2, 5, 17):
+        beta = beta_for(k)
+        prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, beta, lcg.EXP_NONE, 0, tol=1e-9)
+        xr, sr, _ = oracle.solve_local_then_global(A, b, x0, thr_mode=oracle.THR_REL_MAX, thr_param=beta,
+                                                   exp_mode=oracle.EXP_NONE, exp_rounds=0, tol=1e-9)
+        assert sr["K"] == k
+        x = cu(x0)
+        st = lcg.Stats()
+        lcg.solve_local_then_global(ctx, gop, cu(b), x, prm, st)
+        assert st.K == k and abs(st.it_local - sr["it_local"]) <= 1
+        assert st.relres_tilde == pytest.approx(sr["relres_tilde"], rel=1e-6)
+        assert oracle.relres(A, b, x.cpu().numpy()) <= 1e-9
+
+
+def edge_case_problem():
+    """A 64 x 48 operator and b = A x0 + s, s > 0 on 40 cells with distinct
+    values, so the k largest residuals are separated by a threshold beta(k)."""
+    op = gen.random_stencil_2d(5, 64, 48)
+    A = oracle.from_stencil(op)
+    rng = np.random.default_rng(8)
+    x0 = 1.0 + 0.1 * rng.standard_normal(op.n)
+    s = np.zeros(op.n)
+    idx = rng.choice(op.n, size=40, replace=False)
+    s[idx] = np.linspace(1.0, 2.0, 40)
+    b = gen.csr_matvec(A.rowptr, A.col, A.val, x0) + s
+    r = np.abs(b - gen.csr_matvec(A.rowptr, A.col, A.val, x0))
+    order = np.argsort(-r, kind="stable")
+
+    def beta_for(k):
+        return float((r[order[k - 1]] + r[order[k]]) / 2 / r.max())
+
+    return op, A, b, x0, beta_for
+
+
 def test_local_then_global_edge_K_zero_and_full(ctx):
     d = gen.cfg1_heat2d(seed=2, n=40, radius=4)
     A = oracle.from_stencil(d["op"])
