@@ -172,6 +172,14 @@ def stencil_matvec(op: "Stencil", x: np.ndarray) -> np.ndarray:
     return y.ravel()
 
 
+def redblack_colouring(shape) -> np.ndarray:
+    """Colour (x + y + z) mod 2 of every cell, i = x + nx (y + ny z): no two
+    cells of the 5-point / 7-point stencil that are neighbours share a colour."""
+    nx, ny, nz = (tuple(shape) + (1, 1))[:3]
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return ((x + y + z) & 1).astype(np.uint8).ravel()
+
+
 def csr_matvec(rowptr, col, val, x):
     """y = A x for problem set-up (manufactured right-hand sides)."""
     import scipy.sparse as sp

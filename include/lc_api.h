@@ -105,7 +105,7 @@ typedef struct {
     int32_t         grad_layers;  /* dilation layers after Alg 2 (0 = as printed) */
     lc_solve_params global;       /* the whole-system solve (Alg 1 step 11) */
     lc_solve_params local;        /* the subsystem solve (Alg 1 step 5); tol relative to ||rhs_L||_2 */
-    int32_t         gs_sweeps;    /* Gauss-Seidel sweeps of Alg 1 step 7 (0; others: LC_ERR_UNSUPPORTED) */
+    int32_t         gs_sweeps;    /* Gauss-Seidel sweeps of Alg 1 step 7 on x~, 0..64 (see lc_gs_smooth) */
 } lc_params;
 
 /* Per-call statistics in the paper's notation (Sec. 3: N, K, eta = K/N). */
@@ -210,11 +210,30 @@ LC_EXPORT int lc_extract(lc_ctx *ctx, const lc_op *op, const uint8_t *mask, cons
 LC_EXPORT int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double *x,
                  const lc_solve_params *p, lc_stats *stats, void *stream);
 
+/* Gauss-Seidel smoothing (Alg 1 step 7): `sweeps` (0..64) multicolour
+ * Gauss-Seidel sweeps over the whole system A x = b, in place in x (device,
+ * N values).  Colour after colour, every point i of the colour is set to
+ *     s = b_i; for j ascending, j != i: s = fma(-a_ij, x_j, s); x_i = s / a_ii
+ * from the newest neighbour values.  Stencil operators use the red-black
+ * colouring (x + y + z) mod 2; CSR operators need lc_op_set_colouring first
+ * (else LC_ERR_UNSUPPORTED).  Since no two neighbours share a colour, the
+ * result equals the serial sweep bit for bit. */
+LC_EXPORT int lc_gs_smooth(lc_ctx *ctx, const lc_op *op, const double *b, double *x, int32_t sweeps,
+                           void *stream);
+
+/* Colouring of a CSR operator's rows for lc_gs_smooth: colour[n] (device,
+ * uint8, values < ncolours, kept by reference like the operator's arrays),
+ * checked on the device to give no two neighbours (stored a_ij != 0, j != i)
+ * the same colour (LC_ERR_INVALID_ARG otherwise; waits for the check).
+ * colour = NULL removes it.  Stencil operators: LC_ERR_INVALID_ARG. */
+LC_EXPORT int lc_op_set_colouring(lc_op *op, const uint8_t *colour, int32_t ncolours);
+
 /* Alg 1 without host synchronisation: mark (residual or gradient), extract,
  * local Jacobi-PCG from xL0 (tolerance relative to ||rhs||), assemble x~ in
- * place in x, check ||b - A x~|| <= tol ||b||, and only if that fails run the
- * global PCG from x~.  x: in x0, out x.  stats (host, may be NULL) waits for
- * the stream and fills phase times. */
+ * place in x, smooth it by p->gs_sweeps Gauss-Seidel sweeps (lc_gs_smooth),
+ * check ||b - A x~|| <= tol ||b||, and only if that fails run the global PCG
+ * from x~.  x: in x0, out x.  stats (host, may be NULL) waits for the stream
+ * and fills phase times (t_local_ms includes assembly and smoothing). */
 LC_EXPORT int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const double *b, double *x,
                                const lc_params *p, lc_stats *stats, void *stream);
 

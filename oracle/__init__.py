@@ -41,7 +41,7 @@ class _Params(C.Structure):
     _fields_ = [("mark_mode", C.c_int32), ("thr_mode", C.c_int32), ("thr_param", C.c_double),
                 ("exp_mode", C.c_int32), ("exp_rounds", C.c_int32), ("alpha", C.c_double),
                 ("grad_layers", C.c_int32), ("tol", C.c_double), ("tol_local", C.c_double),
-                ("maxit", C.c_int32)]
+                ("maxit", C.c_int32), ("gs_sweeps", C.c_int32), ("gs_ncolours", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -85,8 +85,10 @@ def load(path: str):
     L.orc_pcg.argtypes = csr + [_f64p, _f64p, C.c_double, C.c_int32, C.POINTER(C.c_int32),
                                 C.POINTER(C.c_double)]
     L.orc_pcg.restype = C.c_int32
-    L.orc_solve_local_then_global.argtypes = csr + [_f64p, _f64p, C.POINTER(_Params), C.POINTER(_Stats), _u8p]
+    L.orc_solve_local_then_global.argtypes = csr + [_f64p, _f64p, C.POINTER(_Params), C.POINTER(_Stats), _u8p,
+                                                    _u8p]
     L.orc_solve_local_then_global.restype = C.c_int32
+    L.orc_gs_sweep.argtypes = csr + [_f64p, _f64p, _u8p, C.c_int32]
     L.orc_adjoint_grad_k_2d.argtypes = [C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _f64p]
     return L
 
@@ -227,16 +229,30 @@ def pcg(A: CSR, b, x0, tol=1e-8, maxit=100000):
     return x, st, it.value, rr.value
 
 
+def gs_sweep(A: CSR, b, x, colour, ncolours: int | None = None) -> np.ndarray:
+    """One multicolour Gauss-Seidel sweep (Alg 1 step 7) from x; returns the new x."""
+    colour = np.ascontiguousarray(colour, dtype=np.uint8)
+    nc = int(colour.max()) + 1 if ncolours is None and len(colour) else (ncolours or 0)
+    out = _f(x).copy()
+    lib().orc_gs_sweep(*A.args(), _f(b), out, colour if len(colour) else np.zeros(1, np.uint8), nc)
+    return out
+
+
 def solve_local_then_global(A: CSR, b, x0, mark_mode=MARK_RESIDUAL, thr_mode=THR_REL_MAX, thr_param=1e-3,
                             exp_mode=EXP_DILATE, exp_rounds=2, alpha=1e-3, grad_layers=0,
-                            tol=1e-8, tol_local=None, maxit=100000):
-    """Alg 1 (without its Gauss-Seidel step).  Returns (x, stats dict, mask)."""
+                            tol=1e-8, tol_local=None, maxit=100000, gs_sweeps=0, colour=None):
+    """Alg 1; gs_sweeps multicolour Gauss-Seidel sweeps with the given
+    colouring smooth x~ (step 7).  Returns (x, stats dict, mask)."""
+    if gs_sweeps and colour is None:
+        raise ValueError("Gauss-Seidel smoothing needs a colouring")
+    col = np.zeros(max(A.n, 1), np.uint8) if colour is None else np.ascontiguousarray(colour, dtype=np.uint8)
+    ncol = int(col.max()) + 1 if colour is not None and A.n else 0
     p = _Params(mark_mode, thr_mode, thr_param, exp_mode, exp_rounds, alpha, grad_layers, tol,
-                tol if tol_local is None else tol_local, maxit)
+                tol if tol_local is None else tol_local, maxit, gs_sweeps, ncol)
     s = _Stats()
     x = _f(x0).copy()
     mask = np.zeros(max(A.n, 1), np.uint8)
-    lib().orc_solve_local_then_global(*A.args(), _f(b), x, C.byref(p), C.byref(s), mask)
+    lib().orc_solve_local_then_global(*A.args(), _f(b), x, C.byref(p), C.byref(s), mask, col)
     stats = {f: getattr(s, f) for f, _ in _Stats._fields_}
     return x, stats, mask[:A.n]
 

@@ -37,6 +37,10 @@
  *   R8 local indices follow ascending global index (a symmetric
  *        permutation of the paper's Q; it leaves the subsystem's solution
  *        unchanged).
+ *   R9 Gauss-Seidel smoothing (Alg 1 step 7): multicolour sweeps with a
+ *        caller-given colouring in which no two neighbours share a colour;
+ *        per point s = b_i; for j ascending, j != i: s = fma(-a_ij, x_j, s);
+ *        x_i = s / a_ii.
  */
 #include <math.h>
 #include <stdint.h>
@@ -378,6 +382,30 @@ done:
     return status;
 }
 
+/* ------------------------------------- Gauss-Seidel smoothing (Alg 1 step 7) */
+
+/* One multicolour Gauss-Seidel sweep over A x = b (the whole system, Alg 1
+ * step 7): for colour c = 0 .. ncol-1, for i ascending with colour[i] == c,
+ *     s = b_i; for j ascending, j != i: s = fma(-a_ij, x_j, s); x_i = s / a_ii
+ * using the newest x_j.  The caller's colouring gives no two neighbours the
+ * same colour, so the sweep equals lexicographic Gauss-Seidel on the
+ * colour-ordered system and does not depend on the order inside a colour
+ * (red-black for the 5-point and 7-point stencils). */
+void orc_gs_sweep(int32_t n, const int32_t *rp, const int32_t *ci, const double *av,
+                  const double *b, double *x, const uint8_t *colour, int32_t ncol)
+{
+    for (int32_t c = 0; c < ncol; ++c)
+        for (int32_t i = 0; i < n; ++i) {
+            if (colour[i] != c) continue;
+            double s = b[i], d = 0.0;
+            for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+                if (ci[e] == i) d = av[e];
+                else s = fma(-av[e], x[ci[e]], s);
+            }
+            x[i] = s / d;
+        }
+}
+
 /* -------------------------------------------- Alg 1: local, then global */
 
 #define ORC_MARK_RESIDUAL 0
@@ -394,6 +422,8 @@ typedef struct {
     double  tol;            /* global tolerance eps of Eq. rel-res-conv-criteria */
     double  tol_local;      /* local solve tolerance, relative to ||rhs_L||_2 */
     int32_t maxit;
+    int32_t gs_sweeps;      /* Gauss-Seidel sweeps of step 7 (0 = none) */
+    int32_t gs_ncolours;    /* colours of the caller's colouring */
 } orc_params;
 
 typedef struct {
@@ -401,13 +431,15 @@ typedef struct {
     double tau, relres_tilde, relres_final;
 } orc_stats;
 
-/* Alg 1 (without the Gauss-Seidel smoothing of its step 7): construct the
- * local domain, extract and solve the subsystem from x0[Omega], assemble
- * x~, return it if it meets the criterion, else solve the whole system from
- * x~.  x holds x0 on entry and the solution on exit. */
+/* Alg 1: construct the local domain, extract and solve the subsystem from
+ * x0[Omega], assemble x~, smooth it with gs_sweeps multicolour Gauss-Seidel
+ * sweeps over the whole system (step 7; `colour` may be NULL when
+ * gs_sweeps == 0), return it if it meets the criterion, else solve the whole
+ * system from x~.  x holds x0 on entry and the solution on exit. */
 int32_t orc_solve_local_then_global(int32_t n, const int32_t *rp, const int32_t *ci,
                                     const double *av, const double *b, double *x,
-                                    const orc_params *prm, orc_stats *st, uint8_t *mask_out)
+                                    const orc_params *prm, orc_stats *st, uint8_t *mask_out,
+                                    const uint8_t *colour)
 {
     size_t nn = (size_t)(n > 0 ? n : 1);
     int32_t nnz = rp[n];
@@ -437,6 +469,8 @@ int32_t orc_solve_local_then_global(int32_t n, const int32_t *rp, const int32_t 
         if (status == ORC_BREAKDOWN) goto out;
     }
     orc_assemble(n, x, K, l2g, xl, xt);
+    for (int32_t sw = 0; sw < prm->gs_sweeps; ++sw)
+        orc_gs_sweep(n, rp, ci, av, b, xt, colour, prm->gs_ncolours);
     st->relres_tilde = orc_relres(n, rp, ci, av, b, xt);
     memcpy(x, xt, sizeof(double) * nn);
     if (st->relres_tilde <= prm->tol) {

@@ -112,6 +112,8 @@ def lib():
     L.lc_assemble_diffusion_2d.argtypes = [vp, C.POINTER(i32), vp, d, vp, vp, vp, vp]
     L.lc_op_refresh.argtypes = [vp, vp]
     L.lc_adjoint_grad_k_2d.argtypes = [vp, C.POINTER(i32), vp, vp, vp, vp, vp]
+    L.lc_gs_smooth.argtypes = [vp, vp, vp, vp, i32, vp]
+    L.lc_op_set_colouring.argtypes = [vp, vp, i32]
     _lib = L
     return L
 
@@ -159,6 +161,17 @@ class Context:
 class _Operator:
     n: int
     nnz: int
+
+    def set_colouring(self, colour, ncolours: int | None = None):
+        """lc_op_set_colouring: uint8 device colours of a CSR operator's rows
+        for Gauss-Seidel (None removes; stencil operators refuse it)."""
+        if colour is None:
+            self._colour = None
+            return self.ctx.check(lib().lc_op_set_colouring(self.h, None, 0))
+        if ncolours is None:
+            ncolours = int(colour.max().item()) + 1
+        self._colour = colour
+        return self.ctx.check(lib().lc_op_set_colouring(self.h, _ptr(colour, torch.uint8, "colour"), int(ncolours)))
 
     def set_tuning(self, key: str, value: int):
         """lc_op_set_tuning (launch-shape knobs for the autotuner)."""
@@ -251,6 +264,12 @@ def mark_residual(ctx: Context, op: _Operator, b, x0, params: MarkParams, mask, 
                                             _ptr(tau, torch.float64, "tau"), _stream(stream)))
 
 
+def gs_smooth(ctx: Context, op: _Operator, b, x, sweeps: int, stream=None):
+    """lc_gs_smooth: multicolour Gauss-Seidel sweeps on A x = b, in place in x."""
+    return ctx.check(lib().lc_gs_smooth(ctx.h, op.h, _ptr(b, torch.float64, "b"), _ptr(x, torch.float64, "x"),
+                                        int(sweeps), _stream(stream)))
+
+
 def mark_gradient(ctx: Context, op: _Operator, x0, alpha: float, layers: int, mask, K, gmax=None, stream=None):
     """lc_mark_gradient."""
     return ctx.check(lib().lc_mark_gradient(ctx.h, op.h, _ptr(x0, torch.float64, "x0"), float(alpha), int(layers),
@@ -291,11 +310,12 @@ def kernel_launch_count() -> int:
 
 def default_params(mark_mode=MARK_RESIDUAL, thr_mode=THR_REL_MAX, thr_param=1e-3, exp_mode=EXP_DILATE, exp_rounds=2,
                    alpha=1e-3, grad_layers=2, tol=1e-8, tol_local=None, max_iter=100000,
-                   precision=PREC_FP64, inner_tol=1e-5, max_outer=30) -> Params:
+                   precision=PREC_FP64, inner_tol=1e-5, max_outer=30, gs_sweeps=0) -> Params:
     """Alg 1 parameters with the relative-threshold, 2-layer defaults."""
     g = SolveParams(tol, max_iter, precision, inner_tol, max_outer)
     l = SolveParams(tol if tol_local is None else tol_local, max_iter, precision, inner_tol, max_outer)
-    return Params(mark_mode, MarkParams(thr_mode, thr_param, exp_mode, exp_rounds), alpha, grad_layers, g, l, 0)
+    return Params(mark_mode, MarkParams(thr_mode, thr_param, exp_mode, exp_rounds), alpha, grad_layers, g, l,
+                  gs_sweeps)
 
 
 LC_NOALLOC_MAX_CELLS = 4194304

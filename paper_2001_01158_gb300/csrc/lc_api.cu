@@ -50,6 +50,8 @@ struct lc_op {
     // tuning knobs (lc_op_set_tuning)
     int pcg_minblocks = 3;   // register budget of the structured-grid PCG kernel
     int pcg_grid_cap = 0;    // blocks of the global PCG launch (0: as many as fit)
+    const uint8_t *colour = nullptr;    // CSR: caller's colouring for Gauss-Seidel (device)
+    int ncolours = 0;
     // local solves of up to this many rows on one thread-block cluster of
     // 256-thread CTAs: measured faster than the grid kernel below ~8K rows
     int local_cluster_rows = 8192;
@@ -870,13 +872,60 @@ int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const
     return stats->status;
 }
 
+static constexpr int kMaxGsSweeps = 64;
+
+static int check_gs(lc_ctx *ctx, const lc_op *op, int sweeps) {
+    if (sweeps < 0 || sweeps > kMaxGsSweeps)
+        return fail(ctx, LC_ERR_INVALID_ARG, "gs_sweeps must be 0..%d", kMaxGsSweeps);
+    if (sweeps > 0 && op->kind != 0 && !op->colour)
+        return fail(ctx, LC_ERR_UNSUPPORTED, "Gauss-Seidel on a CSR operator needs a colouring (lc_op_set_colouring)");
+    return LC_OK;
+}
+
+static int gs_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, int sweeps, cudaStream_t s) {
+    if (sweeps <= 0 || op->n == 0) return LC_OK;
+    if (op->kind == 0) LC_CUDA(ctx, lc::launch_gs_stencil(op->st, b, x, sweeps, s));
+    else LC_CUDA(ctx, lc::launch_gs_csr(op->csr, op->colour, op->ncolours, b, x, sweeps, s));
+    return LC_OK;
+}
+
+int lc_gs_smooth(lc_ctx *ctx, const lc_op *op, const double *b, double *x, int32_t sweeps, void *stream) {
+    int rc = check_common(ctx, op);
+    if (rc) return rc;
+    if (!b || !x) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    if ((rc = check_gs(ctx, op, sweeps))) return rc;
+    return gs_impl(ctx, op, b, x, sweeps, (cudaStream_t)stream);
+}
+
+int lc_op_set_colouring(lc_op *op, const uint8_t *colour, int32_t ncolours) {
+    if (!op) return LC_ERR_INVALID_ARG;
+    lc_ctx *ctx = op->ctx;
+    if (op->kind == 0) return fail(ctx, LC_ERR_INVALID_ARG, "stencil operators use the red-black colouring");
+    if (!colour) {
+        op->colour = nullptr;
+        op->ncolours = 0;
+        return LC_OK;
+    }
+    if (ncolours < 1 || ncolours > 255) return fail(ctx, LC_ERR_INVALID_ARG, "ncolours must be 1..255");
+    LC_CUDA(ctx, cudaSetDevice(ctx->device));
+    int *bad = reinterpret_cast<int *>(&op->ctrl->K);
+    LC_CUDA(ctx, cudaMemset(bad, 0, sizeof(int)));
+    LC_CUDA(ctx, lc::launch_check_colouring(op->csr, colour, ncolours, bad, 0));
+    int hbad = 0;
+    LC_CUDA(ctx, cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hbad) return fail(ctx, LC_ERR_INVALID_ARG, "colouring out of range or two neighbours share a colour");
+    op->colour = colour;
+    op->ncolours = ncolours;
+    return LC_OK;
+}
+
 int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_params *p,
                                lc_stats *stats, void *stream) {
     int rc = check_common(ctx, op);
     if (rc) return rc;
     if (!b || !x || !p) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
     if ((rc = check_solve_params(ctx, &p->global)) || (rc = check_solve_params(ctx, &p->local))) return rc;
-    if (p->gs_sweeps != 0) return fail(ctx, LC_ERR_UNSUPPORTED, "Gauss-Seidel smoothing is not provided by this build");
+    if ((rc = check_gs(ctx, op, p->gs_sweeps))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (stats) LC_CUDA(ctx, cudaEventRecord(op->ev[0], s));
     // 1. local domain (Alg 2 or Alg 3)
@@ -896,8 +945,10 @@ int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const double *b, do
     if ((rc = pcg_impl(ctx, op, op->sub.rhs, op->sub.xL0, &p->local, op->ctrl_loc, true, s))) return rc;
     // 4. x~ = x0 with the local solution scattered in (Eq. sol-assemble)
     LC_CUDA(ctx, lc::launch_assemble(op->sub.K, op->sub.l2g, op->sub.xL0, x, op->n, s));
+    // 5. Gauss-Seidel smoothing of x~ over the whole system (step 7)
+    if ((rc = gs_impl(ctx, op, b, x, p->gs_sweeps, s))) return rc;
     if (stats) LC_CUDA(ctx, cudaEventRecord(op->ev[3], s));
-    // 5. convergence check of x~ and, if needed, the global solve from x~
+    // 6. convergence check of x~ and, if needed, the global solve from x~
     if ((rc = pcg_impl(ctx, op, b, x, &p->global, op->ctrl, false, s))) return rc;
     if (!stats) return LC_OK;
     LC_CUDA(ctx, cudaEventRecord(op->ev[4], s));

@@ -315,6 +315,13 @@ cudaError_t launch_extract_csr(const Csr &op, const uint8_t *mask, const double 
 cudaError_t launch_assemble(const int32_t *K_dev, const int32_t *l2g, const double *xbar, double *x, int64_t cap,
                             cudaStream_t s);
 
+// Gauss-Seidel smoothing, Alg 1 step 7 (lc_smooth.cu): `sweeps` multicolour
+// sweeps in place -- red-black for stencils, the caller's colouring for CSR
+cudaError_t launch_gs_stencil(const Stencil &s, const double *b, double *x, int sweeps, cudaStream_t st);
+cudaError_t launch_gs_csr(const Csr &cs, const uint8_t *colour, int ncol, const double *b, double *x, int sweeps,
+                          cudaStream_t st);
+cudaError_t launch_check_colouring(const Csr &cs, const uint8_t *colour, int ncol, int *bad, cudaStream_t st);
+
 // Krylov (lc_pcg.cu)
 struct PcgWork {
     double *r, *z, *p0, *p1, *q;     // capacity n

@@ -32,6 +32,10 @@ PIN_GROUPS = {
     "alg1": [(P.test_local_then_global_agrees_with_global, {}), (P.test_local_then_global_edge_cases, {}),
              (P.test_rtilde_identity_and_bound, {}), (P.test_example1_local_solve_converges_without_global, {})],
     "adjoint": [(P.test_adjoint_gradient_matches_finite_differences, {})],
+    "gs": [(P.test_gs_sweep_is_lexicographic_gs_on_colour_ordered_system, {"seed": sd, "shape": sh})
+           for sd, sh in P.GS_CASES] + [(P.test_gs_sweep_diagonal_and_fixed_point, {}),
+                                        (P.test_gs_sweep_reduces_energy_error, {}),
+                                        (P.test_local_then_global_applies_gs_to_x_tilde, {})],
 }
 
 # (name, pin group, original text, mutated text)
@@ -64,6 +68,11 @@ MUTANTS = [
     ("alg1_skip_local", "alg1", "if (K > 0) {\n        status = orc_pcg(K,", "if (K < 0) {\n        status = orc_pcg(K,"),
     ("adjoint_wrong_k", "adjoint", "double dT = 2.0 * k[m] * k[m] / (den * den);", "double dT = 2.0 * k[c] * k[c] / (den * den);"),
     ("adjoint_drop_boundary", "adjoint", "s += 2.0 * lam[c] * x[c];", "s += 0.0 * lam[c] * x[c];"),
+    ("gs_sign", "gs", "else s = fma(-av[e], x[ci[e]], s);", "else s = fma(av[e], x[ci[e]], s);"),
+    ("gs_wrong_diagonal", "gs", "x[i] = s / d;", "x[i] = s / av[rp[i]];"),
+    ("gs_colours_reversed", "gs", "for (int32_t c = 0; c < ncol; ++c)", "for (int32_t c = ncol - 1; c >= 0; --c)"),
+    ("alg1_gs_one_sweep_short", "gs", "for (int32_t sw = 0; sw < prm->gs_sweeps; ++sw)",
+     "for (int32_t sw = 1; sw < prm->gs_sweeps; ++sw)"),
 ]
 
 

@@ -520,3 +520,84 @@ def test_pcg_finite_termination():
     M = 0.5 * (M + M.T)
     x, st, it, rr = oracle.pcg(_dense_to_csr(M), b, np.zeros(40), tol=1e-12)
     assert st == oracle.OK and it == 2 and rr <= 1e-12
+
+
+# ------------------------------------------------------- Gauss-Seidel (Alg 1 step 7)
+
+GS_CASES = [(0, (7, 5, 1)), (1, (9, 9, 1)), (2, (1, 6, 1)), (3, (12, 10, 1)), (4, (4, 3, 5)), (5, (5, 5, 2))]
+
+
+def gs_problem(seed, shape):
+    nx, ny, nz = shape
+    op = gen.random_stencil_2d(seed, nx, ny) if nz == 1 else gen.random_stencil_3d(seed, nx, ny, nz)
+    A = oracle.from_stencil(op)
+    rng = np.random.default_rng(seed + 40)
+    return A, rng.standard_normal(A.n), rng.standard_normal(A.n), gen.redblack_colouring(shape)
+
+
+def test_redblack_colouring_is_proper():
+    for seed, shape in GS_CASES:
+        A, _, _, col = gs_problem(seed, shape)
+        rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+        off = A.col != rows
+        assert not np.any(col[rows[off]] == col[A.col[off]])
+
+
+@pytest.mark.parametrize("seed,shape", GS_CASES)
+def test_gs_sweep_is_lexicographic_gs_on_colour_ordered_system(seed, shape):
+    """A multicolour sweep equals textbook Gauss-Seidel x <- (D + L)^-1 (b - U x)
+    on P A P^T, P ordering the cells by colour (stably)."""
+    A, b, x, col = gs_problem(seed, shape)
+    got = oracle.gs_sweep(A, b, x, col)
+    perm = np.argsort(col, kind="stable")
+    M = A.dense()[np.ix_(perm, perm)]
+    DL, U = np.tril(M), np.triu(M, 1)
+    ref = np.empty(A.n)
+    ref[perm] = np.linalg.solve(DL, b[perm] - U @ x[perm])
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_gs_sweep_diagonal_and_fixed_point():
+    """Diagonal A: one sweep gives b / d exactly; at the solution of A x = b
+    a sweep changes x only by rounding."""
+    n = 11
+    d = np.linspace(1.0, 3.0, n)
+    D = oracle.csr(np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), d)
+    b = np.random.default_rng(1).standard_normal(n)
+    got = oracle.gs_sweep(D, b, np.zeros(n), np.zeros(n, np.uint8))
+    assert np.array_equal(got, b / d)
+    A, b, _, col = gs_problem(3, (12, 10, 1))
+    xs = np.linalg.solve(A.dense(), b)
+    assert np.allclose(oracle.gs_sweep(A, b, xs, col), xs, rtol=1e-13, atol=1e-13 * np.abs(xs).max())
+
+
+def test_gs_sweep_reduces_energy_error():
+    """Gauss-Seidel on an SPD matrix contracts the A-norm of the error."""
+    A, b, x, col = gs_problem(4, (4, 3, 5))
+    Ad = A.dense()
+    xs = np.linalg.solve(Ad, b)
+    prev = None
+    for _ in range(4):
+        e = x - xs
+        en = float(e @ Ad @ e)
+        if prev is not None:
+            assert en < prev
+        prev = en
+        x = oracle.gs_sweep(A, b, x, col)
+
+
+def test_local_then_global_applies_gs_to_x_tilde():
+    """Alg 1 step 7: with a tolerance that accepts x~ at once, the result is
+    x~ of the run without smoothing followed by the given sweeps."""
+    d = gen.cfg1_heat2d(seed=6, n=40, radius=5)
+    A = oracle.from_stencil(d["op"])
+    col = gen.redblack_colouring(d["op"].shape)
+    x_plain, s_plain, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], tol=1.0)
+    assert s_plain["early_exit"] == 1
+    x_gs, s_gs, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], tol=1.0, gs_sweeps=2, colour=col)
+    ref = oracle.gs_sweep(A, d["b"], oracle.gs_sweep(A, d["b"], x_plain, col), col)
+    assert np.array_equal(x_gs, ref)
+    assert s_gs["relres_tilde"] == oracle.relres(A, d["b"], ref)
+    # and at a real tolerance the smoothed start still reaches it
+    x, s, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], tol=1e-9, gs_sweeps=1, colour=col)
+    assert oracle.relres(A, d["b"], x) <= 1e-9
