@@ -50,6 +50,15 @@ class _Stats(C.Structure):
                 ("tau", C.c_double), ("relres_tilde", C.c_double), ("relres_final", C.c_double)]
 
 
+class _HeatStats(C.Structure):
+    _fields_ = [("picard_its", C.c_int32), ("it_local", C.c_int32), ("it_global", C.c_int32),
+                ("K_sum", C.c_int32), ("early_exits", C.c_int32), ("status", C.c_int32),
+                ("last_update", C.c_double)]
+
+
+BC_DIRICHLET, BC_NEUMANN = 0, 1
+
+
 def lib():
     """Load (building first if needed) the oracle shared library."""
     global _lib
@@ -89,6 +98,13 @@ def load(path: str):
                                                     _u8p]
     L.orc_solve_local_then_global.restype = C.c_int32
     L.orc_gs_sweep.argtypes = csr + [_f64p, _f64p, _u8p, C.c_int32]
+    L.orc_heat2d_system.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, _i32p, _f64p, _f64p, _f64p,
+                                    _i32p, _i32p, _f64p, _f64p]
+    L.orc_heat2d_system.restype = C.c_int32
+    L.orc_heat2d_step.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, _i32p, _f64p, _f64p,
+                                  _f64p, C.c_int32, C.POINTER(_Params), C.c_double, C.c_int32,
+                                  C.POINTER(_HeatStats), _u8p]
+    L.orc_heat2d_step.restype = C.c_int32
     L.orc_adjoint_grad_k_2d.argtypes = [C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _f64p]
     return L
 
@@ -255,6 +271,36 @@ def solve_local_then_global(A: CSR, b, x0, mark_mode=MARK_RESIDUAL, thr_mode=THR
     lib().orc_solve_local_then_global(*A.args(), _f(b), x, C.byref(p), C.byref(s), mask, col)
     stats = {f: getattr(s, f) for f, _ in _Stats._fields_}
     return x, stats, mask[:A.n]
+
+
+def heat2d_system(nx: int, ny: int, h: float, dt: float, bc_type, bc_val, kappa, Tn):
+    """CSR A and b of the Picard-linearised backward-Euler heat system (Sec. 3.2)."""
+    n = nx * ny
+    rp = np.empty(n + 1, np.int32)
+    ci = np.empty(5 * n, np.int32)
+    av = np.empty(5 * n)
+    b = np.empty(n)
+    nz = lib().orc_heat2d_system(nx, ny, h, dt, np.ascontiguousarray(bc_type, np.int32), _f(bc_val), _f(kappa),
+                                 _f(Tn), rp, ci, av, b)
+    return csr(rp, ci[:nz].copy(), av[:nz].copy()), b
+
+
+def heat2d_step(nx: int, ny: int, h: float, dt: float, p: float, bc_type, bc_val, Tn, T0=None, method=1,
+                mark_mode=MARK_RESIDUAL, thr_mode=THR_EPS_NORMB, thr_param=1e-10, exp_mode=EXP_PAPER, exp_rounds=1,
+                alpha=1e-4, grad_layers=0, tol=1e-10, maxit=100000, picard_tol=1e-8, max_picard=100,
+                gs_sweeps=0):
+    """One Picard-iterated backward-Euler step of the 2D heat problem (Sec. 3.2)
+    from T^{n+1,0} = T0 (default Tn).  method 0: global PCG; 1: Alg 1.
+    Returns (T^{n+1}, stats dict)."""
+    prm = _Params(mark_mode, thr_mode, thr_param, exp_mode, exp_rounds, alpha, grad_layers, tol, tol, maxit,
+                  gs_sweeps, 2 if gs_sweeps else 0)
+    T = _f(Tn if T0 is None else T0).copy()
+    hs = _HeatStats()
+    col = np.zeros(nx * ny, np.uint8)
+    col.reshape(ny, nx)[:] = (np.add.outer(np.arange(ny), np.arange(nx)) & 1).astype(np.uint8)
+    lib().orc_heat2d_step(nx, ny, h, dt, p, np.ascontiguousarray(bc_type, np.int32), _f(bc_val), _f(Tn), T,
+                          method, C.byref(prm), picard_tol, max_picard, C.byref(hs), col)
+    return T, {f: getattr(hs, f) for f, _ in _HeatStats._fields_}
 
 
 def adjoint_grad_k_2d(nx: int, ny: int, k, x, lam) -> np.ndarray:

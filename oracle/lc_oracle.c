@@ -518,3 +518,119 @@ void orc_adjoint_grad_k_2d(int32_t nx, int32_t ny, const double *k, const double
             dk[c] = -s;
         }
 }
+
+/* ------------------------------- nonlinear 2D heat conduction (Sec. 3.2) */
+
+#define ORC_BC_DIRICHLET 0
+#define ORC_BC_NEUMANN 1
+
+/* Picard-linearised backward-Euler system of dT/dt = div(kappa(T) grad T) on
+ * an nx x ny grid of cells of width h (Sec. 3.2, Eq. picard-equs), from the
+ * cell conductivities kappa (evaluated at the previous Picard iterate) and
+ * the previous time level Tn.  Sides in the order x-, x+, y-, y+; a Dirichlet
+ * side holds T = bc_val through a ghost at half a cell (coefficient
+ * 2 kappa_P/h^2, its value moved to b), a Neumann side has no flux.  With
+ * c = 1/(h h) and faces visited W, E, S, N:
+ *   T_f  = ((2 kappa_P) kappa_N / (kappa_P + kappa_N)) c    (interior face)
+ *   g    = (2 kappa_P) c                                      (Dirichlet face)
+ *   a_PP = 1/dt, then a_PP = a_PP + T_f or + g per face;  a_PN = -T_f
+ *   b_P  = Tn_P (1/dt), then b_P = b_P + g bc_val per Dirichlet face.
+ * CSR with ascending columns into rp[n+1], ci[5n], av[5n]; returns nnz. */
+int32_t orc_heat2d_system(int32_t nx, int32_t ny, double h, double dt, const int32_t bc_type[4],
+                          const double bc_val[4], const double *kappa, const double *Tn,
+                          int32_t *rp, int32_t *ci, double *av, double *b)
+{
+    const double c = 1.0 / (h * h), inv_dt = 1.0 / dt;
+    int32_t nz = 0;
+    for (int32_t y = 0; y < ny; ++y)
+        for (int32_t x = 0; x < nx; ++x) {
+            const int32_t i = x + nx * y;
+            const double kp = kappa[i];
+            /* faces W, E, S, N: neighbour index or -1 with the side it lies on */
+            const int32_t nb[4] = { x > 0 ? i - 1 : -1, x + 1 < nx ? i + 1 : -1,
+                                    y > 0 ? i - nx : -1, y + 1 < ny ? i + nx : -1 };
+            double tf[4];
+            double d = inv_dt, bi = Tn[i] * inv_dt;
+            for (int f = 0; f < 4; ++f) {
+                tf[f] = 0.0;
+                if (nb[f] >= 0) {
+                    const double kn = kappa[nb[f]];
+                    tf[f] = ((2.0 * kp) * kn / (kp + kn)) * c;
+                    d = d + tf[f];
+                } else if (bc_type[f] == ORC_BC_DIRICHLET) {
+                    const double g = (2.0 * kp) * c;
+                    d = d + g;
+                    bi = bi + g * bc_val[f];
+                }
+            }
+            rp[i] = nz;
+            /* ascending columns: S (i-nx), W (i-1), P, E (i+1), N (i+nx) */
+            if (nb[2] >= 0) { ci[nz] = nb[2]; av[nz++] = -tf[2]; }
+            if (nb[0] >= 0) { ci[nz] = nb[0]; av[nz++] = -tf[0]; }
+            ci[nz] = i; av[nz++] = d;
+            if (nb[1] >= 0) { ci[nz] = nb[1]; av[nz++] = -tf[1]; }
+            if (nb[3] >= 0) { ci[nz] = nb[3]; av[nz++] = -tf[3]; }
+            b[i] = bi;
+        }
+    rp[nx * ny] = nz;
+    return nz;
+}
+
+typedef struct {
+    int32_t picard_its;   /* Picard iterations of the step */
+    int32_t it_local;     /* CG iterations of all local solves */
+    int32_t it_global;    /* CG iterations of all global solves */
+    int32_t K_sum;        /* sum of |Omega_local| over the step's solves */
+    int32_t early_exits;  /* solves whose x~ met the criterion */
+    int32_t status;
+    double  last_update;  /* ||T^{s+1} - T^s||_2 of the last iteration */
+} orc_heat_stats;
+
+/* One time step of the 2D heat problem by Picard iteration (Sec. 3.2, Alg. of
+ * the 2-D heat solution): T holds T^{n+1,0} (normally T^n) on entry and
+ * T^{n+1} on exit.  Each iteration s: kappa = T^p at T^{n+1,s}; assemble the
+ * system; solve it from T^{n+1,s} by the global PCG (method 0) or by Alg 1
+ * with prm's marking and smoothing (method 1; `colour` as for
+ * orc_gs_sweep, NULL without smoothing); stop when ||T^{n+1,s+1} -
+ * T^{n+1,s}||_2 < picard_tol or after max_picard iterations. */
+int32_t orc_heat2d_step(int32_t nx, int32_t ny, double h, double dt, double p,
+                        const int32_t bc_type[4], const double bc_val[4], const double *Tn, double *T,
+                        int32_t method, const orc_params *prm, double picard_tol, int32_t max_picard,
+                        orc_heat_stats *hs, const uint8_t *colour)
+{
+    const int32_t n = nx * ny;
+    double *kappa = (double *)malloc(sizeof(double) * (size_t)n);
+    double *b = (double *)malloc(sizeof(double) * (size_t)n);
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    int32_t *rp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int32_t *ci = (int32_t *)malloc(sizeof(int32_t) * (size_t)(5 * n));
+    double *av = (double *)malloc(sizeof(double) * (size_t)(5 * n));
+    memset(hs, 0, sizeof(*hs));
+    int32_t status = ORC_OK;
+    for (int32_t s = 0; s < max_picard; ++s) {
+        for (int32_t i = 0; i < n; ++i) kappa[i] = pow(T[i], p);
+        orc_heat2d_system(nx, ny, h, dt, bc_type, bc_val, kappa, Tn, rp, ci, av, b);
+        memcpy(x, T, sizeof(double) * (size_t)n);
+        if (method == 0) {
+            int32_t it = 0;
+            status = orc_pcg(n, rp, ci, av, b, x, prm->tol, prm->maxit, &it, NULL);
+            hs->it_global += it;
+        } else {
+            orc_stats st;
+            status = orc_solve_local_then_global(n, rp, ci, av, b, x, prm, &st, NULL, colour);
+            hs->it_local += st.it_local;
+            hs->it_global += st.it_global;
+            hs->K_sum += st.K;
+            hs->early_exits += st.early_exit;
+        }
+        double d2 = 0.0;
+        for (int32_t i = 0; i < n; ++i) d2 += (x[i] - T[i]) * (x[i] - T[i]);
+        memcpy(T, x, sizeof(double) * (size_t)n);
+        hs->picard_its = s + 1;
+        hs->last_update = sqrt(d2);
+        if (status != ORC_OK || hs->last_update < picard_tol) break;
+    }
+    hs->status = status;
+    free(kappa); free(b); free(x); free(rp); free(ci); free(av);
+    return status;
+}

@@ -36,6 +36,9 @@ PIN_GROUPS = {
            for sd, sh in P.GS_CASES] + [(P.test_gs_sweep_diagonal_and_fixed_point, {}),
                                         (P.test_gs_sweep_reduces_energy_error, {}),
                                         (P.test_local_then_global_applies_gs_to_x_tilde, {})],
+    "heat": [(P.test_heat_system_symmetric_and_conservative, {}), (P.test_heat_system_exact_on_linear_steady_profile, {}),
+             (P.test_heat_system_exact_across_a_material_interface, {}),
+             (P.test_heat_step_steady_nonlinear_profile, {}), (P.test_heat_step_methods_agree_and_picard_fixed_point, {})],
 }
 
 # (name, pin group, original text, mutated text)
@@ -73,6 +76,12 @@ MUTANTS = [
     ("gs_colours_reversed", "gs", "for (int32_t c = 0; c < ncol; ++c)", "for (int32_t c = ncol - 1; c >= 0; --c)"),
     ("alg1_gs_one_sweep_short", "gs", "for (int32_t sw = 0; sw < prm->gs_sweeps; ++sw)",
      "for (int32_t sw = 1; sw < prm->gs_sweeps; ++sw)"),
+    ("heat_ghost_half", "heat", "const double g = (2.0 * kp) * c;", "const double g = kp * c;"),
+    ("heat_arithmetic_mean", "heat", "tf[f] = ((2.0 * kp) * kn / (kp + kn)) * c;", "tf[f] = (0.5 * (kp + kn)) * c;"),
+    ("heat_drop_bc_value", "heat", "bi = bi + g * bc_val[f];", "bi = bi + 0.0 * bc_val[f];"),
+    ("heat_kappa_from_Tn", "heat", "for (int32_t i = 0; i < n; ++i) kappa[i] = pow(T[i], p);",
+     "for (int32_t i = 0; i < n; ++i) kappa[i] = pow(Tn[i], p);"),
+    ("heat_wrong_neighbour", "heat", "const double kn = kappa[nb[f]];", "const double kn = kappa[i];"),
 ]
 
 

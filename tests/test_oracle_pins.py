@@ -601,3 +601,97 @@ def test_local_then_global_applies_gs_to_x_tilde():
     # and at a real tolerance the smoothed start still reaches it
     x, s, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], tol=1e-9, gs_sweeps=1, colour=col)
     assert oracle.relres(A, d["b"], x) <= 1e-9
+
+
+# ---------------------------------------------- nonlinear 2D heat (Sec. 3.2)
+
+def heat_grid(n):
+    h = 1.0 / n
+    xc = (np.arange(n) + 0.5) * h
+    return h, xc
+
+
+def test_heat_system_symmetric_and_conservative():
+    """For any conductivities: A is symmetric, and with no-flux sides every
+    row sums to 1/dt (interior fluxes cancel: the scheme conserves heat)."""
+    rng = np.random.default_rng(3)
+    nx, ny = 13, 9
+    kappa = 10 ** rng.uniform(-4, 0, nx * ny)
+    Tn = rng.uniform(0, 1, nx * ny)
+    h, dt = 1.0 / 13, 1e-2
+    A, b = oracle.heat2d_system(nx, ny, h, dt, [oracle.BC_NEUMANN] * 4, [0.0] * 4, kappa, Tn)
+    M = A.dense()
+    assert np.array_equal(M, M.T)
+    assert np.allclose(M.sum(axis=1), 1.0 / dt, rtol=1e-12, atol=1e-9 * np.abs(M).max())
+    assert np.allclose(b, Tn / dt, rtol=1e-15)
+    assert np.all(np.linalg.eigvalsh(M) > 0)
+
+
+def test_heat_system_exact_on_linear_steady_profile():
+    """kappa = 1, Dirichlet T = 1 at x = 0 and T = 0 at x = 1, no flux in y, and
+    dt -> infinity: the cell-centred scheme with half-cell ghosts is exact for
+    the linear profile T = 1 - x at the cell centres."""
+    n = 25
+    h, xc = heat_grid(n)
+    A, b = oracle.heat2d_system(n, 7, h, 1e300, [oracle.BC_DIRICHLET, oracle.BC_DIRICHLET, oracle.BC_NEUMANN,
+                                                  oracle.BC_NEUMANN], [1.0, 0.0, 0.0, 0.0], np.ones(n * 7),
+                                np.zeros(n * 7))
+    x = np.linalg.solve(A.dense(), b)
+    assert np.allclose(x, np.tile(1.0 - xc, 7), rtol=0, atol=1e-12)
+
+
+def test_heat_system_exact_across_a_material_interface():
+    """kappa = 1 on x < 1/2 and 50 on x > 1/2 (the interface on a face),
+    T = 1 and 0 at the ends, steady: the exact solution is piecewise linear
+    with one flux q = 1/(0.5/1 + 0.5/50), which the harmonic-mean face
+    conductance reproduces exactly at the cell centres."""
+    n, ny = 20, 3
+    h, xc = heat_grid(n)
+    k1, k2 = 1.0, 50.0
+    kap = np.tile(np.where(xc < 0.5, k1, k2), ny)
+    bc = [oracle.BC_DIRICHLET, oracle.BC_DIRICHLET, oracle.BC_NEUMANN, oracle.BC_NEUMANN]
+    A, b = oracle.heat2d_system(n, ny, h, 1e300, bc, [1.0, 0.0, 0.0, 0.0], kap, np.zeros(n * ny))
+    x = np.linalg.solve(A.dense(), b)
+    q = 1.0 / (0.5 / k1 + 0.5 / k2)
+    exact = np.where(xc < 0.5, 1.0 - q * xc / k1, q * (1.0 - xc) / k2)
+    assert np.allclose(x, np.tile(exact, ny), rtol=0, atol=1e-12)
+
+
+def test_heat_step_steady_nonlinear_profile():
+    """kappa = T (p = 1) between T = 1 and T = 0.5, a long time step: Picard
+    reaches the steady state of (T T')' = 0, T = sqrt(1 - 0.75 x), to the
+    scheme's second order (checked at two resolutions)."""
+    errs = []
+    for n in (16, 32):
+        h, xc = heat_grid(n)
+        T0 = np.full(n * 3, 0.75)
+        bc = [oracle.BC_DIRICHLET, oracle.BC_DIRICHLET, oracle.BC_NEUMANN, oracle.BC_NEUMANN]
+        T, st = oracle.heat2d_step(n, 3, h, 1e12, 1.0, bc, [1.0, 0.5, 0.0, 0.0], T0, method=0, tol=1e-13,
+                                   picard_tol=1e-12, max_picard=200)
+        assert st["status"] == oracle.OK and st["last_update"] < 1e-12
+        errs.append(np.abs(T - np.tile(np.sqrt(1.0 - 0.75 * xc), 3)).max())
+    assert errs[0] < 1e-3 and 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_heat_step_methods_agree_and_picard_fixed_point():
+    """The paper's E1 setting (99 x 99, kappa = T^3.5, dt = 1e-2): one step by
+    the global PCG and by Alg 1 with either marking agree to ~1e-9 (the paper
+    reports <= 7.6e-9 over 100 steps); the result is a fixed point of the
+    Picard map (its linear residual at its own conductivities is small)."""
+    n = 99
+    h, xc = heat_grid(n)
+    T0 = np.tile(np.exp(-100.0 * xc) + 1e-4, n)
+    bc = [oracle.BC_DIRICHLET, oracle.BC_DIRICHLET, oracle.BC_NEUMANN, oracle.BC_NEUMANN]
+    bv = [1.0, 1e-4, 0.0, 0.0]
+    T_0, s0 = oracle.heat2d_step(n, n, h, 1e-2, 3.5, bc, bv, T0, method=0)
+    T_1, s1 = oracle.heat2d_step(n, n, h, 1e-2, 3.5, bc, bv, T0, method=1, mark_mode=oracle.MARK_GRADIENT,
+                                 alpha=1e-4)
+    T_2, s2 = oracle.heat2d_step(n, n, h, 1e-2, 3.5, bc, bv, T0, method=1)
+    for T, s in ((T_1, s1), (T_2, s2)):
+        assert s["status"] == oracle.OK and s["K_sum"] > 0
+        assert np.linalg.norm(T - T_0) / np.linalg.norm(T_0) < 1e-8
+    A, b = oracle.heat2d_system(n, n, h, 1e-2, bc, bv, T_0 ** 3.5, T0)
+    assert oracle.relres(A, b, T_0) < 1e-7
+    # the heat front moves right (T rises behind it) and T stays within the boundary values
+    assert T_0.min() >= 1e-4 * (1 - 1e-9) and T_0.max() <= 1.0 + 1e-9
+    assert np.all(T_0.reshape(n, n)[:, :4] > T0.reshape(n, n)[:, :4])
