@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--n", type=int, default=2048, help="grid side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched workload")
+    ap.add_argument("--no-heat", action="store_true", help="skip the nonlinear heat runs (Sec. 3.2)")
     return ap.parse_args()
 
 
@@ -169,9 +170,9 @@ def measured_peaks():
 
 def source_digest() -> str:
     """Digest of the global PCG kernel's sources (the kernel file and the
-    shared header with its barrier and reductions)."""
+    device header with its descriptors, barrier and reductions)."""
     h = hashlib.sha256()
-    for name in ("lc_pcg.cu", "lc_internal.cuh"):
+    for name in ("lc_pcg.cu", "lc_device.cuh"):
         with open(os.path.join(ROOT, "paper_2001_01158_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -447,6 +448,8 @@ def run_gpu(args, rank, ws, local):
     }
     if not args.no_batched:
         res["batched_512"] = run_batched(args, rank, dev, ws)
+    if not args.no_heat:
+        res["heat_e1"] = {"99x99_100_steps": run_heat(dev, 99, 100), "1024x1024_10_steps": run_heat(dev, 1024, 10)}
     if rank == 0 and not args.no_cpu_baseline:
         from oracle.build import build_oracle
         build_oracle()
@@ -454,6 +457,57 @@ def run_gpu(args, rank, ws, local):
         res["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(res), flush=True)
+
+
+def run_heat(dev, n, steps):
+    """The paper's nonlinear 2D heat test (Sec. 3.2: kappa = T^3.5, T = 1 / 1e-4 at
+    x = 0 / 1, no flux in y, dt = 1e-2, T0 = exp(-100 x) + 1e-4, Picard to
+    ||dT|| < 1e-8, linear tolerance 1e-10) on n x n cells for `steps` steps,
+    by the global PCG, Alg 1 with gradient marking (alpha = 1e-4) and Alg 1
+    with the paper's residual marking (eps ||b||/sqrt(N), E_max = 1).  Times
+    are CUDA-event sums over all linear solves (the paper's CPU_total) and
+    over whole steps (with assembly and the Picard update norms)."""
+    import numpy as np
+    import torch
+
+    import paper_2001_01158_gb300 as lcg
+
+    ctx = lcg.Context(dev.index)
+    xc = (np.arange(n) + 0.5) / n
+    T0 = torch.as_tensor(np.tile(np.exp(-100.0 * xc) + 1e-4, n), dtype=torch.float64, device=dev)
+    bt, bv = [lcg.BC_DIRICHLET, lcg.BC_DIRICHLET, lcg.BC_NEUMANN, lcg.BC_NEUMANN], [1.0, 1e-4, 0.0, 0.0]
+    D, Tx, Ty, b = (torch.empty(n * n, dtype=torch.float64, device=dev) for _ in range(4))
+    work = torch.empty(2 * n * n, dtype=torch.float64, device=dev)
+    lcg.heat2d_assemble(ctx, (n, n), 1.0 / n, 1e-2, bt, bv, T0 ** 3.5, T0, D, Tx, Ty, b)
+    op = lcg.StencilOperator(ctx, (n, n, 1), D, Tx, Ty)
+    methods = {
+        "global": (0, lcg.default_params(tol=1e-10)),
+        "gradient": (1, lcg.default_params(lcg.MARK_GRADIENT, alpha=1e-4, grad_layers=0, tol=1e-10)),
+        "residual": (1, lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_EPS_NORMB, 1e-10, lcg.EXP_PAPER, 1, tol=1e-10)),
+    }
+    out, finals = {}, {}
+    for name, (method, prm) in methods.items():
+        hp = lcg.heat_params(1.0 / n, 1e-2, 3.5, bt, bv, method=method, params=prm)
+        T = T0.clone()
+        Tn = torch.empty_like(T)
+        solve_ms = total_ms = 0.0
+        pic = lin = K = 0
+        for _ in range(steps):
+            Tn.copy_(T)
+            st = lcg.heat2d_step(ctx, op, hp, Tn, T, D, Tx, Ty, b, work)
+            solve_ms += st.t_solve_ms
+            total_ms += st.t_total_ms
+            pic += st.picard_its
+            lin += st.it_local + st.it_global
+            K += st.K_sum
+        finals[name] = T
+        out[name] = {"linear_solve_ms": solve_ms, "step_ms": total_ms, "systems": pic, "cg_iterations": lin,
+                     "eta_mean": K / max(1, pic) / (n * n)}
+    for name in ("gradient", "residual"):
+        out[name]["speedup_vs_global"] = out["global"]["linear_solve_ms"] / out[name]["linear_solve_ms"]
+        out[name]["rel_diff_vs_global"] = float(torch.linalg.norm(finals[name] - finals["global"]) /
+                                                torch.linalg.norm(finals["global"]))
+    return out
 
 
 def run_batched(args, rank, dev, ws):

@@ -320,6 +320,66 @@ LC_EXPORT int lc_op_refresh(lc_op *op, void *stream);
 LC_EXPORT int lc_adjoint_grad_k_2d(lc_ctx *ctx, const int32_t shape[2], const double *k, const double *x,
                                    const double *lam, double *dk, void *stream);
 
+/* ---- nonlinear 2D heat conduction (Sec. 3.2) --------------------------------
+ *
+ * dT/dt = div(kappa(T) grad T), kappa = T^p, on an nx x ny grid of square
+ * cells of width h; backward Euler in time and Picard iteration (Eq.
+ * picard-equs): T^{n+1,s+1} solves the linear system with kappa evaluated at
+ * T^{n+1,s}.  The paper's test: 99 x 99 cells on the unit square, p = 3.5,
+ * T = 1 at x = 0 and 1e-4 at x = 1, no flux at y = 0, 1, dt = 1e-2, linear
+ * tolerance 1e-10, Picard until ||T^{s+1} - T^s||_2 < 1e-8. */
+enum { LC_BC_DIRICHLET = 0, LC_BC_NEUMANN = 1 };
+
+/* Picard-linearised system from cell conductivities kappa (device, N) and
+ * the previous time level Tn (device, N), as the 5-point stencil arrays of
+ * lc_op_create_stencil (D, Tx, Ty, device, N each) and the right-hand side b
+ * (device, N).  With c = 1/(h h), faces visited W, E, S, N:
+ *   interior face T_f = ((2 kappa_P) kappa_N / (kappa_P + kappa_N)) c,
+ *   Dirichlet side g = (2 kappa_P) c (ghost at half a cell), Neumann: none,
+ *   D_P = 1/dt + each T_f or g in that order, Tx/Ty = T_f of the east/north
+ *   face (0 on the last column/row), b_P = Tn_P (1/dt) + g T_side per
+ *   Dirichlet side in that order.
+ * bc_type[4] and bc_val[4] list the sides x-, x+, y-, y+. */
+LC_EXPORT int lc_heat2d_assemble(lc_ctx *ctx, const int32_t shape[2], double h, double dt,
+                                 const int32_t bc_type[4], const double bc_val[4], const double *kappa,
+                                 const double *Tn, double *D, double *Tx, double *Ty, double *b, void *stream);
+
+typedef struct {
+    double    h;            /* cell width (> 0) */
+    double    dt;           /* time step (> 0) */
+    double    p;            /* kappa(T) = T^p */
+    int32_t   bc_type[4];   /* sides x-, x+, y-, y+: LC_BC_* */
+    double    bc_val[4];    /* Dirichlet values */
+    int32_t   method;       /* 0: global Jacobi-PCG with params.global; 1: Alg 1 with params */
+    lc_params params;
+    double    picard_tol;   /* stop when ||T^{s+1} - T^s||_2 < picard_tol */
+    int32_t   max_picard;   /* >= 1 */
+} lc_heat2d_params;
+
+typedef struct {
+    int32_t picard_its;     /* Picard iterations of the step */
+    int32_t it_local;       /* CG iterations of all local solves */
+    int32_t it_global;      /* CG iterations of all global solves */
+    int32_t K_sum;          /* sum of |Omega_local| over the step's solves */
+    int32_t early_exits;    /* solves whose x~ met the criterion */
+    int32_t status;         /* lc_status of the last solve */
+    double  last_update;    /* ||T^{s+1} - T^s||_2 of the last iteration */
+    float   t_solve_ms;     /* CUDA-event time of the linear solves */
+    float   t_total_ms;     /* the whole step */
+} lc_heat2d_stats;
+
+/* One time step by Picard iteration: T (device, N) holds T^{n+1,0} on entry
+ * (normally T^n) and T^{n+1} on exit; Tn (device, N) is T^n.  op must be the
+ * 2D stencil operator created on D, Tx, Ty (device, N each), which this call
+ * overwrites with each iteration's system (and refreshes the operator); b
+ * (device, N) receives each right-hand side; work (device, 2N) is scratch.
+ * Each iteration: kappa = T^p, assemble, solve from the previous iterate,
+ * ||T^{s+1} - T^s||_2 (read on the host: the call waits for the stream).
+ * stats (host) is filled. */
+LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp, const double *Tn, double *T,
+                             double *D, double *Tx, double *Ty, double *b, double *work, lc_heat2d_stats *stats,
+                             void *stream);
+
 /* ---- kernel tuning ----------------------------------------------------------
  *
  * Launch-shape knobs of an operator's kernels, for the autotuner; not part

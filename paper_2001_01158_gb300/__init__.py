@@ -69,6 +69,24 @@ class Stats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+BC_DIRICHLET, BC_NEUMANN = 0, 1
+
+
+class HeatParams(C.Structure):
+    _fields_ = [("h", C.c_double), ("dt", C.c_double), ("p", C.c_double), ("bc_type", C.c_int32 * 4),
+                ("bc_val", C.c_double * 4), ("method", C.c_int32), ("params", Params), ("picard_tol", C.c_double),
+                ("max_picard", C.c_int32)]
+
+
+class HeatStats(C.Structure):
+    _fields_ = [("picard_its", C.c_int32), ("it_local", C.c_int32), ("it_global", C.c_int32),
+                ("K_sum", C.c_int32), ("early_exits", C.c_int32), ("status", C.c_int32),
+                ("last_update", C.c_double), ("t_solve_ms", C.c_float), ("t_total_ms", C.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class _Subsys(C.Structure):
     _fields_ = [(f, C.c_void_p) for f in ("g2l", "l2g", "rowptr", "col", "val", "rhs", "xL0", "K", "nnz")]
 
@@ -113,6 +131,9 @@ def lib():
     L.lc_op_refresh.argtypes = [vp, vp]
     L.lc_adjoint_grad_k_2d.argtypes = [vp, C.POINTER(i32), vp, vp, vp, vp, vp]
     L.lc_gs_smooth.argtypes = [vp, vp, vp, vp, i32, vp]
+    L.lc_heat2d_assemble.argtypes = [vp, C.POINTER(i32), d, d, C.POINTER(i32), C.POINTER(d), vp, vp, vp, vp, vp,
+                                     vp, vp]
+    L.lc_heat2d_step.argtypes = [vp, vp, C.POINTER(HeatParams), vp, vp, vp, vp, vp, vp, vp, C.POINTER(HeatStats), vp]
     L.lc_op_set_colouring.argtypes = [vp, vp, i32]
     _lib = L
     return L
@@ -262,6 +283,39 @@ def mark_residual(ctx: Context, op: _Operator, b, x0, params: MarkParams, mask, 
                                             C.byref(params), _ptr(mask, torch.uint8, "mask"),
                                             _ptr(r0, torch.float64, "r0"), _ptr(K, torch.int32, "K"),
                                             _ptr(tau, torch.float64, "tau"), _stream(stream)))
+
+
+def heat2d_assemble(ctx: Context, shape, h: float, dt: float, bc_type, bc_val, kappa, Tn, D, Tx, Ty, b,
+                    stream=None):
+    """lc_heat2d_assemble: the Picard-linearised heat system (Sec. 3.2) as stencil arrays and b."""
+    sh = (C.c_int32 * 2)(*shape[:2])
+    return ctx.check(lib().lc_heat2d_assemble(ctx.h, sh, float(h), float(dt), (C.c_int32 * 4)(*bc_type),
+                                              (C.c_double * 4)(*bc_val), _ptr(kappa, torch.float64, "kappa"),
+                                              _ptr(Tn, torch.float64, "Tn"), _ptr(D, torch.float64, "D"),
+                                              _ptr(Tx, torch.float64, "Tx"), _ptr(Ty, torch.float64, "Ty"),
+                                              _ptr(b, torch.float64, "b"), _stream(stream)))
+
+
+def heat_params(h: float, dt: float, p: float, bc_type, bc_val, method: int = 1, params: "Params | None" = None,
+                picard_tol: float = 1e-8, max_picard: int = 100) -> HeatParams:
+    """lc_heat2d_params; params defaults to Alg 1 with the paper's residual
+    marking (eps ||b|| / sqrt(N) with eps = 1e-10, E_max = 1) at tolerance 1e-10."""
+    if params is None:
+        params = default_params(MARK_RESIDUAL, THR_EPS_NORMB, 1e-10, EXP_PAPER, 1, tol=1e-10)
+    return HeatParams(h, dt, p, (C.c_int32 * 4)(*bc_type), (C.c_double * 4)(*bc_val), method, params, picard_tol,
+                      max_picard)
+
+
+def heat2d_step(ctx: Context, op: "StencilOperator", hp: HeatParams, Tn, T, D, Tx, Ty, b, work,
+                stats: HeatStats | None = None, stream=None) -> HeatStats:
+    """lc_heat2d_step: one Picard-iterated backward-Euler step (T in: T^{n+1,0}, out: T^{n+1})."""
+    st = stats if stats is not None else HeatStats()
+    ctx.check(lib().lc_heat2d_step(ctx.h, op.h, C.byref(hp), _ptr(Tn, torch.float64, "Tn"),
+                                   _ptr(T, torch.float64, "T"), _ptr(D, torch.float64, "D"),
+                                   _ptr(Tx, torch.float64, "Tx"), _ptr(Ty, torch.float64, "Ty"),
+                                   _ptr(b, torch.float64, "b"), _ptr(work, torch.float64, "work"), C.byref(st),
+                                   _stream(stream)))
+    return st
 
 
 def gs_smooth(ctx: Context, op: _Operator, b, x, sweeps: int, stream=None):

@@ -46,7 +46,7 @@ struct lc_op {
     lc::ExtractWork ew{};
     lc_subsys sub{};                 // internal subsystem buffers
     lc::PcgWork pw{};
-    cudaEvent_t ev[6] = {};
+    cudaEvent_t ev[8] = {};
     // tuning knobs (lc_op_set_tuning)
     int pcg_minblocks = 3;   // register budget of the structured-grid PCG kernel
     int pcg_grid_cap = 0;    // blocks of the global PCG launch (0: as many as fit)
@@ -870,6 +870,94 @@ int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const
     stats->status = status_of(c);
     if (stats->status == LC_ERR_TIMEOUT) return fail(ctx, LC_ERR_TIMEOUT, "grid barrier timed out");
     return stats->status;
+}
+
+static int check_gs(lc_ctx *ctx, const lc_op *op, int sweeps);
+
+static int check_heat_bc(lc_ctx *ctx, const int32_t bc_type[4], const double bc_val[4], lc::HeatBc &bc) {
+    if (!bc_type || !bc_val) return fail(ctx, LC_ERR_INVALID_ARG, "null boundary conditions");
+    for (int f = 0; f < 4; ++f) {
+        if (bc_type[f] != LC_BC_DIRICHLET && bc_type[f] != LC_BC_NEUMANN)
+            return fail(ctx, LC_ERR_INVALID_ARG, "unknown boundary type %d", bc_type[f]);
+        if (bc_type[f] == LC_BC_DIRICHLET && !std::isfinite(bc_val[f]))
+            return fail(ctx, LC_ERR_INVALID_ARG, "Dirichlet values must be finite");
+        bc.type[f] = bc_type[f];
+        bc.val[f] = bc_val[f];
+    }
+    return LC_OK;
+}
+
+int lc_heat2d_assemble(lc_ctx *ctx, const int32_t shape[2], double h, double dt, const int32_t bc_type[4],
+                       const double bc_val[4], const double *kappa, const double *Tn, double *D, double *Tx,
+                       double *Ty, double *b, void *stream) {
+    if (!ctx) return LC_ERR_INVALID_ARG;
+    if (!shape || !kappa || !Tn || !D || !Tx || !Ty || !b) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    if (shape[0] <= 0 || shape[1] <= 0) return fail(ctx, LC_ERR_INVALID_ARG, "shape must be positive");
+    if ((int64_t)shape[0] * shape[1] >= (int64_t)INT32_MAX) return fail(ctx, LC_ERR_TOO_LARGE, "grid too large");
+    if (!(h > 0.0) || !(dt > 0.0) || !std::isfinite(h) || !std::isfinite(dt))
+        return fail(ctx, LC_ERR_INVALID_ARG, "h and dt must be positive and finite");
+    lc::HeatBc bc;
+    int rc = check_heat_bc(ctx, bc_type, bc_val, bc);
+    if (rc) return rc;
+    LC_CUDA(ctx, cudaSetDevice(ctx->device));
+    LC_CUDA(ctx, lc::launch_heat_assemble(shape[0], shape[1], h, dt, bc, kappa, Tn, D, Tx, Ty, b,
+                                          (cudaStream_t)stream));
+    return LC_OK;
+}
+
+int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp, const double *Tn, double *T, double *D,
+                   double *Tx, double *Ty, double *b, double *work, lc_heat2d_stats *hs, void *stream) {
+    int rc = check_common(ctx, op);
+    if (rc) return rc;
+    if (!hp || !Tn || !T || !D || !Tx || !Ty || !b || !work || !hs)
+        return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    if (op->kind != 0 || op->st.dim != 2) return fail(ctx, LC_ERR_INVALID_ARG, "needs a 2D stencil operator");
+    if (op->st.D != D || op->st.Tx != Tx || op->st.Ty != Ty)
+        return fail(ctx, LC_ERR_INVALID_ARG, "D, Tx, Ty must be the arrays the operator was created on");
+    if (!(hp->h > 0.0) || !(hp->dt > 0.0) || !std::isfinite(hp->h) || !std::isfinite(hp->dt) ||
+        !std::isfinite(hp->p))
+        return fail(ctx, LC_ERR_INVALID_ARG, "h, dt must be positive and p finite");
+    if (hp->max_picard < 1 || !(hp->picard_tol >= 0.0)) return fail(ctx, LC_ERR_INVALID_ARG, "bad Picard limits");
+    if (hp->method != 0 && hp->method != 1) return fail(ctx, LC_ERR_INVALID_ARG, "method must be 0 or 1");
+    lc::HeatBc bc;
+    if ((rc = check_heat_bc(ctx, hp->bc_type, hp->bc_val, bc))) return rc;
+    if ((rc = check_solve_params(ctx, &hp->params.global))) return rc;
+    if (hp->method == 1 && ((rc = check_solve_params(ctx, &hp->params.local)) ||
+                            (rc = check_gs(ctx, op, hp->params.gs_sweeps))))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = op->n;
+    double *kappa = work, *Tprev = work + n;
+    double *part = op->pw.partials, *d2 = op->pw.partials + lc::kMaxGrid;
+    memset(hs, 0, sizeof *hs);
+    LC_CUDA(ctx, cudaEventRecord(op->ev[6], s));
+    for (int it = 0; it < hp->max_picard; ++it) {
+        LC_CUDA(ctx, lc::launch_heat_kappa(n, T, hp->p, kappa, s));
+        LC_CUDA(ctx, lc::launch_heat_assemble(op->st.nx, op->st.ny, hp->h, hp->dt, bc, kappa, Tn, D, Tx, Ty, b, s));
+        if ((rc = lc_op_refresh(op, stream))) return rc;
+        LC_CUDA(ctx, cudaMemcpyAsync(Tprev, T, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        lc_stats st;
+        rc = hp->method == 0 ? lc_pcg_solve(ctx, op, b, T, &hp->params.global, &st, stream)
+                             : lc_solve_local_then_global(ctx, op, b, T, &hp->params, &st, stream);
+        hs->status = rc;
+        if (rc) return rc;
+        hs->it_local += st.it_local;
+        hs->it_global += st.it_global;
+        hs->K_sum += st.K;
+        hs->early_exits += st.early_exit;
+        hs->t_solve_ms += st.t_total_ms;
+        LC_CUDA(ctx, lc::launch_diff2(n, T, Tprev, part, d2, s));
+        double h2 = 0.0;
+        LC_CUDA(ctx, cudaMemcpyAsync(&h2, d2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        LC_CUDA(ctx, cudaStreamSynchronize(s));
+        hs->picard_its = it + 1;
+        hs->last_update = std::sqrt(h2);
+        if (hs->last_update < hp->picard_tol) break;
+    }
+    LC_CUDA(ctx, cudaEventRecord(op->ev[7], s));
+    LC_CUDA(ctx, cudaEventSynchronize(op->ev[7]));
+    cudaEventElapsedTime(&hs->t_total_ms, op->ev[6], op->ev[7]);
+    return LC_OK;
 }
 
 static constexpr int kMaxGsSweeps = 64;

@@ -1,0 +1,225 @@
+// lc_device.cuh -- descriptors and device helpers shared by the lc kernels:
+// operator descriptors, the control block, bit helpers, warp/block
+// reductions and the bounded grid barrier.
+//
+// Nothing here is part of the public ABI (include/lc_api.h).  All kernels
+// are written for sm_103a: 32-wide warps, 152 SMs, FP64 at roughly 1/12 of
+// a DP op per HBM byte -- so every bit-exact kernel spends exactly the FP64
+// operations its canonical order names and does abs/max/compare on integer
+// bit patterns.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lc_api.h"
+
+namespace lc {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kTreeChunk = 1024;                       // canonical sum-of-squares chunk
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
+constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
+constexpr int kMaxExpRounds = 64;
+constexpr int kMaxGrid = 4096;                          // persistent-kernel blocks (partials capacity)
+
+// ---------------------------------------------------------------- descriptors
+
+// Structured operator: the diagonal D and face conductances T (off-diagonal
+// -T); dinv = 1/D precomputed at creation.  Cell i = x + nx*(y + ny*z).
+struct Stencil {
+    int dim;
+    int nx, ny, nz;
+    int64_t n;
+    const double *D, *Tx, *Ty, *Tz;
+    const double *dinv;
+    // FP32 copies for the mixed-precision inner solve (fl32 of the above)
+    const float *D32, *Tx32, *Ty32, *Tz32, *dinv32;
+    // symmetric Jacobi scaling S = D^-1/2 (FP64 solve): S^-1 = D^1/2 and the
+    // scaled face conductances T_f / sqrt(D_P D_N) of S A S (unit diagonal);
+    // dn32 = fl32(D 2^-2h), h = floor(e/2), e the largest binary exponent of
+    // D, stored biased (+1023) in *dexp
+    const double *sc, *sq, *Txh, *Tyh;
+    const float *dn32;
+    const int *dexp;
+};
+
+// CSR operator; rows ascending, diagonal present.  `n_dev`, if not null,
+// holds the row count on the device (used for extracted subsystems whose
+// size is only known on the device); otherwise `n` is the count.
+struct Csr {
+    int32_t n;
+    const int32_t *n_dev;
+    const int32_t *rp, *ci;
+    const double *av;
+    const float *av32;
+};
+
+// Device-resident control block of one operator (one per lc_op).
+struct Ctrl {
+    // grid barrier
+    unsigned long long bar_count;   // arrivals since the launch started (zeroed before it)
+    int32_t status;                 // first error a kernel raised (LC_OK if none)
+    int32_t done;                   // local solve: 1 if the cluster kernel solved the system
+    // marking
+    unsigned long long maxabs_bits; // max |r| (or max g) as bits, NaN excluded
+    double tau;
+    int32_t K;
+    int32_t nnzB;
+    int32_t added[kMaxExpRounds];   // Alg 3: K0 of each round
+    // Krylov
+    int32_t iters;
+    int32_t restarts;
+    int32_t converged;              // 1 ok, 0 not converged, -1 breakdown
+    int32_t early;                  // converged at set-up (x0 already met the criterion)
+    double relres0;                 // relative residual of the starting iterate
+    double relres;                  // final relative residual (true residual)
+    double bnorm2;                  // ||b||^2
+    // mixed-precision refinement
+    int32_t outer;
+    int32_t pad1;
+    double scale;                   // ||r|| of the current outer residual
+};
+
+// ---------------------------------------------------------------- bit helpers
+
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & kAbsMask;
+}
+// |v| > t exactly as IEEE compares it, given tbits = abs_bits(t), t >= 0 or
+// NaN: a NaN |v| never exceeds, nothing exceeds a NaN t or +inf.
+__device__ __forceinline__ bool abs_gt(double v, unsigned long long tbits) {
+    unsigned long long a = abs_bits(v);
+    return a > tbits && a <= kInfBits && tbits <= kInfBits;
+}
+// bits of |v| for a max that ignores NaN (as `if (|v| > m) m = |v|` does)
+__device__ __forceinline__ unsigned long long maxable_bits(double v) {
+    unsigned long long a = abs_bits(v);
+    return a <= kInfBits ? a : 0ull;
+}
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_down_sync(kFull, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+__device__ __forceinline__ int warp_isum(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+
+// Deterministic block sum of NV values per thread (result valid in thread 0).
+// `sm` needs NV * 32 doubles.
+template <int NV, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sm[k * 32 + warp] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            T t = lane < nw ? sm[k * 32 + lane] : T(0);
+            v[k] = warp_sum(t);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_max(v);
+    __syncthreads();
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < nw ? sm[lane] : 0ull;
+        v = warp_max(v);
+    }
+    return v;
+}
+
+__device__ __forceinline__ int block_isum(int v, int *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_isum(v);
+    __syncthreads();
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < nw ? sm[lane] : 0;
+        v = warp_isum(v);
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------- grid barrier
+
+// Spin limit of every grid-wide wait: ~2 s at 2 GHz, after which the block
+// records LC_ERR_TIMEOUT in ctrl->status and returns false; the other blocks
+// stop at their own next wait, bounded the same way, and kernels exit.  Co-residency of all
+// blocks is guaranteed by the cooperative launch.
+constexpr long long kBarrierTimeoutCycles = 4000000000ll;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Counting barrier: arrival k of a block (k = 0, 1, ...) takes the counter
+// from somewhere in [k n, (k+1) n) and the barrier opens when it reaches
+// (k+1) n, so the target follows from the value the arrival returns: one
+// atomic per block and arrival, no generation word, no reset between
+// barriers.  A block never sees the counter past its own target before it
+// arrives (no block passes barrier k before all arrived).
+__device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned int nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();   // the block's writes (ordered by the barrier above) before the arrival
+        const unsigned long long old = atomicAdd(&ctrl->bar_count, 1ull);
+        const unsigned long long target = (old / nblocks + 1) * nblocks;
+        int ok = 1;
+        if (old + 1 < target) {
+            const long long t0 = clock64();
+            while (ld_acquire_u64(&ctrl->bar_count) < target) {
+                if (clock64() - t0 > kBarrierTimeoutCycles) { ok = 0; break; }
+            }
+        }
+        __threadfence();
+        if (!ok) atomicCAS(&ctrl->status, LC_OK, LC_ERR_TIMEOUT);
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Loads of data that other blocks of the same (persistent) kernel write:
+// bypass L1, which is not coherent across SMs.
+template <typename T>
+__device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+
+
+}  // namespace lc

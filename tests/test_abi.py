@@ -53,3 +53,31 @@ def test_struct_layouts_match_header():
     assert C.sizeof(lcg.Params) == 120
     assert C.sizeof(lcg.Stats) == 88
     assert lcg.Params.global_.offset == 48 and lcg.Params.local.offset == 80
+
+
+LAYOUT_PROBE = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "lc_api.h"
+int main(void) {
+    printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lc_mark_params), sizeof(lc_solve_params),
+           sizeof(lc_params), sizeof(lc_stats), sizeof(lc_heat2d_params), sizeof(lc_heat2d_stats),
+           offsetof(lc_params, global), offsetof(lc_heat2d_params, params), offsetof(lc_heat2d_params, max_picard),
+           offsetof(lc_heat2d_stats, t_total_ms));
+    return 0;
+}
+"""
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """ctypes layouts of the binding equal what a C compiler makes of lc_api.h."""
+    import subprocess
+    src = tmp_path / "probe.c"
+    src.write_text(LAYOUT_PROBE)
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [C.sizeof(lcg.MarkParams), C.sizeof(lcg.SolveParams), C.sizeof(lcg.Params), C.sizeof(lcg.Stats),
+            C.sizeof(lcg.HeatParams), C.sizeof(lcg.HeatStats), lcg.Params.global_.offset,
+            lcg.HeatParams.params.offset, lcg.HeatParams.max_picard.offset, lcg.HeatStats.t_total_ms.offset]
+    assert got == want
