@@ -448,6 +448,8 @@ def run_gpu(args, rank, ws, local):
     }
     if not args.no_batched:
         res["batched_512"] = run_batched(args, rank, dev, ws)
+    if not args.no_batched:
+        res["multigroup_64"] = run_multigroup(args, dev)
     if not args.no_heat:
         res["heat_e1"] = {"99x99_100_steps": run_heat(dev, 99, 100), "1024x1024_10_steps": run_heat(dev, 1024, 10)}
     if rank == 0 and not args.no_cpu_baseline:
@@ -515,14 +517,26 @@ def run_batched(args, rank, dev, ws):
     sources covering 1-30 % of cells): all of Alg 1 in one autotuned,
     graph-captured launch (FP32 inner CG, FP64 refinement, relres 1e-8),
     against the same systems solved one after another by global FP64 PCG."""
+    import gen
+    return batched_items(gen.cfg4_batch(seed=rank), dev, max(3, min(args.steps, 10)))
+
+
+def run_multigroup(args, dev):
+    """Multi-group stand-in (64 group systems on one 88 x 80 mesh with a
+    shared pattern, Sec. 3.3's structure): one source iteration's 64 solves
+    batched in one launch, against sequential FP64 Alg 1 and sequential
+    global FP64 PCG."""
+    import gen
+    return batched_items(gen.mg_standin(seed=0), dev, max(3, min(args.steps, 10)), seq_alg1=True)
+
+
+def batched_items(items, dev, reps, seq_alg1=False):
     import numpy as np
     import torch
 
-    import gen
     import paper_2001_01158_gb300 as lcg
     from paper_2001_01158_gb300.autotune import tune_batch
 
-    items = gen.cfg4_batch(seed=rank)
     T = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)  # noqa: E731
     ctx = lcg.Context(dev.index)
     systems = [(d["op"].shape[0], d["op"].shape[1], T(d["op"].D), T(d["op"].Tx), T(d["op"].Ty)) for d in items]
@@ -533,7 +547,6 @@ def run_batched(args, rank, dev, ws):
     cfg = tune_batch(batch, b, x0, prm)
     x = x0.clone()
     batch.capture(b, x, prm)
-    reps = max(3, min(args.steps, 10))
     for _ in range(2):
         x.copy_(x0)
         batch.replay()
@@ -549,30 +562,40 @@ def run_batched(args, rank, dev, ws):
         ts.append(e0.elapsed_time(e1))
     st = batch.stats()
     ms_batched = statistics.median(ts)
-    # the same systems, one at a time, by the global FP64 PCG
-    sp = lcg.SolveParams(1e-8, 200000, lcg.PREC_FP64, 0.0, 0)
     ops = [lcg.StencilOperator(ctx, (s[0], s[1], 1), s[2], s[3], s[4]) for s in systems]
     xs = [T(d["x0"]) for d in items]
     bs = [T(d["b"]) for d in items]
-    for op_, b_, x_ in zip(ops[:8], bs[:8], xs[:8]):   # warm-up
-        lcg.pcg_solve(ctx, op_, b_, x_.clone(), sp)
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for op_, b_, x_ in zip(ops, bs, xs):
-        lcg.pcg_solve(ctx, op_, b_, x_, sp)
-    e1.record()
-    torch.cuda.synchronize(dev)
-    ms_seq = e0.elapsed_time(e1)
+
+    def sequential(solve):
+        for op_, b_, x_ in zip(ops[:8], bs[:8], xs[:8]):   # warm-up
+            solve(op_, b_, x_.clone())
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for op_, b_, x_ in zip(ops, bs, xs):
+            solve(op_, b_, x_.clone())
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+
+    # the same systems, one at a time, by the global FP64 PCG (and by FP64 Alg 1)
+    sp = lcg.SolveParams(1e-8, 200000, lcg.PREC_FP64, 0.0, 0)
+    ms_seq = sequential(lambda o, bb, xx: lcg.pcg_solve(ctx, o, bb, xx, sp))
     cells = batch.cells
-    return {"systems": batch.nsys, "cells": cells, "ms_per_batch": ms_batched,
-            "ms_per_system": ms_batched / batch.nsys, "cells_per_s": cells / (ms_batched * 1e-3),
-            "sequential_global_fp64_ms": ms_seq, "speedup_vs_sequential_global_fp64": ms_seq / ms_batched,
-            "eta_mean": statistics.mean(s["eta"] for s in st),
-            "relres_max": max(s["relres_final"] for s in st), "all_converged": all(s["status"] == 0 for s in st),
-            "inner_iterations_mean": statistics.mean(s["it_global"] for s in st),
-            "autotuned": {"block": cfg["block"], "ctas_per_sm": cfg["ctas_per_sm"]},
-            "launch": "one persistent kernel, CUDA-graph replay"}
+    out = {"systems": batch.nsys, "cells": cells, "ms_per_batch": ms_batched,
+           "ms_per_system": ms_batched / batch.nsys, "cells_per_s": cells / (ms_batched * 1e-3),
+           "sequential_global_fp64_ms": ms_seq, "speedup_vs_sequential_global_fp64": ms_seq / ms_batched,
+           "eta_mean": statistics.mean(s["eta"] for s in st),
+           "relres_max": max(s["relres_final"] for s in st), "all_converged": all(s["status"] == 0 for s in st),
+           "inner_iterations_mean": statistics.mean(s["it_global"] for s in st),
+           "autotuned": {"block": cfg["block"], "ctas_per_sm": cfg["ctas_per_sm"]},
+           "launch": "one persistent kernel, CUDA-graph replay"}
+    if seq_alg1:
+        prm64 = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8)
+        ms_a = sequential(lambda o, bb, xx: lcg.solve_local_then_global(ctx, o, bb, xx, prm64))
+        out["sequential_alg1_fp64_ms"] = ms_a
+        out["speedup_vs_sequential_alg1_fp64"] = ms_a / ms_batched
+    return out
 
 
 def main():

@@ -321,6 +321,47 @@ def cfg5_adjoint(seed: int = 0, n: int = 1024, radius: float = 80.0, dt: float =
     return {"k": k, "k_target": k_target, "b": b, "dt": dt, "n": n}
 
 
+def mg_standin(seed: int = 0, groups: int = 64, nx: int = 88, ny: int = 80, dt: float = 1.0,
+               hot_radius: float = 6.0, shift: float = 2.0):
+    """Multi-group radiation-diffusion stand-in (the structure of Sec. 3.3's
+    systems on synthetic data): `groups` 5-point systems on one nx x ny mesh
+    (88 x 80 = 7040 cells, the paper's cell count) with the same sparsity
+    pattern and group-dependent coefficients.  A smooth density rho and an
+    electron temperature Te with a hot spot give Kramers-like cross sections
+    sigma_g = rho nu_g^-3 / sqrt(Te) over log-spaced group energies nu_g;
+    diffusion coefficients kappa_g = 1/(3 sigma_g); A_g = operator_2d(kappa_g,
+    dt) plus sigma_g on the diagonal (absorption).  Between two source
+    iterations the hot spot moves by `shift` cells, so the emission
+    4 pi sigma_g B_g changes only near it: x0_g is the previous iterate (a
+    smooth field), b_g = A_g x0_g + 4 pi sigma_g (B_g(Te_new) - B_g(Te_old)).
+    B_g(T) = T^4 nu_g^3 / (exp(nu_g / T) - 1) (Planck shape, arbitrary units)."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.meshgrid(np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    rho = 1.0 + 0.5 * np.sin(2 * np.pi * xx / nx + rng.uniform(0, 6.3)) * np.cos(2 * np.pi * yy / ny)
+    c = np.array([rng.uniform(0.3, 0.7) * nx, rng.uniform(0.3, 0.7) * ny])
+    ang = rng.uniform(0, 2 * np.pi)
+    c_new = c + shift * np.array([math.cos(ang), math.sin(ang)])
+
+    def temperature(cc):
+        return 0.1 + 0.9 * np.exp(-((xx - cc[0]) ** 2 + (yy - cc[1]) ** 2) / (2.0 * hot_radius ** 2))
+
+    te_old, te_new = temperature(c), temperature(c_new)
+    nu = np.logspace(-1.0, 1.0, groups)
+    out = []
+    for g in range(groups):
+        sigma = rho * nu[g] ** -3 / np.sqrt(te_old)
+        op = operator_2d(1.0 / (3.0 * sigma), dt)
+        op.D += sigma.ravel()
+
+        def planck(t):
+            return t ** 4 * nu[g] ** 3 / np.expm1(nu[g] / t)
+
+        x0 = (planck(te_old) / planck(te_old).max()).ravel()
+        emis = 4.0 * np.pi * sigma * (planck(te_new) - planck(te_old))
+        out.append({"op": op, "x0": x0, "b": stencil_matvec(op, x0) + emis.ravel(), "nu": float(nu[g])})
+    return out
+
+
 def random_stencil_2d(seed: int, nx: int, ny: int, dt: float = 1.0, kmax: float = 100.0) -> Stencil:
     """Small random 5-point operator (k log-uniform in [1, kmax]) for tests."""
     rng = np.random.default_rng(seed)
