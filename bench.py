@@ -450,6 +450,8 @@ def run_gpu(args, rank, ws, local):
         res["batched_512"] = run_batched(args, rank, dev, ws)
     if not args.no_batched:
         res["multigroup_64"] = run_multigroup(args, dev)
+    if not args.no_batched:
+        res["csr_3t_1024"] = run_csr3t(dev, 1024)
     if not args.no_heat:
         res["heat_e1"] = {"99x99_100_steps": run_heat(dev, 99, 100), "1024x1024_10_steps": run_heat(dev, 1024, 10)}
     if rank == 0 and not args.no_cpu_baseline:
@@ -519,6 +521,56 @@ def run_batched(args, rank, dev, ws):
     against the same systems solved one after another by global FP64 PCG."""
     import gen
     return batched_items(gen.cfg4_batch(seed=rank), dev, max(3, min(args.steps, 10)))
+
+
+def run_csr3t(dev, n):
+    """A 3T-like coupled system (three interleaved temperatures per cell of an
+    n x n grid, 9-point diffusion each, 3 x 3 cell coupling; 3 n^2 unknowns)
+    through the general CSR path: Alg 1 (residual marking) against the global
+    Jacobi-PCG from the same start, and the CSR PCG kernel's algorithmic HBM
+    rate (per row and iteration: row pointer 4 B + 12 B per entry + z, p_old
+    in and p, q out 32 B + phase B 64 B)."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2001_01158_gb300 as lcg
+
+    rp, ci, av = gen.threeT_2d(11, n, n)
+    nrows, nnz = len(rp) - 1, len(ci)
+    rng = np.random.default_rng(5)
+    x0 = 1.0 + 0.1 * rng.standard_normal(nrows)
+    s = np.zeros(nrows)
+    c = rng.integers(n // 4, 3 * n // 4, size=2)
+    yy, xx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    disc = (((xx - c[0]) ** 2 + (yy - c[1]) ** 2) <= (n / 40.0) ** 2).ravel()
+    s[3 * np.flatnonzero(disc)] = 1.0   # radiation source in a disc
+    b = gen.csr_matvec(rp, ci, av, x0) + s
+    T = lambda a, dt=torch.float64: torch.as_tensor(a, dtype=dt, device=dev)  # noqa: E731
+    ctx = lcg.Context(dev.index)
+    op = lcg.CsrOperator(ctx, T(rp, torch.int32), T(ci, torch.int32), T(av))
+    bd, x0d = T(b), T(x0)
+    sp = lcg.SolveParams(1e-8, 200000, lcg.PREC_FP64, 0.0, 0)
+    prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8)
+    out = {}
+    for name, run in (("global", lambda x, st: lcg.pcg_solve(ctx, op, bd, x, sp, st)),
+                      ("alg1", lambda x, st: lcg.solve_local_then_global(ctx, op, bd, x, prm, st))):
+        st = lcg.Stats()
+        run(x0d.clone(), st)   # warm-up
+        times, its = [], []
+        for _ in range(3):
+            x = x0d.clone()
+            run(x, st)
+            times.append(st.t_total_ms)
+            its.append((st.it_local, st.it_global, st.K, st.t_global_ms))
+        out[name] = {"ms": statistics.median(times), "it_local": its[-1][0], "it_global": its[-1][1],
+                     "K": its[-1][2]}
+        if name == "global":
+            byts = nrows * 100 + 12 * nnz
+            out[name]["pcg_alg_GBs"] = byts * its[-1][1] / (its[-1][3] * 1e-3) / 1e9
+    out["rows"], out["nnz"] = nrows, nnz
+    out["speedup_alg1_vs_global"] = out["global"]["ms"] / out["alg1"]["ms"]
+    return out
 
 
 def run_multigroup(args, dev):

@@ -362,6 +362,109 @@ def mg_standin(seed: int = 0, groups: int = 64, nx: int = 88, ny: int = 80, dt: 
     return out
 
 
+def _csr_from_coo(n, rows, cols, vals):
+    """Sorted, duplicate-summed CSR (int32 indices, FP64 values) of COO triplets."""
+    import scipy.sparse as sp
+    M = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+    M.sum_duplicates()
+    M.sort_indices()
+    return (M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64))
+
+
+def _ninepoint_edges(rng, nx: int, ny: int, k: np.ndarray, shear: np.ndarray):
+    """Edges (i, j, w) of a 9-point stencil on an nx x ny grid: axis faces with
+    the harmonic mean of k, diagonals with a fraction |shear| of it (the
+    cross terms a distorted quadrilateral mesh produces); all w > 0."""
+    idx = np.arange(nx * ny).reshape(ny, nx)
+    out_i, out_j, out_w = [], [], []
+
+    def add(a, b, w):
+        out_i.append(a.ravel()); out_j.append(b.ravel()); out_w.append(w.ravel())
+
+    kk = k.reshape(ny, nx)
+    sh = shear.reshape(ny, nx)
+    add(idx[:, :-1], idx[:, 1:], _harmonic(kk[:, :-1], kk[:, 1:]) * (1.0 - 0.5 * np.abs(sh[:, :-1])))
+    add(idx[:-1, :], idx[1:, :], _harmonic(kk[:-1, :], kk[1:, :]) * (1.0 - 0.5 * np.abs(sh[:-1, :])))
+    add(idx[:-1, :-1], idx[1:, 1:], 0.5 * _harmonic(kk[:-1, :-1], kk[1:, 1:]) * np.maximum(sh[:-1, :-1], 0.0) + 1e-3)
+    add(idx[:-1, 1:], idx[1:, :-1], 0.5 * _harmonic(kk[:-1, 1:], kk[1:, :-1]) * np.maximum(-sh[:-1, 1:], 0.0) + 1e-3)
+    return np.concatenate(out_i), np.concatenate(out_j), np.concatenate(out_w)
+
+
+def _laplacian_coo(n, ei, ej, ew, diag):
+    rows = np.concatenate([ei, ej, ei, ej, np.arange(n)])
+    cols = np.concatenate([ej, ei, ei, ej, np.arange(n)])
+    vals = np.concatenate([-ew, -ew, ew, ew, diag])
+    return rows, cols, vals
+
+
+def ninepoint_2d(seed: int, nx: int, ny: int, dt: float = 1.0, kmax: float = 100.0):
+    """A 9-point diffusion operator as a general CSR matrix (the pattern of the
+    paper's deforming-mesh systems, Sec. 3.3): k log-uniform in [1, kmax],
+    a smooth random mesh shear in [-0.8, 0.8] weighting the diagonal
+    couplings; A = I/dt + sum_e w_e (e_i - e_j)(e_i - e_j)^T + a Dirichlet
+    ghost 2 k on the outer faces.  Symmetric, strictly diagonally dominant,
+    SPD.  Returns (rowptr, col, val)."""
+    rng = np.random.default_rng(seed)
+    n = nx * ny
+    k = 10.0 ** rng.uniform(0.0, math.log10(kmax), n)
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    ph = rng.uniform(0, 2 * np.pi, 2)
+    shear = (0.8 * np.sin(2 * np.pi * xx / max(nx, 2) + ph[0]) * np.cos(2 * np.pi * yy / max(ny, 2) + ph[1])).ravel()
+    ei, ej, ew = _ninepoint_edges(rng, nx, ny, k, shear)
+    diag = np.full(n, 1.0 / dt)
+    kk = k.reshape(ny, nx)
+    ghost = np.zeros((ny, nx))
+    ghost[:, 0] += 2 * kk[:, 0]; ghost[:, -1] += 2 * kk[:, -1]; ghost[0, :] += 2 * kk[0, :]; ghost[-1, :] += 2 * kk[-1, :]
+    return _csr_from_coo(n, *_laplacian_coo(n, ei, ej, ew, diag + ghost.ravel()))
+
+
+def threeT_2d(seed: int, nx: int, ny: int, dt: float = 1.0):
+    """A 3T-like coupled system (radiation, electron and ion temperatures per
+    cell, interleaved: unknown 3 c + v), the coupled 3 x 3 block rows of the
+    paper's 3T systems (Sec. 3.4) on synthetic data: three 9-point diffusion
+    operators with conductivities of very different size (radiation 1..1e3,
+    electron 1..10, ion 1e-3..1e-2) plus per-cell energy exchange
+    w_er (T_e - T_r)^2 + w_ei (T_e - T_i)^2 terms (w log-uniform): symmetric,
+    SPD.  Returns (rowptr, col, val)."""
+    rng = np.random.default_rng(seed)
+    nc = nx * ny
+    n = 3 * nc
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    ph = rng.uniform(0, 2 * np.pi, 2)
+    shear = (0.6 * np.sin(2 * np.pi * xx / max(nx, 2) + ph[0]) * np.cos(2 * np.pi * yy / max(ny, 2) + ph[1])).ravel()
+    rows, cols, vals = [], [], []
+    for v, (lo, hi) in enumerate([(0.0, 3.0), (0.0, 1.0), (-3.0, -2.0)]):
+        k = 10.0 ** rng.uniform(lo, hi, nc)
+        ei, ej, ew = _ninepoint_edges(rng, nx, ny, k, shear)
+        kk = k.reshape(ny, nx)
+        ghost = np.zeros((ny, nx))
+        ghost[:, 0] += 2 * kk[:, 0]; ghost[:, -1] += 2 * kk[:, -1]; ghost[0, :] += 2 * kk[0, :]; ghost[-1, :] += 2 * kk[-1, :]
+        r, c, w = _laplacian_coo(nc, ei, ej, ew, np.full(nc, 1.0 / dt) + ghost.ravel())
+        rows.append(3 * r + v); cols.append(3 * c + v); vals.append(w)
+    cell = np.arange(nc)
+    for (a, b), (lo, hi) in [((1, 0), (0.0, 2.0)), ((1, 2), (-1.0, 1.0))]:
+        w = 10.0 ** rng.uniform(lo, hi, nc)
+        ei, ej = 3 * cell + a, 3 * cell + b
+        rows.append(np.concatenate([ei, ej, ei, ej]))
+        cols.append(np.concatenate([ej, ei, ei, ej]))
+        vals.append(np.concatenate([-w, -w, w, w]))
+    return _csr_from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def greedy_colouring(rowptr, col) -> np.ndarray:
+    """Smallest colour not taken by an earlier neighbour, rows in ascending
+    order: a proper colouring for multicolour Gauss-Seidel on a CSR pattern."""
+    n = len(rowptr) - 1
+    colour = np.zeros(n, np.uint8)
+    for i in range(n):
+        taken = set(colour[col[rowptr[i]:rowptr[i + 1]][col[rowptr[i]:rowptr[i + 1]] < i]].tolist())
+        c = 0
+        while c in taken:
+            c += 1
+        colour[i] = c
+    return colour
+
+
 def random_stencil_2d(seed: int, nx: int, ny: int, dt: float = 1.0, kmax: float = 100.0) -> Stencil:
     """Small random 5-point operator (k log-uniform in [1, kmax]) for tests."""
     rng = np.random.default_rng(seed)

@@ -789,6 +789,7 @@ int lc_op_create_csr(lc_ctx *ctx, lc_op **out, int32_t n, int64_t nnz, const int
     if (!op) return LC_ERR_NO_MEMORY;
     op->ctx = ctx;
     op->kind = 1;
+    op->pcg_minblocks = 4;   // 64 registers, no spills: 32 warps per SM for the row-per-thread SpMV
     op->n = n;
     op->nnz = nnz;
     op->csr.n = n;

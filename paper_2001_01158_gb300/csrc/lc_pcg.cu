@@ -515,7 +515,7 @@ struct OpCsr {
     int32_t n;   // resolved at kernel start (device-side count of an extracted subsystem)
     const int32_t *done = nullptr;   // set: the cluster kernel may have solved the system already
     static constexpr int kSmem = 1;
-    static constexpr bool kTunable = false;
+    static constexpr bool kTunable = true;
     static constexpr bool kScaled = false;
     __device__ bool skipped() const { return done && *done; }
     __device__ void resolve() { if (cs.n_dev) n = *cs.n_dev; }
@@ -1037,9 +1037,9 @@ cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ct
     OpCsr<double> od{op, op.av, op.n};
     if (after_cluster) {
         od.done = &ctrl->done;
-        return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, 1, s, false);
+        return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s, false);
     }
-    if (a.precision != LC_PREC_MIXED) return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, 1, s);
+    if (a.precision != LC_PREC_MIXED) return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);
     VD.z = nullptr;
     const float *av32 = op.av32;
     if (!av32) {   // per-solve FP32 copy of the values into the workspace
@@ -1051,7 +1051,7 @@ cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ct
     note_launches(1);
     Vecs<float> VF = vecs32(w, w.dinv32);
     OpCsr<float> of{op, av32, op.n};
-    return launch_ir(od, of, units, VD, VF, w.partials, a, ctrl, grid_hint, 1, s);
+    return launch_ir(od, of, units, VD, VF, w.partials, a, ctrl, grid_hint, a.minblocks, s);
 }
 
 cudaError_t launch_dinv_stencil(int64_t n, const double *D, double *dinv, float *D32, const double *Tx,

@@ -695,3 +695,31 @@ def test_heat_step_methods_agree_and_picard_fixed_point():
     # the heat front moves right (T rises behind it) and T stays within the boundary values
     assert T_0.min() >= 1e-4 * (1 - 1e-9) and T_0.max() <= 1.0 + 1e-9
     assert np.all(T_0.reshape(n, n)[:, :4] > T0.reshape(n, n)[:, :4])
+
+
+# ------------------------------------------- general CSR operators (9-point, 3T)
+
+@pytest.mark.parametrize("kind", ["ninepoint", "threeT"])
+def test_general_csr_generators_are_spd_sorted_and_coloured(kind):
+    """The 9-point and 3T-like generators give symmetric, SPD, (weakly)
+    diagonally dominant CSR with sorted unique columns and the expected
+    pattern; greedy colouring is proper."""
+    if kind == "ninepoint":
+        rp, ci, av = gen.ninepoint_2d(4, 11, 9)
+        width = 9
+    else:
+        rp, ci, av = gen.threeT_2d(5, 7, 6)
+        width = 11
+    A = oracle.csr(rp, ci, av)
+    M = A.dense()
+    assert np.array_equal(M, M.T)
+    assert np.all(np.diag(M) >= np.abs(M).sum(1) - np.abs(np.diag(M)))
+    np.linalg.cholesky(M)
+    for i in range(A.n):
+        cols = ci[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(cols) > 0) and i in cols
+    assert np.diff(rp).max() == width
+    col = gen.greedy_colouring(rp, ci)
+    rows = np.repeat(np.arange(A.n), np.diff(rp))
+    off = ci != rows
+    assert not np.any(col[rows[off]] == col[ci[off]])
