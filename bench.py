@@ -404,7 +404,7 @@ def run_gpu(args, rank, ws, local):
                    "l2": "inputs larger than L2 (operator + 20 resident systems + PCG vectors > 1 GB)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "pcg_kernel<Op2DW<double,2,true>> (global Jacobi-PCG on D^-1/2 A D^-1/2, FP64)",
+                     "kernel": "pcg_kernel<Op2DW<double,4,true>> (global Jacobi-PCG on D^-1/2 A D^-1/2, FP64)",
                      "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_cell_iter": ITER_BYTES,
                      "impl_bytes_per_cell_iter": IMPL_ITER_BYTES},
         "roofline_fp64_issue": {"bound": "alu", "achieved": dp_achieved, "peak": DP_PEAK_GOPS,

@@ -396,6 +396,12 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  *       FP64 instructions and bytes per iteration.  0 iterates on A with the
  *       explicit Jacobi preconditioner.  The stopping test is the same in
  *       both: ||b - A x||_2 / ||b||_2 <= tol on the unscaled system.
+ *   "pcg_wide"      0 or 1 (default 1): the scaled 2-D FP64 solve gives each
+ *       lane four adjacent cells (else two) when nx is a multiple of 4.
+ *   "local_single"  0 or 1 (default 0): the FP64 local solve of
+ *       lc_solve_local_then_global takes one grid-wide reduction per CG
+ *       iteration (Chronopoulos-Gear arrangement: same iterates in exact
+ *       arithmetic) instead of two.
  *   "local_cluster_rows" >= 0 (default 8192): the FP64 local solve of
  *       lc_solve_local_then_global runs on one thread-block cluster, its
  *       vectors in distributed shared memory, when the subsystem has at most

@@ -221,5 +221,57 @@ __device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned int nblocks) {
 template <typename T>
 __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 
+// ---------------------------------------------------------------- grid reductions
+
+struct NoPost {
+    __device__ void operator()(double *) const {}
+};
+
+// Block sums of NV thread values into partial slots `slot0..`, barrier, and
+// the grid-wide sums (identical in every block): warp 0 adds the block
+// partials lane-strided and reduces them in a fixed order.  Thread 0 then
+// runs post(t) on t[0..NV) = the totals, which may append ND derived scalars
+// t[NV..NV+ND) (the CG step lengths): FP64 divisions and tests run once per
+// block instead of once per thread -- FP64 issue is scarce.  Every thread
+// reads the totals and derived values back.  False if a wait timed out.
+template <int NV, int ND = 0, typename T, class Post = NoPost>
+__device__ __forceinline__ bool grid_sums(T (&v)[NV], int slot0, double *part, double *red, Ctrl *ctrl,
+                                          double (&out)[NV + ND], Post post = Post()) {
+    T tmp[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tmp[k] = v[k];
+    block_sum<NV, T>(tmp, reinterpret_cast<T *>(red));
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[(size_t)(slot0 + k) * kMaxGrid + blockIdx.x] = (double)tmp[k];
+    if (!grid_sync(ctrl, gridDim.x)) return false;
+    if (threadIdx.x < 32) {
+        double acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += ldcg(part + (size_t)(slot0 + k) * kMaxGrid + b);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = warp_sum(acc[k]);
+        if (threadIdx.x == 0) {
+            double t[NV + ND];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) t[k] = acc[k];
+            post(t);
+#pragma unroll
+            for (int k = 0; k < NV + ND; ++k) red[96 + k] = t[k];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV + ND; ++k) out[k] = red[96 + k];
+    __syncthreads();
+    return true;
+}
+
+// A flag stored as a double by post(): tested with an integer compare.
+__device__ __forceinline__ bool flag_set(double f) { return __double_as_longlong(f) != 0; }
+
 
 }  // namespace lc

@@ -125,6 +125,7 @@ cudaError_t launch_diff2(int64_t n, const double *x, const double *y, double *pa
 // Krylov (lc_pcg.cu)
 struct PcgWork {
     double *r, *z, *p0, *p1, *q;     // capacity n
+    double *e0, *e1;                 // capacity n (single-reduction CSR solve)
     double *dinv;                    // CSR: per-row 1/a_ii (capacity n)
     double *partials;                // kMaxGrid * 8
     float *r32, *z32, *p032, *p132, *q32, *x32, *dinv32;   // mixed precision (capacity n)
@@ -141,6 +142,7 @@ struct PcgArgs {
     double inner_tol;     // mixed: reduction asked of each FP32 inner solve
     int32_t max_outer;    // mixed: refinement sweeps
     int32_t scaled;       // FP64 2D: iterate on the symmetrically scaled system (tuning)
+    int32_t wide;         // FP64 2D scaled: four cells per lane (tuning)
 };
 cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                cudaStream_t s);
@@ -148,6 +150,10 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
 // ctrl -- no reset of ctrl, and the kernel returns at once if ctrl->done
 cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                            cudaStream_t s, bool after_cluster = false);
+// FP64 Jacobi-PCG of a CSR system with one grid reduction per iteration
+// (lc_pcg1.cu); after_cluster as for launch_pcg_csr
+cudaError_t launch_pcg_csr_single(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
+                                  cudaStream_t s, bool after_cluster);
 // FP64 Jacobi-PCG of a CSR system on one thread-block cluster (lc_cluster.cu),
 // when it has at most max_rows rows and they fit the cluster's shared memory
 // (cluster_local_rows(); 0 if the device cannot run the cluster); sets

@@ -63,26 +63,42 @@ union VecU {
     T e[N];
 };
 
+// four doubles move as two double2 accesses
 template <typename T, int N>
 __device__ __forceinline__ void vld(const T *a, T (&out)[N]) {
-    VecU<T, N> u;
-    u.v = *reinterpret_cast<const typename VecType<T, N>::type *>(a);
+    if constexpr (N == 4 && sizeof(T) == 8) {
+        const double2 lo = reinterpret_cast<const double2 *>(a)[0], hi = reinterpret_cast<const double2 *>(a)[1];
+        out[0] = lo.x; out[1] = lo.y; out[2] = hi.x; out[3] = hi.y;
+    } else {
+        VecU<T, N> u;
+        u.v = *reinterpret_cast<const typename VecType<T, N>::type *>(a);
 #pragma unroll
-    for (int k = 0; k < N; ++k) out[k] = u.e[k];
+        for (int k = 0; k < N; ++k) out[k] = u.e[k];
+    }
 }
 template <typename T, int N>
 __device__ __forceinline__ void vld_cg(const T *a, T (&out)[N]) {
-    VecU<T, N> u;
-    u.v = __ldcg(reinterpret_cast<const typename VecType<T, N>::type *>(a));
+    if constexpr (N == 4 && sizeof(T) == 8) {
+        const double2 lo = __ldcg(reinterpret_cast<const double2 *>(a)), hi = __ldcg(reinterpret_cast<const double2 *>(a) + 1);
+        out[0] = lo.x; out[1] = lo.y; out[2] = hi.x; out[3] = hi.y;
+    } else {
+        VecU<T, N> u;
+        u.v = __ldcg(reinterpret_cast<const typename VecType<T, N>::type *>(a));
 #pragma unroll
-    for (int k = 0; k < N; ++k) out[k] = u.e[k];
+        for (int k = 0; k < N; ++k) out[k] = u.e[k];
+    }
 }
 template <typename T, int N>
 __device__ __forceinline__ void vst(T *a, const T (&in)[N]) {
-    VecU<T, N> u;
+    if constexpr (N == 4 && sizeof(T) == 8) {
+        reinterpret_cast<double2 *>(a)[0] = make_double2(in[0], in[1]);
+        reinterpret_cast<double2 *>(a)[1] = make_double2(in[2], in[3]);
+    } else {
+        VecU<T, N> u;
 #pragma unroll
-    for (int k = 0; k < N; ++k) u.e[k] = in[k];
-    *reinterpret_cast<typename VecType<T, N>::type *>(a) = u.v;
+        for (int k = 0; k < N; ++k) u.e[k] = in[k];
+        *reinterpret_cast<typename VecType<T, N>::type *>(a) = u.v;
+    }
 }
 
 template <typename T>
@@ -567,56 +583,6 @@ struct OpCsr {
 
 // -------------------------------------------------------------- building blocks
 
-struct NoPost {
-    __device__ void operator()(double *) const {}
-};
-
-// Block sums of NV thread values into partial slots `slot0..`, barrier, and
-// the grid-wide sums (identical in every block): warp 0 adds the block
-// partials lane-strided and reduces them in a fixed order.  Thread 0 then
-// runs post(t) on t[0..NV) = the totals, which may append ND derived scalars
-// t[NV..NV+ND) (the CG step lengths): FP64 divisions and tests run once per
-// block instead of once per thread -- FP64 issue is scarce.  Every thread
-// reads the totals and derived values back.  False if a wait timed out.
-template <int NV, int ND = 0, typename T, class Post = NoPost>
-__device__ __forceinline__ bool grid_sums(T (&v)[NV], int slot0, double *part, double *red, Ctrl *ctrl,
-                                          double (&out)[NV + ND], Post post = Post()) {
-    T tmp[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) tmp[k] = v[k];
-    block_sum<NV, T>(tmp, reinterpret_cast<T *>(red));
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) part[(size_t)(slot0 + k) * kMaxGrid + blockIdx.x] = (double)tmp[k];
-    if (!grid_sync(ctrl, gridDim.x)) return false;
-    if (threadIdx.x < 32) {
-        double acc[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32)
-#pragma unroll
-            for (int k = 0; k < NV; ++k) acc[k] += ldcg(part + (size_t)(slot0 + k) * kMaxGrid + b);
-#pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] = warp_sum(acc[k]);
-        if (threadIdx.x == 0) {
-            double t[NV + ND];
-#pragma unroll
-            for (int k = 0; k < NV; ++k) t[k] = acc[k];
-            post(t);
-#pragma unroll
-            for (int k = 0; k < NV + ND; ++k) red[96 + k] = t[k];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV + ND; ++k) out[k] = red[96 + k];
-    __syncthreads();
-    return true;
-}
-
-// A flag stored as a double by post(): tested with an integer compare.
-__device__ __forceinline__ bool flag_set(double f) { return __double_as_longlong(f) != 0; }
-
 // r = b - A x (z = dinv r if V.z), with the grid sums of b.b, r.z, r.r.
 template <class OP, typename T>
 __device__ bool residual_phase(const OP &op, const Vecs<T> &V, double *part, double *red, Ctrl *ctrl, double &bb,
@@ -1000,6 +966,18 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
         // at least 4 rows per warp so the recomputed halo rows stay a small overhead
         const int64_t units = ((int64_t)((op.nx + 63) / 64) * op.ny + 4 * wpb - 1) / (4 * wpb);
         Op2DW<double, 2> od{op, coef64(op)};
+        if (!mixed && a.scaled && op.sc && a.wide && op.nx % 4 == 0) {
+            // four cells per lane: half the strip-end halos and segment starts
+            const int64_t units4 = ((int64_t)((op.nx + 127) / 128) * op.ny + 4 * wpb - 1) / (4 * wpb);
+            Op2DW<double, 4, true> os{op, Coef<double>{op.D, op.Txh, op.Tyh, nullptr}, op.sc, op.sq, op.dn32,
+                                      op.dexp};
+            Vecs<double> VS = VD;
+            VS.x = w.z;
+            VS.z = w.r;
+            VS.dinv = nullptr;
+            VS.xu = a.x;
+            return launch_pcg(os, units4, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+        }
         if (!mixed && a.scaled && op.sc) {
             // the symmetrically scaled system: x^ in the z workspace, z = r^
             Op2DW<double, 2, true> os{op, Coef<double>{op.D, op.Txh, op.Tyh, nullptr}, op.sc, op.sq, op.dn32,

@@ -181,9 +181,9 @@ def test_pcg_matches_oracle(ctx, name, op):
 SCALED_SHAPES = [(64, 16), (130, 37), (300, 260), (2, 50)]
 
 
-@pytest.mark.parametrize("nx,ny", SCALED_SHAPES)
-@pytest.mark.parametrize("scaled", [0, 1])
-def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled):
+@pytest.mark.parametrize("nx,ny", SCALED_SHAPES + [(128, 40), (4, 9)])
+@pytest.mark.parametrize("scaled,wide", [(0, 0), (1, 0), (1, 1)])
+def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide):
     """The 2-D FP64 solve on D^-1/2 A D^-1/2 (pcg_scaled = 1) and on A with the
     explicit Jacobi preconditioner (0) are the same Jacobi-PCG iteration in
     exact arithmetic: both match the oracle's iteration count within one and
@@ -195,7 +195,8 @@ def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled):
     assert st == oracle.OK
     gop = stencil_op(ctx, op)
     gop.set_tuning("pcg_scaled", scaled)
-    assert gop.get_tuning("pcg_scaled") == scaled
+    gop.set_tuning("pcg_wide", wide)
+    assert gop.get_tuning("pcg_scaled") == scaled and gop.get_tuning("pcg_wide") == wide
     x = cu(x0)
     stats = lcg.Stats()
     lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(tol, 100000, lcg.PREC_FP64, 0.0, 0), stats)
@@ -295,13 +296,13 @@ def test_local_then_global_matches_oracle(ctx, mode, n):
 
 @pytest.mark.parametrize("n,radius,beta,rounds", [(96, 10, 1e-3, 2), (256, 40, 1e-3, 3), (384, 90, 1e-4, 4),
                                                    (300, 150, 1e-6, 8)])
-@pytest.mark.parametrize("cluster,threads", [(1 << 30, 256), (1 << 30, 1024), (0, 256)])
-def test_local_solve_cluster_and_grid_match_oracle(ctx, n, radius, beta, rounds, cluster, threads):
+@pytest.mark.parametrize("cluster,threads,single", [(1 << 30, 256, 0), (1 << 30, 1024, 0), (0, 256, 0), (0, 256, 1)])
+def test_local_solve_cluster_and_grid_match_oracle(ctx, n, radius, beta, rounds, cluster, threads, single):
     """The local solve on one thread-block cluster (vectors in distributed
-    shared memory) and on the whole grid give the oracle's local iteration
-    count within one and the same Alg 1 result; subsystems from a few hundred
-    rows to more than the cluster holds (that one falls back to the grid
-    kernel)."""
+    shared memory), on the whole grid, and on the whole grid with one
+    reduction per iteration give the oracle's local iteration count within
+    one and the same Alg 1 result; subsystems from a few hundred rows to more
+    than the cluster holds (that one falls back to the grid kernel)."""
     d = gen.cfg1_heat2d(seed=n + radius, n=n, radius=radius)
     A = oracle.from_stencil(d["op"])
     tol = 1e-8
@@ -311,6 +312,7 @@ def test_local_solve_cluster_and_grid_match_oracle(ctx, n, radius, beta, rounds,
     gop = stencil_op(ctx, d["op"])
     gop.set_tuning("local_cluster_rows", cluster)
     gop.set_tuning("local_cluster_threads", threads)
+    gop.set_tuning("local_single", single)
     assert gop.get_tuning("local_cluster_rows") == cluster and gop.get_tuning("local_cluster_threads") == threads
     x = cu(d["x0"])
     st = lcg.Stats()
@@ -445,3 +447,33 @@ def test_mixed_precision_rejects_bad_parameters(ctx):
         with pytest.raises(lcg.LcError) as e:
             lcg.pcg_solve(ctx, gop, cu(np.ones(op.n)), x, bad)
         assert e.value.code == lcg.LC_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("mode", ["residual", "gradient"])
+@pytest.mark.parametrize("single", [0, 1])
+def test_local_single_reduction_on_csr_and_stencil(ctx, mode, single):
+    """Alg 1 with the single-reduction local solve (one grid barrier per CG
+    iteration) against the oracle, on stencil and CSR operators."""
+    d = gen.cfg1_heat2d(seed=21, n=160, radius=14)
+    A = oracle.from_stencil(d["op"])
+    tol = 1e-8
+    if mode == "residual":
+        okw = dict(mark_mode=oracle.MARK_RESIDUAL, thr_mode=oracle.THR_REL_MAX, thr_param=1e-3,
+                   exp_mode=oracle.EXP_DILATE, exp_rounds=2)
+        prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=tol)
+    else:
+        okw = dict(mark_mode=oracle.MARK_GRADIENT, alpha=0.3, grad_layers=2)
+        prm = lcg.default_params(lcg.MARK_GRADIENT, alpha=0.3, grad_layers=2, tol=tol)
+    xr, sr, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], tol=tol, **okw)
+    for gop in (stencil_op(ctx, d["op"]), csr_op(ctx, A)):
+        gop.set_tuning("local_single", single)
+        gop.set_tuning("local_cluster_rows", 0)
+        x = cu(d["x0"])
+        st = lcg.Stats()
+        lcg.solve_local_then_global(ctx, gop, cu(d["b"]), x, prm, st)
+        xg = x.cpu().numpy()
+        assert st.K == sr["K"] and abs(st.it_local - sr["it_local"]) <= 1
+        assert abs(st.it_global - sr["it_global"]) <= 1
+        assert st.relres_tilde == pytest.approx(sr["relres_tilde"], rel=1e-6)
+        assert oracle.relres(A, d["b"], xg) <= tol
+        assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
