@@ -320,6 +320,16 @@ LC_EXPORT int lc_op_refresh(lc_op *op, void *stream);
 LC_EXPORT int lc_adjoint_grad_k_2d(lc_ctx *ctx, const int32_t shape[2], const double *k, const double *x,
                                    const double *lam, double *dk, void *stream);
 
+/* Reproducible dot product of two device vectors of the operator's size N:
+ * *out (device) = sum_i x_i y_i, where every product x_i y_i is rounded once
+ * to FP64, the products are added exactly as 128-bit integers relative to
+ * the largest product's exponent (products more than 2^40 below it are
+ * rounded at that resolution), and the total is rounded once (to nearest).
+ * The result does not depend on the order of the additions or on the launch
+ * configuration.  NaN if a product is not finite.  Uses the operator's
+ * workspace: work on one operator stays serialised on one stream. */
+LC_EXPORT int lc_op_dot(lc_ctx *ctx, const lc_op *op, const double *x, const double *y, double *out, void *stream);
+
 /* ---- nonlinear 2D heat conduction (Sec. 3.2) --------------------------------
  *
  * dT/dt = div(kappa(T) grad T), kappa = T^p, on an nx x ny grid of square

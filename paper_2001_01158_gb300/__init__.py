@@ -131,6 +131,7 @@ def lib():
     L.lc_op_refresh.argtypes = [vp, vp]
     L.lc_adjoint_grad_k_2d.argtypes = [vp, C.POINTER(i32), vp, vp, vp, vp, vp]
     L.lc_gs_smooth.argtypes = [vp, vp, vp, vp, i32, vp]
+    L.lc_op_dot.argtypes = [vp, vp, vp, vp, vp, vp]
     L.lc_heat2d_assemble.argtypes = [vp, C.POINTER(i32), d, d, C.POINTER(i32), C.POINTER(d), vp, vp, vp, vp, vp,
                                      vp, vp]
     L.lc_heat2d_step.argtypes = [vp, vp, C.POINTER(HeatParams), vp, vp, vp, vp, vp, vp, vp, C.POINTER(HeatStats), vp]
@@ -316,6 +317,12 @@ def heat2d_step(ctx: Context, op: "StencilOperator", hp: HeatParams, Tn, T, D, T
                                    _ptr(b, torch.float64, "b"), _ptr(work, torch.float64, "work"), C.byref(st),
                                    _stream(stream)))
     return st
+
+
+def dot(ctx: Context, op: _Operator, x, y, out, stream=None):
+    """lc_op_dot: reproducible FP64 dot product into the device scalar `out`."""
+    return ctx.check(lib().lc_op_dot(ctx.h, op.h, _ptr(x, torch.float64, "x"), _ptr(y, torch.float64, "y"),
+                                     _ptr(out, torch.float64, "out"), _stream(stream)))
 
 
 def gs_smooth(ctx: Context, op: _Operator, b, x, sweeps: int, stream=None):

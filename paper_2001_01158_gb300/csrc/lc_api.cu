@@ -892,6 +892,14 @@ int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const
     return stats->status;
 }
 
+int lc_op_dot(lc_ctx *ctx, const lc_op *op, const double *x, const double *y, double *out, void *stream) {
+    int rc = check_common(ctx, op);
+    if (rc) return rc;
+    if (!x || !y || !out) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    LC_CUDA(ctx, lc::launch_dot(op->n, x, y, out, op->pw.partials, (cudaStream_t)stream));
+    return LC_OK;
+}
+
 static int check_gs(lc_ctx *ctx, const lc_op *op, int sweeps);
 
 static int check_heat_bc(lc_ctx *ctx, const int32_t bc_type[4], const double bc_val[4], lc::HeatBc &bc) {

@@ -122,6 +122,10 @@ cudaError_t launch_heat_assemble(int nx, int ny, double h, double dt, const Heat
 // *out = sum (x - y)^2 (deterministic); part: >= 608 doubles of scratch
 cudaError_t launch_diff2(int64_t n, const double *x, const double *y, double *part, double *out, cudaStream_t s);
 
+// Reproducible dot product (lc_dot.cu): *out = sum x_i y_i, products summed
+// exactly in fixed point; scratch >= 2 + 2 * 608 64-bit words
+cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *out, double *scratch, cudaStream_t s);
+
 // Krylov (lc_pcg.cu)
 struct PcgWork {
     double *r, *z, *p0, *p1, *q;     // capacity n

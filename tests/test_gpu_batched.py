@@ -110,3 +110,39 @@ def test_batched_rejects_unsupported_parameters(setup):
         with pytest.raises(lcg.LcError) as e:
             batch.solve(b, x, p)
         assert e.value.code == lcg.LC_ERR_UNSUPPORTED
+
+
+def test_batched_full_size_512_systems():
+    """The bench's batched workload at its full size (512 systems, sides
+    log-uniform in [64, 512], 35 M cells) in the launch configuration the
+    bench times (autotuned, graph replay): every system reaches relres 1e-8
+    by the oracle's evaluation; on a sample of 24 systems the local domain,
+    subsystem size and threshold equal the oracle's and the solution is
+    within 1e-6 of the oracle's FP64 one."""
+    from paper_2001_01158_gb300.autotune import tune_batch
+    ctx = lcg.Context(0)
+    items = gen.cfg4_batch(seed=0)
+    systems = [(d["op"].shape[0], d["op"].shape[1], cu(d["op"].D), cu(d["op"].Tx), cu(d["op"].Ty)) for d in items]
+    batch = lcg.Batch(ctx, systems)
+    b = cu(np.concatenate([d["b"] for d in items]))
+    x0 = cu(np.concatenate([d["x0"] for d in items]))
+    prm = lcg.batch_params(beta=1e-3, layers=2, tol=1e-8, inner_tol=1e-4)
+    tune_batch(batch, b, x0, prm)
+    x = x0.clone()
+    batch.capture(b, x, prm)
+    x.copy_(x0)
+    batch.replay()
+    torch.cuda.synchronize()
+    st = batch.stats()
+    xs = x.cpu().numpy()
+    sample = set(np.random.default_rng(1).choice(len(items), size=24, replace=False).tolist())
+    for s, d in enumerate(items):
+        A = oracle.from_stencil(d["op"])
+        xg = xs[batch.offsets[s]:batch.offsets[s + 1]]
+        assert st[s]["status"] == 0 and oracle.relres(A, d["b"], xg) <= 1e-8, s
+        if s in sample:
+            m = oracle.mark_residual(A, d["b"], d["x0"], oracle.THR_REL_MAX, 1e-3, oracle.EXP_DILATE, 2)
+            ex = oracle.extract(A, m["mask"], d["b"], d["x0"])
+            assert st[s]["K"] == m["K"] and st[s]["nnzB"] == len(ex["B"].col) and st[s]["tau"] == m["tau"], s
+            xr, _, _, _ = oracle.pcg(A, d["b"], d["x0"], tol=1e-13)
+            assert np.linalg.norm(xg - xr) <= 1e-6 * np.linalg.norm(xr), s
