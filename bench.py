@@ -444,7 +444,18 @@ def run_gpu(args, rank, ws, local):
             "inner_iterations": statistics.mean(s["it_global"] for s in per_mixed),
             "refinement_sweeps": statistics.mean(s["restarts"] for s in per_mixed),
             "relres_max": max(s["relres_final"] for s in per_mixed),
-            "err_vs_fp64_reference": mixed_err},
+            "err_vs_fp64_reference": mixed_err,
+            # the FP32 inner CG inside the global refinement: algorithmic 60 B per
+            # cell and inner iteration (FP32 Jacobi-PCG; the scaled kernel moves
+            # 52 B), FP64 residual passes at 48 B per cell and sweep, over the
+            # launch's CUDA-event time
+            "roofline_global_solve": {
+                "bound": "hbm", "unit": "GB/s", "peak": peak,
+                "achieved": sum(N * (60 * s["it_global"] + 48 * (1 + s["restarts"])) for s in per_mixed) /
+                (sum(s["t_global_ms"] for s in per_mixed) * 1e-3) / 1e9,
+                "frac": sum(N * (60 * s["it_global"] + 48 * (1 + s["restarts"])) for s in per_mixed) /
+                (sum(s["t_global_ms"] for s in per_mixed) * 1e-3) / 1e9 / peak,
+                "kernel": "ir_kernel<Op2DW<double,2>, Op2DW<float,4,true>>"}},
         "speedup_vs_global_pcg": ms_glob / ms_res,
         "speedup_mixed_vs_global_pcg": ms_glob / ms_mixed,
     }

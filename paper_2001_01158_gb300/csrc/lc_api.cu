@@ -62,6 +62,7 @@ struct lc_op {
     double *sc = nullptr, *sq = nullptr, *Txh = nullptr, *Tyh = nullptr;
     float *dn32 = nullptr;
     int *dexp = nullptr;
+    float *Txh32 = nullptr, *Tyh32 = nullptr, *sq32 = nullptr;
 };
 
 namespace {
@@ -156,6 +157,9 @@ void carve(lc_op *op, Carver &c) {
             op->Tyh = c.take<double>(n);
             op->dn32 = c.take<float>(n);
             op->dexp = c.take<int>(1);
+            op->Txh32 = c.take<float>(n);
+            op->Tyh32 = c.take<float>(n);
+            op->sq32 = c.take<float>(n);
         }
     }
 }
@@ -772,6 +776,7 @@ int lc_op_create_stencil(lc_ctx *ctx, lc_op **out, int32_t dim, const int32_t sh
     op->st.dinv32 = op->dinv32;
     op->st.sc = op->sc; op->st.sq = op->sq; op->st.Txh = op->Txh; op->st.Tyh = op->Tyh;
     op->st.dn32 = op->dn32; op->st.dexp = op->dexp;
+    op->st.Txh32 = op->Txh32; op->st.Tyh32 = op->Tyh32; op->st.sq32 = op->sq32;
     int *bad = reinterpret_cast<int *>(&op->ctrl->K);
     cudaError_t e = cudaMemset(bad, 0, sizeof(int));
     if (e == cudaSuccess) e = lc::launch_check_stencil(op->st, bad, 0);

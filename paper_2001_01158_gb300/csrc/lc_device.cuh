@@ -42,6 +42,9 @@ struct Stencil {
     const double *sc, *sq, *Txh, *Tyh;
     const float *dn32;
     const int *dexp;
+    // the same scaling in FP32 for the mixed-precision inner solve: fl32 of
+    // the scaled faces and of D^1/2 (weights of its true-residual norm)
+    const float *Txh32, *Tyh32, *sq32;
 };
 
 // CSR operator; rows ascending, diagonal present.  `n_dev`, if not null,

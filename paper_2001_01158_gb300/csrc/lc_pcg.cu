@@ -174,7 +174,7 @@ struct Op2DW {
     Stencil s;
     Coef<T> c;
     const double *sc = nullptr, *sq = nullptr;   // UNIT: D^-1/2, D^1/2
-    const float *d32 = nullptr;                  // UNIT: fl32(D 2^-2h) for the stopping norm
+    const float *d32 = nullptr;                  // UNIT, FP64: fl32(D 2^-2h); FP32: fl32(D^1/2) (stopping norm)
     const int *dexp = nullptr;                   // UNIT: h = (*dexp - 1023) >> 1
     static constexpr int kSW = 32 * CPL;
     static constexpr int kSmem = 1;
@@ -215,8 +215,13 @@ struct Op2DW {
                         xv[k] = fmaT(alpha, pv[k], xv[k]);
                         rv[k] = fmaT(-alpha, qv[k], rv[k]);
                         acc[0] = fmaT(rv[k], rv[k], acc[0]);
-                        const float f = approx_abs_f32((double)rv[k], nscale);
-                        rrf = fmaf(dv[k] * f, f, rrf);
+                        if constexpr (sizeof(T) == 8) {   // FP64: sum D r^^2 from the bits of r^
+                            const float f = approx_abs_f32((double)rv[k], nscale);
+                            rrf = fmaf(dv[k] * f, f, rrf);
+                        } else {                          // FP32: sum (D^1/2 r^)^2 directly
+                            const float t = dv[k] * rv[k];
+                            rrf = fmaf(t, t, rrf);
+                        }
                     }
                 } else {
                     T dv[CPL], zv[CPL];
@@ -737,17 +742,27 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) ir_kernel(OPD opd, OPF opf,
         }
         if (rr <= stop) { result = 1; break; }
         if (outer >= max_outer || it >= maxit) { result = 0; break; }
-        // inner problem: fl32(A) d = fl32(r / ||r||), d = 0
+        // inner problem: fl32(A) d = fl32(r / ||r||), d = 0; on the scaled
+        // operator S fl32(A) S d^ = fl32(S r / ||r||), d = S d^
         const double sc = sqrt(rr), inv = 1.0 / sc;
         float acc[2] = {0.f, 0.f};
         opf.each_cell([&](int64_t i) {
-            const float ri = (float)(ldcg(VD.r + i) * inv);
-            const float zi = VF.dinv[i] * ri;
-            VF.r[i] = ri;
-            VF.z[i] = zi;
-            VF.x[i] = 0.f;
-            acc[0] = fmaf(ri, zi, acc[0]);
-            acc[1] = fmaf(ri, ri, acc[1]);
+            if constexpr (OPF::kScaled) {
+                const float ri = (float)(opf.sc[i] * ldcg(VD.r + i) * inv);
+                const float t = opf.d32[i] * ri;
+                VF.r[i] = ri;
+                VF.x[i] = 0.f;
+                acc[0] = fmaf(ri, ri, acc[0]);
+                acc[1] = fmaf(t, t, acc[1]);
+            } else {
+                const float ri = (float)(ldcg(VD.r + i) * inv);
+                const float zi = VF.dinv[i] * ri;
+                VF.r[i] = ri;
+                VF.z[i] = zi;
+                VF.x[i] = 0.f;
+                acc[0] = fmaf(ri, zi, acc[0]);
+                acc[1] = fmaf(ri, ri, acc[1]);
+            }
         });
         double o[2];
         if (!grid_sums<2, 0, float>(acc, 6, part, red, ctrl, o)) return;
@@ -756,7 +771,10 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) ir_kernel(OPD opd, OPF opf,
         if (res == -2) return;
         if (res == -1) { result = -1; break; }
         // x += ||r|| d in FP64
-        opd.each_cell([&](int64_t i) { VD.x[i] = fma(sc, (double)ldcg(VF.x + i), VD.x[i]); });
+        if constexpr (OPF::kScaled)
+            opd.each_cell([&](int64_t i) { VD.x[i] = fma(sc, opf.sc[i] * (double)ldcg(VF.x + i), VD.x[i]); });
+        else
+            opd.each_cell([&](int64_t i) { VD.x[i] = fma(sc, (double)ldcg(VF.x + i), VD.x[i]); });
         ++outer;
         if (!grid_sync(ctrl, gridDim.x)) return;
     }
@@ -990,6 +1008,14 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
             return launch_pcg(os, units, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
         }
         if (!mixed) return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+        if (op.nx % 4 == 0 && a.scaled && op.Txh32) {   // the inner solve on the scaled system
+            Op2DW<float, 4, true> of{op, Coef<float>{op.D32, op.Txh32, op.Tyh32, nullptr}, op.sc, op.sq, op.sq32,
+                                     nullptr};
+            Vecs<float> VS = VF;
+            VS.z = VF.r;
+            VS.dinv = nullptr;
+            return launch_ir(od, of, units, VD, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+        }
         if (op.nx % 4 == 0) {   // FP32 copies are the library's own, 256-byte aligned: float4 lanes
             Op2DW<float, 4> of{op, coef32(op)};
             return launch_ir(od, of, units, VD, VF, w.partials, a, ctrl, grid_hint, a.minblocks, s);
@@ -1051,7 +1077,7 @@ __global__ void max_exponent_kernel(int64_t n, const double *__restrict__ D, int
 
 __global__ void scaling_2d_kernel(int nx, int ny, const double *__restrict__ D, const double *__restrict__ Tx,
                                   const double *__restrict__ Ty, double *sc, double *sq, double *Txh, double *Tyh,
-                                  float *dn32, const int *dexp) {
+                                  float *dn32, const int *dexp, float *Txh32, float *Tyh32, float *sq32) {
     const int64_t n = (int64_t)nx * ny;
     const int h = (*dexp - 1023) >> 1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1060,9 +1086,14 @@ __global__ void scaling_2d_kernel(int nx, int ny, const double *__restrict__ D, 
         const double s = 1.0 / r;
         sc[i] = s;
         sq[i] = r;
-        Txh[i] = x + 1 < nx ? Tx[i] * s * (1.0 / sqrt(D[i + 1])) : 0.0;
-        Tyh[i] = y + 1 < ny ? Ty[i] * s * (1.0 / sqrt(D[i + nx])) : 0.0;
+        const double tx = x + 1 < nx ? Tx[i] * s * (1.0 / sqrt(D[i + 1])) : 0.0;
+        const double ty = y + 1 < ny ? Ty[i] * s * (1.0 / sqrt(D[i + nx])) : 0.0;
+        Txh[i] = tx;
+        Tyh[i] = ty;
         dn32[i] = (float)ldexp(D[i], -2 * h);
+        Txh32[i] = (float)tx;
+        Tyh32[i] = (float)ty;
+        sq32[i] = (float)r;
     }
 }
 }  // namespace
@@ -1072,7 +1103,9 @@ cudaError_t launch_scaling_2d(const Stencil &st, double *sc, double *sq, double 
     cudaError_t e = cudaMemsetAsync(dexp, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     max_exponent_kernel<<<152 * 4, 256, 0, s>>>(st.n, st.D, dexp);
-    scaling_2d_kernel<<<152 * 8, 256, 0, s>>>(st.nx, st.ny, st.D, st.Tx, st.Ty, sc, sq, Txh, Tyh, dn32, dexp);
+    scaling_2d_kernel<<<152 * 8, 256, 0, s>>>(st.nx, st.ny, st.D, st.Tx, st.Ty, sc, sq, Txh, Tyh, dn32, dexp,
+                                              const_cast<float *>(st.Txh32), const_cast<float *>(st.Tyh32),
+                                              const_cast<float *>(st.sq32));
     note_launches(2);
     return cudaGetLastError();
 }
