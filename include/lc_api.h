@@ -320,6 +320,17 @@ LC_EXPORT int lc_op_refresh(lc_op *op, void *stream);
 LC_EXPORT int lc_adjoint_grad_k_2d(lc_ctx *ctx, const int32_t shape[2], const double *k, const double *x,
                                    const double *lam, double *dk, void *stream);
 
+/* Self-test of the failure path of the grid-wide waits: a cooperative launch
+ * of `blocks` blocks on the operator's control block whose barrier waits for
+ * one arrival more than there are blocks, so it can only end by its limit
+ * (limit_ms in (0, 2000]; the solvers' own limit is ~2 s).  Every block gives
+ * up, records LC_ERR_TIMEOUT and returns: *status_out (host) receives the
+ * recorded status (LC_ERR_TIMEOUT when the path works).  Nothing faults or
+ * hangs, the context stays usable, and the control block is cleared
+ * afterwards.  Waits for the device. */
+LC_EXPORT int lc_selftest_barrier_timeout(lc_ctx *ctx, lc_op *op, int32_t blocks, double limit_ms,
+                                          int32_t *status_out);
+
 /* Reproducible dot product of two device vectors of the operator's size N:
  * *out (device) = sum_i x_i y_i, where every product x_i y_i is rounded once
  * to FP64, the products are added exactly as 128-bit integers relative to

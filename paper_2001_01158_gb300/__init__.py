@@ -132,6 +132,7 @@ def lib():
     L.lc_adjoint_grad_k_2d.argtypes = [vp, C.POINTER(i32), vp, vp, vp, vp, vp]
     L.lc_gs_smooth.argtypes = [vp, vp, vp, vp, i32, vp]
     L.lc_op_dot.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.lc_selftest_barrier_timeout.argtypes = [vp, vp, i32, d, C.POINTER(i32)]
     L.lc_heat2d_assemble.argtypes = [vp, C.POINTER(i32), d, d, C.POINTER(i32), C.POINTER(d), vp, vp, vp, vp, vp,
                                      vp, vp]
     L.lc_heat2d_step.argtypes = [vp, vp, C.POINTER(HeatParams), vp, vp, vp, vp, vp, vp, vp, C.POINTER(HeatStats), vp]
@@ -317,6 +318,13 @@ def heat2d_step(ctx: Context, op: "StencilOperator", hp: HeatParams, Tn, T, D, T
                                    _ptr(b, torch.float64, "b"), _ptr(work, torch.float64, "work"), C.byref(st),
                                    _stream(stream)))
     return st
+
+
+def selftest_barrier_timeout(ctx: Context, op: _Operator, blocks: int, limit_ms: float) -> int:
+    """lc_selftest_barrier_timeout: the status a barrier that cannot complete records."""
+    st = C.c_int32()
+    ctx.check(lib().lc_selftest_barrier_timeout(ctx.h, op.h, int(blocks), float(limit_ms), C.byref(st)))
+    return st.value
 
 
 def dot(ctx: Context, op: _Operator, x, y, out, stream=None):

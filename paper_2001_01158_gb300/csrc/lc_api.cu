@@ -897,6 +897,25 @@ int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const
     return stats->status;
 }
 
+int lc_selftest_barrier_timeout(lc_ctx *ctx, lc_op *op, int32_t blocks, double limit_ms, int32_t *status_out) {
+    int rc = check_common(ctx, op);
+    if (rc) return rc;
+    if (!status_out || !(limit_ms > 0.0) || limit_ms > 2000.0)
+        return fail(ctx, LC_ERR_INVALID_ARG, "limit_ms must be in (0, 2000]");
+    int clk_khz = 0;
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, ctx->device);
+    if (clk_khz <= 0) clk_khz = 2070000;
+    const long long cycles = (long long)(limit_ms * (double)clk_khz);
+    int *passed = reinterpret_cast<int *>(&op->ctrl->K);
+    LC_CUDA(ctx, lc::launch_barrier_timeout_selftest(op->ctrl, passed, blocks, cycles, 0));
+    LC_CUDA(ctx, cudaDeviceSynchronize());
+    lc::Ctrl c;
+    if ((rc = read_ctrl(ctx, op->ctrl, &c))) return rc;
+    *status_out = c.K ? LC_OK : c.status;   // a block that got through would be a barrier bug
+    LC_CUDA(ctx, cudaMemset(op->ctrl, 0, sizeof(lc::Ctrl)));
+    return LC_OK;
+}
+
 int lc_op_dot(lc_ctx *ctx, const lc_op *op, const double *x, const double *y, double *out, void *stream) {
     int rc = check_common(ctx, op);
     if (rc) return rc;

@@ -197,7 +197,8 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 // atomic per block and arrival, no generation word, no reset between
 // barriers.  A block never sees the counter past its own target before it
 // arrives (no block passes barrier k before all arrived).
-__device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned int nblocks) {
+__device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned int nblocks,
+                                          long long limit_cycles = kBarrierTimeoutCycles) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -208,7 +209,7 @@ __device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned int nblocks) {
         if (old + 1 < target) {
             const long long t0 = clock64();
             while (ld_acquire_u64(&ctrl->bar_count) < target) {
-                if (clock64() - t0 > kBarrierTimeoutCycles) { ok = 0; break; }
+                if (clock64() - t0 > limit_cycles) { ok = 0; break; }
             }
         }
         __threadfence();

@@ -126,6 +126,11 @@ cudaError_t launch_diff2(int64_t n, const double *x, const double *y, double *pa
 // exactly in fixed point; scratch >= 2 + 2 * 608 64-bit words
 cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *out, double *scratch, cudaStream_t s);
 
+// Self-test of the bounded grid barrier (lc_selftest.cu): a barrier that
+// cannot complete; *passed counts blocks that wrongly got through
+cudaError_t launch_barrier_timeout_selftest(Ctrl *ctrl, int *passed, int blocks, long long limit_cycles,
+                                            cudaStream_t s);
+
 // Krylov (lc_pcg.cu)
 struct PcgWork {
     double *r, *z, *p0, *p1, *q;     // capacity n
