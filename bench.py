@@ -465,6 +465,7 @@ def run_gpu(args, rank, ws, local):
         res["multigroup_64"] = run_multigroup(args, dev)
     if not args.no_batched:
         res["csr_3t_1024"] = run_csr3t(dev, 1024)
+        res["aniso3d_256"] = run_aniso3d(dev, 256)
     if not args.no_heat:
         res["heat_e1"] = {"99x99_100_steps": run_heat(dev, 99, 100), "1024x1024_10_steps": run_heat(dev, 1024, 10)}
     if rank == 0 and not args.no_cpu_baseline:
@@ -583,6 +584,48 @@ def run_csr3t(dev, n):
             out[name]["pcg_alg_GBs"] = byts * its[-1][1] / (its[-1][3] * 1e-3) / 1e9
     out["rows"], out["nnz"] = nrows, nnz
     out["speedup_alg1_vs_global"] = out["global"]["ms"] / out["alg1"]["ms"]
+    return out
+
+
+def run_aniso3d(dev, n):
+    """The 3D anisotropic workload (n^3 cells, k ratios 1:10:100 with a
+    lognormal perturbation, a source box): global FP64 Jacobi-PCG and Alg 1
+    with FP32 inner CG + FP64 refinement, both to relres 1e-10, the mixed
+    result's difference from the FP64 one, and each global solve's algorithmic
+    HBM rate (FP64 128 B, FP32 inner 64 B per cell and iteration)."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2001_01158_gb300 as lcg
+
+    d = gen.cfg3_aniso3d(seed=0, n=n)
+    op = d["op"]
+    T = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)  # noqa: E731
+    ctx = lcg.Context(dev.index)
+    gop = lcg.StencilOperator(ctx, op.shape, T(op.D), T(op.Tx), T(op.Ty), T(op.Tz))
+    b, x0 = T(d["b"]), T(d["x0"])
+    N = op.n
+    sp = lcg.SolveParams(1e-10, 200000, lcg.PREC_FP64, 0.0, 0)
+    prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-10,
+                             precision=lcg.PREC_MIXED, inner_tol=1e-5)
+    out = {}
+    st = lcg.Stats()
+    x64 = x0.clone()
+    lcg.pcg_solve(ctx, gop, b, x64.clone(), sp, st)   # warm-up
+    x64 = x0.clone()
+    lcg.pcg_solve(ctx, gop, b, x64, sp, st)
+    out["global_fp64"] = {"ms": st.t_total_ms, "iterations": st.it_global,
+                          "alg_GBs": N * 128 * st.it_global / (st.t_global_ms * 1e-3) / 1e9}
+    xm = x0.clone()
+    lcg.solve_local_then_global(ctx, gop, b, xm.clone(), prm, st)   # warm-up
+    xm = x0.clone()
+    lcg.solve_local_then_global(ctx, gop, b, xm, prm, st)
+    out["alg1_mixed"] = {"ms": st.t_total_ms, "K": st.K, "inner_iterations": st.it_global,
+                         "relres": st.relres_final,
+                         "global_alg_GBs": N * 64 * st.it_global / (st.t_global_ms * 1e-3) / 1e9,
+                         "rel_diff_vs_fp64": float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))}
+    out["speedup_mixed_vs_fp64"] = out["global_fp64"]["ms"] / out["alg1_mixed"]["ms"]
     return out
 
 

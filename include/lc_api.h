@@ -93,7 +93,8 @@ typedef struct {
     double  tol;         /* stop when ||b - A x||_2 <= tol ||b||_2 (Eq. rel-res-conv-criteria) */
     int32_t max_iter;    /* total CG iterations (all refinement sweeps together) */
     int32_t precision;   /* LC_PREC_FP64, or LC_PREC_MIXED: FP32 inner CG, FP64 refinement */
-    double  inner_tol;   /* MIXED: relative reduction asked of each FP32 inner solve (e.g. 1e-5) */
+    double  inner_tol;   /* MIXED: relative reduction asked of each FP32 inner solve (e.g. 1e-5); a
+                            sweep that needs less asks for half of what the outer test still misses */
     int32_t max_outer;   /* MIXED: refinement sweeps (e.g. 20) */
 } lc_solve_params;
 

@@ -59,10 +59,10 @@ struct lc_op {
     int local_cluster_threads = 256;
     int pcg_scaled = 1;
     int pcg_wide = 1;        // 2D scaled FP64: four cells per lane (when nx % 4 == 0; 3.5 % faster at 2048^2)      // 2D FP64: iterate on D^-1/2 A D^-1/2 (fewer FP64 instructions)
-    double *sc = nullptr, *sq = nullptr, *Txh = nullptr, *Tyh = nullptr;
+    double *sc = nullptr, *sq = nullptr, *Txh = nullptr, *Tyh = nullptr, *Tzh = nullptr;
     float *dn32 = nullptr;
     int *dexp = nullptr;
-    float *Txh32 = nullptr, *Tyh32 = nullptr, *sq32 = nullptr;
+    float *Txh32 = nullptr, *Tyh32 = nullptr, *Tzh32 = nullptr, *sq32 = nullptr;
 };
 
 namespace {
@@ -150,17 +150,17 @@ void carve(lc_op *op, Carver &c) {
         op->Ty32 = c.take<float>(n);
         op->Tz32 = op->st.dim == 3 ? c.take<float>(n) : nullptr;
         op->dinv32 = c.take<float>(n);
-        if (op->st.dim == 2) {
-            op->sc = c.take<double>(n);
-            op->sq = c.take<double>(n);
-            op->Txh = c.take<double>(n);
-            op->Tyh = c.take<double>(n);
-            op->dn32 = c.take<float>(n);
-            op->dexp = c.take<int>(1);
-            op->Txh32 = c.take<float>(n);
-            op->Tyh32 = c.take<float>(n);
-            op->sq32 = c.take<float>(n);
-        }
+        op->sc = c.take<double>(n);
+        op->sq = c.take<double>(n);
+        op->Txh = c.take<double>(n);
+        op->Tyh = c.take<double>(n);
+        op->Tzh = op->st.dim == 3 ? c.take<double>(n) : nullptr;
+        op->dn32 = c.take<float>(n);
+        op->dexp = c.take<int>(1);
+        op->Txh32 = c.take<float>(n);
+        op->Tyh32 = c.take<float>(n);
+        op->Tzh32 = op->st.dim == 3 ? c.take<float>(n) : nullptr;
+        op->sq32 = c.take<float>(n);
     }
 }
 
@@ -405,8 +405,8 @@ int lc_op_refresh(lc_op *op, void *stream) {
     LC_CUDA(op->ctx, lc::launch_dinv_stencil(op->n, op->st.D, op->dinv, op->D32, op->st.Tx, op->st.Ty, op->st.Tz,
                                              op->Tx32, op->Ty32, op->Tz32, op->dinv32, (cudaStream_t)stream));
     if (op->st.sc)
-        LC_CUDA(op->ctx, lc::launch_scaling_2d(op->st, op->sc, op->sq, op->Txh, op->Tyh, op->dn32, op->dexp,
-                                               (cudaStream_t)stream));
+        LC_CUDA(op->ctx, lc::launch_scaling(op->st, op->sc, op->sq, op->Txh, op->Tyh, op->Tzh, op->dn32, op->dexp,
+                                            op->Txh32, op->Tyh32, op->Tzh32, op->sq32, (cudaStream_t)stream));
     return LC_OK;
 }
 
@@ -774,17 +774,18 @@ int lc_op_create_stencil(lc_ctx *ctx, lc_op **out, int32_t dim, const int32_t sh
     op->st.dinv = op->dinv;
     op->st.D32 = op->D32; op->st.Tx32 = op->Tx32; op->st.Ty32 = op->Ty32; op->st.Tz32 = op->Tz32;
     op->st.dinv32 = op->dinv32;
-    op->st.sc = op->sc; op->st.sq = op->sq; op->st.Txh = op->Txh; op->st.Tyh = op->Tyh;
+    op->st.sc = op->sc; op->st.sq = op->sq; op->st.Txh = op->Txh; op->st.Tyh = op->Tyh; op->st.Tzh = op->Tzh;
     op->st.dn32 = op->dn32; op->st.dexp = op->dexp;
-    op->st.Txh32 = op->Txh32; op->st.Tyh32 = op->Tyh32; op->st.sq32 = op->sq32;
+    op->st.Txh32 = op->Txh32; op->st.Tyh32 = op->Tyh32; op->st.Tzh32 = op->Tzh32; op->st.sq32 = op->sq32;
     int *bad = reinterpret_cast<int *>(&op->ctrl->K);
     cudaError_t e = cudaMemset(bad, 0, sizeof(int));
     if (e == cudaSuccess) e = lc::launch_check_stencil(op->st, bad, 0);
     if (e == cudaSuccess)
         e = lc::launch_dinv_stencil(n, D, op->dinv, op->D32, Tx, Ty, op->st.Tz, op->Tx32, op->Ty32, op->Tz32,
                                     op->dinv32, 0);
-    if (e == cudaSuccess && dim == 2)
-        e = lc::launch_scaling_2d(op->st, op->sc, op->sq, op->Txh, op->Tyh, op->dn32, op->dexp, 0);
+    if (e == cudaSuccess)
+        e = lc::launch_scaling(op->st, op->sc, op->sq, op->Txh, op->Tyh, op->Tzh, op->dn32, op->dexp, op->Txh32,
+                               op->Tyh32, op->Tzh32, op->sq32, 0);
     int hbad = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "stencil set-up"); lc_op_destroy(op); return rc; }

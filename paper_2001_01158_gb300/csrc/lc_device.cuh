@@ -39,12 +39,12 @@ struct Stencil {
     // scaled face conductances T_f / sqrt(D_P D_N) of S A S (unit diagonal);
     // dn32 = fl32(D 2^-2h), h = floor(e/2), e the largest binary exponent of
     // D, stored biased (+1023) in *dexp
-    const double *sc, *sq, *Txh, *Tyh;
+    const double *sc, *sq, *Txh, *Tyh, *Tzh;
     const float *dn32;
     const int *dexp;
     // the same scaling in FP32 for the mixed-precision inner solve: fl32 of
     // the scaled faces and of D^1/2 (weights of its true-residual norm)
-    const float *Txh32, *Tyh32, *sq32;
+    const float *Txh32, *Tyh32, *Tzh32, *sq32;
 };
 
 // CSR operator; rows ascending, diagonal present.  `n_dev`, if not null,

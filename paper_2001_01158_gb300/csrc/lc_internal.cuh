@@ -174,10 +174,13 @@ cudaError_t launch_dinv_stencil(int64_t n, const double *D, double *dinv, float 
                                 const double *Ty, const double *Tz, float *Tx32, float *Ty32, float *Tz32,
                                 float *dinv32, cudaStream_t s);
 cudaError_t launch_check_stencil(const Stencil &op, int *bad, cudaStream_t s);
-// 2D: sc = D^-1/2, sq = D^1/2, Txh/Tyh = T / sqrt(D_P D_N) (0 on the last
-// column/row), dn32 and dexp as described in Stencil; two launches
-cudaError_t launch_scaling_2d(const Stencil &st, double *sc, double *sq, double *Txh, double *Tyh, float *dn32,
-                              int *dexp, cudaStream_t s);
+// Symmetric scaling S = D^-1/2 of a stencil operator (2D or 3D): sc = S,
+// sq = S^-1, T^ = T S_P S_N per face (0 on the last column/row/plane; Tzh only
+// in 3D), dn32 and dexp as described in Stencil, FP32 copies of the scaled
+// faces and of sq; two launches
+cudaError_t launch_scaling(const Stencil &st, double *sc, double *sq, double *Txh, double *Tyh, double *Tzh,
+                           float *dn32, int *dexp, float *Txh32, float *Tyh32, float *Tzh32, float *sq32,
+                           cudaStream_t s);
 cudaError_t launch_check_csr(int32_t n, const int32_t *rp, const int32_t *ci, const double *av, int *bad,
                              cudaStream_t s);
 

@@ -381,20 +381,53 @@ struct Op2DW {
 // plane (tile + one-cell xy halo) built once into shared memory (four
 // rotating planes: one barrier per plane), z-neighbours from the planes
 // above and below.
-template <typename T>
+//
+// UNIT = the symmetrically scaled system, as for Op2DW: unit diagonal, z = r^,
+// stopping norm sum D r^^2 in FP32, c holding D (residual passes) and the
+// scaled faces.
+template <typename T, bool UNIT = false>
 struct Op3D {
     Stencil s;
     Coef<T> c;
+    const double *sc = nullptr, *sq = nullptr;   // UNIT: D^-1/2, D^1/2
+    const float *d32 = nullptr;                  // UNIT, FP64: fl32(D 2^-2h); FP32: fl32(D^1/2)
+    const int *dexp = nullptr;                   // UNIT, FP64: h = (*dexp - 1023) >> 1
     static constexpr int kSmem = 2 * (kTileX + 2) * (kTileY + 2);
     static constexpr bool kTunable = true;
-    static constexpr bool kScaled = false;
+    static constexpr bool kScaled = UNIT;
     __device__ bool skipped() const { return false; }
     __device__ void resolve() {}
-    __device__ void prologue(const Vecs<T> &) const {}
-    __device__ void epilogue(const Vecs<T> &) const {}
-    __device__ void zero_solution(const Vecs<T> &V) const { each_cell([&](int64_t i) { V.x[i] = T(0); }); }
-    __device__ void phaseB_block(const Vecs<T> &V, const T *p, T alpha, T (&acc)[2], int) const {
-        phaseB_generic(*this, V, p, alpha, acc);
+    __device__ int dn_shift() const { return UNIT ? (*dexp - 1023) >> 1 : 0; }
+    __device__ void prologue(const Vecs<T> &V) const {
+        if (UNIT) each_cell([&](int64_t i) { V.x[i] = V.xu[i] * sq[i]; });
+    }
+    __device__ void epilogue(const Vecs<T> &V) const {
+        if (UNIT) each_cell([&](int64_t i) { V.xu[i] = V.x[i] * sc[i]; });
+    }
+    __device__ void zero_solution(const Vecs<T> &V) const {
+        each_cell([&](int64_t i) { (UNIT ? V.xu : V.x)[i] = T(0); });
+    }
+    __device__ void phaseB_block(const Vecs<T> &V, const T *p, T alpha, T (&acc)[2], int nscale) const {
+        if (!UNIT) {
+            phaseB_generic(*this, V, p, alpha, acc);
+            return;
+        }
+        float rrf = 0.f;
+        each_cell([&](int64_t i) {
+            const T xi = fmaT(alpha, p[i], V.x[i]);
+            const T ri = fmaT(-alpha, V.q[i], V.r[i]);
+            V.x[i] = xi;
+            V.r[i] = ri;
+            acc[0] = fmaT(ri, ri, acc[0]);
+            if constexpr (sizeof(T) == 8) {
+                const float f = approx_abs_f32((double)ri, nscale);
+                rrf = fmaf(d32[i] * f, f, rrf);
+            } else {
+                const float t = d32[i] * ri;
+                rrf = fmaf(t, t, rrf);
+            }
+        });
+        acc[1] = (T)rrf;
     }
     __device__ int64_t units() const {
         const int64_t tx = (s.nx + kTileX - 1) / kTileX, ty = (s.ny + kTileY - 1) / kTileY;
@@ -426,7 +459,7 @@ struct Op3D {
         const int64_t sxy = (int64_t)s.nx * s.ny;
         each_cell([&](int64_t i) {
             const int xx = (int)(i % s.nx), yy = (int)((i / s.nx) % s.ny), zz = (int)(i / sxy);
-            T ax = c.D[i] * ldcg(V.x + i);
+            T ax = UNIT ? ldcg(V.x + i) : c.D[i] * ldcg(V.x + i);
             if (zz > 0) ax = fmaT(-c.Tz[i - sxy], ldcg(V.x + i - sxy), ax);
             if (yy > 0) ax = fmaT(-c.Ty[i - s.nx], ldcg(V.x + i - s.nx), ax);
             if (xx > 0) ax = fmaT(-c.Tx[i - 1], ldcg(V.x + i - 1), ax);
@@ -434,9 +467,16 @@ struct Op3D {
             if (yy + 1 < s.ny) ax = fmaT(-c.Ty[i], ldcg(V.x + i + s.nx), ax);
             if (zz + 1 < s.nz) ax = fmaT(-c.Tz[i], ldcg(V.x + i + sxy), ax);
             const T bi = V.b[i];
+            bb = fmaT(bi, bi, bb);
+            if (UNIT) {   // r^ = S b - A^ x^;  ||r||^2 = sum D r^^2
+                const T rh = (T)sc[i] * bi - ax;
+                V.r[i] = rh;
+                rz = fmaT(rh, rh, rz);
+                rr = fmaT(c.D[i] * rh, rh, rr);
+                return;
+            }
             const T ri = bi - ax;
             V.r[i] = ri;
-            bb = fmaT(bi, bi, bb);
             rr = fmaT(ri, ri, rr);
             if (V.z) {
                 const T zi = V.dinv[i] * ri;
@@ -494,7 +534,7 @@ struct Op3D {
             T pn = T(0), phn = T(0), d = T(0), tzm = T(0), tym = T(0), txm = T(0), txp = T(0), typ = T(0), tzp = T(0);
             if (act) {
                 pn = pat(V, pold, first, beta, xx, yy, z + 1);
-                d = c.D[i];
+                if (!UNIT) d = c.D[i];
                 if (z > 0) tzm = c.Tz[i - sxy];
                 if (yy > 0) tym = c.Ty[i - s.nx];
                 if (xx > 0) txm = c.Tx[i - 1];
@@ -508,7 +548,7 @@ struct Op3D {
             if (has_h) pl[hy * kEx + hx] = ph;
             __syncthreads();
             if (act) {
-                T qi = d * pc;
+                T qi = UNIT ? pc : d * pc;
                 qi = fmaT(-tzm, pm, qi);
                 qi = fmaT(-tym, pl[cc - kEx], qi);
                 qi = fmaT(-txm, pl[cc - 1], qi);
@@ -766,7 +806,12 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) ir_kernel(OPD opd, OPF opf,
         });
         double o[2];
         if (!grid_sums<2, 0, float>(acc, 6, part, red, ctrl, o)) return;
-        const double stop_in = (inner_tol * inner_tol) * o[1];
+        // the inner solve reduces its residual by inner_tol, or -- when less is
+        // missing -- by half of what the outer test still needs (no over-solving
+        // in the last sweep)
+        const double need = 0.5 * sqrt(stop / rr);
+        const double red_in = need > inner_tol ? need : inner_tol;
+        const double stop_in = (red_in * red_in) * o[1];
         const int res = cg_iterations(opf, VF, part, red, sm, ctrl, o[0], stop_in, maxit, it, pin);
         if (res == -2) return;
         if (res == -1) { result = -1; break; }
@@ -972,7 +1017,24 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
         const int64_t units = (int64_t)((op.nx + kTileX - 1) / kTileX) * ((op.ny + kTileY - 1) / kTileY) *
                               ((op.nz + kTileZ - 1) / kTileZ);
         Op3D<double> od{op, coef64(op)};
+        if (!mixed && a.scaled && op.sc) {   // the symmetrically scaled system (as in 2D)
+            Op3D<double, true> os{op, Coef<double>{op.D, op.Txh, op.Tyh, op.Tzh}, op.sc, op.sq, op.dn32, op.dexp};
+            Vecs<double> VS = VD;
+            VS.x = w.z;
+            VS.z = w.r;
+            VS.dinv = nullptr;
+            VS.xu = a.x;
+            return launch_pcg(os, units, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+        }
         if (!mixed) return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+        if (a.scaled && op.Txh32) {
+            Op3D<float, true> of{op, Coef<float>{op.D32, op.Txh32, op.Tyh32, op.Tzh32}, op.sc, op.sq, op.sq32,
+                                 nullptr};
+            Vecs<float> VS = VF;
+            VS.z = VF.r;
+            VS.dinv = nullptr;
+            return launch_ir(od, of, units, VD, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+        }
         Op3D<float> of{op, coef32(op)};
         return launch_ir(od, of, units, VD, VF, w.partials, a, ctrl, grid_hint, a.minblocks, s);
     }
@@ -1075,37 +1137,40 @@ __global__ void max_exponent_kernel(int64_t n, const double *__restrict__ D, int
     if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(dexp, m);
 }
 
-__global__ void scaling_2d_kernel(int nx, int ny, const double *__restrict__ D, const double *__restrict__ Tx,
-                                  const double *__restrict__ Ty, double *sc, double *sq, double *Txh, double *Tyh,
-                                  float *dn32, const int *dexp, float *Txh32, float *Tyh32, float *sq32) {
-    const int64_t n = (int64_t)nx * ny;
+__global__ void scaling_kernel(Stencil st, double *sc, double *sq, double *Txh, double *Tyh, double *Tzh,
+                               float *dn32, const int *dexp, float *Txh32, float *Tyh32, float *Tzh32, float *sq32) {
+    const int64_t n = st.n, sxy = (int64_t)st.nx * st.ny;
     const int h = (*dexp - 1023) >> 1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % nx), y = (int)(i / nx);
-        const double r = sqrt(D[i]);
+        const int x = (int)(i % st.nx), y = (int)((i / st.nx) % st.ny), z = (int)(i / sxy);
+        const double r = sqrt(st.D[i]);
         const double s = 1.0 / r;
         sc[i] = s;
         sq[i] = r;
-        const double tx = x + 1 < nx ? Tx[i] * s * (1.0 / sqrt(D[i + 1])) : 0.0;
-        const double ty = y + 1 < ny ? Ty[i] * s * (1.0 / sqrt(D[i + nx])) : 0.0;
+        const double tx = x + 1 < st.nx ? st.Tx[i] * s * (1.0 / sqrt(st.D[i + 1])) : 0.0;
+        const double ty = y + 1 < st.ny ? st.Ty[i] * s * (1.0 / sqrt(st.D[i + st.nx])) : 0.0;
         Txh[i] = tx;
         Tyh[i] = ty;
-        dn32[i] = (float)ldexp(D[i], -2 * h);
         Txh32[i] = (float)tx;
         Tyh32[i] = (float)ty;
+        if (st.dim == 3) {
+            const double tz = z + 1 < st.nz ? st.Tz[i] * s * (1.0 / sqrt(st.D[i + sxy])) : 0.0;
+            Tzh[i] = tz;
+            Tzh32[i] = (float)tz;
+        }
+        dn32[i] = (float)ldexp(st.D[i], -2 * h);
         sq32[i] = (float)r;
     }
 }
 }  // namespace
 
-cudaError_t launch_scaling_2d(const Stencil &st, double *sc, double *sq, double *Txh, double *Tyh, float *dn32,
-                              int *dexp, cudaStream_t s) {
+cudaError_t launch_scaling(const Stencil &st, double *sc, double *sq, double *Txh, double *Tyh, double *Tzh,
+                           float *dn32, int *dexp, float *Txh32, float *Tyh32, float *Tzh32, float *sq32,
+                           cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(dexp, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     max_exponent_kernel<<<152 * 4, 256, 0, s>>>(st.n, st.D, dexp);
-    scaling_2d_kernel<<<152 * 8, 256, 0, s>>>(st.nx, st.ny, st.D, st.Tx, st.Ty, sc, sq, Txh, Tyh, dn32, dexp,
-                                              const_cast<float *>(st.Txh32), const_cast<float *>(st.Tyh32),
-                                              const_cast<float *>(st.sq32));
+    scaling_kernel<<<152 * 8, 256, 0, s>>>(st, sc, sq, Txh, Tyh, Tzh, dn32, dexp, Txh32, Tyh32, Tzh32, sq32);
     note_launches(2);
     return cudaGetLastError();
 }

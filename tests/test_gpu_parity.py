@@ -207,6 +207,30 @@ def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide):
     assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
 
 
+@pytest.mark.parametrize("shape", [(16, 8, 8), (17, 9, 10), (33, 20, 7), (40, 1, 3), (5, 4, 3)])
+@pytest.mark.parametrize("scaled", [0, 1])
+def test_pcg_3d_scaled_and_unscaled_match_oracle(ctx, shape, scaled):
+    """The 3D FP64 solve on D^-1/2 A D^-1/2 and on A with the explicit Jacobi
+    preconditioner both match the oracle's Jacobi-PCG (iterations within one,
+    solution within 1e-9); so does the 3D mixed-precision solve on the scaled
+    system (relres 1e-10)."""
+    op = gen.random_stencil_3d(sum(shape) + 3, *shape)
+    A, b, x0 = rhs_and_x0(op, 17)
+    tol = 1e-9
+    xr, st, it_ref, _ = oracle.pcg(A, b, x0, tol=tol)
+    gop = stencil_op(ctx, op)
+    gop.set_tuning("pcg_scaled", scaled)
+    x = cu(x0)
+    stats = lcg.Stats()
+    lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(tol, 100000, lcg.PREC_FP64, 0.0, 0), stats)
+    xg = x.cpu().numpy()
+    assert oracle.relres(A, b, xg) <= tol and abs(stats.it_global - it_ref) <= 1
+    assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
+    x = cu(x0)
+    lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(1e-10, 100000, lcg.PREC_MIXED, 1e-5, 30), stats)
+    assert oracle.relres(A, b, x.cpu().numpy()) <= 1e-10
+
+
 @pytest.mark.parametrize("cscale,bscale", [(1e25, 1e35), (1e-25, 1e-30), (1.0, 1e-140), (1e5, 1e150),
                                             (1e45, 1e50), (1e-45, 1e-40)])
 def test_pcg_scaled_extreme_magnitudes(ctx, cscale, bscale):
