@@ -114,6 +114,13 @@ __device__ __forceinline__ float spmv32(const BatchView &V, const Sys &S, const 
     return q;
 }
 
+// Reduction asked of a sweep's inner solve: inner_tol, or -- when the outer
+// test (rr <= stop) misses by less -- half of what is still missing.
+__device__ __forceinline__ double sweep_tol(double inner_tol, double stop, double rr) {
+    const double need = 0.5 * sqrt(stop / rr);
+    return need > inner_tol ? need : inner_tol;
+}
+
 // FP32 Jacobi-CG on (A32 | B32) d = r32 from d = 0 over `n` unknowns at `o`
 // (cells of the system, or rows of its subsystem); stops when the residual
 // fell by inner_tol or after max_inner iterations.  Returns iterations.
@@ -295,7 +302,8 @@ __device__ void solve_system(const BatchView &V, const BatchParams &P, int s, co
             const double sc = sqrt(rr), inv = 1.0 / sc;
             for (int l = threadIdx.x; l < K; l += BS) V.r32[S.o + l] = (float)(V.r[S.o + l] * inv);
             __syncthreads();
-            it_l += inner_cg<BS, true>(V, S, blk, K, S.o, V.dl32 + S.o, P.inner_tol, P.max_inner, breakdown);
+            it_l += inner_cg<BS, true>(V, S, blk, K, S.o, V.dl32 + S.o, sweep_tol(P.inner_tol, stop, rr), P.max_inner,
+                                       breakdown);
             for (int l = threadIdx.x; l < K; l += BS) V.xl[S.o + l] = fma(sc, (double)V.d32[S.o + l], V.xl[S.o + l]);
             __syncthreads();
             ++outer_l;
@@ -325,7 +333,8 @@ __device__ void solve_system(const BatchView &V, const BatchParams &P, int s, co
         const double sc = sqrt(rr), inv = 1.0 / sc;
         for (int i = threadIdx.x; i < n; i += BS) V.r32[S.o + i] = (float)(V.r[S.o + i] * inv);
         __syncthreads();
-        it_g += inner_cg<BS, false>(V, S, blk, n, S.o, V.dinv32 + S.o, P.inner_tol, P.max_inner, breakdown);
+        it_g += inner_cg<BS, false>(V, S, blk, n, S.o, V.dinv32 + S.o, sweep_tol(P.inner_tol, stop, rr), P.max_inner,
+                                    breakdown);
         for (int i = threadIdx.x; i < n; i += BS) V.x[S.o + i] = fma(sc, (double)V.d32[S.o + i], V.x[S.o + i]);
         __syncthreads();
         ++outer_g;
