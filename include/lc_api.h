@@ -420,6 +420,11 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  *       both: ||b - A x||_2 / ||b||_2 <= tol on the unscaled system.
  *   "pcg_wide"      0 or 1 (default 1): the scaled 2-D FP64 solve gives each
  *       lane four adjacent cells (else two) when nx is a multiple of 4.
+ *   "pcg_big"       0 or 1 (default 1): 2-D solves (FP64 and mixed) launch
+ *       one block of 768 threads per SM instead of blocks of 256 (the same
+ *       warps and register budget as pcg_minblocks 3, a third of the block
+ *       partials and barrier arrivals per grid-wide reduction); pcg_minblocks
+ *       then has no effect on them.  3-D and CSR solves ignore it.
  *   "local_single"  0 or 1 (default 0): the FP64 local solve of
  *       lc_solve_local_then_global takes one grid-wide reduction per CG
  *       iteration (Chronopoulos-Gear arrangement: same iterates in exact

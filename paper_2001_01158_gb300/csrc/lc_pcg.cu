@@ -179,6 +179,7 @@ struct Op2DW {
     static constexpr int kSW = 32 * CPL;
     static constexpr int kSmem = 1;
     static constexpr bool kTunable = true;    // register budget selectable (pcg_minblocks)
+    static constexpr bool kAnyBlock = true;   // strips are per warp: any block size
     static constexpr bool kScaled = UNIT;
     __device__ bool skipped() const { return false; }
     __device__ void resolve() {}
@@ -394,6 +395,7 @@ struct Op3D {
     const int *dexp = nullptr;                   // UNIT, FP64: h = (*dexp - 1023) >> 1
     static constexpr int kSmem = 2 * (kTileX + 2) * (kTileY + 2);
     static constexpr bool kTunable = true;
+    static constexpr bool kAnyBlock = false;   // one tile per block of kPcgThreads
     static constexpr bool kScaled = UNIT;
     __device__ bool skipped() const { return false; }
     __device__ void resolve() {}
@@ -577,6 +579,7 @@ struct OpCsr {
     const int32_t *done = nullptr;   // set: the cluster kernel may have solved the system already
     static constexpr int kSmem = 1;
     static constexpr bool kTunable = true;
+    static constexpr bool kAnyBlock = false;   // rows strided by kPcgThreads
     static constexpr bool kScaled = false;
     __device__ bool skipped() const { return done && *done; }
     __device__ void resolve() { if (cs.n_dev) n = *cs.n_dev; }
@@ -687,9 +690,9 @@ __device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, doubl
 
 // -------------------------------------------------------------- kernels
 
-template <class OP, int MINB>
-__global__ void __launch_bounds__(kPcgThreads, MINB) pcg_kernel(OP op, Vecs<double> V, double *part, double tol,
-                                                                int maxit, int max_restarts, Ctrl *ctrl) {
+template <class OP, int MINB, int THREADS = kPcgThreads>
+__global__ void __launch_bounds__(THREADS, MINB) pcg_kernel(OP op, Vecs<double> V, double *part, double tol,
+                                                            int maxit, int max_restarts, Ctrl *ctrl) {
     __shared__ double red[128];
     __shared__ double sm[OP::kSmem];
     if (op.skipped()) return;
@@ -752,10 +755,10 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) pcg_kernel(OP op, Vecs<doub
 }
 
 // Iterative refinement: FP64 residual and update around FP32 inner CG.
-template <class OPD, class OPF, int MINB>
-__global__ void __launch_bounds__(kPcgThreads, MINB) ir_kernel(OPD opd, OPF opf, Vecs<double> VD, Vecs<float> VF,
-                                                               double *part, double tol, double inner_tol,
-                                                               int maxit, int max_outer, Ctrl *ctrl) {
+template <class OPD, class OPF, int MINB, int THREADS = kPcgThreads>
+__global__ void __launch_bounds__(THREADS, MINB) ir_kernel(OPD opd, OPF opf, Vecs<double> VD, Vecs<float> VF,
+                                                           double *part, double tol, double inner_tol,
+                                                           int maxit, int max_outer, Ctrl *ctrl) {
     __shared__ double red[128];
     __shared__ float sm[OPF::kSmem];
     opd.resolve();
@@ -914,11 +917,11 @@ __global__ void check_csr_kernel(int32_t n, const int32_t *rp, const int32_t *ci
 
 // -------------------------------------------------------------- launch
 
-int coop_grid(const void *kernel, int64_t units, int cap) {
+int coop_grid(const void *kernel, int64_t units, int cap, int threads = kPcgThreads) {
     int dev = 0, sms = 152, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kPcgThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
     int64_t g = (int64_t)sms * (per < 1 ? 1 : per);
     if (cap > 0 && g > cap) g = cap;
     if (g > units) g = units;
@@ -928,10 +931,16 @@ int coop_grid(const void *kernel, int64_t units, int cap) {
 
 // minblocks = the register budget asked of the compiler (blocks of 256
 // threads that must fit on one SM): 1 = unconstrained, 2..4 = at most
-// 128 / 85 / 64 registers per thread.
+// 128 / 85 / 64 registers per thread.  big: one block of kBigThreads per SM
+// instead (operators with per-warp work only): the register budget of three
+// blocks of 256, a third of the block partials and barrier arrivals per
+// grid reduction.
+constexpr int kBigThreads = 768;
+
 template <class OP>
-const void *pcg_kernel_for(int minblocks) {
-    if constexpr (!OP::kTunable) return (const void *)pcg_kernel<OP, 1>;
+const void *pcg_kernel_for(int minblocks, bool big) {
+    if constexpr (OP::kAnyBlock)
+        if (big) return (const void *)pcg_kernel<OP, 1, kBigThreads>;
     switch (minblocks) {
         case 2: return (const void *)pcg_kernel<OP, 2>;
         case 3: return (const void *)pcg_kernel<OP, 3>;
@@ -940,8 +949,9 @@ const void *pcg_kernel_for(int minblocks) {
     }
 }
 template <class OPD, class OPF>
-const void *ir_kernel_for(int minblocks) {
-    if constexpr (!OPD::kTunable) return (const void *)ir_kernel<OPD, OPF, 1>;
+const void *ir_kernel_for(int minblocks, bool big) {
+    if constexpr (OPD::kAnyBlock && OPF::kAnyBlock)
+        if (big) return (const void *)ir_kernel<OPD, OPF, 1, kBigThreads>;
     switch (minblocks) {
         case 2: return (const void *)ir_kernel<OPD, OPF, 2>;
         case 3: return (const void *)ir_kernel<OPD, OPF, 3>;
@@ -951,14 +961,14 @@ const void *ir_kernel_for(int minblocks) {
 }
 
 cudaError_t coop_launch(const void *k, int64_t units, int cap, void **args, Ctrl *ctrl, cudaStream_t s,
-                        bool reset = true) {
-    const int grid = coop_grid(k, units, cap);
+                        bool reset = true, int threads = kPcgThreads) {
+    const int grid = coop_grid(k, units, cap, threads);
     if (reset) {
         reset_ctrl_kernel<<<1, 1, 0, s>>>(ctrl);
         note_launches(1);
     }
     note_launches(1);
-    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kPcgThreads), args, 0, s);
+    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(threads), args, 0, s);
 }
 
 template <class OP>
@@ -971,7 +981,11 @@ cudaError_t launch_pcg(const OP &op, int64_t units, const Vecs<double> &V, doubl
     int mi = a.maxit, mr = a.max_restarts;
     Ctrl *c = ctrl;
     void *args[] = {&o, &v, &pt, &t, &mi, &mr, &c};
-    return coop_launch(pcg_kernel_for<OP>(minblocks), units, cap, args, ctrl, s, reset);
+    const bool big = a.big && OP::kAnyBlock;
+    const int threads = big ? kBigThreads : kPcgThreads;
+    // units counts blocks of kPcgThreads: the same warps in fewer, larger blocks
+    const int64_t ub = (units * kPcgThreads + threads - 1) / threads;
+    return coop_launch(pcg_kernel_for<OP>(minblocks, big), ub, cap, args, ctrl, s, reset, threads);
 }
 
 template <class OPD, class OPF>
@@ -986,7 +1000,10 @@ cudaError_t launch_ir(const OPD &opd, const OPF &opf, int64_t units, const Vecs<
     int mi = a.maxit, mo = a.max_outer;
     Ctrl *c = ctrl;
     void *args[] = {&od, &of, &vd, &vf, &pt, &t, &ti, &mi, &mo, &c};
-    return coop_launch(ir_kernel_for<OPD, OPF>(minblocks), units, cap, args, ctrl, s);
+    const bool big = a.big && OPD::kAnyBlock && OPF::kAnyBlock;
+    const int threads = big ? kBigThreads : kPcgThreads;
+    const int64_t ub = (units * kPcgThreads + threads - 1) / threads;
+    return coop_launch(ir_kernel_for<OPD, OPF>(minblocks, big), ub, cap, args, ctrl, s, true, threads);
 }
 
 Vecs<double> vecs64(const PcgArgs &a, const PcgWork &w, const double *dinv) {

@@ -182,12 +182,12 @@ SCALED_SHAPES = [(64, 16), (130, 37), (300, 260), (2, 50)]
 
 
 @pytest.mark.parametrize("nx,ny", SCALED_SHAPES + [(128, 40), (4, 9)])
-@pytest.mark.parametrize("scaled,wide", [(0, 0), (1, 0), (1, 1)])
-def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide):
+@pytest.mark.parametrize("scaled,wide,big", [(0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 0, 0), (1, 1, 0)])
+def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide, big):
     """The 2-D FP64 solve on D^-1/2 A D^-1/2 (pcg_scaled = 1) and on A with the
     explicit Jacobi preconditioner (0) are the same Jacobi-PCG iteration in
     exact arithmetic: both match the oracle's iteration count within one and
-    its solution within 1e-9."""
+    its solution within 1e-9, with 768-thread blocks (pcg_big) or 256."""
     op = gen.random_stencil_2d(nx + 7 * ny, nx, ny)
     A, b, x0 = rhs_and_x0(op, 13)
     tol = 1e-9
@@ -196,7 +196,9 @@ def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide):
     gop = stencil_op(ctx, op)
     gop.set_tuning("pcg_scaled", scaled)
     gop.set_tuning("pcg_wide", wide)
+    gop.set_tuning("pcg_big", big)
     assert gop.get_tuning("pcg_scaled") == scaled and gop.get_tuning("pcg_wide") == wide
+    assert gop.get_tuning("pcg_big") == big
     x = cu(x0)
     stats = lcg.Stats()
     lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(tol, 100000, lcg.PREC_FP64, 0.0, 0), stats)
@@ -431,11 +433,14 @@ MIXED = [p for p in PROBLEMS if p[1].n >= 20]
 def test_mixed_precision_pcg_reaches_fp64_tolerance(ctx, name, op):
     """FP32 inner CG inside FP64 refinement reaches the FP64 relative residual
     of the plain FP64 solve; its error against the oracle's FP64 solution is
-    stated (and bounded loosely by the conditioning)."""
+    stated (and bounded loosely by the conditioning).  Stencil operators with
+    768- and 256-thread blocks (pcg_big 1 and 0), and CSR."""
     A, b, x0 = rhs_and_x0(op, 21)
     tol = 1e-10
     xr, st, _, _ = oracle.pcg(A, b, x0, tol=1e-13)
-    for gop in (stencil_op(ctx, op), csr_op(ctx, A)):
+    small = stencil_op(ctx, op)
+    small.set_tuning("pcg_big", 0)
+    for gop in (stencil_op(ctx, op), small, csr_op(ctx, A)):
         x = cu(x0)
         stats = lcg.Stats()
         lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(tol, 100000, lcg.PREC_MIXED, 1e-4, 30), stats)
