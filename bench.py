@@ -53,10 +53,11 @@ WORKLOAD = ("2D 2048x2048 5-point FP64 diffusion, 64 rectangles k in [1,1e3], Ga
 SETUP_BYTES = 64
 ITER_BYTES = 120
 IMPL_ITER_BYTES = 100
-# FP64 instructions the scaled kernel issues per cell: 9 per iteration (phase
-# A: 1 for p, 4 fma for q, 1 for p.q; phase B: x, r, r.r), 10 per residual pass
+# FP64 instructions the scaled kernel issues per cell: 8 per iteration (phase
+# A: 1 for p, 4 fma for q -- p.q runs on FP32 pairs; phase B: x, r, r.r),
+# 10 per residual pass
 DP_SETUP = 10
-DP_ITER = 9
+DP_ITER = 8
 DP_PEAK_GOPS = 152 * 2 * 2.07   # FP64 FMA instructions per second, in G (nominal 1.25 TFLOP/s)
 
 
@@ -406,13 +407,14 @@ def run_gpu(args, rank, ws, local):
                    "l2": "inputs larger than L2 (operator + 20 resident systems + PCG vectors > 1 GB)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "pcg_kernel<Op2DW<double,4,true>> (global Jacobi-PCG on D^-1/2 A D^-1/2, FP64)",
+                     "kernel": "pcg_kernel<Op2DW<double,4,true,true>> "
+                               "(global Jacobi-PCG on D^-1/2 A D^-1/2, FP64 vectors)",
                      "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_cell_iter": ITER_BYTES,
                      "impl_bytes_per_cell_iter": IMPL_ITER_BYTES},
         "roofline_fp64_issue": {"bound": "alu", "achieved": dp_achieved, "peak": DP_PEAK_GOPS,
                                 "unit": "G FP64 instr/s", "frac": dp_achieved / DP_PEAK_GOPS,
                                 "alg_fp64_instr_per_cell_iter": DP_ITER,
-                                "note": "same kernel; ncu shows the FP64 pipe ~72% busy at ~55% DRAM throughput"},
+                                "note": "same kernel; ncu shows the FP64 pipe ~66% busy at ~61% DRAM throughput"},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": e2e_ms / total_sys, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * N,

@@ -425,6 +425,14 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  *       warps and register budget as pcg_minblocks 3, a third of the block
  *       partials and barrier arrivals per grid-wide reduction); pcg_minblocks
  *       then has no effect on them.  3-D and CSR solves ignore it.
+ *   "pcg_pairdot"   0 or 1 (default 1): the scaled 2-D FP64 solve with four
+ *       cells per lane takes its dot products (p.q, r^.r^) and the block
+ *       sums of its grid reductions on pairs of FP32 numbers (hi + lo, 47
+ *       significand bits, built from the FP64 bits with integer
+ *       instructions; error-free FP32 products and two-sums) instead of on
+ *       the FP64 pipe, which is the scarcer one on this GPU.  The vectors
+ *       (x, r, p, q) stay FP64; alpha and beta differ from all-FP64 sums in
+ *       rounding only.
  *   "local_single"  0 or 1 (default 0): the FP64 local solve of
  *       lc_solve_local_then_global takes one grid-wide reduction per CG
  *       iteration (Chronopoulos-Gear arrangement: same iterates in exact

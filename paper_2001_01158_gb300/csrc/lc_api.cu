@@ -59,6 +59,7 @@ struct lc_op {
     int local_cluster_threads = 256;
     int pcg_scaled = 1;      // 2D FP64: iterate on D^-1/2 A D^-1/2 (fewer FP64 instructions)
     int pcg_big = 1;         // 2D solves: one 768-thread block per SM (2 % faster at 2048^2, mixed 5 %)
+    int pcg_pairdot = 1;     // 2D scaled wide FP64: dots and block sums on FP32 pairs (7 % faster at 2048^2)
     int pcg_wide = 1;        // 2D scaled FP64: four cells per lane (when nx % 4 == 0; 3.5 % faster at 2048^2)
     double *sc = nullptr, *sq = nullptr, *Txh = nullptr, *Tyh = nullptr, *Tzh = nullptr;
     float *dn32 = nullptr;
@@ -135,7 +136,7 @@ void carve(lc_op *op, Carver &c) {
     op->pw.e0 = c.take<double>(n);
     op->pw.e1 = c.take<double>(n);
     op->pw.dinv = c.take<double>(n);
-    op->pw.partials = c.take<double>((size_t)lc::kMaxGrid * 8);
+    op->pw.partials = c.take<double>((size_t)lc::kMaxGrid * lc::kPartialSlots);
     op->pw.r32 = c.take<float>(n);
     op->pw.z32 = c.take<float>(n);
     op->pw.p032 = c.take<float>(n);
@@ -331,7 +332,7 @@ int pcg_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_
              bool local, cudaStream_t s) {
     lc::PcgArgs a{b,           x,           p->tol,        p->max_iter,  3,
                   op->pcg_minblocks, p->precision, p->inner_tol, p->max_outer, op->pcg_scaled, op->pcg_wide,
-                  op->pcg_big};
+                  op->pcg_big, op->pcg_pairdot};
     lc::PcgWork w = op->pw;
     LC_CUDA(ctx, cudaMemsetAsync(&ctrl->status, 0, sizeof(int32_t), s));
     if (local) {
@@ -693,6 +694,11 @@ int lc_op_set_tuning(lc_op *op, const char *key, int32_t value) {
         op->local_cluster_rows = value;
         return LC_OK;
     }
+    if (!strcmp(key, "pcg_pairdot")) {
+        if (value < 0 || value > 1) return fail(op->ctx, LC_ERR_INVALID_ARG, "pcg_pairdot must be 0 or 1");
+        op->pcg_pairdot = value;
+        return LC_OK;
+    }
     if (!strcmp(key, "pcg_big")) {
         if (value < 0 || value > 1) return fail(op->ctx, LC_ERR_INVALID_ARG, "pcg_big must be 0 or 1");
         op->pcg_big = value;
@@ -727,6 +733,7 @@ int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value) {
     if (!strcmp(key, "local_single")) { *value = op->local_single; return LC_OK; }
     if (!strcmp(key, "pcg_wide")) { *value = op->pcg_wide; return LC_OK; }
     if (!strcmp(key, "pcg_big")) { *value = op->pcg_big; return LC_OK; }
+    if (!strcmp(key, "pcg_pairdot")) { *value = op->pcg_pairdot; return LC_OK; }
     return LC_ERR_INVALID_ARG;
 }
 

@@ -22,6 +22,7 @@ constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
 constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
 constexpr int kMaxExpRounds = 64;
 constexpr int kMaxGrid = 4096;                          // persistent-kernel blocks (partials capacity)
+constexpr int kPartialSlots = 16;                       // grid-reduction slots of kMaxGrid partials each
 
 // ---------------------------------------------------------------- descriptors
 
@@ -231,23 +232,17 @@ struct NoPost {
     __device__ void operator()(double *) const {}
 };
 
-// Block sums of NV thread values into partial slots `slot0..`, barrier, and
-// the grid-wide sums (identical in every block): warp 0 adds the block
-// partials lane-strided and reduces them in a fixed order.  Thread 0 then
-// runs post(t) on t[0..NV) = the totals, which may append ND derived scalars
-// t[NV..NV+ND) (the CG step lengths): FP64 divisions and tests run once per
-// block instead of once per thread -- FP64 issue is scarce.  Every thread
-// reads the totals and derived values back.  False if a wait timed out.
-template <int NV, int ND = 0, typename T, class Post = NoPost>
-__device__ __forceinline__ bool grid_sums(T (&v)[NV], int slot0, double *part, double *red, Ctrl *ctrl,
-                                          double (&out)[NV + ND], Post post = Post()) {
-    T tmp[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) tmp[k] = v[k];
-    block_sum<NV, T>(tmp, reinterpret_cast<T *>(red));
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) part[(size_t)(slot0 + k) * kMaxGrid + blockIdx.x] = (double)tmp[k];
+// The grid-wide part of a reduction whose block partials sit in slots
+// `slot0..` (thread 0 wrote them): barrier, then warp 0 adds the block
+// partials lane-strided and reduces them in a fixed order (identical in
+// every block).  Thread 0 then runs post(t) on t[0..NV) = the totals, which
+// may append ND derived scalars t[NV..NV+ND) (the CG step lengths): FP64
+// divisions and tests run once per block instead of once per thread -- FP64
+// issue is scarce.  Every thread reads the totals and derived values back.
+// False if a wait timed out.
+template <int NV, int ND, class Post>
+__device__ __forceinline__ bool grid_tail(int slot0, double *part, double *red, Ctrl *ctrl, double (&out)[NV + ND],
+                                          Post post) {
     if (!grid_sync(ctrl, gridDim.x)) return false;
     if (threadIdx.x < 32) {
         double acc[NV];
@@ -272,6 +267,77 @@ __device__ __forceinline__ bool grid_sums(T (&v)[NV], int slot0, double *part, d
     for (int k = 0; k < NV + ND; ++k) out[k] = red[96 + k];
     __syncthreads();
     return true;
+}
+
+// Block sums of NV thread values into partial slots `slot0..`, then the
+// grid-wide sums (grid_tail).
+template <int NV, int ND = 0, typename T, class Post = NoPost>
+__device__ __forceinline__ bool grid_sums(T (&v)[NV], int slot0, double *part, double *red, Ctrl *ctrl,
+                                          double (&out)[NV + ND], Post post = Post()) {
+    T tmp[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tmp[k] = v[k];
+    block_sum<NV, T>(tmp, reinterpret_cast<T *>(red));
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[(size_t)(slot0 + k) * kMaxGrid + blockIdx.x] = (double)tmp[k];
+    return grid_tail<NV, ND>(slot0, part, red, ctrl, out, post);
+}
+
+// (ah, al) += (bh, bl) for FP32 pairs (Knuth's two-sum of the high parts).
+__device__ __forceinline__ void pair_add(float &ah, float &al, float bh, float bl) {
+    const float s = __fadd_rn(ah, bh);
+    const float bv = __fsub_rn(s, ah);
+    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bv)), __fsub_rn(bh, bv));
+    ah = s;
+    al = __fadd_rn(al, __fadd_rn(bl, err));
+}
+
+// grid_sums with the block sums taken on FP32 pairs: thread value k is
+// (h[k] + l[k]) 2^e[k]; warps and the block add pairs with FP32 two-sums
+// (no FP64 instruction per thread), and thread 0 writes the block partial
+// in FP64.  The grid-wide part is grid_tail's.
+template <int NV, int ND = 0, class Post = NoPost>
+__device__ __forceinline__ bool grid_sums_pair(const float (&h)[NV], const float (&l)[NV], const int (&e)[NV],
+                                               int slot0, double *part, double *red, Ctrl *ctrl,
+                                               double (&out)[NV + ND], Post post = Post()) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    float a[NV], b[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) { a[k] = h[k]; b[k] = l[k]; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float bh = __shfl_down_sync(kFull, a[k], o), bl = __shfl_down_sync(kFull, b[k], o);
+            pair_add(a[k], b[k], bh, bl);
+        }
+    float *fs = reinterpret_cast<float *>(red);   // 2 NV x 32 floats
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) { fs[(2 * k) * 32 + warp] = a[k]; fs[(2 * k + 1) * 32 + warp] = b[k]; }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            a[k] = lane < nw ? fs[(2 * k) * 32 + lane] : 0.0f;
+            b[k] = lane < nw ? fs[(2 * k + 1) * 32 + lane] : 0.0f;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const float bh = __shfl_down_sync(kFull, a[k], o), bl = __shfl_down_sync(kFull, b[k], o);
+                pair_add(a[k], b[k], bh, bl);
+            }
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                part[(size_t)(slot0 + k) * kMaxGrid + blockIdx.x] = ldexp((double)a[k] + (double)b[k], e[k]);
+    }
+    return grid_tail<NV, ND>(slot0, part, red, ctrl, out, post);
 }
 
 // A flag stored as a double by post(): tested with an integer compare.

@@ -122,6 +122,44 @@ __device__ __forceinline__ float approx_abs_f32(double v, int nscale) {
     return __uint_as_float(((unsigned)e << 23) | (unsigned)((bits >> 29) & 0x7fffff));
 }
 
+// Dot products on FP32 pairs.  GB300 issues FP64 at 1/64 of its FP32 rate and
+// the FP64 pipe is what bounds the scaled 2D iteration, while most issue
+// slots sit idle; so its dot products can run on the FP32 and integer pipes:
+// v * 2^-ns is split into hi + lo (the top 24 and the next 23 significand
+// bits, 47 of v's 53) from v's bits, products and sums use the error-free
+// FP32 transformations (Dekker's product through FMA, Knuth's two-sum), and
+// the pair accumulates with a relative error near 2^-45 per term -- far
+// below what alpha and beta need (the iterates then differ from FP64 sums in
+// rounding only).  hi is the approx_abs_f32 value with v's sign.  Values
+// below 2^-126 (scaled) give 0, above FP32's range +-inf.
+__device__ __forceinline__ void split_f2(double v, int ns, float &hi, float &lo) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023 - ns;   // unbiased exponent of v 2^-ns
+    const unsigned mh = (unsigned)(bits >> 29) & 0x7fffffu, ml = (unsigned)(bits >> 6) & 0x7fffffu;
+    hi = e + 127 <= 0 ? 0.0f
+                      : __uint_as_float(sign | (e + 127 >= 255 ? 0x7f800000u : ((unsigned)(e + 127) << 23) | mh));
+    // ml 2^(e-46) = (1.ml - 1) 2^(e-23), the power of two (with v's sign) from bits
+    lo = e + 104 <= 0 || e + 127 >= 255
+             ? 0.0f
+             : __fmul_rn(__fsub_rn(__uint_as_float(0x3f800000u | ml), 1.0f),
+                         __uint_as_float(sign | ((unsigned)(e + 104) << 23)));
+}
+// (sh, sl) += (ah + al)(bh + bl), dropping al bl
+__device__ __forceinline__ void f2_add_prod(float ah, float al, float bh, float bl, float &sh, float &sl) {
+    const float p = __fmul_rn(ah, bh);
+    const float t = fmaf(al, bh, fmaf(ah, bl, fmaf(ah, bh, -p)));   // the product's error and cross terms
+    const float s = __fadd_rn(sh, p);
+    const float bv = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(err, t));
+}
+// the pair's value times 2^(2 ns), in FP64 (once per thread and phase)
+__device__ __forceinline__ double f2_value(float sh, float sl, int ns) {
+    return ldexp((double)sh + (double)sl, 2 * ns);
+}
+
 template <typename T>
 struct Coef {
     const T *D, *Tx, *Ty, *Tz;
@@ -169,7 +207,7 @@ __device__ __forceinline__ void phaseB_generic(const OP &op, const Vecs<T> &V, c
 // no separate vector), r.z = r^.r^; the stopping norm ||r||^2 = sum D r^^2
 // is accumulated in FP32 from approx_abs_f32 and confirmed in FP64 by the
 // true-residual pass.  c holds D (for that pass) and the scaled faces.
-template <typename T, int CPL, bool UNIT = false>
+template <typename T, int CPL, bool UNIT = false, bool F2D = false>
 struct Op2DW {
     Stencil s;
     Coef<T> c;
@@ -181,6 +219,7 @@ struct Op2DW {
     static constexpr bool kTunable = true;    // register budget selectable (pcg_minblocks)
     static constexpr bool kAnyBlock = true;   // strips are per warp: any block size
     static constexpr bool kScaled = UNIT;
+    static constexpr bool kPairDots = F2D;    // phase A's block sums on FP32 pairs
     __device__ bool skipped() const { return false; }
     __device__ void resolve() {}
     __device__ int dn_shift() const { return UNIT ? (*dexp - 1023) >> 1 : 0; }
@@ -313,8 +352,12 @@ struct Op2DW {
         }
     }
     __device__ __forceinline__ void load(const T *a, int64_t i, T (&v)[CPL]) const { vld<T, CPL>(a + i, v); }
-    __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *) const {
+    // F2D: p.q as an FP32 pair of the values scaled by 2^-nscale (a sum
+    // scaled by 2^-2 nscale), into pair[0..2) if given, else added to pq
+    __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *,
+                                 int nscale, float *pair = nullptr) const {
         const int lane = threadIdx.x & 31;
+        float fh = 0.f, fl = 0.f;
         each_segment([&](int x0, int y0, int y1) {
             const int xa = x0 + CPL * lane;          // first column of this lane
             const bool act = xa < s.nx;               // nx is a multiple of CPL: all CPL cells valid
@@ -367,7 +410,14 @@ struct Op2DW {
                     qi = fmaT(-txe[k], pe[k], qi);
                     qi = fmaT(-typ[k], pn[k], qi);
                     q[k] = qi;
-                    pq = fmaT(pc[k], qi, pq);
+                    if constexpr (F2D) {
+                        float ph_, pl_, qh_, ql_;
+                        split_f2((double)pc[k], nscale, ph_, pl_);
+                        split_f2((double)qi, nscale, qh_, ql_);
+                        f2_add_prod(ph_, pl_, qh_, ql_, fh, fl);
+                    } else {
+                        pq = fmaT(pc[k], qi, pq);
+                    }
                 }
                 vst<T, CPL>(pout + i, pc);
                 vst<T, CPL>(V.q + i, q);
@@ -375,6 +425,10 @@ struct Op2DW {
                 for (int k = 0; k < CPL; ++k) { tym[k] = typ[k]; pm[k] = pc[k]; pc[k] = pn[k]; }
             }
         });
+        if constexpr (F2D) {
+            if (pair) { pair[0] = fh; pair[1] = fl; }
+            else pq += f2_value(fh, fl, nscale);
+        }
     }
 };
 
@@ -397,6 +451,7 @@ struct Op3D {
     static constexpr bool kTunable = true;
     static constexpr bool kAnyBlock = false;   // one tile per block of kPcgThreads
     static constexpr bool kScaled = UNIT;
+    static constexpr bool kPairDots = false;
     __device__ bool skipped() const { return false; }
     __device__ void resolve() {}
     __device__ int dn_shift() const { return UNIT ? (*dexp - 1023) >> 1 : 0; }
@@ -495,7 +550,8 @@ struct Op3D {
         const T zi = ldcg(V.z + i);
         return first ? zi : fmaT(beta, ldcg(pold + i), zi);
     }
-    __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *sm) const {
+    __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *sm,
+                                 int, float * = nullptr) const {
         const int64_t nu = units();
         for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) phaseA_unit(u, V, pold, pout, first, beta, pq, sm);
     }
@@ -581,6 +637,7 @@ struct OpCsr {
     static constexpr bool kTunable = true;
     static constexpr bool kAnyBlock = false;   // rows strided by kPcgThreads
     static constexpr bool kScaled = false;
+    static constexpr bool kPairDots = false;
     __device__ bool skipped() const { return done && *done; }
     __device__ void resolve() { if (cs.n_dev) n = *cs.n_dev; }
     __device__ void prologue(const Vecs<T> &) const {}
@@ -611,7 +668,8 @@ struct OpCsr {
             }
         });
     }
-    __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *) const {
+    __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *,
+                                 int, float * = nullptr) const {
         each_cell([&](int64_t i) {
             T qi = T(0), pi = T(0);
             const int32_t e1 = cs.rp[i + 1];
@@ -657,16 +715,27 @@ __device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, doubl
         T pq = T(0);
         const T *pold = pin ? V.p1 : V.p0;
         T *pout = pin ? V.p0 : V.p1;
-        op.phaseA_block(V, pold, pout, first, (T)beta, pq, sm);
-        T a1[1] = {pq};
         double o1[3];   // p.q, alpha, breakdown flag
         const double rz_ = rz;
-        if (!grid_sums<1, 2, T>(a1, 3, part, red, ctrl, o1, [rz_](double *t) {
-                const bool ok = t[0] > 0.0 && isfinite(t[0]);
-                t[1] = ok ? rz_ / t[0] : 0.0;
-                t[2] = ok ? 0.0 : 1.0;
-            }))
-            return -2;
+        const auto post1 = [rz_](double *t) {
+            const bool ok = t[0] > 0.0 && isfinite(t[0]);
+            t[1] = ok ? rz_ / t[0] : 0.0;
+            t[2] = ok ? 0.0 : 1.0;
+        };
+        // pair dots: values scaled by 2^-ps, ps half the exponent of r.z, so
+        // that the scaled sums stay near 1 whatever the residual's size
+        const int ps = ((int)((__double_as_longlong(rz) >> 52) & 0x7ff) - 1023) >> 1;
+        if constexpr (OP::kPairDots) {
+            float pr[2] = {0.f, 0.f};
+            op.phaseA_block(V, pold, pout, first, (T)beta, pq, sm, ps, pr);
+            const float h1[1] = {pr[0]}, l1[1] = {pr[1]};
+            const int e1[1] = {2 * ps};
+            if (!grid_sums_pair<1, 2>(h1, l1, e1, 3, part, red, ctrl, o1, post1)) return -2;
+        } else {
+            op.phaseA_block(V, pold, pout, first, (T)beta, pq, sm, nscale);
+            T a1[1] = {pq};
+            if (!grid_sums<1, 2, T>(a1, 3, part, red, ctrl, o1, post1)) return -2;
+        }
         if (flag_set(o1[2])) return -1;
         const T alpha = (T)o1[1];
         pin ^= 1;
@@ -674,11 +743,19 @@ __device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, doubl
         T acc[2] = {T(0), T(0)};
         op.phaseB_block(V, p, alpha, acc, nscale);
         double o2[4];   // r.z, stopping norm, converged flag, beta
-        if (!grid_sums<2, 2, T>(acc, 4, part, red, ctrl, o2, [rz_, stop](double *t) {
-                t[2] = t[1] <= stop ? 1.0 : 0.0;
-                t[3] = t[0] / rz_;
-            }))
-            return -2;
+        const auto post2 = [rz_, stop](double *t) {
+            t[2] = t[1] <= stop ? 1.0 : 0.0;
+            t[3] = t[0] / rz_;
+        };
+        if constexpr (OP::kPairDots) {   // r.z split into a pair, the FP32 norm as it is
+            float h2[2], l2[2] = {0.f, 0.f};
+            split_f2((double)acc[0], 2 * ps, h2[0], l2[0]);
+            h2[1] = (float)acc[1];
+            const int e2[2] = {2 * ps, 0};
+            if (!grid_sums_pair<2, 2>(h2, l2, e2, 4, part, red, ctrl, o2, post2)) return -2;
+        } else {
+            if (!grid_sums<2, 2, T>(acc, 4, part, red, ctrl, o2, post2)) return -2;
+        }
         ++it;
         if (flag_set(o2[2])) return 1;
         if (it >= maxit) return 0;
@@ -1073,6 +1150,11 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
             VS.z = w.r;
             VS.dinv = nullptr;
             VS.xu = a.x;
+            if (a.pairdot) {   // dot products and block sums on FP32 pairs
+                Op2DW<double, 4, true, true> o2{op, Coef<double>{op.D, op.Txh, op.Tyh, nullptr}, op.sc, op.sq,
+                                                op.dn32, op.dexp};
+                return launch_pcg(o2, units4, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+            }
             return launch_pcg(os, units4, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
         }
         if (!mixed && a.scaled && op.sc) {

@@ -148,7 +148,9 @@ __device__ int cg1_iterations(const Cg1Args &a, int32_t n, double *red, double g
         }
         double o[6];   // gamma', delta', r'.r', converged, beta', alpha' (0 on breakdown)
         const double g0 = gam, a0 = alpha;
-        if (!grid_sums<3, 3, double>(acc, 4, a.part, red, a.ctrl, o, [g0, a0, stop](double *t) {
+        // alternate slot sets: a block may already write the next iteration's
+        // partials while a slower one still reads these
+        if (!grid_sums<3, 3, double>(acc, cur ? 7 : 4, a.part, red, a.ctrl, o, [g0, a0, stop](double *t) {
                 t[3] = t[2] <= stop ? 1.0 : 0.0;
                 const double bt = t[0] / g0;
                 const double den = t[1] - bt * t[0] / a0;

@@ -182,12 +182,15 @@ SCALED_SHAPES = [(64, 16), (130, 37), (300, 260), (2, 50)]
 
 
 @pytest.mark.parametrize("nx,ny", SCALED_SHAPES + [(128, 40), (4, 9)])
-@pytest.mark.parametrize("scaled,wide,big", [(0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 0, 0), (1, 1, 0)])
-def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide, big):
+@pytest.mark.parametrize("scaled,wide,big,pairdot", [(0, 0, 1, 0), (1, 0, 1, 0), (1, 1, 1, 0), (0, 0, 0, 0),
+                                                      (1, 1, 0, 0), (1, 1, 1, 1), (1, 1, 0, 1)])
+def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide, big, pairdot):
     """The 2-D FP64 solve on D^-1/2 A D^-1/2 (pcg_scaled = 1) and on A with the
     explicit Jacobi preconditioner (0) are the same Jacobi-PCG iteration in
     exact arithmetic: both match the oracle's iteration count within one and
-    its solution within 1e-9, with 768-thread blocks (pcg_big) or 256."""
+    its solution within 1e-9, with 768-thread blocks (pcg_big) or 256, and
+    with the dot products and block sums on FP32 pairs (pcg_pairdot) or in
+    FP64."""
     op = gen.random_stencil_2d(nx + 7 * ny, nx, ny)
     A, b, x0 = rhs_and_x0(op, 13)
     tol = 1e-9
@@ -197,8 +200,9 @@ def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide, big):
     gop.set_tuning("pcg_scaled", scaled)
     gop.set_tuning("pcg_wide", wide)
     gop.set_tuning("pcg_big", big)
+    gop.set_tuning("pcg_pairdot", pairdot)
     assert gop.get_tuning("pcg_scaled") == scaled and gop.get_tuning("pcg_wide") == wide
-    assert gop.get_tuning("pcg_big") == big
+    assert gop.get_tuning("pcg_big") == big and gop.get_tuning("pcg_pairdot") == pairdot
     x = cu(x0)
     stats = lcg.Stats()
     lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(tol, 100000, lcg.PREC_FP64, 0.0, 0), stats)
@@ -207,6 +211,31 @@ def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide, big):
     assert stats.relres_final <= tol
     assert abs(stats.it_global - it_ref) <= 1
     assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
+
+
+@pytest.mark.parametrize("pairdot", [0, 1])
+def test_pcg_power_of_two_scale_invariance(ctx, pairdot):
+    """Scaling b and x0 by 2^k scales every FP64 quantity of the scaled 2-D
+    solve exactly, and the FP32 stopping norm and the FP32-pair dot products
+    and block sums rescale with it (their exponent shifts follow b.b and
+    r.z): the solution is 2^k times the unscaled one bit for bit, with the
+    same iteration count, from 2^-400 to 2^400."""
+    op = gen.random_stencil_2d(5, 64, 40)
+    A, b, x0 = rhs_and_x0(op, 29)
+    gop = stencil_op(ctx, op)
+    gop.set_tuning("pcg_pairdot", pairdot)
+    sp = lcg.SolveParams(1e-10, 100000, lcg.PREC_FP64, 0.0, 0)
+    runs = {}
+    for k in (0, -400, 400):
+        x = cu(np.ldexp(x0, k))
+        st = lcg.Stats()
+        lcg.pcg_solve(ctx, gop, cu(np.ldexp(b, k)), x, sp, st)
+        runs[k] = (x.cpu().numpy(), st.it_global)
+    x_ref, it_ref = runs[0]
+    assert oracle.relres(A, b, x_ref) <= 1e-10
+    for k in (-400, 400):
+        assert runs[k][1] == it_ref
+        assert np.array_equal(bits(runs[k][0]), bits(np.ldexp(x_ref, k)))
 
 
 @pytest.mark.parametrize("shape", [(16, 8, 8), (17, 9, 10), (33, 20, 7), (40, 1, 3), (5, 4, 3)])
@@ -260,10 +289,12 @@ def test_pcg_scaled_extreme_magnitudes(ctx, cscale, bscale):
     assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
 
 
-def test_pcg_edge_cases(ctx):
-    op = gen.random_stencil_2d(1, 33, 21)
+@pytest.mark.parametrize("nx,pairdot", [(33, 0), (36, 0), (36, 1)])
+def test_pcg_edge_cases(ctx, nx, pairdot):
+    op = gen.random_stencil_2d(1, nx, 21)
     A = oracle.from_stencil(op)
     gop = stencil_op(ctx, op)
+    gop.set_tuning("pcg_pairdot", pairdot)
     sp = lcg.SolveParams(1e-8, 100000, lcg.PREC_FP64, 0.0, 0)
     # b = 0 gives x = 0
     x = cu(np.ones(op.n))
@@ -282,6 +313,7 @@ def test_pcg_edge_cases(ctx):
     rc = lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(1e-14, 3, lcg.PREC_FP64, 0.0, 0), st,
                        allow_not_converged=True)
     assert rc == lcg.LC_ERR_NOT_CONVERGED and st.it_global == 3
+    assert st.relres_final == pytest.approx(oracle.relres(A, b, x.cpu().numpy()), rel=1e-6)
     # a negative definite operator breaks down
     neg = oracle.csr(A.rowptr, A.col, -A.val)
     with pytest.raises(lcg.LcError):
