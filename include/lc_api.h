@@ -420,11 +420,13 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  *       both: ||b - A x||_2 / ||b||_2 <= tol on the unscaled system.
  *   "pcg_wide"      0 or 1 (default 1): the scaled 2-D FP64 solve gives each
  *       lane four adjacent cells (else two) when nx is a multiple of 4.
- *   "pcg_big"       0 or 1 (default 1): 2-D solves (FP64 and mixed) launch
- *       one block of 768 threads per SM instead of blocks of 256 (the same
- *       warps and register budget as pcg_minblocks 3, a third of the block
- *       partials and barrier arrivals per grid-wide reduction); pcg_minblocks
- *       then has no effect on them.  3-D and CSR solves ignore it.
+ *   "pcg_big"       0 or 1 (default 1): 2-D solves (FP64 and mixed) and the
+ *       local subsystem solves of lc_solve_local_then_global launch one block
+ *       of 768 threads per SM instead of blocks of 256 (the same warps and
+ *       register budget as pcg_minblocks 3, a third of the block partials
+ *       and barrier arrivals per grid-wide reduction); pcg_minblocks then has
+ *       no effect on them.  3-D solves and solves with a CSR operator's own
+ *       matrix ignore it.
  *   "pcg_pairdot"   0 or 1 (default 1): the scaled 2-D FP64 solve with four
  *       cells per lane takes its dot products (p.q, r^.r^) and the block
  *       sums of its grid reductions on pairs of FP32 numbers (hi + lo, 47
@@ -447,6 +449,8 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  *       grid kernel above roughly 10,000 rows.)
  *   "local_cluster_threads" 256, 512 or 1024 (default 256): threads per CTA
  *       of that cluster.
+ *   "local_grid_cap" 0..4096 (default 0 = one block per SM): blocks of the
+ *       grid-wide local solve kernel.
  * Unknown keys or out-of-range values return LC_ERR_INVALID_ARG. */
 LC_EXPORT int lc_op_set_tuning(lc_op *op, const char *key, int32_t value);
 LC_EXPORT int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value);

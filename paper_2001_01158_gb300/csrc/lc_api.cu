@@ -56,6 +56,7 @@ struct lc_op {
     // 256-thread CTAs: measured faster than the grid kernel below ~8K rows
     int local_cluster_rows = 8192;
     int local_single = 0;               // local solves: one grid reduction per iteration
+    int local_grid_cap = 0;             // local solves: blocks of the grid kernel (0 = one per SM)
     int local_cluster_threads = 256;
     int pcg_scaled = 1;      // 2D FP64: iterate on D^-1/2 A D^-1/2 (fewer FP64 instructions)
     int pcg_big = 1;         // 2D solves: one 768-thread block per SM (2 % faster at 2048^2, mixed 5 %)
@@ -342,10 +343,11 @@ int pcg_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_
         if (cl)
             LC_CUDA(ctx, lc::launch_pcg_csr_cluster(sub_csr(op), a, op->local_cluster_rows, op->local_cluster_threads,
                                                     ctrl, s));
+        const int cap = op->local_grid_cap > 0 ? op->local_grid_cap : ctx->sms;
         if (op->local_single && p->precision == LC_PREC_FP64)
-            LC_CUDA(ctx, lc::launch_pcg_csr_single(sub_csr(op), a, w, ctrl, ctx->sms, s, cl));
+            LC_CUDA(ctx, lc::launch_pcg_csr_single(sub_csr(op), a, w, ctrl, cap, s, cl));
         else
-            LC_CUDA(ctx, lc::launch_pcg_csr(sub_csr(op), a, w, ctrl, ctx->sms, s, cl));
+            LC_CUDA(ctx, lc::launch_pcg_csr(sub_csr(op), a, w, ctrl, cap, s, cl));
     } else if (op->kind == 0) {
         LC_CUDA(ctx, lc::launch_pcg_stencil(op->st, a, w, ctrl, op->pcg_grid_cap, s));
     } else {
@@ -694,6 +696,11 @@ int lc_op_set_tuning(lc_op *op, const char *key, int32_t value) {
         op->local_cluster_rows = value;
         return LC_OK;
     }
+    if (!strcmp(key, "local_grid_cap")) {
+        if (value < 0 || value > lc::kMaxGrid) return fail(op->ctx, LC_ERR_INVALID_ARG, "local_grid_cap out of range");
+        op->local_grid_cap = value;
+        return LC_OK;
+    }
     if (!strcmp(key, "pcg_pairdot")) {
         if (value < 0 || value > 1) return fail(op->ctx, LC_ERR_INVALID_ARG, "pcg_pairdot must be 0 or 1");
         op->pcg_pairdot = value;
@@ -734,6 +741,7 @@ int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value) {
     if (!strcmp(key, "pcg_wide")) { *value = op->pcg_wide; return LC_OK; }
     if (!strcmp(key, "pcg_big")) { *value = op->pcg_big; return LC_OK; }
     if (!strcmp(key, "pcg_pairdot")) { *value = op->pcg_pairdot; return LC_OK; }
+    if (!strcmp(key, "local_grid_cap")) { *value = op->local_grid_cap; return LC_OK; }
     return LC_ERR_INVALID_ARG;
 }
 

@@ -635,9 +635,9 @@ struct OpCsr {
     const int32_t *done = nullptr;   // set: the cluster kernel may have solved the system already
     static constexpr int kSmem = 1;
     static constexpr bool kTunable = true;
-    static constexpr bool kAnyBlock = false;   // rows strided by kPcgThreads
+    static constexpr bool kAnyBlock = true;    // rows dealt to warps: any block size
     static constexpr bool kScaled = false;
-    static constexpr bool kPairDots = false;
+    static constexpr bool kPairDots = sizeof(T) == 8;   // FP64: block sums on FP32 pairs
     __device__ bool skipped() const { return done && *done; }
     __device__ void resolve() { if (cs.n_dev) n = *cs.n_dev; }
     __device__ void prologue(const Vecs<T> &) const {}
@@ -646,10 +646,15 @@ struct OpCsr {
     __device__ void phaseB_block(const Vecs<T> &V, const T *p, T alpha, T (&acc)[2], int) const {
         phaseB_generic(*this, V, p, alpha, acc);
     }
+    // Rows dealt to warps across blocks: global warp g = warp * gridDim.x +
+    // block takes rows 32 g .. 32 g + 31 (then the same plus all threads), so
+    // a small system (an extracted subsystem) spreads over every SM instead
+    // of filling the first blocks.
     template <class F>
     __device__ __forceinline__ void each_cell(F f) const {
-        for (int64_t i = blockIdx.x * (int64_t)kPcgThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kPcgThreads)
-            f(i);
+        const int64_t g = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i = g * 32 + (threadIdx.x & 31); i < n; i += stride) f(i);
     }
     __device__ void setup_block(const Vecs<T> &V, T &bb, T &rz, T &rr) const {
         each_cell([&](int64_t i) {
@@ -668,8 +673,9 @@ struct OpCsr {
             }
         });
     }
+    // pair (FP64): the thread's p.q split into an FP32 pair scaled by 2^-2 ps
     __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *,
-                                 int, float * = nullptr) const {
+                                 int ps, float *pair = nullptr) const {
         each_cell([&](int64_t i) {
             T qi = T(0), pi = T(0);
             const int32_t e1 = cs.rp[i + 1];
@@ -684,6 +690,8 @@ struct OpCsr {
             V.q[i] = qi;
             pq = fmaT(pi, qi, pq);
         });
+        if constexpr (kPairDots)
+            if (pair) split_f2((double)pq, 2 * ps, pair[0], pair[1]);
     }
 };
 
@@ -708,9 +716,11 @@ __device__ bool residual_phase(const OP &op, const Vecs<T> &V, double *part, dou
 // Returns 1 converged, 0 iteration limit, -1 breakdown, -2 wait timed out.
 template <class OP, typename T>
 __device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, double *red, T *sm, Ctrl *ctrl,
-                             double rz, double stop, int maxit, int &it, int &pin, int nscale = 0) {
+                             double rz, double stop, int maxit, int &it, int &pin, int nscale = 0,
+                             double rr = 0.0) {
     bool first = true;
     double beta = 0.0;
+    double rrp = rr;   // last r.r total (unscaled ops with pair sums: the scale of the next)
     while (true) {
         T pq = T(0);
         const T *pold = pin ? V.p1 : V.p0;
@@ -747,12 +757,19 @@ __device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, doubl
             t[2] = t[1] <= stop ? 1.0 : 0.0;
             t[3] = t[0] / rz_;
         };
-        if constexpr (OP::kPairDots) {   // r.z split into a pair, the FP32 norm as it is
+        if constexpr (OP::kPairDots) {   // r.z split into a pair; the scaled ops' FP32 norm as it is
             float h2[2], l2[2] = {0.f, 0.f};
+            int e2[2] = {2 * ps, 0};
             split_f2((double)acc[0], 2 * ps, h2[0], l2[0]);
-            h2[1] = (float)acc[1];
-            const int e2[2] = {2 * ps, 0};
+            if constexpr (OP::kScaled) {
+                h2[1] = (float)acc[1];
+            } else {   // r.r in FP64, scaled by its own last total
+                const int pr = ((int)((__double_as_longlong(rrp) >> 52) & 0x7ff) - 1023) >> 1;
+                split_f2((double)acc[1], 2 * pr, h2[1], l2[1]);
+                e2[1] = 2 * pr;
+            }
             if (!grid_sums_pair<2, 2>(h2, l2, e2, 4, part, red, ctrl, o2, post2)) return -2;
+            rrp = o2[1];
         } else {
             if (!grid_sums<2, 2, T>(acc, 4, part, red, ctrl, o2, post2)) return -2;
         }
@@ -806,7 +823,7 @@ __global__ void __launch_bounds__(THREADS, MINB) pcg_kernel(OP op, Vecs<double> 
     }
     int it = 0, restarts = 0, pin = 0, result;
     while (true) {
-        result = cg_iterations(op, V, part, red, sm, ctrl, rz, stop_rec, maxit, it, pin, nscale);
+        result = cg_iterations(op, V, part, red, sm, ctrl, rz, stop_rec, maxit, it, pin, nscale, rr);
         if (result == -2) return;
         if (result != 1) break;
         // converged on the recurrence residual: confirm with the true one
@@ -1191,11 +1208,16 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
     return launch_ir(od, of, units, VD, VF, w.partials, a, ctrl, grid_hint, a.minblocks, s);
 }
 
-cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint, cudaStream_t s,
+cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a0, PcgWork &w, Ctrl *ctrl, int grid_hint, cudaStream_t s,
                            bool after_cluster) {
     // the row count may live on the device (extracted subsystem): the kernels
     // are sized for the capacity op.n and read the actual count themselves
     const int64_t units = (op.n + kPcgThreads - 1) / kPcgThreads;
+    // 768-thread blocks only for extracted subsystems: small systems gain
+    // from fewer blocks per reduction (2048^2 Alg 1 local solve: 13.6 ->
+    // 11.7 us per iteration), large gather-bound ones lose warps per SM
+    PcgArgs a = a0;
+    a.big = a0.big && op.n_dev != nullptr;
     csr_dinv_kernel<double><<<152 * 4, 256, 0, s>>>(op, op.av, w.dinv);
     note_launches(1);
     Vecs<double> VD = vecs64(a, w, w.dinv);

@@ -352,6 +352,32 @@ def test_local_then_global_matches_oracle(ctx, mode, n):
         assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
 
 
+@pytest.mark.parametrize("big,cap", [(1, 0), (0, 0), (1, 7), (0, 76), (1, 300)])
+def test_local_grid_kernel_launch_shapes(ctx, big, cap):
+    """The grid-wide local solve (cluster path off) with 768- or 256-thread
+    blocks and 7 to 300 blocks: rows dealt to warps across all blocks, pair
+    block sums; K, the local iteration count within one and the solution
+    within 1e-9 of the oracle's Alg 1."""
+    d = gen.cfg1_heat2d(seed=3, n=160, radius=30)
+    A = oracle.from_stencil(d["op"])
+    okw = dict(mark_mode=oracle.MARK_RESIDUAL, thr_mode=oracle.THR_REL_MAX, thr_param=1e-3,
+               exp_mode=oracle.EXP_DILATE, exp_rounds=2)
+    xr, sr, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], tol=1e-8, **okw)
+    prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8)
+    for gop in (stencil_op(ctx, d["op"]), csr_op(ctx, A)):
+        gop.set_tuning("local_cluster_rows", 0)
+        gop.set_tuning("pcg_big", big)
+        gop.set_tuning("local_grid_cap", cap)
+        assert gop.get_tuning("local_grid_cap") == cap
+        x = cu(d["x0"])
+        st = lcg.Stats()
+        lcg.solve_local_then_global(ctx, gop, cu(d["b"]), x, prm, st)
+        xg = x.cpu().numpy()
+        assert st.K == sr["K"] > 0 and abs(st.it_local - sr["it_local"]) <= 1
+        assert oracle.relres(A, d["b"], xg) <= 1e-8
+        assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
+
+
 @pytest.mark.parametrize("n,radius,beta,rounds", [(96, 10, 1e-3, 2), (256, 40, 1e-3, 3), (384, 90, 1e-4, 4),
                                                    (300, 150, 1e-6, 8)])
 @pytest.mark.parametrize("cluster,threads,single", [(1 << 30, 256, 0), (1 << 30, 1024, 0), (0, 256, 0), (0, 256, 1)])
