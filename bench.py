@@ -47,12 +47,13 @@ WORKLOAD = ("2D 2048x2048 5-point FP64 diffusion, 64 rectangles k in [1,1e3], Ga
 # (64 B); each iteration moves 120 B (phase A: z, p_old, D, Tx, Ty in, p, q
 # out; phase B: x, p, r, q, dinv in, x, r, z out).  The kernel iterates on
 # the symmetrically scaled system D^-1/2 A D^-1/2 (unit diagonal: no D, no
-# dinv, z = r) and moves 100 B per cell and iteration (phase A: r, p_old, Tx,
-# Ty in, p, q out; phase B: x, p, r, q in, fl32(D) for the FP32 stopping norm,
-# x, r out); the roofline reports the algorithmic figure.
+# dinv, z = r) and moves 92 B per cell and iteration (phase A: r, p_old, x,
+# Tx, Ty in, p, q, x out -- x += alpha p_old rides on the p_old load; phase
+# B: r, q in, fl32(D) for the FP32 stopping norm, r out); the roofline
+# reports the algorithmic figure.
 SETUP_BYTES = 64
 ITER_BYTES = 120
-IMPL_ITER_BYTES = 100
+IMPL_ITER_BYTES = 92
 # FP64 instructions the scaled kernel issues per cell: 8 per iteration (phase
 # A: 1 for p, 4 fma for q -- p.q runs on FP32 pairs; phase B: x, r, r.r),
 # 10 per residual pass
@@ -407,14 +408,14 @@ def run_gpu(args, rank, ws, local):
                    "l2": "inputs larger than L2 (operator + 20 resident systems + PCG vectors > 1 GB)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "pcg_kernel<Op2DW<double,4,true,true>> "
+                     "kernel": "pcg_kernel<Op2DW<double,4,true,true,true>> "
                                "(global Jacobi-PCG on D^-1/2 A D^-1/2, FP64 vectors)",
                      "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_cell_iter": ITER_BYTES,
                      "impl_bytes_per_cell_iter": IMPL_ITER_BYTES},
         "roofline_fp64_issue": {"bound": "alu", "achieved": dp_achieved, "peak": DP_PEAK_GOPS,
                                 "unit": "G FP64 instr/s", "frac": dp_achieved / DP_PEAK_GOPS,
                                 "alg_fp64_instr_per_cell_iter": DP_ITER,
-                                "note": "same kernel; ncu shows the FP64 pipe ~66% busy at ~61% DRAM throughput"},
+                                "note": "same kernel; ncu shows the FP64 pipe ~70% busy at ~56% DRAM throughput"},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": e2e_ms / total_sys, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * N,

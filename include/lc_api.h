@@ -435,6 +435,11 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  *       the FP64 pipe, which is the scarcer one on this GPU.  The vectors
  *       (x, r, p, q) stay FP64; alpha and beta differ from all-FP64 sums in
  *       rounding only.
+ *   "pcg_lazy_x"    0 or 1 (default 1): with pcg_pairdot, the update
+ *       x += alpha_k p_k of iteration k is applied in iteration k+1's first
+ *       phase, which loads p_k anyway (for p_k+1 = r + beta p_k), and after
+ *       the last iteration by one extra pass: 8 fewer bytes per cell and
+ *       iteration, the same operations in the same order (bit-identical x).
  *   "local_single"  0 or 1 (default 0): the FP64 local solve of
  *       lc_solve_local_then_global takes one grid-wide reduction per CG
  *       iteration (Chronopoulos-Gear arrangement: same iterates in exact

@@ -154,6 +154,7 @@ struct PcgArgs {
     int32_t wide;         // FP64 2D scaled: four cells per lane (tuning)
     int32_t big;          // 2D solves: one block of 768 threads per SM (tuning)
     int32_t pairdot;      // FP64 2D scaled wide: dot products and block sums on FP32 pairs (tuning)
+    int32_t lazyx;        // FP64 2D scaled wide pair: x += alpha p in the next phase A (tuning)
 };
 cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                cudaStream_t s);

@@ -207,7 +207,7 @@ __device__ __forceinline__ void phaseB_generic(const OP &op, const Vecs<T> &V, c
 // no separate vector), r.z = r^.r^; the stopping norm ||r||^2 = sum D r^^2
 // is accumulated in FP32 from approx_abs_f32 and confirmed in FP64 by the
 // true-residual pass.  c holds D (for that pass) and the scaled faces.
-template <typename T, int CPL, bool UNIT = false, bool F2D = false>
+template <typename T, int CPL, bool UNIT = false, bool F2D = false, bool DX = false>
 struct Op2DW {
     Stencil s;
     Coef<T> c;
@@ -220,6 +220,7 @@ struct Op2DW {
     static constexpr bool kAnyBlock = true;   // strips are per warp: any block size
     static constexpr bool kScaled = UNIT;
     static constexpr bool kPairDots = F2D;    // phase A's block sums on FP32 pairs
+    static constexpr bool kDeferX = DX;       // x += alpha p rides on the next phase A
     __device__ bool skipped() const { return false; }
     __device__ void resolve() {}
     __device__ int dn_shift() const { return UNIT ? (*dexp - 1023) >> 1 : 0; }
@@ -243,16 +244,18 @@ struct Op2DW {
             for (int y = y0; y < y1; ++y) {
                 const int64_t i = (int64_t)y * s.nx + xa;
                 T pv[CPL], qv[CPL], xv[CPL], rv[CPL];
-                vld<T, CPL>(p + i, pv);
+                if constexpr (!DX) {
+                    vld<T, CPL>(p + i, pv);
+                    vld<T, CPL>(V.x + i, xv);
+                }
                 vld<T, CPL>(V.q + i, qv);
-                vld<T, CPL>(V.x + i, xv);
                 vld<T, CPL>(V.r + i, rv);
                 if (UNIT) {
                     float dv[CPL];
                     vld<float, CPL>(d32 + i, dv);
 #pragma unroll
                     for (int k = 0; k < CPL; ++k) {
-                        xv[k] = fmaT(alpha, pv[k], xv[k]);
+                        if constexpr (!DX) xv[k] = fmaT(alpha, pv[k], xv[k]);
                         rv[k] = fmaT(-alpha, qv[k], rv[k]);
                         acc[0] = fmaT(rv[k], rv[k], acc[0]);
                         if constexpr (sizeof(T) == 8) {   // FP64: sum D r^^2 from the bits of r^
@@ -276,7 +279,7 @@ struct Op2DW {
                     }
                     vst<T, CPL>(V.z + i, zv);
                 }
-                vst<T, CPL>(V.x + i, xv);
+                if constexpr (!DX) vst<T, CPL>(V.x + i, xv);
                 vst<T, CPL>(V.r + i, rv);
             }
         });
@@ -341,21 +344,49 @@ struct Op2DW {
         const T zi = ldcg(V.z + i);
         return first ? zi : fmaT(beta, ldcg(pold + i), zi);
     }
+    // p = z + beta p_old; DX and own: also x += ax p_old (the last
+    // iteration's update, on the p_old this load brings anyway)
     __device__ __forceinline__ void pnew(const Vecs<T> &V, const T *pold, bool first, T beta, int64_t i,
-                                        T (&p)[CPL]) const {
+                                        T (&p)[CPL], T ax = T(0), bool own = false) const {
         vld_cg<T, CPL>(V.z + i, p);
         if (!first) {
             T o[CPL];
             vld_cg<T, CPL>(pold + i, o);
+            if constexpr (DX) {
+                if (own) {
+                    T xv[CPL];
+                    vld<T, CPL>(V.x + i, xv);
+#pragma unroll
+                    for (int k = 0; k < CPL; ++k) xv[k] = fmaT(ax, o[k], xv[k]);
+                    vst<T, CPL>(V.x + i, xv);
+                }
+            }
 #pragma unroll
             for (int k = 0; k < CPL; ++k) p[k] = fmaT(beta, o[k], p[k]);
         }
+    }
+    // DX: the update of x the last phase A would have carried
+    __device__ void flush_x(const Vecs<T> &V, const T *p, T alpha) const {
+        const int lane = threadIdx.x & 31;
+        each_segment([&](int x0, int y0, int y1) {
+            const int xa = x0 + CPL * lane;
+            if (xa >= s.nx) return;
+            for (int y = y0; y < y1; ++y) {
+                const int64_t i = (int64_t)y * s.nx + xa;
+                T pv[CPL], xv[CPL];
+                vld<T, CPL>(p + i, pv);
+                vld<T, CPL>(V.x + i, xv);
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) xv[k] = fmaT(alpha, pv[k], xv[k]);
+                vst<T, CPL>(V.x + i, xv);
+            }
+        });
     }
     __device__ __forceinline__ void load(const T *a, int64_t i, T (&v)[CPL]) const { vld<T, CPL>(a + i, v); }
     // F2D: p.q as an FP32 pair of the values scaled by 2^-nscale (a sum
     // scaled by 2^-2 nscale), into pair[0..2) if given, else added to pq
     __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *,
-                                 int nscale, float *pair = nullptr) const {
+                                 int nscale, float *pair = nullptr, T ax = T(0)) const {
         const int lane = threadIdx.x & 31;
         float fh = 0.f, fl = 0.f;
         each_segment([&](int x0, int y0, int y1) {
@@ -368,7 +399,7 @@ struct Op2DW {
             for (int k = 0; k < CPL; ++k) { pm[k] = T(0); pc[k] = T(0); tym[k] = T(0); }
             if (act) {
                 const int64_t i0 = (int64_t)y0 * s.nx + xa;
-                pnew(V, pold, first, beta, i0, pc);
+                pnew(V, pold, first, beta, i0, pc, ax, true);
                 if (y0 > 0) {
                     pnew(V, pold, first, beta, i0 - s.nx, pm);
                     load(c.Ty, i0 - s.nx, tym);
@@ -381,7 +412,10 @@ struct Op2DW {
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) { pn[k] = T(0); d[k] = T(0); tx[k] = T(0); typ[k] = T(0); }
                 if (act) {
-                    if (y + 1 < s.ny) { pnew(V, pold, first, beta, i + s.nx, pn); load(c.Ty, i, typ); }
+                    if (y + 1 < s.ny) {
+                        pnew(V, pold, first, beta, i + s.nx, pn, ax, y + 1 < y1);
+                        load(c.Ty, i, typ);
+                    }
                     if (!UNIT) load(c.D, i, d);
                     load(c.Tx, i, tx);
                     if (lane == 0 && x0 > 0) txw0 = c.Tx[i - 1];
@@ -452,6 +486,7 @@ struct Op3D {
     static constexpr bool kAnyBlock = false;   // one tile per block of kPcgThreads
     static constexpr bool kScaled = UNIT;
     static constexpr bool kPairDots = false;
+    static constexpr bool kDeferX = false;
     __device__ bool skipped() const { return false; }
     __device__ void resolve() {}
     __device__ int dn_shift() const { return UNIT ? (*dexp - 1023) >> 1 : 0; }
@@ -551,7 +586,7 @@ struct Op3D {
         return first ? zi : fmaT(beta, ldcg(pold + i), zi);
     }
     __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *sm,
-                                 int, float * = nullptr) const {
+                                 int, float * = nullptr, T = T(0)) const {
         const int64_t nu = units();
         for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) phaseA_unit(u, V, pold, pout, first, beta, pq, sm);
     }
@@ -638,6 +673,7 @@ struct OpCsr {
     static constexpr bool kAnyBlock = true;    // rows dealt to warps: any block size
     static constexpr bool kScaled = false;
     static constexpr bool kPairDots = sizeof(T) == 8;   // FP64: block sums on FP32 pairs
+    static constexpr bool kDeferX = false;
     __device__ bool skipped() const { return done && *done; }
     __device__ void resolve() { if (cs.n_dev) n = *cs.n_dev; }
     __device__ void prologue(const Vecs<T> &) const {}
@@ -646,15 +682,17 @@ struct OpCsr {
     __device__ void phaseB_block(const Vecs<T> &V, const T *p, T alpha, T (&acc)[2], int) const {
         phaseB_generic(*this, V, p, alpha, acc);
     }
-    // Rows dealt to warps across blocks: global warp g = warp * gridDim.x +
-    // block takes rows 32 g .. 32 g + 31 (then the same plus all threads), so
-    // a small system (an extracted subsystem) spreads over every SM instead
-    // of filling the first blocks.
+    // Extracted subsystems (row count on the device): rows dealt to warps
+    // across blocks -- global warp g = warp * gridDim.x + block takes rows
+    // 32 g .. 32 g + 31, then the same plus all threads -- so a small system
+    // spreads over every SM instead of filling the first blocks.  Other
+    // systems: consecutive rows per block.
     template <class F>
     __device__ __forceinline__ void each_cell(F f) const {
-        const int64_t g = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t i = g * 32 + (threadIdx.x & 31); i < n; i += stride) f(i);
+        const int64_t i0 = cs.n_dev ? ((int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31)
+                                    : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        for (int64_t i = i0; i < n; i += stride) f(i);
     }
     __device__ void setup_block(const Vecs<T> &V, T &bb, T &rz, T &rr) const {
         each_cell([&](int64_t i) {
@@ -675,7 +713,7 @@ struct OpCsr {
     }
     // pair (FP64): the thread's p.q split into an FP32 pair scaled by 2^-2 ps
     __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *,
-                                 int ps, float *pair = nullptr) const {
+                                 int ps, float *pair = nullptr, T = T(0)) const {
         each_cell([&](int64_t i) {
             T qi = T(0), pi = T(0);
             const int32_t e1 = cs.rp[i + 1];
@@ -721,6 +759,7 @@ __device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, doubl
     bool first = true;
     double beta = 0.0;
     double rrp = rr;   // last r.r total (unscaled ops with pair sums: the scale of the next)
+    double alpha_x = 0.0;   // kDeferX: the alpha whose x update rides on the next phase A
     while (true) {
         T pq = T(0);
         const T *pold = pin ? V.p1 : V.p0;
@@ -737,7 +776,7 @@ __device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, doubl
         const int ps = ((int)((__double_as_longlong(rz) >> 52) & 0x7ff) - 1023) >> 1;
         if constexpr (OP::kPairDots) {
             float pr[2] = {0.f, 0.f};
-            op.phaseA_block(V, pold, pout, first, (T)beta, pq, sm, ps, pr);
+            op.phaseA_block(V, pold, pout, first, (T)beta, pq, sm, ps, pr, (T)alpha_x);
             const float h1[1] = {pr[0]}, l1[1] = {pr[1]};
             const int e1[1] = {2 * ps};
             if (!grid_sums_pair<1, 2>(h1, l1, e1, 3, part, red, ctrl, o1, post1)) return -2;
@@ -774,11 +813,18 @@ __device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, doubl
             if (!grid_sums<2, 2, T>(acc, 4, part, red, ctrl, o2, post2)) return -2;
         }
         ++it;
-        if (flag_set(o2[2])) return 1;
-        if (it >= maxit) return 0;
+        const bool conv = flag_set(o2[2]);
+        if (conv || it >= maxit) {
+            if constexpr (OP::kDeferX) {   // the pending x += alpha p, before anyone reads x
+                op.flush_x(V, p, alpha);
+                if (!grid_sync(ctrl, gridDim.x)) return -2;
+            }
+            return conv ? 1 : 0;
+        }
         beta = o2[3];
         rz = o2[0];
         first = false;
+        alpha_x = (double)alpha;
     }
 }
 
@@ -1167,6 +1213,11 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
             VS.z = w.r;
             VS.dinv = nullptr;
             VS.xu = a.x;
+            if (a.pairdot && a.lazyx) {   // and the x update riding on the next phase A
+                Op2DW<double, 4, true, true, true> o3{op, Coef<double>{op.D, op.Txh, op.Tyh, nullptr}, op.sc,
+                                                      op.sq, op.dn32, op.dexp};
+                return launch_pcg(o3, units4, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+            }
             if (a.pairdot) {   // dot products and block sums on FP32 pairs
                 Op2DW<double, 4, true, true> o2{op, Coef<double>{op.D, op.Txh, op.Tyh, nullptr}, op.sc, op.sq,
                                                 op.dn32, op.dexp};

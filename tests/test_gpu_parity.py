@@ -182,15 +182,17 @@ SCALED_SHAPES = [(64, 16), (130, 37), (300, 260), (2, 50)]
 
 
 @pytest.mark.parametrize("nx,ny", SCALED_SHAPES + [(128, 40), (4, 9)])
-@pytest.mark.parametrize("scaled,wide,big,pairdot", [(0, 0, 1, 0), (1, 0, 1, 0), (1, 1, 1, 0), (0, 0, 0, 0),
-                                                      (1, 1, 0, 0), (1, 1, 1, 1), (1, 1, 0, 1)])
-def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide, big, pairdot):
+@pytest.mark.parametrize("scaled,wide,big,pairdot,lazy", [(0, 0, 1, 0, 0), (1, 0, 1, 0, 0), (1, 1, 1, 0, 0),
+                                                           (0, 0, 0, 0, 0), (1, 1, 0, 0, 0), (1, 1, 1, 1, 0),
+                                                           (1, 1, 0, 1, 0), (1, 1, 1, 1, 1), (1, 1, 0, 1, 1)])
+def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide, big, pairdot, lazy):
     """The 2-D FP64 solve on D^-1/2 A D^-1/2 (pcg_scaled = 1) and on A with the
     explicit Jacobi preconditioner (0) are the same Jacobi-PCG iteration in
     exact arithmetic: both match the oracle's iteration count within one and
     its solution within 1e-9, with 768-thread blocks (pcg_big) or 256, and
     with the dot products and block sums on FP32 pairs (pcg_pairdot) or in
-    FP64."""
+    FP64, with x += alpha p carried by the next iteration's first phase
+    (pcg_lazy_x) or not."""
     op = gen.random_stencil_2d(nx + 7 * ny, nx, ny)
     A, b, x0 = rhs_and_x0(op, 13)
     tol = 1e-9
@@ -201,8 +203,10 @@ def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide, big, pa
     gop.set_tuning("pcg_wide", wide)
     gop.set_tuning("pcg_big", big)
     gop.set_tuning("pcg_pairdot", pairdot)
+    gop.set_tuning("pcg_lazy_x", lazy)
     assert gop.get_tuning("pcg_scaled") == scaled and gop.get_tuning("pcg_wide") == wide
     assert gop.get_tuning("pcg_big") == big and gop.get_tuning("pcg_pairdot") == pairdot
+    assert gop.get_tuning("pcg_lazy_x") == lazy
     x = cu(x0)
     stats = lcg.Stats()
     lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(tol, 100000, lcg.PREC_FP64, 0.0, 0), stats)
@@ -213,8 +217,8 @@ def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide, big, pa
     assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
 
 
-@pytest.mark.parametrize("pairdot", [0, 1])
-def test_pcg_power_of_two_scale_invariance(ctx, pairdot):
+@pytest.mark.parametrize("pairdot,lazy", [(0, 0), (1, 0), (1, 1)])
+def test_pcg_power_of_two_scale_invariance(ctx, pairdot, lazy):
     """Scaling b and x0 by 2^k scales every FP64 quantity of the scaled 2-D
     solve exactly, and the FP32 stopping norm and the FP32-pair dot products
     and block sums rescale with it (their exponent shifts follow b.b and
@@ -224,6 +228,7 @@ def test_pcg_power_of_two_scale_invariance(ctx, pairdot):
     A, b, x0 = rhs_and_x0(op, 29)
     gop = stencil_op(ctx, op)
     gop.set_tuning("pcg_pairdot", pairdot)
+    gop.set_tuning("pcg_lazy_x", lazy)
     sp = lcg.SolveParams(1e-10, 100000, lcg.PREC_FP64, 0.0, 0)
     runs = {}
     for k in (0, -400, 400):
@@ -289,12 +294,13 @@ def test_pcg_scaled_extreme_magnitudes(ctx, cscale, bscale):
     assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
 
 
-@pytest.mark.parametrize("nx,pairdot", [(33, 0), (36, 0), (36, 1)])
-def test_pcg_edge_cases(ctx, nx, pairdot):
+@pytest.mark.parametrize("nx,pairdot,lazy", [(33, 0, 0), (36, 0, 0), (36, 1, 0), (36, 1, 1)])
+def test_pcg_edge_cases(ctx, nx, pairdot, lazy):
     op = gen.random_stencil_2d(1, nx, 21)
     A = oracle.from_stencil(op)
     gop = stencil_op(ctx, op)
     gop.set_tuning("pcg_pairdot", pairdot)
+    gop.set_tuning("pcg_lazy_x", lazy)
     sp = lcg.SolveParams(1e-8, 100000, lcg.PREC_FP64, 0.0, 0)
     # b = 0 gives x = 0
     x = cu(np.ones(op.n))
@@ -314,6 +320,10 @@ def test_pcg_edge_cases(ctx, nx, pairdot):
                        allow_not_converged=True)
     assert rc == lcg.LC_ERR_NOT_CONVERGED and st.it_global == 3
     assert st.relres_final == pytest.approx(oracle.relres(A, b, x.cpu().numpy()), rel=1e-6)
+    # ... and x is the third iterate (with pcg_lazy_x, the last update is flushed)
+    x3, _, it3, _ = oracle.pcg(A, b, np.zeros(op.n), tol=1e-14, maxit=3)
+    assert it3 == 3
+    assert np.linalg.norm(x.cpu().numpy() - x3) <= 1e-12 * np.linalg.norm(x3)
     # a negative definite operator breaks down
     neg = oracle.csr(A.rowptr, A.col, -A.val)
     with pytest.raises(lcg.LcError):
