@@ -427,15 +427,15 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  *       and barrier arrivals per grid-wide reduction); pcg_minblocks then has
  *       no effect on them.  3-D solves and solves with a CSR operator's own
  *       matrix ignore it.
- *   "pcg_pairdot"   0 or 1 (default 1): the scaled 2-D FP64 solve with four
- *       cells per lane takes its dot products (p.q, r^.r^) and the block
- *       sums of its grid reductions on pairs of FP32 numbers (hi + lo, 47
+ *   "pcg_pairdot"   0 or 1 (default 1): the scaled 2-D (four cells per lane)
+ *       and 3-D FP64 solves take their dot product p.q and the block sums
+ *       of their grid reductions on pairs of FP32 numbers (hi + lo, 47
  *       significand bits, built from the FP64 bits with integer
  *       instructions; error-free FP32 products and two-sums) instead of on
  *       the FP64 pipe, which is the scarcer one on this GPU.  The vectors
  *       (x, r, p, q) stay FP64; alpha and beta differ from all-FP64 sums in
  *       rounding only.
- *   "pcg_lazy_x"    0 or 1 (default 1): with pcg_pairdot, the update
+ *   "pcg_lazy_x"    0 or 1 (default 1): with pcg_pairdot (2-D and 3-D), the update
  *       x += alpha_k p_k of iteration k is applied in iteration k+1's first
  *       phase, which loads p_k anyway (for p_k+1 = r + beta p_k), and after
  *       the last iteration by one extra pass: 8 fewer bytes per cell and

@@ -173,10 +173,12 @@ __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a
 template <class OP, typename T>
 __device__ __forceinline__ void phaseB_generic(const OP &op, const Vecs<T> &V, const T *p, T alpha, T (&acc)[2]) {
     op.each_cell([&](int64_t i) {
-        const T pi = p[i], qi = V.q[i];
-        V.x[i] = fmaT(alpha, pi, V.x[i]);
-        const T ri = fmaT(-alpha, qi, V.r[i]);
-        const T zi = V.dinv[i] * ri;
+        // every load before the first store (which the compiler cannot prove
+        // apart from them)
+        const T pi = p[i], qi = V.q[i], xi = V.x[i], r0 = V.r[i], di = V.dinv[i];
+        V.x[i] = fmaT(alpha, pi, xi);
+        const T ri = fmaT(-alpha, qi, r0);
+        const T zi = di * ri;
         V.r[i] = ri;
         V.z[i] = zi;
         acc[0] = fmaT(ri, zi, acc[0]);
@@ -221,6 +223,8 @@ struct Op2DW {
     static constexpr bool kScaled = UNIT;
     static constexpr bool kPairDots = F2D;    // phase A's block sums on FP32 pairs
     static constexpr bool kDeferX = DX;       // x += alpha p rides on the next phase A
+    static_assert(!DX || UNIT, "the deferred x update is built for the scaled system");
+    static_assert(!F2D || (UNIT && sizeof(T) == 8), "pair dot products are built for the scaled FP64 solve");
     __device__ bool skipped() const { return false; }
     __device__ void resolve() {}
     __device__ int dn_shift() const { return UNIT ? (*dexp - 1023) >> 1 : 0; }
@@ -474,7 +478,7 @@ struct Op2DW {
 // UNIT = the symmetrically scaled system, as for Op2DW: unit diagonal, z = r^,
 // stopping norm sum D r^^2 in FP32, c holding D (residual passes) and the
 // scaled faces.
-template <typename T, bool UNIT = false>
+template <typename T, bool UNIT = false, bool F2D = false, bool DX = false>
 struct Op3D {
     Stencil s;
     Coef<T> c;
@@ -485,8 +489,10 @@ struct Op3D {
     static constexpr bool kTunable = true;
     static constexpr bool kAnyBlock = false;   // one tile per block of kPcgThreads
     static constexpr bool kScaled = UNIT;
-    static constexpr bool kPairDots = false;
-    static constexpr bool kDeferX = false;
+    static constexpr bool kPairDots = F2D;     // p.q and the block sums on FP32 pairs (as Op2DW)
+    static constexpr bool kDeferX = DX;        // x += alpha p rides on the next phase A (as Op2DW)
+    static_assert(!DX || UNIT, "the deferred x update is built for the scaled system");
+    static_assert(!F2D || (UNIT && sizeof(T) == 8), "pair dot products are built for the scaled FP64 solve");
     __device__ bool skipped() const { return false; }
     __device__ void resolve() {}
     __device__ int dn_shift() const { return UNIT ? (*dexp - 1023) >> 1 : 0; }
@@ -506,16 +512,17 @@ struct Op3D {
         }
         float rrf = 0.f;
         each_cell([&](int64_t i) {
-            const T xi = fmaT(alpha, p[i], V.x[i]);
-            const T ri = fmaT(-alpha, V.q[i], V.r[i]);
-            V.x[i] = xi;
+            const T qi = V.q[i], r0 = V.r[i];   // loads before the stores
+            const float di = d32[i];
+            if constexpr (!DX) V.x[i] = fmaT(alpha, p[i], V.x[i]);
+            const T ri = fmaT(-alpha, qi, r0);
             V.r[i] = ri;
             acc[0] = fmaT(ri, ri, acc[0]);
             if constexpr (sizeof(T) == 8) {
                 const float f = approx_abs_f32((double)ri, nscale);
-                rrf = fmaf(d32[i] * f, f, rrf);
+                rrf = fmaf(di * f, f, rrf);
             } else {
-                const float t = d32[i] * ri;
+                const float t = di * ri;
                 rrf = fmaf(t, t, rrf);
             }
         });
@@ -585,10 +592,36 @@ struct Op3D {
         const T zi = ldcg(V.z + i);
         return first ? zi : fmaT(beta, ldcg(pold + i), zi);
     }
+    // p at an own cell; DX: also x += ax p_old there (the last iteration's update)
+    __device__ __forceinline__ T pat_own(const Vecs<T> &V, const T *pold, bool first, T beta, T ax, int gx, int gy,
+                                         int z) const {
+        if constexpr (DX) {
+            if (z < 0 || z >= s.nz || gx < 0 || gx >= s.nx || gy < 0 || gy >= s.ny) return T(0);
+            const int64_t i = gx + (int64_t)s.nx * gy + (int64_t)s.nx * s.ny * z;
+            const T zi = ldcg(V.z + i);
+            if (first) return zi;
+            const T po = ldcg(pold + i);
+            V.x[i] = fmaT(ax, po, V.x[i]);
+            return fmaT(beta, po, zi);
+        } else {
+            return pat(V, pold, first, beta, gx, gy, z);
+        }
+    }
+    __device__ void flush_x(const Vecs<T> &V, const T *p, T alpha) const {
+        each_cell([&](int64_t i) { V.x[i] = fmaT(alpha, p[i], V.x[i]); });
+    }
+    // F2D: p.q as an FP32 pair of the values scaled by 2^-ps, into pair[0..2)
+    // if given, else added to pq
     __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *sm,
-                                 int, float * = nullptr, T = T(0)) const {
+                                 int ps, float *pair = nullptr, T ax = T(0)) const {
         const int64_t nu = units();
-        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) phaseA_unit(u, V, pold, pout, first, beta, pq, sm);
+        float fh = 0.f, fl = 0.f;
+        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x)
+            phaseA_unit(u, V, pold, pout, first, beta, pq, sm, ps, fh, fl, ax);
+        if constexpr (F2D) {
+            if (pair) { pair[0] = fh; pair[1] = fl; }
+            else pq += f2_value(fh, fl, ps);
+        }
     }
     // 2.5D march: thread (lx, ly) owns column (x, y) and keeps p at z-1, z,
     // z+1 in registers; the first kHalo threads own one cell of the plane's
@@ -605,7 +638,7 @@ struct Op3D {
         else { hx = kEx - 1; hy = 1 + (k - 2 * kEx - kTileY); }
     }
     __device__ void phaseA_unit(int64_t u, const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq,
-                                T *sm) const {
+                                T *sm, int ps, float &fh, float &fl, T ax) const {
         int x0, y0, z0;
         origin(u, x0, y0, z0);
         const int lx = threadIdx.x % kTileX, ly = threadIdx.x / kTileX;
@@ -619,14 +652,14 @@ struct Op3D {
         const int ghx = x0 - 1 + hx, ghy = y0 - 1 + hy;
         const int cc = (ly + 1) * kEx + (lx + 1);
         T pm = T(0), pc = T(0), ph = T(0);
-        if (act) { pm = pat(V, pold, first, beta, xx, yy, z0 - 1); pc = pat(V, pold, first, beta, xx, yy, z0); }
+        if (act) pm = pat(V, pold, first, beta, xx, yy, z0 - 1);
         if (has_h) ph = pat(V, pold, first, beta, ghx, ghy, z0);
+        if (act) pc = pat_own(V, pold, first, beta, ax, xx, yy, z0);   // last: its x store holds later loads back
         for (int z = z0; z < z1; ++z) {
             const int64_t i = xx + (int64_t)s.nx * yy + sxy * z;
             // loads of plane z+1 and coefficients of plane z, before the barrier
             T pn = T(0), phn = T(0), d = T(0), tzm = T(0), tym = T(0), txm = T(0), txp = T(0), typ = T(0), tzp = T(0);
             if (act) {
-                pn = pat(V, pold, first, beta, xx, yy, z + 1);
                 if (!UNIT) d = c.D[i];
                 if (z > 0) tzm = c.Tz[i - sxy];
                 if (yy > 0) tym = c.Ty[i - s.nx];
@@ -636,6 +669,9 @@ struct Op3D {
                 if (z + 1 < s.nz) tzp = c.Tz[i];
             }
             if (has_h) phn = pat(V, pold, first, beta, ghx, ghy, z + 1);
+            if (act)   // last: with DX its x store would hold back the loads above
+                pn = z + 1 < z1 ? pat_own(V, pold, first, beta, ax, xx, yy, z + 1)
+                                : pat(V, pold, first, beta, xx, yy, z + 1);
             T *pl = sm + (z & 1) * kPls;
             pl[cc] = pc;
             if (has_h) pl[hy * kEx + hx] = ph;
@@ -650,7 +686,14 @@ struct Op3D {
                 qi = fmaT(-tzp, pn, qi);
                 pout[i] = pc;
                 V.q[i] = qi;
-                pq = fmaT(pc, qi, pq);
+                if constexpr (F2D) {
+                    float ph_, pl_, qh_, ql_;
+                    split_f2((double)pc, ps, ph_, pl_);
+                    split_f2((double)qi, ps, qh_, ql_);
+                    f2_add_prod(ph_, pl_, qh_, ql_, fh, fl);
+                } else {
+                    pq = fmaT(pc, qi, pq);
+                }
             }
             pm = pc;
             pc = pn;
@@ -781,7 +824,7 @@ __device__ int cg_iterations(const OP &op, const Vecs<T> &V, double *part, doubl
             const int e1[1] = {2 * ps};
             if (!grid_sums_pair<1, 2>(h1, l1, e1, 3, part, red, ctrl, o1, post1)) return -2;
         } else {
-            op.phaseA_block(V, pold, pout, first, (T)beta, pq, sm, nscale);
+            op.phaseA_block(V, pold, pout, first, (T)beta, pq, sm, nscale, nullptr, (T)alpha_x);
             T a1[1] = {pq};
             if (!grid_sums<1, 2, T>(a1, 3, part, red, ctrl, o1, post1)) return -2;
         }
@@ -1181,6 +1224,14 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
             VS.z = w.r;
             VS.dinv = nullptr;
             VS.xu = a.x;
+            if (a.pairdot && a.lazyx) {
+                Op3D<double, true, true, true> o3{op, os.c, op.sc, op.sq, op.dn32, op.dexp};
+                return launch_pcg(o3, units, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+            }
+            if (a.pairdot) {
+                Op3D<double, true, true> o2{op, os.c, op.sc, op.sq, op.dn32, op.dexp};
+                return launch_pcg(o2, units, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+            }
             return launch_pcg(os, units, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
         }
         if (!mixed) return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);

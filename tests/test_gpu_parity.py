@@ -217,14 +217,15 @@ def test_pcg_scaled_and_unscaled_match_oracle(ctx, nx, ny, scaled, wide, big, pa
     assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("pairdot,lazy", [(0, 0), (1, 0), (1, 1)])
-def test_pcg_power_of_two_scale_invariance(ctx, pairdot, lazy):
+def test_pcg_power_of_two_scale_invariance(ctx, dim, pairdot, lazy):
     """Scaling b and x0 by 2^k scales every FP64 quantity of the scaled 2-D
-    solve exactly, and the FP32 stopping norm and the FP32-pair dot products
+    and 3-D solves exactly, and the FP32 stopping norm and the FP32-pair dot products
     and block sums rescale with it (their exponent shifts follow b.b and
     r.z): the solution is 2^k times the unscaled one bit for bit, with the
     same iteration count, from 2^-400 to 2^400."""
-    op = gen.random_stencil_2d(5, 64, 40)
+    op = gen.random_stencil_2d(5, 64, 40) if dim == 2 else gen.random_stencil_3d(5, 24, 12, 10)
     A, b, x0 = rhs_and_x0(op, 29)
     gop = stencil_op(ctx, op)
     gop.set_tuning("pcg_pairdot", pairdot)
@@ -244,8 +245,8 @@ def test_pcg_power_of_two_scale_invariance(ctx, pairdot, lazy):
 
 
 @pytest.mark.parametrize("shape", [(16, 8, 8), (17, 9, 10), (33, 20, 7), (40, 1, 3), (5, 4, 3)])
-@pytest.mark.parametrize("scaled", [0, 1])
-def test_pcg_3d_scaled_and_unscaled_match_oracle(ctx, shape, scaled):
+@pytest.mark.parametrize("scaled,pairdot,lazy", [(0, 1, 1), (1, 0, 0), (1, 1, 0), (1, 1, 1)])
+def test_pcg_3d_scaled_and_unscaled_match_oracle(ctx, shape, scaled, pairdot, lazy):
     """The 3D FP64 solve on D^-1/2 A D^-1/2 and on A with the explicit Jacobi
     preconditioner both match the oracle's Jacobi-PCG (iterations within one,
     solution within 1e-9); so does the 3D mixed-precision solve on the scaled
@@ -256,6 +257,8 @@ def test_pcg_3d_scaled_and_unscaled_match_oracle(ctx, shape, scaled):
     xr, st, it_ref, _ = oracle.pcg(A, b, x0, tol=tol)
     gop = stencil_op(ctx, op)
     gop.set_tuning("pcg_scaled", scaled)
+    gop.set_tuning("pcg_pairdot", pairdot)
+    gop.set_tuning("pcg_lazy_x", lazy)
     x = cu(x0)
     stats = lcg.Stats()
     lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(tol, 100000, lcg.PREC_FP64, 0.0, 0), stats)
