@@ -415,7 +415,7 @@ def run_gpu(args, rank, ws, local):
         "roofline_fp64_issue": {"bound": "alu", "achieved": dp_achieved, "peak": DP_PEAK_GOPS,
                                 "unit": "G FP64 instr/s", "frac": dp_achieved / DP_PEAK_GOPS,
                                 "alg_fp64_instr_per_cell_iter": DP_ITER,
-                                "note": "same kernel; ncu shows the FP64 pipe ~70% busy at ~56% DRAM throughput"},
+                                "note": "same kernel; ncu shows the FP64 pipe ~71% busy at ~57% DRAM throughput"},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": e2e_ms / total_sys, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * N,

@@ -198,13 +198,21 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 // atomic per block and arrival, no generation word, no reset between
 // barriers.  A block never sees the counter past its own target before it
 // arrives (no block passes barrier k before all arrived).
+// The arrival is a release add at GPU scope (it publishes the block's writes,
+// ordered before it by the block barrier), the wait an acquire load: no
+// separate fences.
+__device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long long *p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned int nblocks,
                                           long long limit_cycles = kBarrierTimeoutCycles) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();   // the block's writes (ordered by the barrier above) before the arrival
-        const unsigned long long old = atomicAdd(&ctrl->bar_count, 1ull);
+        const unsigned long long old = atom_add_release_u64(&ctrl->bar_count, 1ull);
         const unsigned long long target = (old / nblocks + 1) * nblocks;
         int ok = 1;
         if (old + 1 < target) {
@@ -213,7 +221,6 @@ __device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned int nblocks,
                 if (clock64() - t0 > limit_cycles) { ok = 0; break; }
             }
         }
-        __threadfence();
         if (!ok) atomicCAS(&ctrl->status, LC_OK, LC_ERR_TIMEOUT);
         s_ok = ok;
     }
