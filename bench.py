@@ -173,10 +173,11 @@ def measured_peaks():
 
 
 def source_digest() -> str:
-    """Digest of the global PCG kernel's sources (the kernel file and the
-    device header with its descriptors, barrier and reductions)."""
+    """Digest of the global PCG kernel's sources (the kernels, the 2D
+    launcher and the device header with its descriptors, barrier and
+    reductions)."""
     h = hashlib.sha256()
-    for name in ("lc_pcg.cu", "lc_device.cuh"):
+    for name in ("lc_pcg_impl.cuh", "lc_pcg.cu", "lc_device.cuh"):
         with open(os.path.join(ROOT, "paper_2001_01158_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -1,7 +1,7 @@
 // lc_api.cu -- host implementation of the C ABI declared in include/lc_api.h.
 //
 // Argument checking, workspace ownership and the stream-ordered sequencing
-// of the kernels of lc_mark.cu, lc_extract.cu and lc_pcg.cu.  No entry point
+// of the kernels of lc_mark.cu, lc_extract.cu and lc_pcg*.cu.  No entry point
 // of the hot path allocates, synchronises or copies to the host unless it
 // is asked for host statistics.
 #include <cmath>

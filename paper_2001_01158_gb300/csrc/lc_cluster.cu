@@ -20,7 +20,7 @@
 //            partials r.z and r.r                          (barrier)
 // Each CTA sums the C slot rows in rank order, so every CTA takes the same
 // decisions.  Iteration, stopping test, true-residual confirmation and
-// restarts follow the grid kernel in lc_pcg.cu (same Ctrl fields).  p is
+// restarts follow the grid kernel of lc_pcg_impl.cuh (same Ctrl fields).  p is
 // computed once per row (the grid kernel recomputes it per entry to save a
 // barrier): FP64 throughput, not latency, bounds a solve on 16 SMs.
 //

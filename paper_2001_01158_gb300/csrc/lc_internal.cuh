@@ -131,7 +131,7 @@ cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *out,
 cudaError_t launch_barrier_timeout_selftest(Ctrl *ctrl, int *passed, int blocks, long long limit_cycles,
                                             cudaStream_t s);
 
-// Krylov (lc_pcg.cu)
+// Krylov (lc_pcg_impl.cuh kernels; lc_pcg.cu, lc_pcg_mixed.cu, lc_pcg3d.cu, lc_pcgcsr.cu launches)
 struct PcgWork {
     double *r, *z, *p0, *p1, *q;     // capacity n
     double *e0, *e1;                 // capacity n (single-reduction CSR solve)
@@ -158,6 +158,11 @@ struct PcgArgs {
 };
 cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                cudaStream_t s);
+// the parts of launch_pcg_stencil in their own translation units
+cudaError_t launch_pcg_stencil3d(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
+                                 cudaStream_t s);
+cudaError_t launch_ir_stencil2d(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
+                                cudaStream_t s);
 // after_cluster: launched right after launch_pcg_csr_cluster on the same
 // ctrl -- no reset of ctrl, and the kernel returns at once if ctrl->done
 cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,

@@ -21,7 +21,7 @@
 // r, s and w are double-buffered: neighbours read this iteration's copy while
 // the owner writes the next one; p and x are touched by their owner only.
 // Stopping test, true-residual confirmation and restarts are those of the
-// two-reduction kernel (lc_pcg.cu), with the same Ctrl fields.
+// two-reduction kernel (lc_pcg_impl.cuh), with the same Ctrl fields.
 #include "lc_internal.cuh"
 
 namespace lc {
