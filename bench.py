@@ -374,27 +374,49 @@ def run_gpu(args, rank, ws, local):
     t_g = sum(s["t_global_ms"] for s in per_glob) * 1e-3
     gbs_global = byts_g / t_g / 1e9 if t_g > 0 else 0.0
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: every system's b and x0
+    # come from pinned host memory and its solution goes back to it.  The
+    # copies run on their own stream, overlapped with the neighbouring
+    # systems' solves (inputs double-buffered on the device), as a serving
+    # loop would run them; each step's copies and solve are all inside the
+    # timed region.
     b_h = [bs[j].cpu().pin_memory() for j in range(nsys)]
     x_h = [xs[j].cpu().pin_memory() for j in range(nsys)]
-    out_h = torch.empty(N, dtype=torch.float64).pin_memory()
-    b_d = torch.empty(N, dtype=torch.float64, device=dev)
+    out_h = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(2)]
+    b_d = [torch.empty(N, dtype=torch.float64, device=dev) for _ in range(2)]
+    x_d = [torch.empty(N, dtype=torch.float64, device=dev) for _ in range(2)]
+    cstream = torch.cuda.Stream(dev)
+    h2d_done = [torch.cuda.Event() for _ in range(2)]
+    solved = [torch.cuda.Event() for _ in range(2)]
     st = lcg.Stats()
 
-    def e2e_step(k):
-        j = k % nsys
-        b_d.copy_(b_h[j], non_blocking=True)
-        work.copy_(x_h[j], non_blocking=True)
-        lcg.solve_local_then_global(ctx, gop, b_d, work, prm_res, st)
-        out_h.copy_(work, non_blocking=True)
+    def h2d(k):
+        j, s = k % nsys, k % 2
+        with torch.cuda.stream(cstream):
+            b_d[s].copy_(b_h[j], non_blocking=True)
+            x_d[s].copy_(x_h[j], non_blocking=True)
+            h2d_done[s].record(cstream)
+
+    def e2e_run(k0, steps):
+        # buffer s = k % 2 is rewritten by h2d(k + 2), issued after the
+        # copy-back of step k on the same (in-order) copy stream
+        h2d(k0)
+        for k in range(k0, k0 + steps):
+            s = k % 2
+            if k + 1 < k0 + steps:
+                h2d(k + 1)   # the next system's inputs while this one solves
+            stream.wait_event(h2d_done[s])
+            lcg.solve_local_then_global(ctx, gop, b_d[s], x_d[s], prm_res, st, stream=stream)
+            solved[s].record(stream)
+            with torch.cuda.stream(cstream):
+                cstream.wait_event(solved[s])
+                out_h[s].copy_(x_d[s], non_blocking=True)
         torch.cuda.synchronize(dev)
 
-    for k in range(args.warmup):
-        e2e_step(k)
+    e2e_run(0, args.warmup)
     barrier(ws)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        e2e_step(args.warmup + k)
+    e2e_run(args.warmup, args.steps)
     barrier(ws)
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, ws, dev)
 
