@@ -208,17 +208,21 @@ __device__ __forceinline__ void phaseB_generic(const OP &op, const Vecs<T> &V, c
 
 // 2D, warp-independent: the grid is cut into column strips of 32*CPL cells,
 // one lane owning CPL adjacent columns (CPL = 2 when rows start aligned, so
-// loads/stores are pairs).  The strip-major list of (strip, row) items is
-// split evenly over all warps of the grid and every warp marches down its own
-// rows: p of the rows above and below in registers, x-neighbours through warp
-// shuffles, the one-cell halo at either end of the strip recomputed by lanes
-// 0 and 31.  No block barrier, no shared memory.
+// loads/stores are pairs; 4 in the scaled FP64 solve when nx is a multiple
+// of 4).  The strip-major list of (strip, row) items is split evenly over
+// all warps of the grid and every warp marches down its own rows: p of the
+// rows above and below in registers, x-neighbours through warp shuffles, the
+// one-cell halo at either end of the strip recomputed by lanes 0 and 31.  No
+// block barrier, no shared memory.
 //
 // UNIT = the symmetrically scaled system S A S x^ = S b, S = D^-1/2, x = S x^
 // (Jacobi-PCG on A in exact arithmetic): unit diagonal, z = r^ (no multiply,
 // no separate vector), r.z = r^.r^; the stopping norm ||r||^2 = sum D r^^2
 // is accumulated in FP32 from approx_abs_f32 and confirmed in FP64 by the
 // true-residual pass.  c holds D (for that pass) and the scaled faces.
+// F2D: p.q and the block sums on FP32 pairs.  DX: x += alpha p applied in
+// the next iteration's phase A (on the p_old it loads) and by flush_x after
+// the last one.
 template <typename T, int CPL, bool UNIT = false, bool F2D = false, bool DX = false>
 struct Op2DW {
     Stencil s;
@@ -228,7 +232,6 @@ struct Op2DW {
     const int *dexp = nullptr;                   // UNIT: h = (*dexp - 1023) >> 1
     static constexpr int kSW = 32 * CPL;
     static constexpr int kSmem = 1;
-    static constexpr bool kTunable = true;    // register budget selectable (pcg_minblocks)
     static constexpr bool kAnyBlock = true;   // strips are per warp: any block size
     static constexpr bool kScaled = UNIT;
     static constexpr bool kPairDots = F2D;    // phase A's block sums on FP32 pairs
@@ -496,7 +499,6 @@ struct Op3D {
     const float *d32 = nullptr;                  // UNIT, FP64: fl32(D 2^-2h); FP32: fl32(D^1/2)
     const int *dexp = nullptr;                   // UNIT, FP64: h = (*dexp - 1023) >> 1
     static constexpr int kSmem = 2 * (kTileX + 2) * (kTileY + 2);
-    static constexpr bool kTunable = true;
     static constexpr bool kAnyBlock = false;   // one tile per block of kPcgThreads
     static constexpr bool kScaled = UNIT;
     static constexpr bool kPairDots = F2D;     // p.q and the block sums on FP32 pairs (as Op2DW)
@@ -722,7 +724,6 @@ struct OpCsr {
     int32_t n;   // resolved at kernel start (device-side count of an extracted subsystem)
     const int32_t *done = nullptr;   // set: the cluster kernel may have solved the system already
     static constexpr int kSmem = 1;
-    static constexpr bool kTunable = true;
     static constexpr bool kAnyBlock = true;    // rows dealt to warps: any block size
     static constexpr bool kScaled = false;
     static constexpr bool kPairDots = sizeof(T) == 8;   // FP64: block sums on FP32 pairs
