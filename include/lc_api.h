@@ -407,8 +407,10 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  * Launch-shape knobs of an operator's kernels, for the autotuner; not part
  * of the method (the paper has no counterpart).  Results do not depend on
  * them beyond the rounding order of the Krylov solve's reductions.
- *   "pcg_minblocks" 1..4 (default 3): register budget of the structured-grid
- *       PCG kernel, as the number of 256-thread blocks that must fit on an SM.
+ *   "pcg_minblocks" 1..4 (default 3 for 2-D, 4 for 3-D and CSR operators):
+ *       register budget of the persistent PCG kernels, as the number of
+ *       256-thread blocks that must fit on an SM (2-D solves and local
+ *       subsystem solves with pcg_big take one 768-thread block instead).
  *   "pcg_grid_cap"  0..4096 (default 0 = all that fit): blocks of the global
  *       PCG launch.
  *   "pcg_scaled"    0 or 1 (default 1): 2-D FP64 solves iterate on the
