@@ -63,7 +63,7 @@ typedef enum {
     LC_ERR_BREAKDOWN = 5,      /* p^T A p <= 0 or not finite (A not SPD, or NaN input) */
     LC_ERR_TIMEOUT = 6,        /* a bounded grid-wide wait inside a persistent kernel gave up */
     LC_ERR_TOO_LARGE = 7,      /* sizes beyond int32 indexing or the documented limits */
-    LC_ERR_UNSUPPORTED = 8     /* valid request this build does not provide */
+    LC_ERR_UNSUPPORTED = 8     /* valid request the library does not provide */
 } lc_status;
 
 /* Threshold of the residual marking. */
