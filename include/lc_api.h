@@ -484,9 +484,11 @@ LC_EXPORT int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value)
  *     message is recorded.
  *   - The operator is not validated: interior face conductances must be > 0
  *     (the dilation uses the grid adjacency).
- *   - The first call on a device looks up the device address of the scratch
- *     array (with that device current); make that first call before any
- *     stream capture.
+ *   - Every call looks up the scratch array's device address on the current
+ *     device (host-side, no GPU work), so the address stays right after the
+ *     device's context is reset.  The first call on a device also loads the
+ *     library's device code there if nothing has loaded it yet; make that
+ *     first call before any stream capture.
  *   - All calls share the one array, which keeps the previous call's
  *     contents; each call clears what must start at zero.  Calls that
  *     overlap on the GPU (other streams, other host threads) race on it and

@@ -403,6 +403,10 @@ def mark_residual_stencil_noalloc(shape, D, Tx, Ty, Tz, b, x0, params: MarkParam
     f.argtypes = [C.c_int32, C.POINTER(C.c_int32), vp, vp, vp, vp, vp, vp, C.POINTER(MarkParams), vp, vp, vp, vp,
                   vp]
     nx, ny, nz = (tuple(shape) + (1,))[:3]
+    # a 3D grid needs its z faces: without Tz the C side would mark only the
+    # first nx*ny cells of buffers that hold nx*ny*nz
+    if Tz is None and nz > 1:
+        raise ValueError(f"shape {tuple(shape)} has nz = {nz} > 1 but Tz is None")
     dim = 3 if Tz is not None else 2
     sh = (C.c_int32 * 3)(nx, ny, nz)
     rc = f(dim, sh, _ptr(D, torch.float64, "D"), _ptr(Tx, torch.float64, "Tx"), _ptr(Ty, torch.float64, "Ty"),

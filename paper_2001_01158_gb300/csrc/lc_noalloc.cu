@@ -9,9 +9,6 @@
 // buffer of multi-pass expansion) lives in the fixed file-scope device array
 // below instead of an operator workspace.  Every device that loads the
 // library holds this array until the process exits.
-#include <cstring>
-#include <mutex>
-
 #include "lc_internal.cuh"
 
 namespace {
@@ -27,26 +24,19 @@ constexpr size_t kScratchBytes = kOffMask + (size_t)kMaxCells;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char *g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once
-// per device with that device current; host code only holds a stand-in for
-// the symbol, never its device address).
+// Device address of the scratch array for the context current on the calling
+// thread.  It is looked up on every call (cudaGetSymbolAddress is a host-side
+// table lookup once the module is loaded) rather than cached: if the device's
+// context is torn down and created again (cudaDeviceReset, or a framework
+// that resets the device), the module is loaded anew and the array may sit at
+// another address, which a cached pointer would not follow.
 int scratch_address(unsigned char **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LC_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return LC_ERR_CUDA;
-        }
-        g_addr[dev] = static_cast<unsigned char *>(p);
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return LC_ERR_CUDA;
     }
-    *out = g_addr[dev];
+    *out = static_cast<unsigned char *>(p);
     return LC_OK;
 }
 

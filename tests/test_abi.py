@@ -81,3 +81,14 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
             C.sizeof(lcg.HeatParams), C.sizeof(lcg.HeatStats), lcg.Params.global_.offset,
             lcg.HeatParams.params.offset, lcg.HeatParams.max_picard.offset, lcg.HeatStats.t_total_ms.offset]
     assert got == want
+
+
+def test_noalloc_binding_rejects_a_3d_shape_without_z_faces():
+    """A grid with nz > 1 given without Tz is refused on the host before the
+    C call: run as 2D, it would mark only the first nx*ny cells."""
+    import torch
+    t = torch.zeros(1, dtype=torch.float64)
+    with pytest.raises(ValueError, match="Tz is None"):
+        lcg.mark_residual_stencil_noalloc((4, 3, 2), t, t, t, None, t, t,
+                                          lcg.MarkParams(lcg.THR_REL_MAX, 1e-3, lcg.EXP_NONE, 0),
+                                          torch.zeros(1, dtype=torch.uint8), t, torch.zeros(1, dtype=torch.int32))

@@ -3,10 +3,11 @@
 Callers that cannot allocate device memory (inside another framework's pool,
 under a fixed budget, or after start-up) use
 lc_mark_residual_stencil_noalloc, whose scratch is a fixed device array in
-the library.  This test calls it through the C ABI twice in a row -- so the
-second call runs on the scratch the first one left behind -- and checks
-that each result equals, bit for bit, the result of lc_mark_residual on an
-operator created the usual way.  It lives in its own file, collected last,
+the library.  This test calls it through the C ABI twice in a row on every case
+-- so the second call runs on the scratch the first one left behind, and
+each case after the first on what a case of another size and mode left --
+and checks that each result equals, bit for bit, the result of
+lc_mark_residual on an operator created the usual way.  It lives in its own file, collected last,
 and builds everything it needs itself."""
 import numpy as np
 import pytest
@@ -77,7 +78,8 @@ def test_noalloc_matches_lc_mark_residual_on_two_calls_in_a_row():
         b, x0 = _inputs(op, k)
         ref = _with_operator(ctx, op, b, x0, params)
         assert 0 < ref[2] < op.n
-        _same(_without_allocation(op, b, x0, params), ref)
+        for _ in range(2):
+            _same(_without_allocation(op, b, x0, params), ref)
 
 
 def test_noalloc_rejects_grids_beyond_its_limit():
