@@ -32,6 +32,7 @@ PIN_GROUPS = {
     "alg1": [(P.test_local_then_global_agrees_with_global, {}), (P.test_local_then_global_edge_cases, {}),
              (P.test_rtilde_identity_and_bound, {}), (P.test_example1_local_solve_converges_without_global, {})],
     "adjoint": [(P.test_adjoint_gradient_matches_finite_differences, {})],
+    "relres": [(P.test_relres_matches_dense_norm, {"k": k}) for k in ALL_K] + [(P.test_relres_exact_values_and_zero_rhs, {})],
     "gs": [(P.test_gs_sweep_is_lexicographic_gs_on_colour_ordered_system, {"seed": sd, "shape": sh})
            for sd, sh in P.GS_CASES] + [(P.test_gs_sweep_diagonal_and_fixed_point, {}),
                                         (P.test_gs_sweep_reduces_energy_error, {}),
@@ -64,6 +65,10 @@ MUTANTS = [
     ("extract_rhs_index", "extract", "else s = fma(-av[e], x0[j], s);", "else s = fma(-av[e], x0[i], s);"),
     ("extract_global_col", "extract", "bci[nz] = g2l[j];", "bci[nz] = j < K ? j : 0;"),
     ("extract_rhs_sign", "extract", "else s = fma(-av[e], x0[j], s);", "else s = fma(av[e], x0[j], s);"),
+    ("relres_no_sqrt", "relres", "return sqrt(rr) / sqrt(bb);", "return rr / bb;"),
+    ("relres_norm_of_x", "relres", "double rr = dot(n, r, r), bb = dot(n, b, b);", "double rr = dot(n, r, r), bb = dot(n, x, x);"),
+    ("relres_drop_b", "relres", "orc_residual(n, rp, ci, av, b, x, r);\n    double rr", "orc_residual(n, rp, ci, av, b, x, r);\n    for (int32_t i = 0; i < n; ++i) r[i] -= b[i];\n    double rr"),
+    ("relres_zero_rhs", "relres", "return rr == 0.0 ? 0.0 : INFINITY;", "return 0.0;"),
     ("pcg_beta_inverted", "pcg", "double beta = rz_new / rz;", "double beta = rz / rz_new;"),
     ("pcg_r_sign", "pcg", "r[i] -= alpha * q[i]; }", "r[i] += alpha * q[i]; }"),
     ("pcg_no_precond", "pcg", "dinv[i] = 1.0 / d;", "dinv[i] = 1.0 / (d * d);"),

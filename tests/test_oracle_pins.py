@@ -107,6 +107,37 @@ def test_residual_matches_dense(k):
     assert np.all(np.abs(r - ref) <= 8e-16 * scale)
 
 
+@pytest.mark.parametrize("k", range(7))
+def test_relres_matches_dense_norm(k):
+    """relres (the convergence test of Sec. 2.3.1, ||b - A x||_2 <= eps ||b||_2)
+    against the dense Euclidean norms, far from and close to the solution."""
+    A = small_ops()[k]
+    Ad = A.dense()
+    rng = np.random.default_rng(100 + k)
+    b = rng.standard_normal(A.n)
+    xs = np.linalg.solve(Ad, b)
+    for x in (rng.standard_normal(A.n), xs + 1e-9 * rng.standard_normal(A.n), np.zeros(A.n)):
+        ref = np.linalg.norm(b - Ad @ x) / np.linalg.norm(b)
+        got = oracle.relres(A, b, x)
+        assert abs(got - ref) <= 1e-6 * ref + 1e-15, (got, ref)
+    # x = 0 gives exactly 1
+    assert oracle.relres(A, b, np.zeros(A.n)) == 1.0
+
+
+def test_relres_exact_values_and_zero_rhs():
+    """Exact cases: on A = I, b = (0, 10) and x = (-3, 6) give r = (3, 4),
+    relres = 5 / 10; b = 0 gives 0 for x = 0 and infinity otherwise."""
+    eye = oracle.csr([0, 1, 2], [0, 1], [1.0, 1.0])
+    assert oracle.relres(eye, np.array([0.0, 10.0]), np.array([-3.0, 6.0])) == 0.5
+    two = oracle.csr([0, 1, 2], [0, 1], [2.0, 2.0])
+    # r = b - 2x = (6, 8) - (0, 0) = (6, 8): 10 / 10
+    assert oracle.relres(two, np.array([6.0, 8.0]), np.zeros(2)) == 1.0
+    # r = (6, 8) - (6, 0) = (0, 8): 8 / 10
+    assert oracle.relres(two, np.array([6.0, 8.0]), np.array([3.0, 0.0])) == 0.8
+    assert oracle.relres(two, np.zeros(2), np.zeros(2)) == 0.0
+    assert oracle.relres(two, np.zeros(2), np.array([0.0, 1.0])) == math.inf
+
+
 def test_residual_canonical_order_is_fma_chain_from_b():
     """R1 fixes r = b; r = fma(-a_ij, x_j, r) ascending.  A 1x3 row where the
     fused chain and a separately rounded sum differ pins both the fusion and
