@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched workload")
     ap.add_argument("--no-heat", action="store_true", help="skip the nonlinear heat runs (Sec. 3.2)")
+    ap.add_argument("--profile-case", choices=PROFILE_CASES, default=None,
+                    help="run one solve of a workload for a profiler capture and print its statistics (no timing)")
     return ap.parse_args()
 
 
@@ -732,8 +734,93 @@ def batched_items(items, dev, reps, seq_alg1=False):
     return out
 
 
+PROFILE_CASES = ["global2d", "alg1", "alg1_gradient", "mixed2d", "fp64_3d", "mixed3d", "csr3t", "batched"]
+
+
+def profile_case(args):
+    """One solve of a workload, for ncu captures (`--side` sets the grid side).
+
+    2D cases: the moving-front system 2 from x^1 (x^1 is solved first by the
+    global PCG, so the launch of interest is the second pcg_kernel / ir_kernel
+    launch of the process: ncu -k regex:<kernel> -s 1 -c 1).  3D cases: the
+    anisotropic n^3 system from x0 = 0 (fp64_3d: one pcg_kernel launch;
+    mixed3d: Alg 1 with FP32 inner CG, one ir_kernel launch).  csr3t: the 3T
+    system on an n x n grid, one global pcg_kernel launch.  batched: the
+    512-system batch solved once without graph capture (one batched_kernel
+    launch)."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2001_01158_gb300 as lcg
+
+    lcg.build()
+    dev = torch.device("cuda", 0)
+    T = lambda v, dt=torch.float64: torch.as_tensor(v, dtype=dt, device=dev)  # noqa: E731
+    ctx = lcg.Context(0)
+    sp = lcg.SolveParams(1e-8, 200000, lcg.PREC_FP64, 0.0, 0)
+    st = lcg.Stats()
+    kind, n = args.profile_case, args.n
+    if kind in ("global2d", "alg1", "alg1_gradient", "mixed2d"):
+        d = gen.cfg2_fronts2d(seed=0, n=n)
+        op, seq = d["op"], d["seq"]
+        gop = lcg.StencilOperator(ctx, op.shape, T(op.D), T(op.Tx), T(op.Ty))
+        x1 = torch.zeros(op.n, dtype=torch.float64, device=dev)
+        lcg.pcg_solve(ctx, gop, T(seq.source(1)), x1, sp)
+        b2 = x1 / op.meta["dt"] + T(seq.source(2))
+        x = x1.clone()
+        if kind == "global2d":
+            lcg.pcg_solve(ctx, gop, b2, x, sp, st)
+        elif kind == "mixed2d":
+            prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8,
+                                     precision=lcg.PREC_MIXED, inner_tol=1e-4)
+            lcg.solve_local_then_global(ctx, gop, b2, x, prm, st)
+        else:
+            prm = (lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8)
+                   if kind == "alg1" else lcg.default_params(lcg.MARK_GRADIENT, alpha=1e-3, grad_layers=2, tol=1e-8))
+            lcg.solve_local_then_global(ctx, gop, b2, x, prm, st)
+    elif kind in ("fp64_3d", "mixed3d"):
+        d = gen.cfg3_aniso3d(seed=0, n=n)
+        op = d["op"]
+        gop = lcg.StencilOperator(ctx, op.shape, T(op.D), T(op.Tx), T(op.Ty), T(op.Tz))
+        x = T(d["x0"])
+        if kind == "fp64_3d":
+            lcg.pcg_solve(ctx, gop, T(d["b"]), x, lcg.SolveParams(1e-10, 200000, lcg.PREC_FP64, 0.0, 0), st)
+        else:
+            prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-10,
+                                     precision=lcg.PREC_MIXED, inner_tol=1e-5)
+            lcg.solve_local_then_global(ctx, gop, T(d["b"]), x, prm, st)
+    elif kind == "csr3t":
+        rp, ci, av = gen.threeT_2d(11, n, n)
+        rng = np.random.default_rng(5)
+        x0 = 1.0 + 0.1 * rng.standard_normal(len(rp) - 1)
+        b = gen.csr_matvec(rp, ci, av, x0)
+        b[3 * (n * (n // 2) + n // 2)] += 1.0
+        gop = lcg.CsrOperator(ctx, T(rp, torch.int32), T(ci, torch.int32), T(av))
+        x = T(x0)
+        lcg.pcg_solve(ctx, gop, T(b), x, sp, st)
+    else:
+        items = gen.cfg4_batch(seed=0)
+        systems = [(it["op"].shape[0], it["op"].shape[1], T(it["op"].D), T(it["op"].Tx), T(it["op"].Ty))
+                   for it in items]
+        batch = lcg.Batch(ctx, systems)
+        x = T(np.concatenate([it["x0"] for it in items]))
+        batch.solve(T(np.concatenate([it["b"] for it in items])), x,
+                    lcg.batch_params(beta=1e-3, layers=2, tol=1e-8, inner_tol=1e-4))
+        torch.cuda.synchronize(dev)
+        s = batch.stats()
+        print(json.dumps({"case": kind, "systems": len(s), "cells": batch.cells,
+                          "inner_iterations_mean": statistics.mean(v["it_global"] for v in s)}))
+        return
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"case": kind, "n": n, **st.as_dict()}))
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args)
+        return
     rank, ws, local = dist_init(args)
     try:
         if args.impl == "reference":
