@@ -407,7 +407,7 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  * Launch-shape knobs of an operator's kernels, for the autotuner; not part
  * of the method (the paper has no counterpart).  Results do not depend on
  * them beyond the rounding order of the Krylov solve's reductions.
- *   "pcg_minblocks" 1..4 (default 3 for 2-D, 4 for 3-D and CSR operators):
+ *   "pcg_minblocks" 1..4 (default 3 for stencil operators, 4 for CSR):
  *       register budget of the persistent PCG kernels, as the number of
  *       256-thread blocks that must fit on an SM (2-D solves and local
  *       subsystem solves with pcg_big take one 768-thread block instead).

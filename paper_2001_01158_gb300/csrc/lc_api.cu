@@ -795,7 +795,7 @@ int lc_op_create_stencil(lc_ctx *ctx, lc_op **out, int32_t dim, const int32_t sh
     op->n = n;
     op->nnz = nnz;
     op->st.dim = dim;
-    op->pcg_minblocks = dim == 3 ? 4 : 3;   // measured best register budgets (2D strips / 3D tiles)
+    op->pcg_minblocks = 3;   // measured best register budget (2D strips and 3D tiles)
     op->st.nx = (int)nx; op->st.ny = (int)ny; op->st.nz = (int)nz;
     op->st.n = n;
     op->st.D = D; op->st.Tx = Tx; op->st.Ty = Ty; op->st.Tz = dim == 3 ? Tz : nullptr;

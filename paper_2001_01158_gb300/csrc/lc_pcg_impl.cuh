@@ -517,28 +517,62 @@ struct Op3D {
     __device__ void zero_solution(const Vecs<T> &V) const {
         each_cell([&](int64_t i) { (UNIT ? V.xu : V.x)[i] = T(0); });
     }
+    // Phase B over the own column of every unit, kBz planes at a time with
+    // all their loads issued before the first store (the compiler keeps a
+    // store through one vector pointer ahead of a later load through
+    // another, so a plane-by-plane loop would wait for every plane's loads
+    // in turn); the per-thread sums keep the plane order.
+    static constexpr int kBz = 4;
     __device__ void phaseB_block(const Vecs<T> &V, const T *p, T alpha, T (&acc)[2], int nscale) const {
-        if (!UNIT) {
-            phaseB_generic(*this, V, p, alpha, acc);
-            return;
-        }
         float rrf = 0.f;
-        each_cell([&](int64_t i) {
-            const T qi = V.q[i], r0 = V.r[i];   // loads before the stores
-            const float di = d32[i];
-            if constexpr (!DX) V.x[i] = fmaT(alpha, p[i], V.x[i]);
-            const T ri = fmaT(-alpha, qi, r0);
-            V.r[i] = ri;
-            acc[0] = fmaT(ri, ri, acc[0]);
-            if constexpr (sizeof(T) == 8) {
-                const float f = approx_abs_f32((double)ri, nscale);
-                rrf = fmaf(di * f, f, rrf);
-            } else {
-                const float t = di * ri;
-                rrf = fmaf(t, t, rrf);
+        const int64_t nu = units();
+        const int64_t sxy = (int64_t)s.nx * s.ny;
+        for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) {
+            int x0, y0, z0;
+            origin(u, x0, y0, z0);
+            const int xx = x0 + (threadIdx.x % kTileX), yy = y0 + (threadIdx.x / kTileX);
+            if (xx >= s.nx || yy >= s.ny) continue;
+            const int z1 = min(z0 + kTileZ, s.nz);
+            const int64_t col = xx + (int64_t)s.nx * yy;
+            for (int zb = z0; zb < z1; zb += kBz) {
+                T qv[kBz], rv[kBz], pv[kBz], xv[kBz], dv[kBz];
+                float fv[kBz];
+#pragma unroll
+                for (int k = 0; k < kBz; ++k) {
+                    if (zb + k >= z1) break;
+                    const int64_t i = col + sxy * (zb + k);
+                    qv[k] = V.q[i];
+                    rv[k] = V.r[i];
+                    if (UNIT) fv[k] = d32[i];
+                    else dv[k] = V.dinv[i];
+                    if (!UNIT || !DX) { pv[k] = p[i]; xv[k] = V.x[i]; }
+                }
+#pragma unroll
+                for (int k = 0; k < kBz; ++k) {
+                    if (zb + k >= z1) break;
+                    const int64_t i = col + sxy * (zb + k);
+                    if (!UNIT || !DX) V.x[i] = fmaT(alpha, pv[k], xv[k]);
+                    const T ri = fmaT(-alpha, qv[k], rv[k]);
+                    V.r[i] = ri;
+                    if constexpr (!UNIT) {
+                        const T zi = dv[k] * ri;
+                        V.z[i] = zi;
+                        acc[0] = fmaT(ri, zi, acc[0]);
+                        acc[1] = fmaT(ri, ri, acc[1]);
+                    } else {
+                        acc[0] = fmaT(ri, ri, acc[0]);
+                        if constexpr (sizeof(T) == 8) {
+                            const float f = approx_abs_f32((double)ri, nscale);
+                            rrf = fmaf(fv[k] * f, f, rrf);
+                        } else {
+                            const float t = fv[k] * ri;
+                            rrf = fmaf(t, t, rrf);
+                        }
+                    }
+                }
             }
-        });
-        acc[1] = (T)rrf;
+        }
+        if constexpr (UNIT) acc[1] = (T)rrf;
     }
     __device__ int64_t units() const {
         const int64_t tx = (s.nx + kTileX - 1) / kTileX, ty = (s.ny + kTileY - 1) / kTileY;
@@ -637,9 +671,14 @@ struct Op3D {
     }
     // 2.5D march: thread (lx, ly) owns column (x, y) and keeps p at z-1, z,
     // z+1 in registers; the first kHalo threads own one cell of the plane's
-    // halo ring each.  Per plane: issue the loads of plane z+1 (own column
-    // and halo) and the coefficients of plane z, publish plane z to shared
-    // memory, one barrier, form q at plane z.  Two plane buffers alternate.
+    // halo ring each.  Per plane: publish plane z (own cell and ring cell) to
+    // shared memory, one barrier, form q at plane z; two plane buffers
+    // alternate.  Software pipeline, one plane ahead: while plane z is
+    // formed, the loads that planes z+1 and z+2 need are already in flight
+    // -- the coefficients of plane z+1, z and p_old (and x) of the own
+    // column at z+2 and of the ring cell at z+1 -- and the arithmetic on
+    // them (p = z + beta p_old, the lazy x update) happens one plane later,
+    // so no load is waited for in the plane that issued it.
     static constexpr int kEx = kTileX + 2, kEy = kTileY + 2, kPls = kEx * kEy;
     static constexpr int kHalo = kPls - kTileX * kTileY;   // 84 ring cells
     __device__ __forceinline__ void halo_cell(int k, int &hx, int &hy) const {
@@ -648,6 +687,29 @@ struct Op3D {
         else if (k < 2 * kEx) { hx = k - kEx; hy = kEy - 1; }
         else if (k < 2 * kEx + kTileY) { hx = 0; hy = 1 + (k - 2 * kEx); }
         else { hx = kEx - 1; hy = 1 + (k - 2 * kEx - kTileY); }
+    }
+    // the face coefficients of cell i at plane z (tzm comes from the plane below)
+    struct Faces { T d, tym, txm, txp, typ, tzp; };
+    __device__ __forceinline__ void load_faces(int64_t i, int xx, int yy, int z, Faces &f) const {
+        f.d = (!UNIT) ? c.D[i] : T(0);
+        f.tym = yy > 0 ? c.Ty[i - s.nx] : T(0);
+        f.txm = xx > 0 ? c.Tx[i - 1] : T(0);
+        f.txp = xx + 1 < s.nx ? c.Tx[i] : T(0);
+        f.typ = yy + 1 < s.ny ? c.Ty[i] : T(0);
+        f.tzp = z + 1 < s.nz ? c.Tz[i] : T(0);
+    }
+    // FP32 faces of the next plane are held in registers; FP64 ones would
+    // cost ten more registers, so the FP64 march only asks L1 for their
+    // lines a plane ahead and loads them in their own plane
+    static constexpr bool kFacesAhead = sizeof(T) == 4;
+    __device__ __forceinline__ void prefetch_faces(int64_t i, int xx, int yy, int z) const {
+        const auto pf = [](const T *a) { asm volatile("prefetch.global.L1 [%0];" ::"l"(a)); };
+        if (!UNIT) pf(c.D + i);
+        if (yy > 0) pf(c.Ty + i - s.nx);
+        if (xx > 0 && (xx & 15) == 0) pf(c.Tx + i - 1);   // other lanes' lines are those of Tx + i
+        pf(c.Tx + i);
+        pf(c.Ty + i);
+        if (z + 1 < s.nz) pf(c.Tz + i);
     }
     __device__ void phaseA_unit(int64_t u, const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq,
                                 T *sm, int ps, float &fh, float &fl, T ax) const {
@@ -662,40 +724,88 @@ struct Op3D {
         int hx = 0, hy = 0;
         if (has_h) halo_cell(threadIdx.x, hx, hy);
         const int ghx = x0 - 1 + hx, ghy = y0 - 1 + hy;
+        const bool hin = has_h && ghx >= 0 && ghx < s.nx && ghy >= 0 && ghy < s.ny;
         const int cc = (ly + 1) * kEx + (lx + 1);
-        T pm = T(0), pc = T(0), ph = T(0);
-        if (act) pm = pat(V, pold, first, beta, xx, yy, z0 - 1);
-        if (has_h) ph = pat(V, pold, first, beta, ghx, ghy, z0);
-        if (act) pc = pat_own(V, pold, first, beta, ax, xx, yy, z0);   // last: its x store holds later loads back
-        for (int z = z0; z < z1; ++z) {
-            const int64_t i = xx + (int64_t)s.nx * yy + sxy * z;
-            // loads of plane z+1 and coefficients of plane z, before the barrier
-            T pn = T(0), phn = T(0), d = T(0), tzm = T(0), tym = T(0), txm = T(0), txp = T(0), typ = T(0), tzp = T(0);
-            if (act) {
-                if (!UNIT) d = c.D[i];
-                if (z > 0) tzm = c.Tz[i - sxy];
-                if (yy > 0) tym = c.Ty[i - s.nx];
-                if (xx > 0) txm = c.Tx[i - 1];
-                if (xx + 1 < s.nx) txp = c.Tx[i];
-                if (yy + 1 < s.ny) typ = c.Ty[i];
-                if (z + 1 < s.nz) tzp = c.Tz[i];
+        const int64_t col = act ? xx + (int64_t)s.nx * yy : 0;
+        const int64_t hcol = hin ? ghx + (int64_t)s.nx * ghy : 0;
+        const auto mkp = [&](T zv, T pv) { return first ? zv : fmaT(beta, pv, zv); };
+        // raw values of the own column one plane ahead of pn and of the ring cell at the next plane
+        T oz = T(0), op = T(0), ox = T(0), hz = T(0), hp = T(0);
+        T pm = T(0), pc = T(0), tzm = T(0);
+        Faces cur{}, nxt{};
+        // prologue: p at z0-1 and z0 (with the lazy x update at z0), raw
+        // values at z0+1 (own) and z0 (ring), coefficients of plane z0
+        if (act) {
+            if (z0 > 0) {
+                const int64_t i = col + sxy * (z0 - 1);
+                pm = mkp(ldcg(V.z + i), first ? T(0) : ldcg(pold + i));
+                tzm = c.Tz[i];
             }
-            if (has_h) phn = pat(V, pold, first, beta, ghx, ghy, z + 1);
-            if (act)   // last: with DX its x store would hold back the loads above
-                pn = z + 1 < z1 ? pat_own(V, pold, first, beta, ax, xx, yy, z + 1)
-                                : pat(V, pold, first, beta, xx, yy, z + 1);
+            const int64_t i = col + sxy * z0;
+            if (kFacesAhead) load_faces(i, xx, yy, z0, cur);
+            else prefetch_faces(i, xx, yy, z0);
+            const T zv = ldcg(V.z + i), pv = first ? T(0) : ldcg(pold + i);
+            if (z0 + 1 < s.nz) {
+                const int64_t j = i + sxy;
+                oz = ldcg(V.z + j);
+                if (!first) op = ldcg(pold + j);
+                if (DX && !first && z0 + 1 < z1) ox = V.x[j];
+            }
+            if constexpr (DX) {
+                if (!first) V.x[i] = fmaT(ax, pv, V.x[i]);
+            }
+            pc = mkp(zv, pv);
+        }
+        if (hin) {
+            const int64_t i = hcol + sxy * z0;
+            hz = ldcg(V.z + i);
+            if (!first) hp = ldcg(pold + i);
+        }
+        for (int z = z0; z < z1; ++z) {
+            // p of the own column at z+1 (the lazy x update there if the cell is
+            // the tile's) and of the ring cell at z, from values loaded a plane ago
+            T pn = T(0), ph = T(0);
+            if (act && z + 1 < s.nz) {
+                pn = mkp(oz, op);
+                if constexpr (DX) {
+                    if (!first && z + 1 < z1) V.x[col + sxy * (z + 1)] = fmaT(ax, op, ox);
+                }
+            }
+            if (hin) ph = mkp(hz, hp);
+            // loads for the next plane: coefficients of z+1, own column at z+2, ring at z+1
+            if (act) {
+                if constexpr (kFacesAhead) {
+                    if (z + 1 < z1) load_faces(col + sxy * (z + 1), xx, yy, z + 1, nxt);
+                } else {
+                    load_faces(col + sxy * z, xx, yy, z, cur);   // lines asked for a plane ago
+                    if (z + 1 < z1) prefetch_faces(col + sxy * (z + 1), xx, yy, z + 1);
+                }
+                oz = op = ox = T(0);
+                if (z + 2 < s.nz && z + 2 <= z1) {
+                    const int64_t j = col + sxy * (z + 2);
+                    oz = ldcg(V.z + j);
+                    if (!first) op = ldcg(pold + j);
+                    if (DX && !first && z + 2 < z1) ox = V.x[j];
+                }
+            }
+            if (hin && z + 1 < z1) {
+                const int64_t j = hcol + sxy * (z + 1);
+                hz = ldcg(V.z + j);
+                if (!first) hp = ldcg(pold + j);
+            }
             T *pl = sm + (z & 1) * kPls;
             pl[cc] = pc;
             if (has_h) pl[hy * kEx + hx] = ph;
             __syncthreads();
             if (act) {
-                T qi = UNIT ? pc : d * pc;
+                const int64_t i = col + sxy * z;
+                T qi = UNIT ? pc : cur.d * pc;
                 qi = fmaT(-tzm, pm, qi);
-                qi = fmaT(-tym, pl[cc - kEx], qi);
-                qi = fmaT(-txm, pl[cc - 1], qi);
-                qi = fmaT(-txp, pl[cc + 1], qi);
-                qi = fmaT(-typ, pl[cc + kEx], qi);
-                qi = fmaT(-tzp, pn, qi);
+                qi = fmaT(-cur.tym, pl[cc - kEx], qi);
+                qi = fmaT(-cur.txm, pl[cc - 1], qi);
+                qi = fmaT(-cur.txp, pl[cc + 1], qi);
+                qi = fmaT(-cur.typ, pl[cc + kEx], qi);
+                qi = fmaT(-cur.tzp, pn, qi);
                 pout[i] = pc;
                 V.q[i] = qi;
                 if constexpr (F2D) {
@@ -709,7 +819,8 @@ struct Op3D {
             }
             pm = pc;
             pc = pn;
-            ph = phn;
+            tzm = cur.tzp;
+            if constexpr (kFacesAhead) cur = nxt;
         }
         __syncthreads();
     }

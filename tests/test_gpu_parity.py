@@ -270,6 +270,32 @@ def test_pcg_3d_scaled_and_unscaled_match_oracle(ctx, shape, scaled, pairdot, la
     assert oracle.relres(A, b, x.cpu().numpy()) <= 1e-10
 
 
+@pytest.mark.parametrize("shape", [(35, 11, 37), (9, 17, 33)])
+@pytest.mark.parametrize("minblocks", [2, 3, 4])
+def test_pcg_3d_several_z_tiles_and_register_budgets(ctx, shape, minblocks):
+    """Grids deeper than one tile (16 planes) with a ragged last tile: the 3D
+    march's plane-ahead pipeline crosses tile boundaries (p of the plane
+    below and above a tile, the lazy x update only on the tile's own planes),
+    at each register budget of the persistent kernel.  FP64 (default scaled
+    kernel: iterations within one, solution within 1e-9 of the oracle) and
+    mixed precision (relres 1e-10)."""
+    op = gen.random_stencil_3d(sum(shape) + minblocks, *shape)
+    A, b, x0 = rhs_and_x0(op, 23)
+    tol = 1e-9
+    xr, st, it_ref, _ = oracle.pcg(A, b, x0, tol=tol)
+    gop = stencil_op(ctx, op)
+    gop.set_tuning("pcg_minblocks", minblocks)
+    x = cu(x0)
+    stats = lcg.Stats()
+    lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(tol, 100000, lcg.PREC_FP64, 0.0, 0), stats)
+    xg = x.cpu().numpy()
+    assert oracle.relres(A, b, xg) <= tol and abs(stats.it_global - it_ref) <= 1
+    assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
+    x = cu(x0)
+    lcg.pcg_solve(ctx, gop, cu(b), x, lcg.SolveParams(1e-10, 100000, lcg.PREC_MIXED, 1e-5, 30), stats)
+    assert oracle.relres(A, b, x.cpu().numpy()) <= 1e-10
+
+
 @pytest.mark.parametrize("cscale,bscale", [(1e25, 1e35), (1e-25, 1e-30), (1.0, 1e-140), (1e5, 1e150),
                                             (1e45, 1e50), (1e-45, 1e-40)])
 def test_pcg_scaled_extreme_magnitudes(ctx, cscale, bscale):
