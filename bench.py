@@ -207,57 +207,92 @@ def ncu_traffic_per_cell_iter():
 
 # ----------------------------------------------------------------- oracle side
 
-def oracle_sample(n_full: int, n: int | None = None):
-    """Alg 1 of the oracle on the same workload family at a reduced
-    resolution n x n (default n_full/2), system 1 (x0 = 0, b = s^1), scaled to
-    ms per n_full^2 system by the cell count (the operator's mass term keeps
-    the Jacobi-PCG iteration count essentially independent of the grid size).
-    Returns (ms_per_system, sample, stats)."""
-    import gen
+class OracleChain:
+    """The bench workload solved by the oracle alone: system j (j = 0 .. 19)
+    is A x = x^j/dt + s^{j+1} started from x^j, with x^0 = 0 and x^{j+1} the
+    oracle's own Alg 1 solution of system j (relres 1e-8) -- the GPU arm's
+    systems, with the oracle's chain of previous solutions instead of the
+    library's (no input of the oracle comes from the CUDA path).  Step k
+    solves system k mod 20; a system is solved only once its start exists,
+    so steps run in order from k = 0."""
+
+    def __init__(self, n: int, seed: int = 0):
+        import numpy as np
+
+        import gen
+        import oracle
+        d = gen.cfg2_fronts2d(seed=seed, n=n)
+        self.A = oracle.from_stencil(d["op"])
+        self.seq, self.dt, self.n = d["seq"], d["op"].meta["dt"], n
+        self.states = {0: np.zeros(self.A.n)}
+
+    def solve(self, k: int):
+        """Alg 1 (residual marking 1e-3 max|r|, 2 layers, relres 1e-8) on
+        system k mod 20; returns (seconds, stats)."""
+        import oracle
+        j = k % self.seq.steps
+        x0 = self.states[j]
+        b = x0 / self.dt + self.seq.source(j + 1)
+        t = time.perf_counter()
+        x, st, _ = oracle.solve_local_then_global(self.A, b, x0, tol=1e-8)
+        dt = time.perf_counter() - t
+        self.states.setdefault(j + 1, x)
+        return dt, st
+
+
+def oracle_legs(n: int, omp_steps: int, serial_systems, warmup: int = 0):
+    """Times the oracle on the bench workload at n x n: the OpenMP build (row
+    loops on all host cores) over the chain's steps 0 .. warmup+omp_steps-1
+    (the first `warmup` untimed), then the serial parity oracle (one thread)
+    on the systems listed in serial_systems, each from the chain's state.
+    Returns a dict with both legs (ms per system, threads, systems)."""
     import oracle
-    n = n or max(64, n_full // 2)
-    d = gen.cfg2_fronts2d(seed=0, n=n)
-    A = oracle.from_stencil(d["op"])
-    b = d["seq"].source(1)
-    import numpy as np
-    x0 = np.zeros(A.n)
-    t = time.perf_counter()
-    x, st, _ = oracle.solve_local_then_global(A, b, x0, tol=1e-8)
-    dt = time.perf_counter() - t
-    scale = (n_full * n_full) / float(n * n)
-    sample = (f"oracle Alg 1 (serial FP64 C, 1 thread) on system 1 of the same workload at {n}x{n} "
-              f"(K={st['K']}, {st['it_local']}+{st['it_global']} CG iterations, {dt:.1f} s), "
-              f"scaled x{scale:g} by cell count to one {n_full}x{n_full} system")
-    return dt * 1e3 * scale, sample, st
+    from oracle.build import build_oracle
+    build_oracle()
+    build_oracle(openmp=True)
+    ch = OracleChain(n)
+    omp_ms, omp_sys = [], []
+    with oracle.openmp_build():
+        threads = oracle.threads()
+        for k in range(warmup + omp_steps):
+            dt, st = ch.solve(k)
+            if k >= warmup:
+                omp_ms.append(dt * 1e3)
+                omp_sys.append(k % ch.seq.steps)
+        # the chain must reach the serial leg's systems
+        k = warmup + omp_steps
+        while any(j not in ch.states for j in serial_systems):
+            ch.solve(k)
+            k += 1
+    ser_ms = []
+    for j in serial_systems:
+        dt, st = ch.solve(j)
+        ser_ms.append(dt * 1e3)
+    return {"omp": {"ms": omp_ms, "threads": threads, "systems": omp_sys},
+            "serial": {"ms": ser_ms, "threads": oracle.threads(), "systems": list(serial_systems)}}
 
 
 def run_reference(args, rank, ws):
+    """The reference arm: the oracle on the host cores, on the GPU arm's
+    workload (full n x n systems, the oracle's own chain of previous
+    solutions), W untimed and K timed steps of the OpenMP build on all host
+    cores; the serial oracle is timed beside it on system 1."""
     if rank != 0:
         return
-    from oracle.build import build_oracle
-    build_oracle()
-    # size each step so the whole run stays near two minutes: time a small
-    # probe, then take the largest n_full/2^j whose predicted time fits
-    budget = 120.0 / max(1, args.warmup + args.steps)
-    t = time.perf_counter()
-    oracle_sample(args.n, 128)
-    per_cell = (time.perf_counter() - t) / (128 * 128)
-    n = max(64, args.n // 2)
-    while n > 128 and per_cell * n * n > budget:
-        n //= 2
-    times = []
-    sample = ""
-    for k in range(args.warmup + args.steps):
-        ms, sample, _ = oracle_sample(args.n, n)
-        if k >= args.warmup:
-            times.append(ms)
-    v = statistics.mean(times) if times else float("nan")
+    legs = oracle_legs(args.n, args.steps, [1], warmup=args.warmup)
+    omp, ser = legs["omp"], legs["serial"]
+    v = statistics.mean(omp["ms"]) if omp["ms"] else float("nan")
+    sample = (f"oracle Alg 1 (OpenMP build of the plain FP64 C oracle, row loops on {omp['threads']} threads) on the "
+              f"full {args.n}x{args.n} systems {omp['systems'][0] if omp['systems'] else '-'}.. of the moving-front "
+              f"sequence, each from the oracle's own previous solution; {args.warmup} untimed + {args.steps} timed steps")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD.replace("2048x2048", f"{args.n}x{args.n}"), "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": omp["threads"], "kind": "oracle", "sample": sample},
+        "cpu_serial": {"value": statistics.mean(ser["ms"]), "unit": UNIT, "cores": ser["threads"], "kind": "oracle",
+                       "sample": f"serial parity oracle (1 thread) on system {ser['systems']} of the same chain"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -497,10 +532,17 @@ def run_gpu(args, rank, ws, local):
     if not args.no_heat:
         res["heat_e1"] = {"99x99_100_steps": run_heat(dev, 99, 100), "1024x1024_10_steps": run_heat(dev, 1024, 10)}
     if rank == 0 and not args.no_cpu_baseline:
-        from oracle.build import build_oracle
-        build_oracle()
-        ms, sample, _ = oracle_sample(args.n)
-        res["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        # a bounded sample: the OpenMP build on the chain's first three
+        # systems, the serial oracle on system 1
+        legs = oracle_legs(args.n, 3, [1])
+        omp, ser = legs["omp"], legs["serial"]
+        res["cpu_baseline"] = {
+            "value": statistics.mean(omp["ms"]), "unit": UNIT, "cores": omp["threads"], "kind": "oracle",
+            "sample": (f"oracle Alg 1 (OpenMP build of the plain FP64 C oracle, row loops on {omp['threads']} threads) "
+                       f"on the full {args.n}x{args.n} systems {omp['systems']} of the same sequence, each from the "
+                       f"oracle's own previous solution"),
+            "serial": {"value": statistics.mean(ser["ms"]), "cores": ser["threads"],
+                       "sample": f"serial parity oracle (1 thread) on system {ser['systems']} of the same chain"}}
     if rank == 0:
         print(json.dumps(res), flush=True)
 
