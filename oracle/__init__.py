@@ -17,6 +17,7 @@ definitions on tiny inputs, closed forms and invariants.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 from dataclasses import dataclass
@@ -67,6 +68,26 @@ def lib():
     return _lib
 
 
+def threads() -> int:
+    """Threads the loaded oracle library's loops use (1: the serial oracle)."""
+    return int(lib().orc_threads())
+
+
+@contextlib.contextmanager
+def openmp_build():
+    """Within this block every function of this module runs on the
+    timing-only OpenMP build of the oracle source (row loops in parallel on
+    all host cores, dot products as OpenMP reductions: another rounding
+    order).  For CPU-baseline timing only; parity uses the serial build."""
+    global _lib
+    saved = lib()
+    _lib = load(build_oracle(openmp=True))
+    try:
+        yield _lib
+    finally:
+        _lib = saved
+
+
 def load(path: str):
     """Open an oracle shared library at `path` and declare its signatures."""
     L = C.CDLL(path)
@@ -89,6 +110,8 @@ def load(path: str):
                                     C.POINTER(C.c_int32)]
     L.orc_extract.restype = C.c_int32
     L.orc_assemble.argtypes = [C.c_int32, _f64p, C.c_int32, _i32p, _f64p, _f64p]
+    L.orc_threads.argtypes = []
+    L.orc_threads.restype = C.c_int32
     L.orc_relres.argtypes = csr + [_f64p, _f64p]
     L.orc_relres.restype = C.c_double
     L.orc_pcg.argtypes = csr + [_f64p, _f64p, C.c_double, C.c_int32, C.POINTER(C.c_int32),

@@ -15,19 +15,25 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "lc_oracle.c")
 OUT_DIR = os.path.join(HERE, "_build")
 OUT = os.path.join(OUT_DIR, "liblc_oracle.so")
+OUT_OMP = os.path.join(OUT_DIR, "liblc_oracle_omp.so")
 
 
-def build_oracle(force: bool = False) -> str:
-    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= os.path.getmtime(SRC):
-        return OUT
+def build_oracle(force: bool = False, openmp: bool = False) -> str:
+    """Build the serial parity oracle (default) or, with openmp=True, the
+    timing-only OpenMP build of the same source (row loops in parallel, dot
+    products as OpenMP reductions: other rounding, never used for parity)."""
+    out = OUT_OMP if openmp else OUT
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(SRC):
+        return out
     os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = OUT + f".tmp{os.getpid()}"
+    tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-Wall", "-o", tmp, SRC, "-lm"]
+           "-Wall"] + (["-fopenmp"] if openmp else []) + ["-o", tmp, SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":
     print(build_oracle(force="--force" in sys.argv))
+    print(build_oracle(force="--force" in sys.argv, openmp=True))

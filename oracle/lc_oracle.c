@@ -47,6 +47,23 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Timing-only variant.  Built with -fopenmp (a separate library), the
+ * row loops of the Krylov solve, the residual and the marking passes run in
+ * parallel over rows and the dot products become OpenMP sum reductions
+ * (another rounding order).  That build only times the method on all host
+ * cores; the serial build below, without -fopenmp, is the parity oracle and
+ * these macros expand to nothing there. */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_ROWS _Pragma("omp parallel for schedule(static)")
+#define ORC_ROWS_SUM _Pragma("omp parallel for schedule(static) reduction(+:s)")
+#define ORC_ROWS_MAX _Pragma("omp parallel for schedule(static) reduction(max:mx)")
+#else
+#define ORC_ROWS
+#define ORC_ROWS_SUM
+#define ORC_ROWS_MAX
+#endif
+
 #define ORC_OK 0
 #define ORC_NOT_CONVERGED 4
 #define ORC_BREAKDOWN 5
@@ -57,6 +74,7 @@
 void orc_residual(int32_t n, const int32_t *rp, const int32_t *ci, const double *av,
                   const double *b, const double *x, double *r)
 {
+    ORC_ROWS
     for (int32_t i = 0; i < n; ++i) {
         double s = b[i];
         for (int32_t e = rp[i]; e < rp[i + 1]; ++e)
@@ -69,6 +87,7 @@ void orc_residual(int32_t n, const int32_t *rp, const int32_t *ci, const double 
 static void spmv(int32_t n, const int32_t *rp, const int32_t *ci, const double *av,
                  const double *x, double *y)
 {
+    ORC_ROWS
     for (int32_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int32_t e = rp[i]; e < rp[i + 1]; ++e)
@@ -80,6 +99,7 @@ static void spmv(int32_t n, const int32_t *rp, const int32_t *ci, const double *
 static double dot(int32_t n, const double *a, const double *b)
 {
     double s = 0.0;
+    ORC_ROWS_SUM
     for (int32_t i = 0; i < n; ++i) s += a[i] * b[i];
     return s;
 }
@@ -134,6 +154,7 @@ double orc_tau_eps_normb(int32_t n, const double *b, double eps)
 static void dilate_once(int32_t n, const int32_t *rp, const int32_t *ci, const double *av,
                         const uint8_t *in, uint8_t *out)
 {
+    ORC_ROWS
     for (int32_t i = 0; i < n; ++i) {
         uint8_t m = in[i];
         for (int32_t e = rp[i]; e < rp[i + 1] && !m; ++e)
@@ -215,9 +236,11 @@ int32_t orc_mark_residual(int32_t n, const int32_t *rp, const int32_t *ci, const
         tau = orc_tau_eps_normb(n, b, param);
     } else {
         double mx = 0.0;
+        ORC_ROWS_MAX
         for (int32_t i = 0; i < n; ++i) if (fabs(r[i]) > mx) mx = fabs(r[i]);
         tau = param * mx;
     }
+    ORC_ROWS
     for (int32_t i = 0; i < n; ++i) mask[i] = fabs(r[i]) > tau ? 1 : 0;
     int32_t done = 0;
     if (exp_mode == ORC_EXP_DILATE) {
@@ -237,6 +260,7 @@ int32_t orc_mark_residual(int32_t n, const int32_t *rp, const int32_t *ci, const
 void orc_gradient(int32_t n, const int32_t *rp, const int32_t *ci, const double *av,
                   const double *x, double *g)
 {
+    ORC_ROWS
     for (int32_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
@@ -336,6 +360,7 @@ int32_t orc_pcg(int32_t n, const int32_t *rp, const int32_t *ci, const double *a
     double *r = (double *)malloc(sz), *z = (double *)malloc(sz), *p = (double *)malloc(sz);
     double *q = (double *)malloc(sz), *dinv = (double *)malloc(sz);
     int32_t status = ORC_NOT_CONVERGED, it = 0;
+    ORC_ROWS
     for (int32_t i = 0; i < n; ++i) {
         double d = 0.0;
         for (int32_t e = rp[i]; e < rp[i + 1]; ++e) if (ci[e] == i) d = av[e];
@@ -352,6 +377,7 @@ int32_t orc_pcg(int32_t n, const int32_t *rp, const int32_t *ci, const double *a
         orc_residual(n, rp, ci, av, b, x, r);
         double rr = dot(n, r, r);
         if (rr <= stop) { status = ORC_OK; break; }
+        ORC_ROWS
         for (int32_t i = 0; i < n; ++i) { z[i] = dinv[i] * r[i]; p[i] = z[i]; }
         double rz = dot(n, r, z);
         int converged = 0;
@@ -360,14 +386,17 @@ int32_t orc_pcg(int32_t n, const int32_t *rp, const int32_t *ci, const double *a
             double pq = dot(n, p, q);
             if (!(pq > 0.0) || !isfinite(pq)) { status = ORC_BREAKDOWN; goto done; }
             double alpha = rz / pq;
+            ORC_ROWS
             for (int32_t i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
             ++it;
             rr = dot(n, r, r);
             if (rr <= stop) { converged = 1; break; }
+            ORC_ROWS
             for (int32_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
             double rz_new = dot(n, r, z);
             double beta = rz_new / rz;
             rz = rz_new;
+            ORC_ROWS
             for (int32_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
         }
         if (!converged) { status = ORC_NOT_CONVERGED; break; }
@@ -633,4 +662,15 @@ int32_t orc_heat2d_step(int32_t nx, int32_t ny, double h, double dt, double p,
     hs->status = status;
     free(kappa); free(b); free(x); free(rp); free(ci); free(av);
     return status;
+}
+
+/* Threads the parallel loops use: omp_get_max_threads() in the OpenMP build,
+ * 1 in the serial oracle. */
+int32_t orc_threads(void)
+{
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
