@@ -23,6 +23,7 @@ C ABI with host buffers, and the oracle timed on the host cores.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import hashlib
 import json
 import math
@@ -240,59 +241,56 @@ class OracleChain:
         return dt, st
 
 
-def oracle_legs(n: int, omp_steps: int, serial_systems, warmup: int = 0):
-    """Times the oracle on the bench workload at n x n: the OpenMP build (row
-    loops on all host cores) over the chain's steps 0 .. warmup+omp_steps-1
-    (the first `warmup` untimed), then the serial parity oracle (one thread)
-    on the systems listed in serial_systems, each from the chain's state.
-    Returns a dict with both legs (ms per system, threads, systems)."""
+def oracle_legs(n: int, serial_steps: int, omp_steps: int, warmup: int = 0):
+    """Times the oracle on the bench workload at n x n, both legs over the
+    chain's steps k = 0, 1, ... (the first `warmup` untimed): the serial
+    parity oracle (one thread) builds the chain over warmup + serial_steps
+    steps; the timing-only OpenMP build (row loops on all host cores) then
+    solves steps 0 .. warmup + omp_steps - 1 from the same chain states.
+    Returns both legs (ms per system, threads, systems)."""
     import oracle
     from oracle.build import build_oracle
     build_oracle()
     build_oracle(openmp=True)
     ch = OracleChain(n)
-    omp_ms, omp_sys = [], []
-    with oracle.openmp_build():
-        threads = oracle.threads()
-        for k in range(warmup + omp_steps):
-            dt, st = ch.solve(k)
-            if k >= warmup:
-                omp_ms.append(dt * 1e3)
-                omp_sys.append(k % ch.seq.steps)
-        # the chain must reach the serial leg's systems
-        k = warmup + omp_steps
-        while any(j not in ch.states for j in serial_systems):
-            ch.solve(k)
-            k += 1
-    ser_ms = []
-    for j in serial_systems:
-        dt, st = ch.solve(j)
-        ser_ms.append(dt * 1e3)
-    return {"omp": {"ms": omp_ms, "threads": threads, "systems": omp_sys},
-            "serial": {"ms": ser_ms, "threads": oracle.threads(), "systems": list(serial_systems)}}
+    legs = {}
+    for name, steps in (("serial", serial_steps), ("omp", omp_steps)):
+        ms, systems = [], []
+        with (oracle.openmp_build() if name == "omp" else contextlib.nullcontext()):
+            threads = oracle.threads()
+            for k in range(warmup + steps):
+                dt, _ = ch.solve(k)
+                if k >= warmup:
+                    ms.append(dt * 1e3)
+                    systems.append(k % ch.seq.steps)
+        legs[name] = {"ms": ms, "threads": threads, "systems": systems}
+    legs["chain"] = ch
+    return legs
 
 
 def run_reference(args, rank, ws):
     """The reference arm: the oracle on the host cores, on the GPU arm's
     workload (full n x n systems, the oracle's own chain of previous
-    solutions), W untimed and K timed steps of the OpenMP build on all host
-    cores; the serial oracle is timed beside it on system 1."""
+    solutions): W untimed and K timed steps of the serial oracle (the value),
+    and the same steps by its OpenMP build on all host cores beside it."""
     if rank != 0:
         return
-    legs = oracle_legs(args.n, args.steps, [1], warmup=args.warmup)
-    omp, ser = legs["omp"], legs["serial"]
-    v = statistics.mean(omp["ms"]) if omp["ms"] else float("nan")
-    sample = (f"oracle Alg 1 (OpenMP build of the plain FP64 C oracle, row loops on {omp['threads']} threads) on the "
-              f"full {args.n}x{args.n} systems {omp['systems'][0] if omp['systems'] else '-'}.. of the moving-front "
-              f"sequence, each from the oracle's own previous solution; {args.warmup} untimed + {args.steps} timed steps")
+    legs = oracle_legs(args.n, args.steps, args.steps, warmup=args.warmup)
+    ser, omp = legs["serial"], legs["omp"]
+    v = statistics.mean(ser["ms"]) if ser["ms"] else float("nan")
+    sample = (f"serial oracle Alg 1 (plain FP64 C, 1 thread) on the full {args.n}x{args.n} systems "
+              f"{ser['systems']} of the moving-front sequence, each from the oracle's own previous solution; "
+              f"{args.warmup} untimed + {args.steps} timed steps")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD.replace("2048x2048", f"{args.n}x{args.n}"), "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": omp["threads"], "kind": "oracle", "sample": sample},
-        "cpu_serial": {"value": statistics.mean(ser["ms"]), "unit": UNIT, "cores": ser["threads"], "kind": "oracle",
-                       "sample": f"serial parity oracle (1 thread) on system {ser['systems']} of the same chain"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": ser["threads"], "kind": "oracle", "sample": sample},
+        "cpu_openmp": {"value": statistics.mean(omp["ms"]) if omp["ms"] else None, "unit": UNIT,
+                       "cores": omp["threads"], "kind": "oracle",
+                       "sample": (f"OpenMP build of the same oracle source (row loops on {omp['threads']} threads, "
+                                  f"timing only) on the same systems {omp['systems']}")},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -379,11 +377,12 @@ def run_gpu(args, rank, ws, local):
     ms_grad, per_grad, _ = timed_loop("grad", args.steps, args.warmup)
     ms_gs, per_gs, _ = timed_loop("gs", args.steps, args.warmup)
     ms_mixed, per_mixed, _ = timed_loop("mixed", args.steps, args.warmup)
-    # error of the mixed-precision result against the FP64 reference state
+    # system 0 (b = s^1, x0 = 0) by mixed precision and by FP64 Alg 1, kept
+    # for the comparison with the oracle's FP64 solution (rank 0, below)
     solve("mixed", 0, lcg.Stats())
-    torch.cuda.synchronize(dev)
-    x_ref = xs[1]
-    mixed_err = float(torch.linalg.norm(work - x_ref) / torch.linalg.norm(x_ref))
+    x_mixed0 = work.cpu().numpy()
+    solve("res", 0, lcg.Stats())
+    x_res0 = work.cpu().numpy()
 
     # roofline of the dominant kernel: the global PCG launch inside Alg 1,
     # timed by CUDA events the library records on the launching stream
@@ -507,7 +506,6 @@ def run_gpu(args, rank, ws, local):
             "inner_iterations": statistics.mean(s["it_global"] for s in per_mixed),
             "refinement_sweeps": statistics.mean(s["restarts"] for s in per_mixed),
             "relres_max": max(s["relres_final"] for s in per_mixed),
-            "err_vs_fp64_reference": mixed_err,
             # the FP32 inner CG inside the global refinement: algorithmic 60 B per
             # cell and inner iteration (FP32 Jacobi-PCG; the scaled kernel moves
             # 52 B), FP64 residual passes at 48 B per cell and sweep, over the
@@ -532,17 +530,36 @@ def run_gpu(args, rank, ws, local):
     if not args.no_heat:
         res["heat_e1"] = {"99x99_100_steps": run_heat(dev, 99, 100), "1024x1024_10_steps": run_heat(dev, 1024, 10)}
     if rank == 0 and not args.no_cpu_baseline:
-        # a bounded sample: the OpenMP build on the chain's first three
-        # systems, the serial oracle on system 1
-        legs = oracle_legs(args.n, 3, [1])
-        omp, ser = legs["omp"], legs["serial"]
+        # the error of the mixed-precision and FP64 results of system 0
+        # against the serial oracle's FP64 Jacobi-PCG solution (relres 1e-12)
+        import numpy as np
+
+        import oracle
+        from oracle.build import build_oracle
+        build_oracle()
+        A0 = oracle.from_stencil(op)
+        x_o, st_o, it_o, rr_o = oracle.pcg(A0, seq.source(1), np.zeros(N), tol=1e-12)
+        n_o = float(np.linalg.norm(x_o))
+        res["local_first_mixed_precision"]["err_vs_fp64_oracle"] = float(np.linalg.norm(x_mixed0 - x_o)) / n_o
+        res["local_first_residual"]["err_vs_fp64_oracle"] = float(np.linalg.norm(x_res0 - x_o)) / n_o
+        res["oracle_reference_solution"] = {
+            "system": 0, "solver": "serial oracle Jacobi-PCG from x0 = 0", "relres": rr_o, "iterations": it_o,
+            "status": st_o}
+        if "aniso3d_256" in res:
+            aniso3d_errors(res["aniso3d_256"])
+        # a bounded sample: the serial oracle on the chain's systems 0 and 1,
+        # the OpenMP build on systems 0, 1, 2
+        legs = oracle_legs(args.n, 2, 3)
+        ser, omp = legs["serial"], legs["omp"]
         res["cpu_baseline"] = {
-            "value": statistics.mean(omp["ms"]), "unit": UNIT, "cores": omp["threads"], "kind": "oracle",
-            "sample": (f"oracle Alg 1 (OpenMP build of the plain FP64 C oracle, row loops on {omp['threads']} threads) "
-                       f"on the full {args.n}x{args.n} systems {omp['systems']} of the same sequence, each from the "
-                       f"oracle's own previous solution"),
-            "serial": {"value": statistics.mean(ser["ms"]), "cores": ser["threads"],
-                       "sample": f"serial parity oracle (1 thread) on system {ser['systems']} of the same chain"}}
+            "value": statistics.mean(ser["ms"]), "unit": UNIT, "cores": ser["threads"], "kind": "oracle",
+            "sample": (f"serial oracle Alg 1 (plain FP64 C, 1 thread) on the full {args.n}x{args.n} systems "
+                       f"{ser['systems']} of the same sequence, each from the oracle's own previous solution"),
+            "openmp": {"value": statistics.mean(omp["ms"]), "cores": omp["threads"],
+                       "sample": (f"OpenMP build of the same oracle source (timing only) on systems "
+                                  f"{omp['systems']}")}}
+    if "aniso3d_256" in res:
+        res["aniso3d_256"].pop("_x", None)
     if rank == 0:
         print(json.dumps(res), flush=True)
 
@@ -693,10 +710,28 @@ def run_aniso3d(dev, n):
     lcg.solve_local_then_global(ctx, gop, b, xm, prm, st)
     out["alg1_mixed"] = {"ms": st.t_total_ms, "K": st.K, "inner_iterations": st.it_global,
                          "relres": st.relres_final,
-                         "global_alg_GBs": N * 64 * st.it_global / (st.t_global_ms * 1e-3) / 1e9,
-                         "rel_diff_vs_fp64": float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))}
+                         "global_alg_GBs": N * 64 * st.it_global / (st.t_global_ms * 1e-3) / 1e9}
     out["speedup_mixed_vs_fp64"] = out["global_fp64"]["ms"] / out["alg1_mixed"]["ms"]
+    # the solutions, for the comparison with the oracle's FP64 solution (rank 0)
+    out["_x"] = {"problem": d, "fp64": x64.cpu().numpy(), "mixed": xm.cpu().numpy()}
     return out
+
+
+def aniso3d_errors(out):
+    """Errors of the 3D FP64 and mixed-precision solutions against the serial
+    oracle's FP64 Jacobi-PCG solution of the same system (relres 1e-10)."""
+    import numpy as np
+
+    import oracle
+    xs = out.pop("_x")
+    d = xs["problem"]
+    A = oracle.from_stencil(d["op"])
+    x_o, st_o, it_o, rr_o = oracle.pcg(A, d["b"], d["x0"], tol=1e-10)
+    n_o = float(np.linalg.norm(x_o))
+    out["global_fp64"]["err_vs_fp64_oracle"] = float(np.linalg.norm(xs["fp64"] - x_o)) / n_o
+    out["alg1_mixed"]["err_vs_fp64_oracle"] = float(np.linalg.norm(xs["mixed"] - x_o)) / n_o
+    out["oracle_reference_solution"] = {"solver": "serial oracle Jacobi-PCG from x0", "relres": rr_o,
+                                        "iterations": it_o, "status": st_o}
 
 
 def run_multigroup(args, dev):

@@ -143,7 +143,11 @@ typedef struct {
 
 /* ---- context and operators ------------------------------------------- */
 
-/* Create a context on CUDA device `device` (sets it current for the call). */
+/* Create a context on CUDA device `device` (sets it current for the call).
+ * lc_ctx_destroy releases the caller's handle; operators and batches created
+ * on the context keep it alive until they are destroyed too, so the handles
+ * may be destroyed in any order (the context's memory is freed with the last
+ * of them).  Using a context handle after lc_ctx_destroy is an error. */
 LC_EXPORT int lc_ctx_create(lc_ctx **ctx, int device);
 LC_EXPORT int lc_ctx_destroy(lc_ctx *ctx);
 
@@ -283,6 +287,22 @@ LC_EXPORT int lc_batch_replay(lc_batch *batch, void *stream);
  * Returns the first non-OK system status, else LC_OK. */
 LC_EXPORT int lc_batch_stats(lc_batch *batch, lc_stats *per_system, void *stream);
 
+/* The local domain and subsystem of system `sys` (0 .. nsys-1) from the
+ * last lc_batch_solve / lc_batch_replay, for inspection: waits for `stream`,
+ * then copies into caller DEVICE buffers (each may be NULL to skip it)
+ *   mask[n]        the final mask (0/1) after thresholding and dilation
+ *   g2l[n]         local index of each cell, -1 outside the domain
+ *   l2g[K]         cell of each local index (ascending)
+ *   rowptr[K+1], col[nnzB], val[nnzB]   B = A[Omega, Omega] in local indices
+ *   rhs[K]         b_B - E x_C^(0) in the canonical order (Eq. loc-equ)
+ * with n = nx[sys] ny[sys] and K, nnzB as lc_batch_stats reports them.
+ * These are the same bits lc_mark_residual and lc_extract produce for the
+ * system (Sec. 2.3, Eq. loc-equ).  The subsystem's starting values x0[Omega]
+ * are not kept (the local solve overwrites them).  Synchronous; invalid
+ * `sys` returns LC_ERR_INVALID_ARG. */
+LC_EXPORT int lc_batch_domain(lc_batch *batch, int32_t sys, uint8_t *mask, int32_t *g2l, int32_t *l2g,
+                              int32_t *rowptr, int32_t *col, double *val, double *rhs, void *stream);
+
 /* Launch-shape knobs (for the autotuner): "block" = 256 | 512 | 1024 threads
  * per CTA (default 512); "ctas_per_sm" = 0 (as many as fit) .. 32. */
 LC_EXPORT int lc_batch_set_tuning(lc_batch *batch, const char *key, int32_t value);
@@ -320,6 +340,24 @@ LC_EXPORT int lc_op_refresh(lc_op *op, void *stream);
  * arrays device, N values. */
 LC_EXPORT int lc_adjoint_grad_k_2d(lc_ctx *ctx, const int32_t shape[2], const double *k, const double *x,
                                    const double *lam, double *dk, void *stream);
+
+/* The whole backward step of x = A(k)^-1 b in one call, for a loss L(x)
+ * with gradient gx = dL/dx at the forward solution x:
+ *   1. A(k) is assembled again from k and dt into the operator's own
+ *      coefficient arrays (lc_assemble_diffusion_2d + lc_op_refresh): no
+ *      state of the forward solve is kept;
+ *   2. lambda solves A lambda = gx by Alg 1 with parameters p (A is
+ *      symmetric, so this is the adjoint A^T lambda = dL/dx); lambda holds
+ *      the starting iterate on entry (e.g. zeros) and dL/db on return;
+ *   3. dk = dL/dk per cell by lc_adjoint_grad_k_2d.
+ * op must be a 2D stencil operator created on the D, Tx, Ty arrays that
+ * lc_assemble_diffusion_2d fills for this grid (the call rewrites them with
+ * the same values for the same k and dt); k, x, gx, lambda, dk are device
+ * arrays of N values.  stats (host, may be NULL) are the adjoint solve's and
+ * wait for the stream; errors as lc_solve_local_then_global.  The paper has
+ * no adjoint: this is the training form of the method's solve. */
+LC_EXPORT int lc_adjoint_grad(lc_ctx *ctx, lc_op *op, const double *k, double dt, const double *x, const double *gx,
+                              double *lambda, double *dk, const lc_params *p, lc_stats *stats, void *stream);
 
 /* Self-test of the failure path of the grid-wide waits: a cooperative launch
  * of `blocks` blocks on the operator's control block whose barrier waits for

@@ -372,6 +372,20 @@ def solve_local_then_global(ctx: Context, op: _Operator, b, x, params: Params, s
                                                       _stream(stream)), allow)
 
 
+def adjoint_grad(ctx: Context, op: "StencilOperator", k, dt: float, x, gx, lam, dk, params: Params,
+                 stats: Stats | None = None, stream=None):
+    """lc_adjoint_grad: re-assembles A(k) into op's arrays, solves A lam = gx by
+    Alg 1 (lam: start in, dL/db out) and writes dL/dk into dk."""
+    L = lib()
+    vp = C.c_void_p
+    L.lc_adjoint_grad.argtypes = [vp, vp, vp, C.c_double, vp, vp, vp, vp, C.POINTER(Params), C.POINTER(Stats), vp]
+    return ctx.check(L.lc_adjoint_grad(ctx.h, op.h, _ptr(k, torch.float64, "k"), float(dt),
+                                       _ptr(x, torch.float64, "x"), _ptr(gx, torch.float64, "gx"),
+                                       _ptr(lam, torch.float64, "lam"), _ptr(dk, torch.float64, "dk"),
+                                       C.byref(params), C.byref(stats) if stats is not None else None,
+                                       _stream(stream)))
+
+
 def kernel_launch_count() -> int:
     """Kernels this library has launched in this process (lc_kernel_launch_count)."""
     return int(lib().lc_kernel_launch_count())
@@ -474,6 +488,31 @@ class Batch:
         allow = (LC_ERR_NOT_CONVERGED, LC_ERR_BREAKDOWN) if allow_not_converged else ()
         self.ctx.check(lib().lc_batch_stats(self.h, st, _stream(stream)), allow)
         return [s.as_dict() for s in st]
+
+    def domain(self, sys: int, stream=None) -> dict:
+        """lc_batch_domain: system `sys`'s final mask and local subsystem
+        (g2l, l2g, rowptr, col, val, rhs) from the last solve, as CPU numpy
+        arrays."""
+        st = self.stats(stream, allow_not_converged=True)[sys]
+        n, K, nz = self.sizes[sys], st["K"], st["nnzB"]
+        dev = self.D.device
+        out = {"mask": torch.empty(n, dtype=torch.uint8, device=dev),
+               "g2l": torch.empty(n, dtype=torch.int32, device=dev),
+               "l2g": torch.empty(max(K, 1), dtype=torch.int32, device=dev),
+               "rowptr": torch.empty(K + 1, dtype=torch.int32, device=dev),
+               "col": torch.empty(max(nz, 1), dtype=torch.int32, device=dev),
+               "val": torch.empty(max(nz, 1), dtype=torch.float64, device=dev),
+               "rhs": torch.empty(max(K, 1), dtype=torch.float64, device=dev)}
+        L = lib()
+        L.lc_batch_domain.argtypes = [C.c_void_p, C.c_int32] + [C.c_void_p] * 8
+        self.ctx.check(L.lc_batch_domain(self.h, sys, *[out[k].data_ptr() for k in
+                                                        ("mask", "g2l", "l2g", "rowptr", "col", "val", "rhs")],
+                                         _stream(stream)))
+        torch.cuda.synchronize(dev)
+        res = {k: v.cpu().numpy() for k, v in out.items()}
+        res["l2g"], res["rhs"] = res["l2g"][:K], res["rhs"][:K]
+        res["col"], res["val"] = res["col"][:nz], res["val"][:nz]
+        return res
 
     def set_tuning(self, key: str, value: int):
         return self.ctx.check(lib().lc_batch_set_tuning(self.h, key.encode(), int(value)))

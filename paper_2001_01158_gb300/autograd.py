@@ -4,10 +4,10 @@ conductivity k and the right-hand side b.
 
 Forward: assemble A(k) on the GPU (lc_assemble_diffusion_2d), refresh the
 operator's derived data, solve by Alg 1 (lc_solve_local_then_global).  Only
-k and x are saved.  Backward: re-assemble A(k) (recomputed, not stored: no
-Krylov state is kept from the forward), solve the adjoint A lambda = dL/dx
-on the same local-then-global path (A is symmetric), then
-dL/db = lambda and dL/dk from the adjoint kernel (lc_adjoint_grad_k_2d).
+k and x are saved.  Backward: one lc_adjoint_grad call, which re-assembles
+A(k) (recomputed, not stored: no Krylov state is kept from the forward),
+solves the adjoint A lambda = dL/dx on the same local-then-global path (A is
+symmetric) and forms dL/db = lambda and dL/dk with the adjoint kernel.
 """
 from __future__ import annotations
 
@@ -15,7 +15,7 @@ import ctypes as C
 
 import torch
 
-from . import (Context, Params, StencilOperator, Stats, _ptr, _stream, default_params, lib,
+from . import (Context, Params, StencilOperator, Stats, _ptr, _stream, adjoint_grad, default_params, lib,
                solve_local_then_global)
 
 __all__ = ["DiffusionSolve", "diffusion_solve"]
@@ -86,13 +86,14 @@ class DiffusionSolve(torch.autograd.Function):
     def backward(ctx, gx):
         k, x = ctx.saved_tensors
         a = _assembled(k)
-        op = a.assemble(k, ctx.dt)            # A(k) recomputed, not stored
+        if a.op is None:
+            a.assemble(k, ctx.dt)
         g = gx.detach().contiguous().view(-1)
         lam = torch.zeros_like(g)
-        solve_local_then_global(a.ctx, op, g, lam, ctx.params)
         dk = torch.empty_like(lam)
-        sh = (C.c_int32 * 2)(*a.shape)
-        a.ctx.check(lib().lc_adjoint_grad_k_2d(a.ctx.h, sh, _ptr(k), _ptr(x), _ptr(lam), _ptr(dk), _stream(None)))
+        st = Stats()
+        adjoint_grad(a.ctx, a.op, k, ctx.dt, x, g, lam, dk, ctx.params, st)   # A(k) recomputed inside
+        ctx.adjoint_stats = st.as_dict()
         return dk.view_as(k), lam.view_as(k), None, None, None
 
 

@@ -26,7 +26,18 @@ struct lc_ctx {
     int device = 0;
     int sms = 0;
     std::string err;
+    // one reference held by the caller (released by lc_ctx_destroy) and one
+    // per operator or batch created on the context: whichever release comes
+    // last frees it, so the destruction order does not matter
+    std::atomic<int> refs{1};
 };
+
+namespace {
+void ctx_ref(lc_ctx *c) { c->refs.fetch_add(1, std::memory_order_relaxed); }
+void ctx_unref(lc_ctx *c) {
+    if (c && c->refs.fetch_sub(1, std::memory_order_acq_rel) == 1) delete c;
+}
+}  // namespace
 
 struct lc_op {
     lc_ctx *ctx = nullptr;
@@ -521,6 +532,7 @@ int lc_batch_create(lc_ctx *ctx, lc_batch **out, int32_t nsys, const int32_t *nx
     lc_batch *bt = new (std::nothrow) lc_batch;
     if (!bt) return LC_ERR_NO_MEMORY;
     bt->ctx = ctx;
+    ctx_ref(ctx);
     bt->nsys = nsys;
     bt->cells = cells;
     bt->nx.assign(nx, nx + nsys);
@@ -529,7 +541,8 @@ int lc_batch_create(lc_ctx *ctx, lc_batch **out, int32_t nsys, const int32_t *nx
     batch_carve(bt, probe);
     if (cudaMalloc(&bt->arena, probe.off) != cudaSuccess) {
         cudaGetLastError();
-        delete bt;
+        bt->arena = nullptr;
+        lc_batch_destroy(bt);
         return fail(ctx, LC_ERR_NO_MEMORY, "batch workspace of %zu bytes", probe.off);
     }
     Carver real;
@@ -568,7 +581,9 @@ int lc_batch_destroy(lc_batch *bt) {
     if (bt->exec) cudaGraphExecDestroy(bt->exec);
     if (bt->graph) cudaGraphDestroy(bt->graph);
     if (bt->arena) cudaFree(bt->arena);
+    lc_ctx *ctx = bt->ctx;
     delete bt;
+    ctx_unref(ctx);
     return LC_OK;
 }
 
@@ -657,6 +672,33 @@ int lc_batch_stats(lc_batch *bt, lc_stats *per_system, void *stream) {
         if (st.status != LC_OK && worst == LC_OK) worst = st.status;
     }
     return worst;
+}
+
+int lc_batch_domain(lc_batch *bt, int32_t sys, uint8_t *mask, int32_t *g2l, int32_t *l2g, int32_t *rowptr,
+                    int32_t *col, double *val, double *rhs, void *stream) {
+    if (!bt) return LC_ERR_INVALID_ARG;
+    if (sys < 0 || sys >= bt->nsys) return fail(bt->ctx, LC_ERR_INVALID_ARG, "system index out of range");
+    lc_ctx *ctx = bt->ctx;
+    LC_CUDA(ctx, cudaSetDevice(ctx->device));
+    LC_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+    const lc::BatchView &v = bt->L.v;
+    int64_t off = 0;
+    for (int32_t t = 0; t < sys; ++t) off += (int64_t)bt->nx[t] * bt->ny[t];
+    const size_t n = (size_t)bt->nx[sys] * bt->ny[sys];
+    int32_t kn[2];   // K, nnz(B) of the last solve
+    LC_CUDA(ctx, cudaMemcpy(kn, v.stat_i + 8 * (int64_t)sys + 1, sizeof kn, cudaMemcpyDeviceToHost));
+    const size_t K = (size_t)kn[0], nz = (size_t)kn[1];
+    // after `layers` dilation rounds the batched kernel's mask is in m0 for an even count, else m1
+    const uint8_t *m = (bt->L.p.layers % 2 == 0) ? v.m0 : v.m1;
+    const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+    if (mask) LC_CUDA(ctx, cudaMemcpy(mask, m + off, n, dd));
+    if (g2l) LC_CUDA(ctx, cudaMemcpy(g2l, v.g2l + off, sizeof(int32_t) * n, dd));
+    if (l2g && K) LC_CUDA(ctx, cudaMemcpy(l2g, v.l2g + off, sizeof(int32_t) * K, dd));
+    if (rowptr) LC_CUDA(ctx, cudaMemcpy(rowptr, v.rowptr + off + sys, sizeof(int32_t) * (K + 1), dd));
+    if (col && nz) LC_CUDA(ctx, cudaMemcpy(col, v.col + 5 * off, sizeof(int32_t) * nz, dd));
+    if (val && nz) LC_CUDA(ctx, cudaMemcpy(val, v.val + 5 * off, sizeof(double) * nz, dd));
+    if (rhs && K) LC_CUDA(ctx, cudaMemcpy(rhs, v.rhs + off, sizeof(double) * K, dd));
+    return LC_OK;
 }
 
 int lc_batch_set_tuning(lc_batch *bt, const char *key, int32_t value) {
@@ -770,7 +812,7 @@ int lc_ctx_create(lc_ctx **out, int device) {
 }
 
 int lc_ctx_destroy(lc_ctx *ctx) {
-    delete ctx;
+    ctx_unref(ctx);
     return LC_OK;
 }
 
@@ -791,6 +833,7 @@ int lc_op_create_stencil(lc_ctx *ctx, lc_op **out, int32_t dim, const int32_t sh
     lc_op *op = new (std::nothrow) lc_op;
     if (!op) return LC_ERR_NO_MEMORY;
     op->ctx = ctx;
+    ctx_ref(ctx);
     op->kind = 0;
     op->n = n;
     op->nnz = nnz;
@@ -843,6 +886,7 @@ int lc_op_create_csr(lc_ctx *ctx, lc_op **out, int32_t n, int64_t nnz, const int
     lc_op *op = new (std::nothrow) lc_op;
     if (!op) return LC_ERR_NO_MEMORY;
     op->ctx = ctx;
+    ctx_ref(ctx);
     op->kind = 1;
     op->pcg_minblocks = 4;   // 64 registers, no spills: 32 warps per SM for the row-per-thread SpMV
     op->n = n;
@@ -872,7 +916,9 @@ int lc_op_destroy(lc_op *op) {
     if (op->ctx) cudaSetDevice(op->ctx->device);
     for (auto &ev : op->ev) if (ev) cudaEventDestroy(ev);
     if (op->arena) cudaFree(op->arena);
+    lc_ctx *ctx = op->ctx;
     delete op;
+    ctx_unref(ctx);
     return LC_OK;
 }
 
@@ -1148,6 +1194,26 @@ int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const double *b, do
     stats->status = st;
     if (st == LC_ERR_TIMEOUT) return fail(ctx, LC_ERR_TIMEOUT, "grid barrier timed out");
     return st;
+}
+
+int lc_adjoint_grad(lc_ctx *ctx, lc_op *op, const double *k, double dt, const double *x, const double *gx,
+                    double *lambda, double *dk, const lc_params *p, lc_stats *stats, void *stream) {
+    int rc = check_common(ctx, op);
+    if (rc) return rc;
+    if (!k || !x || !gx || !lambda || !dk || !p) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
+    if (op->kind != 0 || op->st.dim != 2)
+        return fail(ctx, LC_ERR_INVALID_ARG, "the adjoint needs a 2D stencil operator of lc_assemble_diffusion_2d");
+    const int32_t shape[2] = {op->st.nx, op->st.ny};
+    // A(k) recomputed from k into the operator's own coefficient arrays (no
+    // state of the forward solve is kept), then its derived data
+    if ((rc = lc_assemble_diffusion_2d(ctx, shape, k, dt, const_cast<double *>(op->st.D),
+                                       const_cast<double *>(op->st.Tx), const_cast<double *>(op->st.Ty), stream)))
+        return rc;
+    if ((rc = lc_op_refresh(op, stream))) return rc;
+    // A lambda = dL/dx on the local-then-global path (A is symmetric)
+    rc = lc_solve_local_then_global(ctx, op, gx, lambda, p, stats, stream);
+    if (rc) return rc;
+    return lc_adjoint_grad_k_2d(ctx, shape, k, x, lambda, dk, stream);
 }
 
 }  // extern "C"

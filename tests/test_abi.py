@@ -1,5 +1,6 @@
 """The C-ABI library builds, loads and exports every entry point that
-include/*.h declares (CPU only: no compute calls)."""
+include/*.h declares (CPU only: no compute calls), plus one GPU-marked test
+of the handles' lifetimes."""
 import ctypes as C
 import glob
 import os
@@ -92,3 +93,27 @@ def test_noalloc_binding_rejects_a_3d_shape_without_z_faces():
         lcg.mark_residual_stencil_noalloc((4, 3, 2), t, t, t, None, t, t,
                                           lcg.MarkParams(lcg.THR_REL_MAX, 1e-3, lcg.EXP_NONE, 0),
                                           torch.zeros(1, dtype=torch.uint8), t, torch.zeros(1, dtype=torch.int32))
+
+
+@pytest.mark.gpu
+def test_context_may_be_destroyed_before_its_operators():
+    """Handles are released in any order: an operator destroyed after its
+    context (as a garbage collector may order them) still finds the context
+    it was created on; no CUDA error is left behind for a later call."""
+    import torch
+    lcg.build()
+    L = lcg.lib()
+    ctx = C.c_void_p()
+    assert L.lc_ctx_create(C.byref(ctx), 0) == 0
+    n = 16
+    D = torch.full((n,), 4.0, dtype=torch.float64, device="cuda")
+    T = torch.ones(n, dtype=torch.float64, device="cuda")
+    sh = (C.c_int32 * 3)(4, 4, 1)
+    op = C.c_void_p()
+    assert L.lc_op_create_stencil(ctx, C.byref(op), 2, sh, C.c_void_p(D.data_ptr()), C.c_void_p(T.data_ptr()),
+                                  C.c_void_p(T.data_ptr()), None) == 0
+    assert L.lc_ctx_destroy(ctx) == 0
+    assert L.lc_op_destroy(op) == 0
+    # a new context and operator are created without inheriting an error
+    ctx2 = lcg.Context(0)
+    lcg.StencilOperator(ctx2, (4, 4, 1), D, T, T)

@@ -1,6 +1,7 @@
 """The differentiable solve: operator assembly from conductivity, and the
 adjoint gradients dL/dk, dL/db through torch.autograd, against central
-finite differences (32x32) and against the oracle's FP64 gradient (1024^2).
+finite differences (32x32) and against the oracle's FP64 gradient (1024^2), and
+the single-call lc_adjoint_grad against the oracle.
 The oracle side computes its own states and adjoints with its own solver."""
 import numpy as np
 import pytest
@@ -99,3 +100,42 @@ def test_adjoint_gradient_matches_oracle_at_1024():
     assert np.linalg.norm(dk - dk_o) <= 1e-6 * np.linalg.norm(dk_o)
     assert np.linalg.norm(db - lam_o) <= 1e-6 * np.linalg.norm(lam_o)
     assert float(L.detach()) == pytest.approx(float(((x_o - xt_o) ** 2).sum()), rel=1e-8)
+
+
+@pytest.mark.parametrize("ny,nx", [(80, 96), (33, 1)])
+def test_lc_adjoint_grad_single_call_matches_oracle(ny, nx):
+    """lc_adjoint_grad (re-assembly of A(k), Alg 1 adjoint solve, dL/dk in one
+    C-ABI call) against the oracle's own state, adjoint and gradient, for
+    L = ||x - x_t||^2 with a random x_t."""
+    lcg.build()
+    ctx = lcg.Context(0)
+    rng = np.random.default_rng(ny + nx)
+    k = np.exp(rng.uniform(-1, 2, (ny, nx)))
+    dt = 0.5
+    b = rng.standard_normal(nx * ny)
+    x_t = rng.standard_normal(nx * ny)
+    tol = 1e-12
+    A = oracle.from_stencil(gen.operator_2d(k, dt))
+    z = np.zeros(nx * ny)
+    x_o, s1, _, _ = oracle.pcg(A, b, z, tol=tol)
+    g = 2.0 * (x_o - x_t)
+    lam_o, s2, _, _ = oracle.pcg(A, g, z, tol=tol)
+    assert s1 == s2 == oracle.OK
+    dk_o = oracle.adjoint_grad_k_2d(nx, ny, k.ravel(), x_o, lam_o)
+    # the operator on arrays that lc_assemble_diffusion_2d fills; the adjoint
+    # call re-assembles them itself (here from deliberately wrong contents)
+    D, Tx, Ty = (cu(np.ones(nx * ny)) for _ in range(3))
+    Tx.fill_(0.5)
+    Ty.fill_(0.5)
+    op = lcg.StencilOperator(ctx, (nx, ny, 1), D, Tx, Ty)
+    lam = cu(z)
+    dk = cu(z)
+    st = lcg.Stats()
+    lcg.adjoint_grad(ctx, op, cu(k), dt, cu(x_o), cu(g), lam, dk, lcg.default_params(tol=tol), st)
+    torch.cuda.synchronize()
+    assert st.status == 0 and st.relres_final <= tol
+    lam_g, dk_g = lam.cpu().numpy(), dk.cpu().numpy()
+    assert np.linalg.norm(lam_g - lam_o) <= 1e-9 * np.linalg.norm(lam_o)
+    assert np.linalg.norm(dk_g - dk_o) <= 1e-9 * np.linalg.norm(dk_o)
+    ref = gen.operator_2d(k, dt)   # the operator's arrays now hold A(k)
+    assert np.array_equal(D.cpu().numpy().view(np.int64), np.ascontiguousarray(ref.D).view(np.int64))

@@ -1,8 +1,9 @@
-"""Failure detection on the GPU without a fault: a grid barrier that cannot
+"""Failure detection on the GPU without a fault.  A grid barrier that cannot
 complete (one arrival more than there are blocks) gives up after its short
 limit, every block records LC_ERR_TIMEOUT and returns, the host reads the
 status, and the context keeps working (a solve right after matches the
-oracle)."""
+oracle).  Krylov breakdown on host-made inputs (NaN in b, an indefinite
+operator) is reported as LC_ERR_BREAKDOWN, as the oracle reports it."""
 import time
 
 import numpy as np
@@ -39,3 +40,65 @@ def test_barrier_timeout_is_reported_and_context_survives():
     assert s.status == 0 and oracle.relres(A, b, x.cpu().numpy()) <= 1e-8
     with pytest.raises(lcg.LcError):
         lcg.selftest_barrier_timeout(ctx, gop, 4, 5000.0)   # limit above 2 s refused
+
+
+def _indefinite(op):
+    """The same stencil with its diagonal shrunk to 0.3 x the sum of the
+    row's face conductances: positive diagonal, symmetric, indefinite."""
+    import copy
+    A = oracle.from_stencil(op)
+    Ad = A.dense()
+    off = np.abs(Ad).sum(1) - np.abs(np.diag(Ad))
+    op2 = copy.copy(op)
+    op2.D = 0.3 * off
+    return op2
+
+
+@pytest.mark.parametrize("kind", ["stencil", "csr"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_krylov_breakdown_is_reported_and_context_survives(kind, precision):
+    """Krylov breakdown (p^T A p <= 0 or not finite) on host-made inputs: a NaN
+    in b, and an indefinite operator with a positive diagonal.  The oracle's
+    Jacobi-PCG breaks down on both (checked first); lc_pcg_solve and
+    lc_solve_local_then_global return LC_ERR_BREAKDOWN, and a solve on the
+    same context right after is correct."""
+    lcg.build()
+    ctx = lcg.Context(0)
+    cu = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=DEV)  # noqa: E731
+    op = gen.random_stencil_2d(5, 40, 30)
+    bad = _indefinite(op)
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal(op.n)
+    b_nan = b.copy()
+    b_nan[17] = np.nan
+
+    def make(o):
+        if kind == "stencil":
+            return lcg.StencilOperator(ctx, o.shape, cu(o.D), cu(o.Tx), cu(o.Ty))
+        A = oracle.from_stencil(o)
+        return lcg.CsrOperator(ctx, cu(A.rowptr, torch.int32), cu(A.col, torch.int32), cu(A.val))
+
+    good_op, bad_op = make(op), make(bad)
+    prec = lcg.PREC_FP64 if precision == "fp64" else lcg.PREC_MIXED
+    sp = lcg.SolveParams(1e-8, 2000, prec, 1e-4 if prec == lcg.PREC_MIXED else 0.0, 30)
+    prm = lcg.default_params(tol=1e-8, max_iter=2000, precision=prec, inner_tol=1e-4)
+    for A_case, gop, bb in ((oracle.from_stencil(op), good_op, b_nan), (oracle.from_stencil(bad), bad_op, b)):
+        _, st_o, _, _ = oracle.pcg(A_case, bb, np.zeros(op.n), tol=1e-8, maxit=2000)
+        assert st_o == oracle.BREAKDOWN
+        _, sr, _ = oracle.solve_local_then_global(A_case, bb, np.zeros(op.n), tol=1e-8, maxit=2000)
+        assert sr["status"] == oracle.BREAKDOWN
+        # (the status is read back when stats are asked for; without them the calls are asynchronous)
+        for call in (lambda x, s: lcg.pcg_solve(ctx, gop, cu(bb), x, sp, s),
+                     lambda x, s: lcg.solve_local_then_global(ctx, gop, cu(bb), x, prm, s)):
+            s = lcg.Stats()
+            with pytest.raises(lcg.LcError) as e:
+                call(cu(np.zeros(op.n)), s)
+            assert e.value.code == lcg.LC_ERR_BREAKDOWN and s.status == lcg.LC_ERR_BREAKDOWN
+    # the context and a good operator still work
+    A = oracle.from_stencil(op)
+    for call in (lambda x, s: lcg.pcg_solve(ctx, good_op, cu(b), x, sp, s),
+                 lambda x, s: lcg.solve_local_then_global(ctx, good_op, cu(b), x, prm, s)):
+        x = cu(np.zeros(op.n))
+        s = lcg.Stats()
+        call(x, s)
+        assert s.status == 0 and oracle.relres(A, b, x.cpu().numpy()) <= 1e-8

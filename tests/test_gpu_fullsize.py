@@ -6,9 +6,9 @@ times (the operators' default tuning):
   whole of Alg 1 against the oracle (masks and subsystem bit for bit, the
   solution within 1e-9, relres by the oracle); gradient marking bit for bit.
 - 256^3 anisotropic 3D: marking and subsystem bit for bit; the FP64 and the
-  mixed-precision solves to relres 1e-10, evaluated by the oracle, and the
-  mixed result's difference from the FP64 one (the oracle's own FP64 solve of
-  16.7 M unknowns is too slow for a test; its relres evaluation is not).
+  mixed-precision solves to relres 1e-10, evaluated by the oracle, and both
+  solutions against the oracle's own serial FP64 Jacobi-PCG solution of the
+  16.7 M unknowns (FP64 within 1e-9, mixed precision within 1e-7).
 """
 import numpy as np
 import pytest
@@ -120,5 +120,13 @@ def test_aniso256_marking_and_solves(ctx):
     x64h, xmh = x64.cpu().numpy(), xm.cpu().numpy()
     assert oracle.relres(A, d["b"], x64h) <= 1e-10
     assert oracle.relres(A, d["b"], xmh) <= 1e-10
-    # both meet relres 1e-10; their difference is bounded by the conditioning
-    assert np.linalg.norm(xmh - x64h) / np.linalg.norm(x64h) <= 1e-7
+    # against the oracle's own FP64 Jacobi-PCG solution (serial, same
+    # tolerance): the FP64 solve runs the same algorithm, so it tracks the
+    # oracle's iterates (1e-9); the mixed-precision Alg 1 result meets the
+    # same residual by another path, its error is bounded by the conditioning
+    xo, so, _, _ = oracle.pcg(A, d["b"], d["x0"], tol=1e-10)
+    assert so == oracle.OK
+    no = np.linalg.norm(xo)
+    e64, em = np.linalg.norm(x64h - xo) / no, np.linalg.norm(xmh - xo) / no
+    assert e64 <= 1e-9, e64
+    assert em <= 1e-7, em

@@ -2,7 +2,7 @@
 diffusion systems, Sec. 3.3, on synthetic data): 64 group systems on one
 88 x 80 mesh with a shared sparsity pattern, solved together by the batched
 Alg 1 (one launch) and compared group by group with the oracle: the local
-domain and subsystem sizes equal the oracle's, each group reaches relres
+domain and the subsystem equal the oracle's bit for bit, each group reaches relres
 1e-8 (evaluated by the oracle), and its distance to the oracle's FP64
 solution is bounded."""
 import numpy as np
@@ -45,6 +45,13 @@ def test_multigroup_batched_matches_oracle(groups):
                                                    exp_mode=oracle.EXP_DILATE, exp_rounds=2, tol=tol)
         assert st[g]["K"] == sr["K"] > 0 and st[g]["nnzB"] == sr["nnzB"], g
         assert st[g]["tau"] == sr["tau"], g
+        m = oracle.mark_residual(A, d["b"], d["x0"], oracle.THR_REL_MAX, 1e-3, oracle.EXP_DILATE, 2)
+        ex = oracle.extract(A, m["mask"], d["b"], d["x0"])
+        dom = batch.domain(g)
+        assert np.array_equal(dom["mask"], m["mask"]) and np.array_equal(dom["g2l"], ex["g2l"]), g
+        assert np.array_equal(dom["col"], ex["B"].col) and np.array_equal(dom["rowptr"], ex["B"].rowptr), g
+        assert np.array_equal(dom["val"].view(np.int64), ex["B"].val.view(np.int64)), g
+        assert np.array_equal(dom["rhs"].view(np.int64), ex["rhs"].view(np.int64)), g
         xg = xs[batch.offsets[g]:batch.offsets[g + 1]]
         assert oracle.relres(A, d["b"], xg) <= tol, g
         assert np.linalg.norm(xg - xr) <= 1e-6 * np.linalg.norm(xr), g
