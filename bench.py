@@ -524,6 +524,7 @@ def run_gpu(args, rank, ws, local):
         res["batched_512"] = run_batched(args, rank, dev, ws)
     if not args.no_batched:
         res["multigroup_64"] = run_multigroup(args, dev)
+        res["batched_8_largest"] = run_batched_largest(args, dev)
     if not args.no_batched:
         res["csr_3t_1024"] = run_csr3t(dev, 1024)
         res["aniso3d_256"] = run_aniso3d(dev, 256)
@@ -734,6 +735,18 @@ def aniso3d_errors(out):
                                         "iterations": it_o, "status": st_o}
 
 
+def run_batched_largest(args, dev):
+    """The 8 largest systems of the 512-system workload (sides 500..512) as a
+    batch of their own: a batch whose time is one large system's, where the
+    autotuner's thread-block clusters (several SMs per system) pay."""
+    import numpy as np
+
+    import gen
+    items = gen.cfg4_batch(seed=0)
+    big = np.argsort([-d["op"].n for d in items])[:8]
+    return batched_items([items[i] for i in big], dev, max(3, min(args.steps, 10)))
+
+
 def run_multigroup(args, dev):
     """Multi-group stand-in (64 group systems on one 88 x 80 mesh with a
     shared pattern, Sec. 3.3's structure): one source iteration's 64 solves
@@ -741,6 +754,28 @@ def run_multigroup(args, dev):
     global FP64 PCG."""
     import gen
     return batched_items(gen.mg_standin(seed=0), dev, max(3, min(args.steps, 10)), seq_alg1=True)
+
+
+def batched_roofline(stats, ms):
+    """Algorithmic bytes of one batched launch over its time.  Per system of
+    n cells, K local rows, nnz(B) entries: marking 48 B (residual) + 9 B
+    (threshold and two layers) + 5 B (compaction) per cell, 130 B per local
+    row (gather); the local refinement: 60 B per row plus 8 B per entry of B
+    per FP32 inner iteration, 32 B per row plus 12 B per entry per FP64
+    residual sweep (two sweeps assumed); the global refinement: 60 B per cell
+    per FP32 inner iteration (FP32 Jacobi-PCG on the stencil), 48 B per cell
+    per FP64 residual pass (sweeps + 1) and 16 B per cell per x update."""
+    byts = 0.0
+    for s in stats:
+        n, K, nz = s["n"], s["K"], s["nnzB"]
+        sweeps = s["restarts"]
+        byts += n * (48 + 9 + 5) + 130 * K
+        byts += s["it_local"] * (60 * K + 8 * nz) + 2 * (32 * K + 12 * nz)
+        byts += n * (60 * s["it_global"] + 48 * (sweeps + 1) + 16 * sweeps)
+    peak, kind = measured_peaks()
+    achieved = byts / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "alg_bytes": byts, "peak_source": f"{kind} hbm_gbs", "kernel": "batched_kernel (whole batch, one launch)"}
 
 
 def batched_items(items, dev, reps, seq_alg1=False):
@@ -801,7 +836,8 @@ def batched_items(items, dev, reps, seq_alg1=False):
            "eta_mean": statistics.mean(s["eta"] for s in st),
            "relres_max": max(s["relres_final"] for s in st), "all_converged": all(s["status"] == 0 for s in st),
            "inner_iterations_mean": statistics.mean(s["it_global"] for s in st),
-           "autotuned": {"block": cfg["block"], "ctas_per_sm": cfg["ctas_per_sm"]},
+           "autotuned": {k: cfg[k] for k in ("block", "ctas_per_sm", "cluster", "big_cells")},
+           "roofline": batched_roofline(st, ms_batched),
            "launch": "one persistent kernel, CUDA-graph replay"}
     if seq_alg1:
         prm64 = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8)

@@ -304,7 +304,12 @@ LC_EXPORT int lc_batch_domain(lc_batch *batch, int32_t sys, uint8_t *mask, int32
                               int32_t *rowptr, int32_t *col, double *val, double *rhs, void *stream);
 
 /* Launch-shape knobs (for the autotuner): "block" = 256 | 512 | 1024 threads
- * per CTA (default 512); "ctas_per_sm" = 0 (as many as fit) .. 32. */
+ * per CTA (default 512); "ctas_per_sm" = 0 (as many as fit) .. 32;
+ * "cluster" = 1 | 2 | 4 | 8 | 16 CTAs per thread-block cluster (default 1: every
+ * system on one CTA); "big_cells" (default 65536): with clusters, every
+ * system of at least this many cells is solved by a whole cluster (its rows
+ * split among the cluster's CTAs), the others by one CTA each.  Results do
+ * not depend on the knobs beyond the rounding order of the solves' sums. */
 LC_EXPORT int lc_batch_set_tuning(lc_batch *batch, const char *key, int32_t value);
 
 /* ---- operators from conductivity, and the adjoint -----------------------------
@@ -480,6 +485,12 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  *       phase, which loads p_k anyway (for p_k+1 = r + beta p_k), and after
  *       the last iteration by one extra pass: 8 fewer bytes per cell and
  *       iteration, the same operations in the same order (bit-identical x).
+ *   "csr_store_p"   0 or 1 (default 1): the global solve of a CSR operator
+ *       forms p = z + beta p_old once per row, stores it and, after one more
+ *       grid barrier, reads it at the columns of the product; with 0 every
+ *       entry recomputes p at its column (two loads and two FP64 FMAs per
+ *       entry, no extra barrier).  The same arithmetic per value of p: the
+ *       iterates are bit-identical.  Extracted subsystems always recompute. 
  *   "local_single"  0 or 1 (default 0): the FP64 local solve of
  *       lc_solve_local_then_global takes one grid-wide reduction per CG
  *       iteration (Chronopoulos-Gear arrangement: same iterates in exact

@@ -1,23 +1,33 @@
-"""Autotuner for the batched launch: picks the CTA size and the number of
-CTAs per SM by timing CUDA-graph replays of the batch's own solve, and
-caches the choice in a JSON file keyed by the GPU and the batch's size class.
+"""Autotuner for the batched launch: picks the CTA size, whether the large
+systems run on thread-block clusters (and of how many CTAs), and the size
+from which a system counts as large, by timing CUDA-graph replays of the
+batch's own solve; caches the choice in a JSON file keyed by the GPU and the
+batch's size class.
 
     from paper_2001_01158_gb300.autotune import tune_batch
     cfg = tune_batch(batch, b, x0, params)      # applies the best config
 
-The cache file defaults to ~/.cache/lc_autotune.json (LC_AUTOTUNE_CACHE
-overrides it).  A cached choice is applied without timing.
+Each candidate is timed as the median of several replays.  Among the
+candidates within `slack` (3 %) of the fastest, the first in CANDIDATES
+order wins, so that timing noise between runs does not flip the choice
+between near-equal configurations.  The cache file defaults to
+~/.cache/lc_autotune.json (LC_AUTOTUNE_CACHE overrides it).  A cached choice
+is applied without timing.
 """
 from __future__ import annotations
 
 import json
 import math
 import os
+import statistics
 
 import torch
 
-BLOCKS = (256, 512, 1024)
-CTAS_PER_SM = (0, 1, 2)
+# (block, ctas_per_sm, cluster, big_cells), in order of preference
+CANDIDATES = [(1024, 0, 1, 65536), (512, 0, 1, 65536)] + \
+             [(1024, 0, c, t) for c in (4, 8, 2) for t in (65536, 32768, 131072)] + \
+             [(512, 0, 4, 65536), (512, 0, 8, 65536)]
+KEYS = ("block", "ctas_per_sm", "cluster", "big_cells")
 
 
 def _cache_path() -> str:
@@ -31,7 +41,7 @@ def size_class(batch) -> str:
 
 
 def _key(batch) -> str:
-    return f"{torch.cuda.get_device_name()}|batched|{size_class(batch)}"
+    return f"{torch.cuda.get_device_name()}|batched-v2|{size_class(batch)}"
 
 
 def load_cache() -> dict:
@@ -51,43 +61,49 @@ def _save_cache(cache: dict):
     os.replace(tmp, p)
 
 
-def time_config(batch, b, x0, params, block, ctas, reps=2) -> float:
-    """Milliseconds of one graph replay (min of `reps`) for a configuration."""
-    batch.set_tuning("block", block)
-    batch.set_tuning("ctas_per_sm", ctas)
+def apply(batch, cfg):
+    for k in KEYS:
+        batch.set_tuning(k, int(cfg[k]))
+
+
+def time_config(batch, b, x0, params, cand, reps=5) -> float:
+    """Median milliseconds of `reps` graph replays for a candidate."""
+    apply(batch, dict(zip(KEYS, cand)))
     x = x0.clone()
     batch.capture(b, x, params)
-    best = float("inf")
-    for _ in range(reps + 1):
+    x.copy_(x0)
+    batch.replay()   # warm-up
+    ts = []
+    for _ in range(reps):
         x.copy_(x0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         batch.replay()
         e1.record()
         torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1))
-    return best
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
 
 
-def tune_batch(batch, b, x0, params, use_cache=True, verbose=False) -> dict:
-    """Choose and apply the fastest (block, ctas_per_sm); returns the choice."""
+def tune_batch(batch, b, x0, params, use_cache=True, verbose=False, slack=0.03) -> dict:
+    """Choose and apply the fastest configuration; returns the choice."""
     key = _key(batch)
     cache = load_cache() if use_cache else {}
     if key in cache:
         cfg = cache[key]
     else:
         results = []
-        for block in BLOCKS:
-            for ctas in CTAS_PER_SM:
-                ms = time_config(batch, b, x0, params, block, ctas)
-                results.append((ms, block, ctas))
-                if verbose:
-                    print(f"autotune {key}: block={block} ctas_per_sm={ctas}: {ms:.3f} ms", flush=True)
-        ms, block, ctas = min(results)
-        cfg = {"block": block, "ctas_per_sm": ctas, "ms": ms, "candidates": [list(r) for r in results]}
+        for cand in CANDIDATES:
+            ms = time_config(batch, b, x0, params, cand)
+            results.append((ms,) + cand)
+            if verbose:
+                print(f"autotune {key}: {dict(zip(KEYS, cand))}: {ms:.3f} ms", flush=True)
+        best = min(r[0] for r in results)
+        pick = next(r for r in results if r[0] <= best * (1.0 + slack))
+        cfg = dict(zip(KEYS, pick[1:]))
+        cfg.update({"ms": pick[0], "best_ms": best, "candidates": [list(r) for r in results]})
         if use_cache:
             cache[key] = cfg
             _save_cache(cache)
-    batch.set_tuning("block", cfg["block"])
-    batch.set_tuning("ctas_per_sm", cfg["ctas_per_sm"])
+    apply(batch, cfg)
     return cfg

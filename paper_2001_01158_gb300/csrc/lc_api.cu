@@ -73,6 +73,7 @@ struct lc_op {
     int pcg_big = 1;         // 2D solves: one 768-thread block per SM (2 % faster at 2048^2, mixed 5 %)
     int pcg_pairdot = 1;     // 2D scaled wide FP64: dots and block sums on FP32 pairs (7 % faster at 2048^2)
     int pcg_lazy_x = 1;      // 2D scaled wide FP64 pair: x update in the next phase A (4.6 % faster at 2048^2)
+    int csr_store_p = 1;     // global CSR solves: p stored once per row before the product
     int pcg_wide = 1;        // 2D scaled FP64: four cells per lane (when nx % 4 == 0; 3.5 % faster at 2048^2)
     double *sc = nullptr, *sq = nullptr, *Txh = nullptr, *Tyh = nullptr, *Tzh = nullptr;
     float *dn32 = nullptr;
@@ -345,7 +346,7 @@ int pcg_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_
              bool local, cudaStream_t s) {
     lc::PcgArgs a{b,           x,           p->tol,        p->max_iter,  3,
                   op->pcg_minblocks, p->precision, p->inner_tol, p->max_outer, op->pcg_scaled, op->pcg_wide,
-                  op->pcg_big, op->pcg_pairdot, op->pcg_lazy_x};
+                  op->pcg_big, op->pcg_pairdot, op->pcg_lazy_x, op->csr_store_p};
     lc::PcgWork w = op->pw;
     LC_CUDA(ctx, cudaMemsetAsync(&ctrl->status, 0, sizeof(int32_t), s));
     if (local) {
@@ -462,7 +463,7 @@ void batch_carve(lc_batch *bt, Carver &c) {
     v.ny = c.take<int32_t>(S);
     v.off = c.take<int64_t>(S);
     v.order = c.take<int32_t>(S);
-    v.next = c.take<int32_t>(1);
+    v.next = c.take<int32_t>(2);
     v.stat_i = c.take<int32_t>(8 * S);
     v.stat_d = c.take<double>(4 * S);
     v.D32 = c.take<float>(T);
@@ -571,6 +572,8 @@ int lc_batch_create(lc_ctx *ctx, lc_batch **out, int32_t nsys, const int32_t *nx
     }
     bt->L.block = 512;
     bt->L.ctas_per_sm = 0;
+    bt->L.cluster = 1;
+    bt->L.big_cells = 65536;
     *out = bt;
     return LC_OK;
 }
@@ -587,9 +590,20 @@ int lc_batch_destroy(lc_batch *bt) {
     return LC_OK;
 }
 
+// systems solved by whole clusters: those of at least big_cells cells (the
+// queue is sorted by size, largest first)
+static void batch_split(lc_batch *bt) {
+    int32_t nbig = 0;
+    if (bt->L.cluster > 1)
+        for (int32_t s = 0; s < bt->nsys; ++s)
+            if ((int64_t)bt->nx[s] * bt->ny[s] >= bt->L.big_cells) ++nbig;
+    bt->L.v.nbig = nbig;
+}
+
 static int batch_enqueue(lc_batch *bt, cudaStream_t s) {
     lc_ctx *ctx = bt->ctx;
-    LC_CUDA(ctx, cudaMemsetAsync(bt->L.v.next, 0, sizeof(int32_t), s));
+    batch_split(bt);
+    LC_CUDA(ctx, cudaMemsetAsync(bt->L.v.next, 0, 2 * sizeof(int32_t), s));
     LC_CUDA(ctx, lc::launch_batched(&bt->L, ctx->sms, s));
     return LC_OK;
 }
@@ -714,6 +728,17 @@ int lc_batch_set_tuning(lc_batch *bt, const char *key, int32_t value) {
         bt->L.ctas_per_sm = value;
         return LC_OK;
     }
+    if (!strcmp(key, "cluster")) {
+        if (value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+            return fail(bt->ctx, LC_ERR_INVALID_ARG, "cluster must be 1, 2, 4, 8 or 16");
+        bt->L.cluster = value;
+        return LC_OK;
+    }
+    if (!strcmp(key, "big_cells")) {
+        if (value < 1) return fail(bt->ctx, LC_ERR_INVALID_ARG, "big_cells must be >= 1");
+        bt->L.big_cells = value;
+        return LC_OK;
+    }
     return fail(bt->ctx, LC_ERR_INVALID_ARG, "unknown tuning key '%s'", key);
 }
 
@@ -742,6 +767,11 @@ int lc_op_set_tuning(lc_op *op, const char *key, int32_t value) {
     if (!strcmp(key, "pcg_lazy_x")) {
         if (value < 0 || value > 1) return fail(op->ctx, LC_ERR_INVALID_ARG, "pcg_lazy_x must be 0 or 1");
         op->pcg_lazy_x = value;
+        return LC_OK;
+    }
+    if (!strcmp(key, "csr_store_p")) {
+        if (value < 0 || value > 1) return fail(op->ctx, LC_ERR_INVALID_ARG, "csr_store_p must be 0 or 1");
+        op->csr_store_p = value;
         return LC_OK;
     }
     if (!strcmp(key, "local_grid_cap")) {
@@ -791,6 +821,7 @@ int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value) {
     if (!strcmp(key, "pcg_pairdot")) { *value = op->pcg_pairdot; return LC_OK; }
     if (!strcmp(key, "local_grid_cap")) { *value = op->local_grid_cap; return LC_OK; }
     if (!strcmp(key, "pcg_lazy_x")) { *value = op->pcg_lazy_x; return LC_OK; }
+    if (!strcmp(key, "csr_store_p")) { *value = op->csr_store_p; return LC_OK; }
     return LC_ERR_INVALID_ARG;
 }
 

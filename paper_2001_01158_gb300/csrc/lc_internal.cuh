@@ -38,7 +38,8 @@ struct BatchView {
     double *rhs, *xl;
     float *dl32;               // 1/diag(B) in FP32
     float *r32, *z32, *p32, *q32, *d32;
-    int32_t *next;             // work-queue counter
+    int32_t *next;             // work-queue counters: [0] systems solved by clusters, [1] by single CTAs
+    int nbig;                  // the first nbig systems of `order` are solved by clusters (0 without clusters)
     int32_t *stat_i;           // [nsys][8]: status, K, nnzB, it_local, it_global, outer_local, outer_global, early
     double *stat_d;            // [nsys][4]: tau, relres_tilde, relres_final, bnorm
 };
@@ -55,6 +56,8 @@ struct BatchLaunch {
     BatchParams p;
     int block;       // 256, 512 or 1024
     int ctas_per_sm; // 0 = as many as fit
+    int cluster;     // CTAs per thread-block cluster: 1 (none), 2, 4, 8 or 16
+    int64_t big_cells;  // with clusters: systems of at least this many cells are solved by a whole cluster
 };
 
 cudaError_t launch_batched(const void *launch_desc, int sms, cudaStream_t s);
@@ -155,6 +158,7 @@ struct PcgArgs {
     int32_t big;          // 2D solves: one block of 768 threads per SM (tuning)
     int32_t pairdot;      // FP64 2D scaled wide: dot products and block sums on FP32 pairs (tuning)
     int32_t lazyx;        // FP64 2D scaled wide pair: x += alpha p in the next phase A (tuning)
+    int32_t store_p;      // global CSR systems: p stored once per row before the product (tuning)
 };
 cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                cudaStream_t s);

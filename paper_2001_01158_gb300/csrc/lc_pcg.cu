@@ -16,12 +16,24 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
     auto al16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
     const bool vec = op.nx % 2 == 0 && al16(op.D) && al16(op.Tx) && al16(op.Ty);
     const int wpb = kPcgThreads / 32;
+    int sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // blocks for strips of `width` columns: 4 rows per warp so the recomputed
+    // halo rows stay a small overhead -- unless that leaves SMs idle (small
+    // grids: 99 x 99 filled 5 SMs, 22 us per iteration), then 2 or 1 rows
+    const auto units_for = [&](int width) {
+        const int64_t rows = (int64_t)((op.nx + width - 1) / width) * op.ny;
+        for (int r = 4;; r /= 2) {
+            const int64_t u = (rows + (int64_t)r * wpb - 1) / ((int64_t)r * wpb);
+            if (r == 1 || u >= sms) return u;
+        }
+    };
     if (vec) {
-        // at least 4 rows per warp so the recomputed halo rows stay a small overhead
-        const int64_t units = ((int64_t)((op.nx + 63) / 64) * op.ny + 4 * wpb - 1) / (4 * wpb);
+        const int64_t units = units_for(64);
         if (a.scaled && op.sc && a.wide && op.nx % 4 == 0) {
             // four cells per lane: half the strip-end halos and segment starts
-            const int64_t units4 = ((int64_t)((op.nx + 127) / 128) * op.ny + 4 * wpb - 1) / (4 * wpb);
+            const int64_t units4 = units_for(128);
             const Coef<double> ch{op.D, op.Txh, op.Tyh, nullptr};
             Vecs<double> VS = VD;
             VS.x = w.z;
@@ -53,7 +65,16 @@ cudaError_t launch_pcg_stencil(const Stencil &op, const PcgArgs &a, PcgWork &w, 
         Op2DW<double, 2> od{op, coef64(op)};
         return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);
     }
-    const int64_t units = ((int64_t)((op.nx + 31) / 32) * op.ny + 4 * wpb - 1) / (4 * wpb);
+    const int64_t units = units_for(32);
+    if (a.scaled && op.sc) {   // odd widths: the scaled system one cell per lane
+        Op2DW<double, 1, true> os{op, Coef<double>{op.D, op.Txh, op.Tyh, nullptr}, op.sc, op.sq, op.dn32, op.dexp};
+        Vecs<double> VS = VD;
+        VS.x = w.z;
+        VS.z = w.r;
+        VS.dinv = nullptr;
+        VS.xu = a.x;
+        return launch_pcg(os, units, VS, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+    }
     Op2DW<double, 1> od{op, coef64(op)};
     return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);
 }

@@ -828,12 +828,18 @@ struct Op3D {
 
 // CSR: one row per thread; the p of every referenced column is recomputed
 // from z and p_old (rows are independent, no shared memory).
-template <typename T>
+// SP (store p): phase A first forms p = z + beta p_old once per row and
+// stores it, then -- after a grid barrier -- the product reads p at the
+// columns: one FP64 FMA and one load per entry instead of two of each, for
+// one barrier more per iteration (large global systems, where the
+// recomputation's FP64 work and L2 loads bound the iteration).
+template <typename T, bool SP = false>
 struct OpCsr {
     Csr cs;
     const T *av;
     int32_t n;   // resolved at kernel start (device-side count of an extracted subsystem)
     const int32_t *done = nullptr;   // set: the cluster kernel may have solved the system already
+    Ctrl *bar = nullptr;             // SP: the control block of the launch's grid barrier
     static constexpr int kSmem = 1;
     static constexpr bool kAnyBlock = true;    // rows dealt to warps: any block size
     static constexpr bool kScaled = false;
@@ -879,20 +885,41 @@ struct OpCsr {
     // pair (FP64): the thread's p.q split into an FP32 pair scaled by 2^-2 ps
     __device__ void phaseA_block(const Vecs<T> &V, const T *pold, T *pout, bool first, T beta, T &pq, T *,
                                  int ps, float *pair = nullptr, T = T(0)) const {
-        each_cell([&](int64_t i) {
-            T qi = T(0), pi = T(0);
-            const int32_t e1 = cs.rp[i + 1];
-            for (int32_t e = cs.rp[i]; e < e1; ++e) {
-                const int32_t j = cs.ci[e];
-                const T zj = ldcg(V.z + j);
-                const T pj = first ? zj : fmaT(beta, ldcg(pold + j), zj);
-                if (j == i) pi = pj;
-                qi = fmaT(av[e], pj, qi);
-            }
-            pout[i] = pi;
-            V.q[i] = qi;
-            pq = fmaT(pi, qi, pq);
-        });
+        if constexpr (SP) {
+            // own rows: z and p_old were written by this thread (the same row mapping in every phase)
+            each_cell([&](int64_t i) {
+                const T zi = V.z[i];
+                pout[i] = first ? zi : fmaT(beta, pold[i], zi);
+            });
+            grid_sync(bar, gridDim.x);   // a timeout is recorded; the next reduction's wait ends the solve
+            each_cell([&](int64_t i) {
+                T qi = T(0), pi = T(0);
+                const int32_t e1 = cs.rp[i + 1];
+                for (int32_t e = cs.rp[i]; e < e1; ++e) {
+                    const int32_t j = cs.ci[e];
+                    const T pj = ldcg(pout + j);
+                    if (j == i) pi = pj;
+                    qi = fmaT(av[e], pj, qi);
+                }
+                V.q[i] = qi;
+                pq = fmaT(pi, qi, pq);
+            });
+        } else {
+            each_cell([&](int64_t i) {
+                T qi = T(0), pi = T(0);
+                const int32_t e1 = cs.rp[i + 1];
+                for (int32_t e = cs.rp[i]; e < e1; ++e) {
+                    const int32_t j = cs.ci[e];
+                    const T zj = ldcg(V.z + j);
+                    const T pj = first ? zj : fmaT(beta, ldcg(pold + j), zj);
+                    if (j == i) pi = pj;
+                    qi = fmaT(av[e], pj, qi);
+                }
+                pout[i] = pi;
+                V.q[i] = qi;
+                pq = fmaT(pi, qi, pq);
+            });
+        }
         if constexpr (kPairDots)
             if (pair) split_f2((double)pq, 2 * ps, pair[0], pair[1]);
     }
@@ -999,7 +1026,7 @@ template <class OP, int MINB, int THREADS = kPcgThreads>
 __global__ void __launch_bounds__(THREADS, MINB) pcg_kernel(OP op, Vecs<double> V, double *part, double tol,
                                                             int maxit, int max_restarts, Ctrl *ctrl) {
     __shared__ double red[128];
-    __shared__ double sm[OP::kSmem];
+    __shared__ __align__(16) double sm[OP::kSmem];
     if (op.skipped()) return;
     op.resolve();
     if (OP::kScaled) {   // x^ = D^1/2 x into the workspace (the caller's x stays untouched until the end)
@@ -1065,7 +1092,7 @@ __global__ void __launch_bounds__(THREADS, MINB) ir_kernel(OPD opd, OPF opf, Vec
                                                            double *part, double tol, double inner_tol,
                                                            int maxit, int max_outer, Ctrl *ctrl) {
     __shared__ double red[128];
-    __shared__ float sm[OPF::kSmem];
+    __shared__ __align__(16) float sm[OPF::kSmem];
     opd.resolve();
     opf.resolve();
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;

@@ -23,7 +23,17 @@ cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a0, PcgWork &w, Ctrl *c
         od.done = &ctrl->done;
         return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s, false);
     }
-    if (a.precision != LC_PREC_MIXED) return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+    // a global system stores p once per row (OpCsr SP); an extracted
+    // subsystem, latency-bound, recomputes it at the columns (no extra barrier)
+    const bool sp = a.store_p && op.n_dev == nullptr;
+    if (a.precision != LC_PREC_MIXED) {
+        if (sp) {
+            OpCsr<double, true> os{op, op.av, op.n};
+            os.bar = ctrl;
+            return launch_pcg(os, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+        }
+        return launch_pcg(od, units, VD, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+    }
     VD.z = nullptr;
     const float *av32 = op.av32;
     if (!av32) {   // per-solve FP32 copy of the values into the workspace
@@ -34,6 +44,11 @@ cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a0, PcgWork &w, Ctrl *c
     csr_dinv_kernel<float><<<152 * 4, 256, 0, s>>>(op, av32, w.dinv32);
     note_launches(1);
     Vecs<float> VF = vecs32(w, w.dinv32);
+    if (sp) {
+        OpCsr<float, true> ofs{op, av32, op.n};
+        ofs.bar = ctrl;
+        return launch_ir(od, ofs, units, VD, VF, w.partials, a, ctrl, grid_hint, a.minblocks, s);
+    }
     OpCsr<float> of{op, av32, op.n};
     return launch_ir(od, of, units, VD, VF, w.partials, a, ctrl, grid_hint, a.minblocks, s);
 }

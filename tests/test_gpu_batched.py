@@ -63,12 +63,25 @@ def setup():
     return ctx, items, batch, b, x0
 
 
-@pytest.mark.parametrize("block", [256, 512, 1024])
-def test_batched_matches_oracle_per_system(setup, block):
+# (block, cluster, big_cells): one CTA per system, and thread-block clusters
+# of 2, 4, 8 and 16 CTAs taking every system from big_cells cells on -- down to
+# systems with fewer rows than the cluster has CTAs (empty row ranges)
+CONFIGS = [(256, 1, 65536), (512, 1, 65536), (1024, 1, 65536), (1024, 2, 1000), (512, 4, 30), (1024, 8, 200),
+           (1024, 16, 1)]
+
+
+def set_config(batch, block, cluster, big):
+    batch.set_tuning("block", block)
+    batch.set_tuning("cluster", cluster)
+    batch.set_tuning("big_cells", big)
+
+
+@pytest.mark.parametrize("block,cluster,big", CONFIGS)
+def test_batched_matches_oracle_per_system(setup, block, cluster, big):
     ctx, items, batch, b, x0 = setup
     tol = 1e-8
     prm = lcg.batch_params(beta=1e-3, layers=2, tol=tol, inner_tol=1e-4)
-    batch.set_tuning("block", block)
+    set_config(batch, block, cluster, big)
     x = x0.clone()
     batch.solve(b, x, prm)
     st = batch.stats()
@@ -86,10 +99,11 @@ def test_batched_matches_oracle_per_system(setup, block):
         assert np.linalg.norm(xg - xr) <= 1e-6 * np.linalg.norm(xr), s
 
 
-def test_graph_replay_equals_direct_launch(setup):
+@pytest.mark.parametrize("cluster", [1, 4])
+def test_graph_replay_equals_direct_launch(setup, cluster):
     ctx, items, batch, b, x0 = setup
     prm = lcg.batch_params()
-    batch.set_tuning("block", 512)
+    set_config(batch, 512, cluster, 1000)
     x1 = x0.clone()
     batch.solve(b, x1, prm)
     torch.cuda.synchronize()
@@ -108,9 +122,10 @@ def test_autotuner_picks_a_configuration(setup, tmp_path, monkeypatch):
     ctx, items, batch, b, x0 = setup
     monkeypatch.setenv("LC_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     cfg = autotune.tune_batch(batch, b, x0, lcg.batch_params())
-    assert cfg["block"] in (256, 512, 1024) and len(cfg["candidates"]) == 9
+    assert cfg["block"] in (256, 512, 1024) and len(cfg["candidates"]) == len(autotune.CANDIDATES)
+    assert cfg["ms"] <= 1.03 * cfg["best_ms"]
     again = autotune.tune_batch(batch, b, x0, lcg.batch_params())   # from the cache
-    assert again["block"] == cfg["block"] and again["ctas_per_sm"] == cfg["ctas_per_sm"]
+    assert all(again[k] == cfg[k] for k in autotune.KEYS)
 
 
 def test_batched_rejects_unsupported_parameters(setup):

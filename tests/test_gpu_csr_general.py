@@ -119,6 +119,33 @@ def test_pcg_and_alg1_match_oracle(ctx, kind, nx, ny):
     assert oracle.relres(A, b, x.cpu().numpy()) <= 1e-10
 
 
+@pytest.mark.parametrize("kind,nx,ny", [("threeT", 97, 61), ("ninepoint", 130, 37)])
+def test_csr_store_p_is_bit_identical(ctx, kind, nx, ny):
+    """The global CSR solve with p stored once per row (csr_store_p 1, the
+    default) and with p recomputed at every column (0) performs the same
+    operations on the same values: identical iterations and bits of x, FP64
+    and mixed precision; both match the oracle."""
+    A, b, x0 = problem(kind, nx, ny)
+    gop = csr_op(ctx, A)
+    xr, _, it_r, _ = oracle.pcg(A, b, x0, tol=1e-8)
+    out = {}
+    for sp in (1, 0):
+        gop.set_tuning("csr_store_p", sp)
+        res = []
+        for prm in (lcg.SolveParams(1e-8, 100000, lcg.PREC_FP64, 0.0, 0),
+                    lcg.SolveParams(1e-10, 100000, lcg.PREC_MIXED, 1e-4, 30)):
+            x = cu(x0)
+            st = lcg.Stats()
+            lcg.pcg_solve(ctx, gop, cu(b), x, prm, st)
+            res.append((x.cpu().numpy(), st.it_global))
+        out[sp] = res
+    for k in range(2):
+        assert out[0][k][1] == out[1][k][1]
+        assert np.array_equal(bits(out[0][k][0]), bits(out[1][k][0]))
+    assert abs(out[1][0][1] - it_r) <= 1
+    assert np.linalg.norm(out[1][0][0] - xr) <= 1e-9 * np.linalg.norm(xr)
+
+
 @pytest.mark.parametrize("kind,nx,ny", CASES, ids=IDS)
 def test_gs_greedy_colouring_bit_exact(ctx, kind, nx, ny):
     A, b, x0 = problem(kind, nx, ny)

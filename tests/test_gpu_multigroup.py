@@ -32,9 +32,13 @@ def groups():
     return ctx, items, batch, cu(np.concatenate([d["b"] for d in items])), cu(np.concatenate([d["x0"] for d in items]))
 
 
-def test_multigroup_batched_matches_oracle(groups):
+@pytest.mark.parametrize("cluster", [1, 4])
+def test_multigroup_batched_matches_oracle(groups, cluster):
+    """One CTA per group, and clusters of 4 CTAs per group."""
     ctx, items, batch, b, x0 = groups
     tol = 1e-8
+    batch.set_tuning("cluster", cluster)
+    batch.set_tuning("big_cells", 4096)
     x = x0.clone()
     batch.solve(b, x, lcg.batch_params(beta=1e-3, layers=2, tol=tol, inner_tol=1e-4))
     st = batch.stats()

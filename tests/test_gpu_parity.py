@@ -270,7 +270,7 @@ def test_pcg_3d_scaled_and_unscaled_match_oracle(ctx, shape, scaled, pairdot, la
     assert oracle.relres(A, b, x.cpu().numpy()) <= 1e-10
 
 
-@pytest.mark.parametrize("shape", [(35, 11, 37), (9, 17, 33)])
+@pytest.mark.parametrize("shape", [(35, 11, 37), (9, 17, 33), (40, 17, 37), (64, 24, 20)])
 @pytest.mark.parametrize("minblocks", [2, 3, 4])
 def test_pcg_3d_several_z_tiles_and_register_budgets(ctx, shape, minblocks):
     """Grids deeper than one tile (16 planes) with a ragged last tile: the 3D
@@ -278,7 +278,9 @@ def test_pcg_3d_several_z_tiles_and_register_budgets(ctx, shape, minblocks):
     below and above a tile, the lazy x update only on the tile's own planes),
     at each register budget of the persistent kernel.  FP64 (default scaled
     kernel: iterations within one, solution within 1e-9 of the oracle) and
-    mixed precision (relres 1e-10)."""
+    mixed precision (relres 1e-10); with nx a multiple of 4 the FP32 inner
+    solve streams its planes through shared memory by asynchronous copies
+    across several blocks (halos that other blocks wrote)."""
     op = gen.random_stencil_3d(sum(shape) + minblocks, *shape)
     A, b, x0 = rhs_and_x0(op, 23)
     tol = 1e-9
