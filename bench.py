@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--no-heat", action="store_true", help="skip the nonlinear heat runs (Sec. 3.2)")
     ap.add_argument("--profile-case", choices=PROFILE_CASES, default=None,
                     help="run one solve of a workload for a profiler capture and print its statistics (no timing)")
+    ap.add_argument("--systems", type=int, default=512,
+                    help="--profile-case batched: the first this many systems of the 512-system workload")
     return ap.parse_args()
 
 
@@ -859,8 +861,8 @@ def profile_case(args):
     anisotropic n^3 system from x0 = 0 (fp64_3d: one pcg_kernel launch;
     mixed3d: Alg 1 with FP32 inner CG, one ir_kernel launch).  csr3t: the 3T
     system on an n x n grid, one global pcg_kernel launch.  batched: the
-    512-system batch solved once without graph capture (one batched_kernel
-    launch)."""
+    first --systems systems of the 512-system batch solved once without
+    graph capture (one batched_kernel launch)."""
     import numpy as np
     import torch
 
@@ -913,7 +915,7 @@ def profile_case(args):
         x = T(x0)
         lcg.pcg_solve(ctx, gop, T(b), x, sp, st)
     else:
-        items = gen.cfg4_batch(seed=0)
+        items = gen.cfg4_batch(seed=0)[:args.systems]
         systems = [(it["op"].shape[0], it["op"].shape[1], T(it["op"].D), T(it["op"].Tx), T(it["op"].Ty))
                    for it in items]
         batch = lcg.Batch(ctx, systems)
