@@ -6,23 +6,23 @@
 // arithmetic.  Here one cluster of C CTAs (16 where the GPU schedules it,
 // else 8 or 4) keeps every vector of the solve in distributed shared memory:
 // CTA c owns rows [c R, (c+1) R), R = ceil(K / C), and holds x, r, z, q,
-// dinv and p of those rows.  A row's neighbours are read from
+// dinv and two buffers of p of those rows.  A row's neighbours are read from
 // the owning CTA's shared memory (DSMEM) and the cluster synchronises with
 // its hardware barrier.  The matrix itself is read from global memory (L2
 // resident after the first iteration).
 //
-// Per iteration, three cluster barriers (hardware barriers, cheap next to a
+// Per iteration, two cluster barriers (hardware barriers, cheap next to a
 // grid-wide one):
-//   phase P  p_i = z_i + beta p_i in place, own rows     (barrier)
-//   phase A  q_i = sum_j a_ij p_j, p_j from the owner; block partial p.q
-//            (barrier: every CTA has stored its partial in every CTA's slot row)
+//   phase A  q_i = sum_j a_ij p_j with p_j = z_j + beta p_old,j formed from
+//            the owner's z and previous p; p_i stored into the other buffer;
+//            block partial p.q  (barrier: every CTA has stored its partial
+//            in every CTA's slot row)
 //   phase B  alpha = rz / pq; x += alpha p; r -= alpha q; z = dinv r;
 //            partials r.z and r.r                          (barrier)
-// Each CTA sums the C slot rows in rank order, so every CTA takes the same
-// decisions.  Iteration, stopping test, true-residual confirmation and
-// restarts follow the grid kernel of lc_pcg_impl.cuh (same Ctrl fields).  p is
-// computed once per row (the grid kernel recomputes it per entry to save a
-// barrier): FP64 throughput, not latency, bounds a solve on 16 SMs.
+// Each CTA adds the C slot rows by the same shuffle tree, so every CTA takes
+// the same decisions.  Iteration, stopping test, true-residual confirmation
+// and restarts follow the grid kernel of lc_pcg_impl.cuh (same Ctrl
+// fields).
 //
 // The kernel first decides whether to take the system (K <= max_rows and the
 // rows fit); it records the decision in ctrl->done, and the grid kernel
@@ -42,14 +42,14 @@ namespace {
 
 constexpr int kClThreads = 1024;
 constexpr int kClMax = 16;
-constexpr int kClVecs = 6;                                  // x, r, z, q, dinv, p
+constexpr int kClVecs = 7;                                  // x, r, z, q, dinv, p, p (previous)
 constexpr int kClUnroll = 5;                                // row entries loaded together
 constexpr int kClFixed = (3 * kClMax * 4 + 128) * 8;        // three slot arrays + block-sum scratch
 
 struct ClMem {
     double *slotS, *slotA, *slotB;   // [kClMax][4]: partial sums, one row per source CTA
     double *red;                     // block_sum scratch (128)
-    double *x, *r, *z, *q, *dinv, *p;
+    double *x, *r, *z, *q, *dinv, *p, *p2;
 };
 
 __device__ __forceinline__ ClMem carve_cl(double *base, int rcap) {
@@ -66,6 +66,7 @@ __device__ __forceinline__ ClMem carve_cl(double *base, int rcap) {
     m.q = v + 3 * rc;
     m.dinv = v + 4 * rc;
     m.p = v + 5 * rc;
+    m.p2 = v + 6 * rc;
     return m;
 }
 
@@ -74,11 +75,13 @@ struct ClNoPost {
 };
 
 // Cluster-wide sums of NV per-thread values: block sum, the block's result
-// stored into slot row `rank` of every CTA, cluster barrier, and thread 0 of
-// each CTA adds the rows in rank order (identical results in every CTA) and
-// runs post(t) on them, which may append ND derived scalars (the step
-// lengths; one FP64 division per CTA instead of one per thread).  Every
-// thread reads totals and derived values back from shared memory.
+// stored into slot row `rank` of every CTA, cluster barrier, and warp 0 of
+// each CTA adds the C rows by a fixed shuffle tree (identical results in
+// every CTA; log2 C dependent FP64 additions instead of C -- an FP64 warp
+// instruction holds the FP64 pipe as long with one active lane as with 32);
+// thread 0 runs post(t) on the totals, which may append ND derived scalars
+// (the step lengths; one FP64 division per CTA instead of one per thread).
+// Every thread reads totals and derived values back from shared memory.
 template <int NV, int ND = 0, class Post = ClNoPost>
 __device__ __forceinline__ void cl_sums(cg::cluster_group &cl, double (&v)[NV], double *slots, double *red, int C,
                                         double (&out)[NV + ND], Post post = Post()) {
@@ -94,17 +97,22 @@ __device__ __forceinline__ void cl_sums(cg::cluster_group &cl, double (&v)[NV], 
         }
     }
     cl.sync();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        const int lane = (int)threadIdx.x;
+        int top = 1;
+        while (top < C) top <<= 1;
         double t[NV + ND];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (int c = 0; c < C; ++c) s += slots[c * 4 + k];
+            double s = lane < C ? slots[lane * 4 + k] : 0.0;
+            for (int o = top >> 1; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
             t[k] = s;
         }
-        post(t);
+        if (lane == 0) {
+            post(t);
 #pragma unroll
-        for (int k = 0; k < NV + ND; ++k) red[96 + k] = t[k];
+            for (int k = 0; k < NV + ND; ++k) red[96 + k] = t[k];
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -156,6 +164,44 @@ __device__ __forceinline__ double cl_row_dot(cg::cluster_group &cl, const Csr &c
     for (int t = 0; t < kClUnroll; ++t)
         if (jj[t] >= 0) acc = fma(aa[t], vv[t], acc);
     for (int e = e0 + kClUnroll; e < e1; ++e) acc = fma(__ldg(cs.av + e), cl_load(cl, vec, __ldg(cs.ci + e), pt, rank), acc);
+    return acc;
+}
+
+// q_i = sum_e a_e p_(col e) with p_j = z_j + beta p_old,j (p_j = z_j on the
+// first iteration) formed where it is read, from the owners' z and p_old;
+// *pi receives p_i.  The same value of p_j as its owner forms for itself.
+__device__ __forceinline__ double cl_row_dot_p(cg::cluster_group &cl, const Csr &cs, int i, double *z, double *pold,
+                                              bool first, double beta, const ClPart &pt, int rank, double *pi) {
+    const int e0 = cs.rp[i], e1 = cs.rp[i + 1];
+    double acc = 0.0, pc = 0.0;
+    const auto pat = [&](int j) {
+        const double zj = cl_load(cl, z, j, pt, rank);
+        return first ? zj : fma(beta, cl_load(cl, pold, j, pt, rank), zj);
+    };
+    int jj[kClUnroll];
+    double aa[kClUnroll];
+#pragma unroll
+    for (int t = 0; t < kClUnroll; ++t) {
+        const bool in = e0 + t < e1;
+        jj[t] = in ? __ldg(cs.ci + e0 + t) : -1;
+        aa[t] = in ? __ldg(cs.av + e0 + t) : 0.0;
+    }
+    double vv[kClUnroll];
+#pragma unroll
+    for (int t = 0; t < kClUnroll; ++t) vv[t] = jj[t] >= 0 ? pat(jj[t]) : 0.0;
+#pragma unroll
+    for (int t = 0; t < kClUnroll; ++t)
+        if (jj[t] >= 0) {
+            if (jj[t] == i) pc = vv[t];
+            acc = fma(aa[t], vv[t], acc);
+        }
+    for (int e = e0 + kClUnroll; e < e1; ++e) {
+        const int j = __ldg(cs.ci + e);
+        const double pj = pat(j);
+        if (j == i) pc = pj;
+        acc = fma(__ldg(cs.av + e), pj, acc);
+    }
+    *pi = pc;
     return acc;
 }
 
@@ -229,21 +275,24 @@ __global__ void __launch_bounds__(kClThreads, 1)
 
     // CG iterations from the current r, z; 1 converged (recurrence residual),
     // 0 iteration limit, -1 breakdown
+    // p is formed inside the product from z and the previous p (two buffers,
+    // swapped every iteration), so no barrier separates its update from the
+    // product: two cluster barriers per iteration
+    double *pbuf[2] = {m.p, m.p2};
     auto iterate = [&](double rz, double stop, int &it) -> int {
         bool first = true;
         double beta = 0.0;
+        int cur = 0;
         while (true) {
-            for (int i = r0 + tid; i < r1; i += nth) {
-                const int li = i - r0;
-                m.p[li] = first ? m.z[li] : fma(beta, m.p[li], m.z[li]);
-            }
-            cl.sync();   // every p in place before any row reads its neighbours
+            double *p = pbuf[cur], *pold = pbuf[cur ^ 1];
             double a1[1] = {0.0};
             for (int i = r0 + tid; i < r1; i += nth) {
                 const int li = i - r0;
-                const double qi = cl_row_dot(cl, cs, i, m.p, pt, rank);
+                double pi;
+                const double qi = cl_row_dot_p(cl, cs, i, m.z, pold, first, beta, pt, rank, &pi);
+                p[li] = pi;
                 m.q[li] = qi;
-                a1[0] = fma(m.p[li], qi, a1[0]);
+                a1[0] = fma(pi, qi, a1[0]);
             }
             double o1[3];   // p.q, alpha, breakdown flag
             cl_sums<1, 2>(cl, a1, m.slotA, m.red, C, o1, [rz](double *t) {
@@ -256,7 +305,7 @@ __global__ void __launch_bounds__(kClThreads, 1)
             double acc[2] = {0.0, 0.0};
             for (int i = r0 + tid; i < r1; i += nth) {
                 const int li = i - r0;
-                const double xi = fma(alpha, m.p[li], m.x[li]);
+                const double xi = fma(alpha, p[li], m.x[li]);
                 const double ri = fma(-alpha, m.q[li], m.r[li]);
                 const double zi = m.dinv[li] * ri;
                 m.x[li] = xi;
@@ -276,6 +325,7 @@ __global__ void __launch_bounds__(kClThreads, 1)
             beta = o2[3];
             rz = o2[0];
             first = false;
+            cur ^= 1;
         }
     };
 
