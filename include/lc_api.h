@@ -485,6 +485,16 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  *       phase, which loads p_k anyway (for p_k+1 = r + beta p_k), and after
  *       the last iteration by one extra pass: 8 fewer bytes per cell and
  *       iteration, the same operations in the same order (bit-identical x).
+ *   "graph_max_cells" >= 0 (default 65536): for operators of at most this
+ *       many unknowns, each lc_pcg_solve and lc_solve_local_then_global call
+ *       runs as one CUDA graph, captured the first time a call signature is
+ *       seen (the same b and x pointers, parameters, stats requested or not,
+ *       and tuning) and replayed afterwards; its launches then reach the GPU
+ *       together instead of one host call at a time (small systems are
+ *       bound by that).  Every data-dependent decision of a solve is taken on
+ *       the device, so a replay computes exactly what direct launches do.  If
+ *       a capture fails, the operator launches directly from then on.  0
+ *       disables it.
  *   "csr_store_p"   0 or 1 (default 1): the global solve of a CSR operator
  *       forms p = z + beta p_old once per row, stores it and, after one more
  *       grid barrier, reads it at the columns of the product; with 0 every

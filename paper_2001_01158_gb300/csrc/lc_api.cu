@@ -79,6 +79,22 @@ struct lc_op {
     float *dn32 = nullptr;
     int *dexp = nullptr;
     float *Txh32 = nullptr, *Tyh32 = nullptr, *Tzh32 = nullptr, *sq32 = nullptr;
+    // Small systems: each lc_pcg_solve / lc_solve_local_then_global call is
+    // replayed as one CUDA graph, captured on first use and cached per call
+    // signature (the same b, x, parameters and tuning), so that the solve's
+    // launches reach the GPU together instead of one host call at a time.
+    struct GraphSlot {
+        bool valid = false;
+        unsigned char key[sizeof(lc_params) + 4 * sizeof(void *) + 16] = {};
+        size_t keylen = 0;
+        cudaGraphExec_t exec = nullptr;
+        long long launches = 0;   // kernels in the graph
+    };
+    int64_t graph_max_cells = 65536;   // 0: never
+    GraphSlot gslot[2];                // [0] lc_pcg_solve, [1] lc_solve_local_then_global
+    cudaStream_t cap = nullptr;        // private capture stream (created on first use)
+    int graph_broken = 0;              // a capture failed: direct launches from then on
+    unsigned tuning_gen = 0;           // bumped by every tuning change (part of the key)
 };
 
 namespace {
@@ -513,6 +529,94 @@ int batch_params(lc_ctx *ctx, const lc_params *p, lc::BatchParams &bp) {
 
 }  // namespace
 
+namespace {
+
+// Runs enqueue(stream) -- a solve's whole sequence of stream-ordered work --
+// directly, or, for operators of at most graph_max_cells cells, as a cached
+// CUDA graph: captured on a private stream the first time a call signature
+// (key) is seen and replayed on `s` afterwards.  Every decision of the
+// sequence that depends on data is taken on the device, so a replay does
+// what a direct call does; kernel sizes depend only on the operator, the
+// parameters and the tuning, all of which are in the key.  If a capture
+// fails (an operation the graph cannot hold), the operator runs its calls
+// directly from then on.
+template <class F>
+int run_graphed(lc_ctx *ctx, lc_op *op, int slot, const void *key, size_t keylen, cudaStream_t s, F enqueue) {
+    if (op->n > op->graph_max_cells || op->graph_broken || keylen > sizeof(op->gslot[0].key)) return enqueue(s, false);
+    lc_op::GraphSlot &g = op->gslot[slot];
+    if (!(g.valid && g.keylen == keylen && memcmp(g.key, key, keylen) == 0)) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        g.valid = false;
+        if (!op->cap && cudaStreamCreateWithFlags(&op->cap, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            op->graph_broken = 1;
+            return enqueue(s, false);
+        }
+        if (cudaStreamBeginCapture(op->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            op->graph_broken = 1;
+            return enqueue(s, false);
+        }
+        const long long l0 = lc::g_launches.load(std::memory_order_relaxed);
+        const int rc = enqueue(op->cap, true);
+        const long long nl = lc::g_launches.load(std::memory_order_relaxed) - l0;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(op->cap, &graph);
+        if (rc == LC_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        lc::g_launches.fetch_sub(nl, std::memory_order_relaxed);   // counted when the graph runs
+        if (rc != LC_OK || e != cudaSuccess || !g.exec) {
+            cudaGetLastError();
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            if (rc != LC_OK && rc != LC_ERR_CUDA) return rc;   // an argument error, not the capture's
+            op->graph_broken = 1;
+            return enqueue(s, false);
+        }
+        memcpy(g.key, key, keylen);
+        g.keylen = keylen;
+        g.launches = nl;
+        g.valid = true;
+    }
+    LC_CUDA(ctx, cudaGraphLaunch(g.exec, s));
+    lc::g_launches.fetch_add(g.launches, std::memory_order_relaxed);
+    return LC_OK;
+}
+
+// An event of the stats: inside a capture it must become a node of the graph
+// (an external record), else the replay would not record it.
+cudaError_t record(cudaEvent_t ev, cudaStream_t q, bool capturing) {
+    return cudaEventRecordWithFlags(ev, q, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
+// Milliseconds between two recorded events (0, and the error cleared, if the
+// runtime cannot time them).
+float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 0.f;
+    }
+    return ms;
+}
+
+// the signature of a solve call, for run_graphed
+template <class P>
+size_t call_key(unsigned char *k, const lc_op *op, const void *b, const void *x, const P *p, bool stats) {
+    size_t n = 0;
+    const auto put = [&](const void *v, size_t sz) { memcpy(k + n, v, sz); n += sz; };
+    put(&b, sizeof b);
+    put(&x, sizeof x);
+    put(p, sizeof *p);
+    const unsigned char st = stats ? 1 : 0;
+    put(&st, 1);
+    put(&op->tuning_gen, sizeof op->tuning_gen);
+    return n;
+}
+
+}  // namespace
+
 extern "C" {
 
 int lc_batch_create(lc_ctx *ctx, lc_batch **out, int32_t nsys, const int32_t *nx, const int32_t *ny, const double *D,
@@ -744,6 +848,12 @@ int lc_batch_set_tuning(lc_batch *bt, const char *key, int32_t value) {
 
 int lc_op_set_tuning(lc_op *op, const char *key, int32_t value) {
     if (!op || !key) return LC_ERR_INVALID_ARG;
+    ++op->tuning_gen;
+    if (!strcmp(key, "graph_max_cells")) {
+        if (value < 0) return fail(op->ctx, LC_ERR_INVALID_ARG, "graph_max_cells must be >= 0");
+        op->graph_max_cells = value;
+        return LC_OK;
+    }
     if (!strcmp(key, "pcg_minblocks")) {
         if (value < 1 || value > 4) return fail(op->ctx, LC_ERR_INVALID_ARG, "pcg_minblocks must be 1..4");
         op->pcg_minblocks = value;
@@ -822,6 +932,7 @@ int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value) {
     if (!strcmp(key, "local_grid_cap")) { *value = op->local_grid_cap; return LC_OK; }
     if (!strcmp(key, "pcg_lazy_x")) { *value = op->pcg_lazy_x; return LC_OK; }
     if (!strcmp(key, "csr_store_p")) { *value = op->csr_store_p; return LC_OK; }
+    if (!strcmp(key, "graph_max_cells")) { *value = (int32_t)op->graph_max_cells; return LC_OK; }
     return LC_ERR_INVALID_ARG;
 }
 
@@ -946,6 +1057,8 @@ int lc_op_destroy(lc_op *op) {
     if (!op) return LC_OK;
     if (op->ctx) cudaSetDevice(op->ctx->device);
     for (auto &ev : op->ev) if (ev) cudaEventDestroy(ev);
+    for (auto &g : op->gslot) if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (op->cap) cudaStreamDestroy(op->cap);
     if (op->arena) cudaFree(op->arena);
     lc_ctx *ctx = op->ctx;
     delete op;
@@ -984,10 +1097,17 @@ int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const
     if (!b || !x) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
     if ((rc = check_solve_params(ctx, p))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    if (stats) LC_CUDA(ctx, cudaEventRecord(op->ev[0], s));
-    if ((rc = pcg_impl(ctx, op, b, x, p, op->ctrl, false, s))) return rc;
+    unsigned char key[sizeof(lc_params) + 4 * sizeof(void *) + 16];
+    const size_t kl = call_key(key, op, b, x, p, stats != nullptr);
+    rc = run_graphed(ctx, const_cast<lc_op *>(op), 0, key, kl, s, [&](cudaStream_t q, bool cap) -> int {
+        if (stats) LC_CUDA(ctx, record(op->ev[0], q, cap));
+        const int r = pcg_impl(ctx, op, b, x, p, op->ctrl, false, q);
+        if (r) return r;
+        if (stats) LC_CUDA(ctx, record(op->ev[1], q, cap));
+        return LC_OK;
+    });
+    if (rc) return rc;
     if (!stats) return LC_OK;
-    LC_CUDA(ctx, cudaEventRecord(op->ev[1], s));
     LC_CUDA(ctx, cudaStreamSynchronize(s));
     lc::Ctrl c;
     if ((rc = read_ctrl(ctx, op->ctrl, &c))) return rc;
@@ -998,7 +1118,7 @@ int lc_pcg_solve(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const
     stats->early_exit = c.early;
     stats->relres_tilde = c.relres0;
     stats->relres_final = c.relres;
-    cudaEventElapsedTime(&stats->t_global_ms, op->ev[0], op->ev[1]);
+    stats->t_global_ms = elapsed_ms(op->ev[0], op->ev[1]);
     stats->t_total_ms = stats->t_global_ms;
     stats->status = status_of(c);
     if (stats->status == LC_ERR_TIMEOUT) return fail(ctx, LC_ERR_TIMEOUT, "grid barrier timed out");
@@ -1174,32 +1294,38 @@ int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const double *b, do
     if (!b || !x || !p) return fail(ctx, LC_ERR_INVALID_ARG, "null argument");
     if ((rc = check_solve_params(ctx, &p->global)) || (rc = check_solve_params(ctx, &p->local))) return rc;
     if ((rc = check_gs(ctx, op, p->gs_sweeps))) return rc;
+    if (p->mark_mode != LC_MARK_RESIDUAL && p->mark_mode != LC_MARK_GRADIENT)
+        return fail(ctx, LC_ERR_INVALID_ARG, "unknown marking mode %d", p->mark_mode);
     cudaStream_t s = (cudaStream_t)stream;
-    if (stats) LC_CUDA(ctx, cudaEventRecord(op->ev[0], s));
-    // 1. local domain (Alg 2 or Alg 3)
-    if (p->mark_mode == LC_MARK_RESIDUAL) {
-        rc = mark_residual_impl(ctx, op, b, x, &p->mark, op->mask_own, nullptr, op->sub.K, nullptr, s);
-    } else if (p->mark_mode == LC_MARK_GRADIENT) {
-        rc = mark_gradient_impl(ctx, op, x, p->alpha, p->grad_layers, op->mask_own, op->sub.K, nullptr, s);
-    } else {
-        rc = fail(ctx, LC_ERR_INVALID_ARG, "unknown marking mode %d", p->mark_mode);
-    }
+    unsigned char key[sizeof(lc_params) + 4 * sizeof(void *) + 16];
+    const size_t kl = call_key(key, op, b, x, p, stats != nullptr);
+    rc = run_graphed(ctx, const_cast<lc_op *>(op), 1, key, kl, s, [&](cudaStream_t q, bool cap) -> int {
+        int r;
+        if (stats) LC_CUDA(ctx, record(op->ev[0], q, cap));
+        // 1. local domain (Alg 2 or Alg 3)
+        if (p->mark_mode == LC_MARK_RESIDUAL)
+            r = mark_residual_impl(ctx, op, b, x, &p->mark, op->mask_own, nullptr, op->sub.K, nullptr, q);
+        else
+            r = mark_gradient_impl(ctx, op, x, p->alpha, p->grad_layers, op->mask_own, op->sub.K, nullptr, q);
+        if (r) return r;
+        if (stats) LC_CUDA(ctx, record(op->ev[1], q, cap));
+        // 2. subsystem B x_B = b_B - E x_C (Eq. loc-equ)
+        if ((r = extract_impl(ctx, op, op->mask_own, b, x, op->sub, q))) return r;
+        if (stats) LC_CUDA(ctx, record(op->ev[2], q, cap));
+        // 3. local solve from x0 restricted to the domain, in place in sub.xL0
+        if ((r = pcg_impl(ctx, op, op->sub.rhs, op->sub.xL0, &p->local, op->ctrl_loc, true, q))) return r;
+        // 4. x~ = x0 with the local solution scattered in (Eq. sol-assemble)
+        LC_CUDA(ctx, lc::launch_assemble(op->sub.K, op->sub.l2g, op->sub.xL0, x, op->n, q));
+        // 5. Gauss-Seidel smoothing of x~ over the whole system (step 7)
+        if ((r = gs_impl(ctx, op, b, x, p->gs_sweeps, q))) return r;
+        if (stats) LC_CUDA(ctx, record(op->ev[3], q, cap));
+        // 6. convergence check of x~ and, if needed, the global solve from x~
+        if ((r = pcg_impl(ctx, op, b, x, &p->global, op->ctrl, false, q))) return r;
+        if (stats) LC_CUDA(ctx, record(op->ev[4], q, cap));
+        return LC_OK;
+    });
     if (rc) return rc;
-    if (stats) LC_CUDA(ctx, cudaEventRecord(op->ev[1], s));
-    // 2. subsystem B x_B = b_B - E x_C (Eq. loc-equ)
-    if ((rc = extract_impl(ctx, op, op->mask_own, b, x, op->sub, s))) return rc;
-    if (stats) LC_CUDA(ctx, cudaEventRecord(op->ev[2], s));
-    // 3. local solve from x0 restricted to the domain, in place in sub.xL0
-    if ((rc = pcg_impl(ctx, op, op->sub.rhs, op->sub.xL0, &p->local, op->ctrl_loc, true, s))) return rc;
-    // 4. x~ = x0 with the local solution scattered in (Eq. sol-assemble)
-    LC_CUDA(ctx, lc::launch_assemble(op->sub.K, op->sub.l2g, op->sub.xL0, x, op->n, s));
-    // 5. Gauss-Seidel smoothing of x~ over the whole system (step 7)
-    if ((rc = gs_impl(ctx, op, b, x, p->gs_sweeps, s))) return rc;
-    if (stats) LC_CUDA(ctx, cudaEventRecord(op->ev[3], s));
-    // 6. convergence check of x~ and, if needed, the global solve from x~
-    if ((rc = pcg_impl(ctx, op, b, x, &p->global, op->ctrl, false, s))) return rc;
     if (!stats) return LC_OK;
-    LC_CUDA(ctx, cudaEventRecord(op->ev[4], s));
     LC_CUDA(ctx, cudaStreamSynchronize(s));
     lc::Ctrl cg, cl;
     if ((rc = read_ctrl(ctx, op->ctrl, &cg)) || (rc = read_ctrl(ctx, op->ctrl_loc, &cl))) return rc;
@@ -1215,11 +1341,11 @@ int lc_solve_local_then_global(lc_ctx *ctx, const lc_op *op, const double *b, do
     stats->restarts = cg.restarts;
     stats->relres_tilde = cg.relres0;
     stats->relres_final = cg.relres;
-    cudaEventElapsedTime(&stats->t_mark_ms, op->ev[0], op->ev[1]);
-    cudaEventElapsedTime(&stats->t_extract_ms, op->ev[1], op->ev[2]);
-    cudaEventElapsedTime(&stats->t_local_ms, op->ev[2], op->ev[3]);
-    cudaEventElapsedTime(&stats->t_global_ms, op->ev[3], op->ev[4]);
-    cudaEventElapsedTime(&stats->t_total_ms, op->ev[0], op->ev[4]);
+    stats->t_mark_ms = elapsed_ms(op->ev[0], op->ev[1]);
+    stats->t_extract_ms = elapsed_ms(op->ev[1], op->ev[2]);
+    stats->t_local_ms = elapsed_ms(op->ev[2], op->ev[3]);
+    stats->t_global_ms = elapsed_ms(op->ev[3], op->ev[4]);
+    stats->t_total_ms = elapsed_ms(op->ev[0], op->ev[4]);
     int st = cl.status != LC_OK ? cl.status : (cl.converged == -1 && cg.K > 0 ? LC_ERR_BREAKDOWN : LC_OK);
     if (st == LC_OK) st = status_of(cg);
     stats->status = st;

@@ -102,3 +102,49 @@ def test_krylov_breakdown_is_reported_and_context_survives(kind, precision):
         s = lcg.Stats()
         call(x, s)
         assert s.status == 0 and oracle.relres(A, b, x.cpu().numpy()) <= 1e-8
+
+
+@pytest.mark.parametrize("kind", ["stencil", "csr"])
+def test_graph_replay_matches_direct_launches(kind):
+    """Small systems run each solve call as a cached CUDA graph; the result
+    and the statistics equal those of direct launches bit for bit, over
+    repeated calls (replays) with changing data in the same buffers."""
+    lcg.build()
+    ctx = lcg.Context(0)
+    cu = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=DEV)  # noqa: E731
+    op = gen.random_stencil_2d(11, 50, 41)
+    A = oracle.from_stencil(op)
+
+    def make():
+        if kind == "stencil":
+            return lcg.StencilOperator(ctx, op.shape, cu(op.D), cu(op.Tx), cu(op.Ty))
+        return lcg.CsrOperator(ctx, cu(A.rowptr, torch.int32), cu(A.col, torch.int32), cu(A.val))
+
+    graphed, direct = make(), make()
+    direct.set_tuning("graph_max_cells", 0)
+    assert graphed.get_tuning("graph_max_cells") >= op.n
+    rng = np.random.default_rng(3)
+    prm = lcg.default_params(tol=1e-10)
+    sp = lcg.SolveParams(1e-10, 100000, lcg.PREC_FP64, 0.0, 0)
+    bg, bd, xg, xd = (cu(np.zeros(op.n)) for _ in range(4))
+    for rep in range(3):
+        x0 = 1.0 + 0.1 * rng.standard_normal(op.n)
+        b = gen.csr_matvec(A.rowptr, A.col, A.val, x0)
+        b[rng.integers(op.n)] += 1.0
+        for call in ("alg1", "pcg"):
+            res = []
+            for gop, bb, xx in ((graphed, bg, xg), (direct, bd, xd)):
+                bb.copy_(cu(b))
+                xx.copy_(cu(x0))
+                st = lcg.Stats()
+                if call == "alg1":
+                    lcg.solve_local_then_global(ctx, gop, bb, xx, prm, st)
+                else:
+                    lcg.pcg_solve(ctx, gop, bb, xx, sp, st)
+                res.append((xx.cpu().numpy().copy(), st.as_dict()))
+            (x1, s1), (x2, s2) = res
+            assert np.array_equal(x1.view(np.int64), x2.view(np.int64)), (rep, call)
+            for k in ("K", "nnzB", "it_local", "it_global", "restarts", "early_exit", "status"):
+                assert s1[k] == s2[k], (rep, call, k)
+            assert s1["relres_final"] == s2["relres_final"]
+            assert oracle.relres(A, b, x1) <= 1e-10
