@@ -849,7 +849,7 @@ def batched_items(items, dev, reps, seq_alg1=False):
     return out
 
 
-PROFILE_CASES = ["global2d", "alg1", "alg1_gradient", "mixed2d", "fp64_3d", "mixed3d", "csr3t", "batched"]
+PROFILE_CASES = ["global2d", "alg1", "alg1_gradient", "mixed2d", "fp64_3d", "mixed3d", "csr3t", "batched", "heat"]
 
 
 def profile_case(args):
@@ -862,7 +862,9 @@ def profile_case(args):
     mixed3d: Alg 1 with FP32 inner CG, one ir_kernel launch).  csr3t: the 3T
     system on an n x n grid, one global pcg_kernel launch.  batched: the
     first --systems systems of the 512-system batch solved once without
-    graph capture (one batched_kernel launch)."""
+    graph capture (one batched_kernel launch).  heat: the first linear
+    system of the nonlinear heat test on an n x n grid, by the global PCG and
+    then by Alg 1 with gradient marking."""
     import numpy as np
     import torch
 
@@ -905,6 +907,18 @@ def profile_case(args):
             prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-10,
                                      precision=lcg.PREC_MIXED, inner_tol=1e-5)
             lcg.solve_local_then_global(ctx, gop, T(d["b"]), x, prm, st)
+    elif kind == "heat":   # the first linear system of the heat test (Sec. 3.2) on n x n cells
+        xc = (np.arange(n) + 0.5) / n
+        T0 = T(np.tile(np.exp(-100.0 * xc) + 1e-4, n))
+        bt, bv = [lcg.BC_DIRICHLET, lcg.BC_DIRICHLET, lcg.BC_NEUMANN, lcg.BC_NEUMANN], [1.0, 1e-4, 0.0, 0.0]
+        D, Tx, Ty, b = (torch.empty(n * n, dtype=torch.float64, device=dev) for _ in range(4))
+        lcg.heat2d_assemble(ctx, (n, n), 1.0 / n, 1e-2, bt, bv, T0 ** 3.5, T0, D, Tx, Ty, b)
+        gop = lcg.StencilOperator(ctx, (n, n, 1), D, Tx, Ty)
+        x = T0.clone()
+        lcg.pcg_solve(ctx, gop, b, x, lcg.SolveParams(1e-10, 100000, lcg.PREC_FP64, 0.0, 0), st)
+        x = T0.clone()
+        lcg.solve_local_then_global(ctx, gop, b, x,
+                                    lcg.default_params(lcg.MARK_GRADIENT, alpha=1e-4, grad_layers=0, tol=1e-10), st)
     elif kind == "csr3t":
         rp, ci, av = gen.threeT_2d(11, n, n)
         rng = np.random.default_rng(5)

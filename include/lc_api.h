@@ -515,6 +515,10 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  *       grid kernel above roughly 10,000 rows.)
  *   "local_cluster_threads" 256, 512 or 1024 (default 256): threads per CTA
  *       of that cluster.
+ *   "local_cluster_ctas" 0, 2, 4, 8 or 16 (default 0 = the largest cluster the
+ *       GPU schedules, 16 on a GB300): CTAs of that cluster.  Fewer CTAs give
+ *       cheaper barriers and less FP64 throughput; a subsystem whose rows do
+ *       not fit goes to the grid-wide kernel as before.
  *   "local_grid_cap" 0..4096 (default 0 = one block per SM): blocks of the
  *       grid-wide local solve kernel.
  * Unknown keys or out-of-range values return LC_ERR_INVALID_ARG. */

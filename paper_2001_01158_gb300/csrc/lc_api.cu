@@ -69,6 +69,7 @@ struct lc_op {
     int local_single = 0;               // local solves: one grid reduction per iteration
     int local_grid_cap = 0;             // local solves: blocks of the grid kernel (0 = one per SM)
     int local_cluster_threads = 256;
+    int local_cluster_ctas = 0;         // CTAs of that cluster (0: the largest the GPU schedules)
     int pcg_scaled = 1;      // 2D FP64: iterate on D^-1/2 A D^-1/2 (fewer FP64 instructions)
     int pcg_big = 1;         // 2D solves: one 768-thread block per SM (2 % faster at 2048^2, mixed 5 %)
     int pcg_pairdot = 1;     // 2D scaled wide FP64: dots and block sums on FP32 pairs (7 % faster at 2048^2)
@@ -371,7 +372,7 @@ int pcg_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_
         const bool cl = op->local_cluster_rows > 0 && p->precision == LC_PREC_FP64 && lc::cluster_local_rows() > 0;
         if (cl)
             LC_CUDA(ctx, lc::launch_pcg_csr_cluster(sub_csr(op), a, op->local_cluster_rows, op->local_cluster_threads,
-                                                    ctrl, s));
+                                                    op->local_cluster_ctas, ctrl, s));
         const int cap = op->local_grid_cap > 0 ? op->local_grid_cap : ctx->sms;
         if (op->local_single && p->precision == LC_PREC_FP64)
             LC_CUDA(ctx, lc::launch_pcg_csr_single(sub_csr(op), a, w, ctrl, cap, s, cl));
@@ -909,6 +910,12 @@ int lc_op_set_tuning(lc_op *op, const char *key, int32_t value) {
         op->local_single = value;
         return LC_OK;
     }
+    if (!strcmp(key, "local_cluster_ctas")) {
+        if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16)
+            return fail(op->ctx, LC_ERR_INVALID_ARG, "local_cluster_ctas must be 0, 2, 4, 8 or 16");
+        op->local_cluster_ctas = value;
+        return LC_OK;
+    }
     if (!strcmp(key, "local_cluster_threads")) {
         if (value != 256 && value != 512 && value != 1024)
             return fail(op->ctx, LC_ERR_INVALID_ARG, "local_cluster_threads must be 256, 512 or 1024");
@@ -925,6 +932,7 @@ int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value) {
     if (!strcmp(key, "pcg_scaled")) { *value = op->pcg_scaled; return LC_OK; }
     if (!strcmp(key, "local_cluster_rows")) { *value = op->local_cluster_rows; return LC_OK; }
     if (!strcmp(key, "local_cluster_threads")) { *value = op->local_cluster_threads; return LC_OK; }
+    if (!strcmp(key, "local_cluster_ctas")) { *value = op->local_cluster_ctas; return LC_OK; }
     if (!strcmp(key, "local_single")) { *value = op->local_single; return LC_OK; }
     if (!strcmp(key, "pcg_wide")) { *value = op->pcg_wide; return LC_OK; }
     if (!strcmp(key, "pcg_big")) { *value = op->pcg_big; return LC_OK; }

@@ -437,19 +437,22 @@ int cluster_local_rows() {
     return c.C * c.rcap;
 }
 
-cudaError_t launch_pcg_csr_cluster(const Csr &op, const PcgArgs &a, int max_rows, int threads, Ctrl *ctrl,
+cudaError_t launch_pcg_csr_cluster(const Csr &op, const PcgArgs &a, int max_rows, int threads, int ctas, Ctrl *ctrl,
                                    cudaStream_t s) {
     const ClConfig c = cluster_config();
     if (c.C == 0) return cudaErrorNotSupported;
     if (threads < 32 || threads > kClThreads || threads % 32) return cudaErrorInvalidValue;
+    // fewer CTAs than the largest cluster the GPU schedules: cheaper barriers,
+    // less FP64 throughput (the kernel hands larger systems to the grid kernel)
+    const int C = ctas > 0 && ctas < c.C ? ctas : c.C;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(c.C);
+    cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = c.smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = c.C;
+    at[0].val.clusterDim.x = C;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;

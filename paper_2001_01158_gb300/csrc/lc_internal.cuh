@@ -180,7 +180,7 @@ cudaError_t launch_pcg_csr_single(const Csr &op, const PcgArgs &a, PcgWork &w, C
 // (cluster_local_rows(); 0 if the device cannot run the cluster); sets
 // ctrl->done
 int cluster_local_rows();
-cudaError_t launch_pcg_csr_cluster(const Csr &op, const PcgArgs &a, int max_rows, int threads, Ctrl *ctrl,
+cudaError_t launch_pcg_csr_cluster(const Csr &op, const PcgArgs &a, int max_rows, int threads, int ctas, Ctrl *ctrl,
                                    cudaStream_t s);
 cudaError_t launch_dinv_stencil(int64_t n, const double *D, double *dinv, float *D32, const double *Tx,
                                 const double *Ty, const double *Tz, float *Tx32, float *Ty32, float *Tz32,
