@@ -573,6 +573,25 @@ LC_EXPORT const char *lc_last_error(const lc_ctx *ctx);
  * For accounting only: a benchmark reads it before and after a timed region. */
 LC_EXPORT int64_t lc_kernel_launch_count(void);
 
+/* Bounds-checked builds only (the library compiled with -DLC_CHECKED, a
+ * development build): every index the kernels take from data (CSR column
+ * indices, the local domain's index maps) is tested against its range; a
+ * failing index is replaced by a valid one and recorded.  This call waits
+ * for nothing (synchronise first), collects and clears the records:
+ * *failures (may be NULL) = the number of kernel files with a recorded
+ * failure, `where` (len bytes, may be NULL) = "file:line" of the first.
+ * Returns LC_OK, or LC_ERR_UNSUPPORTED in an ordinary build. */
+LC_EXPORT int lc_checked_status(int32_t *failures, char *where, int32_t len);
+
+/* Bounds-checked builds only: positive control of the checks.  Launches on
+ * `stream` one thread that asks for element 4 of a 4-element device array
+ * through the check; the check records the failure and substitutes element 0,
+ * so nothing is accessed out of range.  After a synchronise,
+ * lc_checked_status reports one failure in lc_api.cu.  Returns LC_OK,
+ * LC_ERR_CUDA if the launch failed, or LC_ERR_UNSUPPORTED (launching
+ * nothing) in an ordinary build. */
+LC_EXPORT int lc_checked_selftest(void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ from dataclasses import dataclass
 
 import torch
 
-from .build import LIB, build_library
+from .build import CHECKED_LIB, LIB, build_library
 
 __all__ = [
     "LcError", "Context", "StencilOperator", "CsrOperator", "MarkParams", "SolveParams", "Params", "Stats",
@@ -94,9 +94,16 @@ class _Subsys(C.Structure):
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile liblc.so for sm_103a (in-tree) and return its path."""
-    return build_library(force=force)
+def build(force: bool = False, checked: bool = False) -> str:
+    """Compile liblc.so for sm_103a (in-tree) and return its path; with
+    checked=True the bounds-checked build (-DLC_CHECKED) instead."""
+    return build_library(force=force, checked=checked)
+
+
+def library_path() -> str:
+    """The library this process loads: the bounds-checked build when the
+    environment sets LC_CHECKED=1, else the ordinary one."""
+    return CHECKED_LIB if os.environ.get("LC_CHECKED", "0") == "1" else LIB
 
 
 def lib():
@@ -104,10 +111,11 @@ def lib():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB):
-        raise RuntimeError(f"{LIB} is missing: build it with paper_2001_01158_gb300.build() "
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2001_01158_gb300.build() "
                            "(the library has no CPU fallback)")
-    L = C.CDLL(LIB)
+    L = C.CDLL(path)
     vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
     L.lc_ctx_create.argtypes = [C.POINTER(vp), C.c_int]
     L.lc_ctx_destroy.argtypes = [vp]
@@ -137,6 +145,8 @@ def lib():
                                      vp, vp]
     L.lc_heat2d_step.argtypes = [vp, vp, C.POINTER(HeatParams), vp, vp, vp, vp, vp, vp, vp, C.POINTER(HeatStats), vp]
     L.lc_op_set_colouring.argtypes = [vp, vp, i32]
+    L.lc_checked_status.argtypes = [C.POINTER(i32), C.c_char_p, i32]
+    L.lc_checked_selftest.argtypes = [vp]
     _lib = L
     return L
 
@@ -389,6 +399,27 @@ def adjoint_grad(ctx: Context, op: "StencilOperator", k, dt: float, x, gx, lam, 
 def kernel_launch_count() -> int:
     """Kernels this library has launched in this process (lc_kernel_launch_count)."""
     return int(lib().lc_kernel_launch_count())
+
+
+def checked_selftest(stream=None) -> None:
+    """Record one deliberate, harmless index-check failure (lc_checked_selftest);
+    raises LcError with LC_ERR_UNSUPPORTED in an ordinary build."""
+    rc = lib().lc_checked_selftest(_stream(stream))
+    if rc:
+        raise LcError(rc, lib().lc_error_string(rc).decode())
+
+
+def checked_status() -> tuple[int, str]:
+    """(number of kernel files with a failed index check, "file:line" of the
+    first) from the bounds-checked build, clearing the records
+    (lc_checked_status; synchronise the device first).  Raises LcError with
+    LC_ERR_UNSUPPORTED when the loaded library is the ordinary build."""
+    n = C.c_int32(0)
+    buf = C.create_string_buffer(256)
+    rc = lib().lc_checked_status(C.byref(n), buf, len(buf))
+    if rc:
+        raise LcError(rc, buf.value.decode())
+    return int(n.value), buf.value.decode()
 
 
 def default_params(mark_mode=MARK_RESIDUAL, thr_mode=THR_REL_MAX, thr_param=1e-3, exp_mode=EXP_DILATE, exp_rounds=2,

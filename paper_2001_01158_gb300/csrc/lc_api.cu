@@ -14,12 +14,30 @@
 #include <vector>
 
 #include <atomic>
+#include <mutex>
 
 #include "lc_internal.cuh"
 
 namespace lc {
 static std::atomic<long long> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// the check words of the translation units of a bounds-checked build
+static std::mutex g_check_mu;
+static std::vector<std::pair<unsigned (*)(), const char *>> &check_units() {
+    static std::vector<std::pair<unsigned (*)(), const char *>> v;
+    return v;
+}
+void register_check_word(unsigned (*take)(), const char *unit) {
+    std::lock_guard<std::mutex> g(g_check_mu);
+    check_units().push_back({take, unit});
+}
+#ifdef LC_CHECKED
+namespace {
+__device__ int g_selftest_probe[4];
+__global__ void checked_selftest_kernel(int i) { g_selftest_probe[LC_IDX(i, 4)] += 1; }
+}  // namespace
+#endif
 }  // namespace lc
 
 struct lc_ctx {
@@ -420,6 +438,40 @@ const char *lc_error_string(int code) {
 const char *lc_last_error(const lc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int64_t lc_kernel_launch_count(void) { return (int64_t)lc::g_launches.load(std::memory_order_relaxed); }
+
+int lc_checked_selftest(void *stream) {
+#ifndef LC_CHECKED
+    (void)stream;
+    return LC_ERR_UNSUPPORTED;
+#else
+    lc::checked_selftest_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(4);
+    lc::note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? LC_OK : LC_ERR_CUDA;
+#endif
+}
+
+int lc_checked_status(int32_t *failures, char *where, int32_t len) {
+    if (failures) *failures = 0;
+    if (where && len > 0) where[0] = 0;
+#ifndef LC_CHECKED
+    if (where && len > 0) snprintf(where, (size_t)len, "not a bounds-checked build");
+    return LC_ERR_UNSUPPORTED;
+#else
+    std::lock_guard<std::mutex> g(lc::g_check_mu);
+    int32_t bad = 0;
+    for (const auto &u : lc::check_units()) {
+        const unsigned line = u.first();
+        if (!line) continue;
+        if (!bad && where && len > 0) {
+            const char *base = strrchr(u.second, '/');
+            snprintf(where, (size_t)len, "%s:%u", base ? base + 1 : u.second, line);
+        }
+        ++bad;
+    }
+    if (failures) *failures = bad;
+    return LC_OK;
+#endif
+}
 
 int lc_assemble_diffusion_2d(lc_ctx *ctx, const int32_t shape[2], const double *k, double dt, double *D,
                              double *Tx, double *Ty, void *stream) {

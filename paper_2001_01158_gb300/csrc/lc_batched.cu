@@ -228,6 +228,7 @@ struct Sys {
     int64_t orp;   // offset of B's row pointers (o + s)
     int y0, y1;    // this CTA's grid rows
     int l0, l1;    // this CTA's rows of the subsystem
+    int K;         // rows of the subsystem
 };
 
 // canonical residual of cell i (local index), FP64
@@ -288,7 +289,7 @@ __device__ int inner_cg(const BatchView &V, const Sys &S, Team<BS> &tm, int lo, 
             float qi = 0.f;
             const int32_t e0 = V.rowptr[S.orp + i], e1 = ldn<TEAM>(V.rowptr + S.orp + i + 1, i + 1 == S.l1);
             for (int32_t e = e0; e < e1; ++e) {
-                const int32_t c = V.col[S.oe + e];
+                const int32_t c = LC_IDX(V.col[S.oe + e], S.K);
                 qi = fmaf(V.val32[S.oe + e], ldn<TEAM>(p + c, c < S.l0 || c >= S.l1), qi);
             }
             return qi;
@@ -387,7 +388,7 @@ __device__ void solve_system(const BatchView &V, const BatchParams &P, int s, Te
     const int rows = (S.ny + tm.size - 1) / tm.size;
     S.y0 = min(S.ny, tm.rank * rows);
     S.y1 = min(S.ny, S.y0 + rows);
-    S.l0 = S.l1 = 0;
+    S.l0 = S.l1 = S.K = 0;
     const int lo = S.y0 * S.nx, hi = S.y1 * S.nx;
     int32_t *st = V.stat_i + 8 * (int64_t)s;
     double *sd = V.stat_d + 4 * (int64_t)s;
@@ -470,12 +471,13 @@ __device__ void solve_system(const BatchView &V, const BatchParams &P, int s, Te
     const int l0 = (int)(first & 0xffffffffull), l1 = (int)(run & 0xffffffffull);   // this CTA's local rows
     S.l0 = l0;
     S.l1 = l1;
+    S.K = K;
     if (tm.rank == 0 && threadIdx.x == 0) rp[K] = nzB;
     tm.sync();
 
     // ---- gather B (FP64 and FP32 values), rhs (canonical order), xL0, 1/diag
     for (int l = l0 + threadIdx.x; l < l1; l += BS) {
-        const int i = l2g[l];
+        const int i = LC_IDX(l2g[l], S.n);
         const int ux = i % S.nx, uy = i / S.nx;
         const int64_t g = S.o + i;
         int32_t e = rp[l];
@@ -510,7 +512,7 @@ __device__ void solve_system(const BatchView &V, const BatchParams &P, int s, Te
                 double a = 0.0;
                 const int32_t e1 = ldn<TEAM>(rp + l + 1, l + 1 == S.l1);   // rp[K] is rank 0's
                 for (int32_t e = rp[l]; e < e1; ++e) {
-                    const int32_t c = V.col[S.oe + e];
+                    const int32_t c = LC_IDX(V.col[S.oe + e], S.K);
                     a = fma(V.val[S.oe + e], ldn<TEAM>(V.xl + S.o + c, c < S.l0 || c >= S.l1), a);
                 }
                 const double rl = V.rhs[S.o + l] - a;
@@ -532,7 +534,7 @@ __device__ void solve_system(const BatchView &V, const BatchParams &P, int s, Te
         }
     }
     // ---- assembly x~ = x0 with the local solution
-    for (int l = l0 + threadIdx.x; l < l1; l += BS) V.x[S.o + l2g[l]] = V.xl[S.o + l];
+    for (int l = l0 + threadIdx.x; l < l1; l += BS) V.x[S.o + LC_IDX(l2g[l], S.n)] = V.xl[S.o + l];
     tm.sync();
 
     // ---- check of x~ and global solve: iterative refinement on A

@@ -126,6 +126,7 @@ __device__ __forceinline__ bool cl_flag(double f) { return __double_as_longlong(
 struct ClPart {
     int R;
     float inv;
+    int K;   // rows of the system (the range of a column index)
     __device__ __forceinline__ int owner(int j) const {
         int o = (int)((float)j * inv);
         if (o * R > j) --o;
@@ -137,6 +138,7 @@ struct ClPart {
 // Row j's entry of a distributed vector (`vec` = this CTA's array; the same
 // offset in the owner's shared memory).
 __device__ __forceinline__ double cl_load(cg::cluster_group &cl, double *vec, int j, const ClPart &pt, int rank) {
+    j = LC_IDX(j, pt.K);
     const int owner = pt.owner(j);
     const int lj = j - owner * pt.R;
     if (owner == rank) return vec[lj];
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(kClThreads, 1)
         ctrl->early = 0;
     }
     const ClMem m = carve_cl(cl_smem, rcap);
-    const ClPart pt{R, 1.0f / (float)R};
+    const ClPart pt{R, 1.0f / (float)R, K};
     const int r0 = min(K, rank * R), r1 = min(K, r0 + R);
     const int tid = (int)threadIdx.x, nth = (int)blockDim.x;
 

@@ -24,6 +24,46 @@ constexpr int kMaxExpRounds = 64;
 constexpr int kMaxGrid = 4096;                          // persistent-kernel blocks (partials capacity)
 constexpr int kPartialSlots = 16;                       // grid-reduction slots of kMaxGrid partials each
 
+// ---------------------------------------------------------------- bounds-checked build
+//
+// Built with -DLC_CHECKED (a separate library, `build_library(checked=True)`),
+// every index a kernel takes from data -- CSR column indices, the
+// compaction's g2l / l2g maps -- is tested against its range before it is
+// used.  A failing index is replaced by 0 (an element that exists) and the
+// first failure's source line is recorded in the translation unit's check
+// word; lc_checked_status() collects and clears the words of all units.  It
+// stands in for a memory checker that this environment does not run; the
+// ordinary build compiles LC_IDX to the bare index.
+void register_check_word(unsigned (*take)(), const char *unit);
+#ifdef LC_CHECKED
+namespace {
+__device__ unsigned g_check_word;
+template <class I>
+__device__ __forceinline__ I checked_index(I i, long long n, unsigned line) {
+    if (!((long long)i >= 0 && (long long)i < n)) {
+        atomicCAS(&g_check_word, 0u, line);
+        return I(0);
+    }
+    return i;
+}
+unsigned take_check_word() {
+    unsigned v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_check_word, sizeof v) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_check_word, &z, sizeof z) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
+struct CheckWordRegistration {
+    CheckWordRegistration() { register_check_word(&take_check_word, __BASE_FILE__); }
+} check_word_registration;
+}  // namespace
+#define LC_IDX(i, n) ::lc::checked_index((i), (long long)(n), (unsigned)__LINE__)
+#else
+#define LC_IDX(i, n) (i)
+#endif
+
 // ---------------------------------------------------------------- descriptors
 
 // Structured operator: the diagonal D and face conductances T (off-diagonal

@@ -44,7 +44,7 @@ __device__ __forceinline__ unsigned count_local_nbrs(const Stencil &op, const ui
 __device__ __forceinline__ unsigned count_local_csr(const Csr &op, const uint8_t *__restrict__ mask, int64_t i) {
     unsigned c = 0;
     const int32_t e1 = op.rp[i + 1];
-    for (int32_t e = op.rp[i]; e < e1; ++e) c += mask[op.ci[e]];
+    for (int32_t e = op.rp[i]; e < e1; ++e) c += mask[LC_IDX(op.ci[e], op.n)];
     return c;   // includes the diagonal (mask[i] == 1 for a local row)
 }
 
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kXThreads) write_maps_kernel(OP op, int64_t n,
             if (v[k]) {
                 const int32_t l = (int32_t)(off & 0xffffffffull);
                 g2l[i] = l;
-                l2g[l] = (int32_t)i;
+                l2g[LC_IDX(l, n)] = (int32_t)i;
                 rowptr[l] = (int32_t)(off >> 32);
             } else {
                 g2l[i] = -1;
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) gather_stencil_kernel(Stencil op, const i
     const int32_t K = *Kp;
     const int64_t sxy = (int64_t)op.nx * op.ny;
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < K; l += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = l2g[l];
+        const int64_t i = LC_IDX(l2g[l], op.n);
         const unsigned ux = (unsigned)(i % op.nx);
         const unsigned uy = (unsigned)((i / op.nx) % op.ny);
         const unsigned uz = DIM == 3 ? (unsigned)(i / sxy) : 0u;
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256) gather_stencil_kernel(Stencil op, const i
         // neighbour j with coefficient -T (T > 0): local -> entry, else rhs
         auto visit = [&](int64_t j, double T) {
             const int32_t gj = g2l[j];
-            if (gj >= 0) { col[e] = gj; val[e] = -T; ++e; }
+            if (gj >= 0) { col[e] = LC_IDX(gj, K); val[e] = -T; ++e; }
             else s = __fma_rn(T, x0[j], s);
         };
         if (DIM == 3 && uz > 0) visit(i - sxy, op.Tz[i - sxy]);
@@ -220,14 +220,14 @@ __global__ void __launch_bounds__(256) gather_csr_kernel(Csr op, const int32_t *
                                                          double *__restrict__ rhs, double *__restrict__ xL0) {
     const int32_t K = *Kp;
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < K; l += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = l2g[l];
+        const int32_t i = LC_IDX(l2g[l], op.n);
         int32_t e = rowptr[l];
         double s = b[i];
         const int32_t e1 = op.rp[i + 1];
         for (int32_t a = op.rp[i]; a < e1; ++a) {
-            const int32_t j = op.ci[a];
+            const int32_t j = LC_IDX(op.ci[a], op.n);
             const int32_t gj = g2l[j];
-            if (gj >= 0) { col[e] = gj; val[e] = op.av[a]; ++e; }
+            if (gj >= 0) { col[e] = LC_IDX(gj, K); val[e] = op.av[a]; ++e; }
             else s = __fma_rn(-op.av[a], x0[j], s);
         }
         rhs[l] = s;
@@ -236,10 +236,10 @@ __global__ void __launch_bounds__(256) gather_csr_kernel(Csr op, const int32_t *
 }
 
 __global__ void assemble_kernel(const int32_t *__restrict__ Kp, const int32_t *__restrict__ l2g,
-                                const double *__restrict__ xbar, double *__restrict__ x) {
+                                const double *__restrict__ xbar, double *__restrict__ x, int64_t n) {
     const int32_t K = *Kp;
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < K; l += (int64_t)gridDim.x * blockDim.x)
-        x[l2g[l]] = xbar[l];
+        x[LC_IDX(l2g[l], n)] = xbar[l];
 }
 
 inline unsigned flat_grid(int64_t n) {
@@ -291,7 +291,7 @@ cudaError_t launch_extract_csr(const Csr &op, const uint8_t *mask, const double 
 
 cudaError_t launch_assemble(const int32_t *K_dev, const int32_t *l2g, const double *xbar, double *x, int64_t cap,
                             cudaStream_t s) {
-    assemble_kernel<<<flat_grid(cap), 256, 0, s>>>(K_dev, l2g, xbar, x);
+    assemble_kernel<<<flat_grid(cap), 256, 0, s>>>(K_dev, l2g, xbar, x, cap);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -50,7 +50,7 @@ __device__ __forceinline__ double csr_residual_row(const Csr &op, const double *
                                                    const double *__restrict__ x, int32_t i) {
     double r = b[i];
     const int32_t e1 = op.rp[i + 1];
-    for (int32_t e = op.rp[i]; e < e1; ++e) r = __fma_rn(-op.av[e], x[op.ci[e]], r);
+    for (int32_t e = op.rp[i]; e < e1; ++e) r = __fma_rn(-op.av[e], x[LC_IDX(op.ci[e], op.n)], r);
     return r;
 }
 
@@ -256,7 +256,7 @@ __global__ void dilate_csr_kernel(Csr op, const uint8_t *__restrict__ in, uint8_
         if (!m) {
             const int32_t e1 = op.rp[i + 1];
             for (int32_t e = op.rp[i]; e < e1; ++e) {
-                const int32_t j = op.ci[e];
+                const int32_t j = LC_IDX(op.ci[e], op.n);
                 if (j != i && op.av[e] != 0.0 && in[j]) { m = 1; break; }
             }
         }
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(256) expand_paper_csr_kernel(Csr op, const dou
             double t = 0.0;
             const int32_t e1 = op.rp[j + 1];
             for (int32_t e = op.rp[j]; e < e1; ++e) {
-                const int32_t i = op.ci[e];
+                const int32_t i = LC_IDX(op.ci[e], op.n);
                 if (i == j || !in[i]) continue;
                 if (op.av[e] != 0.0) nbr = true;
                 t = __dadd_rn(t, fabs(__dmul_rn(op.av[e], x0[i])));
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(256) gradient_csr_kernel(Csr op, const double 
         double s = 0.0;
         const int32_t e1 = op.rp[i + 1];
         for (int32_t e = op.rp[i]; e < e1; ++e) {
-            const int32_t j = op.ci[e];
+            const int32_t j = LC_IDX(op.ci[e], op.n);
             if (j == i || op.av[e] == 0.0) continue;
             s = __dadd_rn(s, fabs(__dsub_rn(xi, x[j])));
         }

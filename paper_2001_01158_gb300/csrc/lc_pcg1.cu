@@ -74,7 +74,7 @@ __device__ bool cg1_setup(const Cg1Args &a, int32_t n, double *red, double &bb, 
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
         double ri = a.b[i];
         const int32_t e1 = cs.rp[i + 1];
-        for (int32_t e = cs.rp[i]; e < e1; ++e) ri = fma(-cs.av[e], ldcg(a.x + cs.ci[e]), ri);
+        for (int32_t e = cs.rp[i]; e < e1; ++e) ri = fma(-cs.av[e], ldcg(a.x + LC_IDX(cs.ci[e], n)), ri);
         a.r[0][i] = ri;
         acc[0] = fma(a.b[i], a.b[i], acc[0]);
         acc[1] = fma(ri, ri, acc[1]);
@@ -88,7 +88,7 @@ __device__ bool cg1_setup(const Cg1Args &a, int32_t n, double *red, double &bb, 
         double wi = 0.0;
         const int32_t e1 = cs.rp[i + 1];
         for (int32_t e = cs.rp[i]; e < e1; ++e) {
-            const int32_t j = cs.ci[e];
+            const int32_t j = LC_IDX(cs.ci[e], n);
             wi = fma(cs.av[e], a.dinv[j] * ldcg(a.r[0] + j), wi);
         }
         const double ri = a.r[0][i], ui = a.dinv[i] * ri;
@@ -128,7 +128,7 @@ __device__ int cg1_iterations(const Cg1Args &a, int32_t n, double *red, double g
             double wi = 0.0;
             const int32_t e1 = cs.rp[i + 1];
             for (int32_t e = cs.rp[i]; e < e1; ++e) {
-                const int32_t j = cs.ci[e];
+                const int32_t j = LC_IDX(cs.ci[e], n);
                 double uj;
                 if (j == i) {
                     uj = un_i;

@@ -869,7 +869,7 @@ struct OpCsr {
         each_cell([&](int64_t i) {
             T ax = T(0);
             const int32_t e1 = cs.rp[i + 1];
-            for (int32_t e = cs.rp[i]; e < e1; ++e) ax = fmaT(av[e], ldcg(V.x + cs.ci[e]), ax);
+            for (int32_t e = cs.rp[i]; e < e1; ++e) ax = fmaT(av[e], ldcg(V.x + LC_IDX(cs.ci[e], n)), ax);
             const T bi = V.b[i];
             const T ri = bi - ax;
             V.r[i] = ri;
@@ -896,7 +896,7 @@ struct OpCsr {
                 T qi = T(0), pi = T(0);
                 const int32_t e1 = cs.rp[i + 1];
                 for (int32_t e = cs.rp[i]; e < e1; ++e) {
-                    const int32_t j = cs.ci[e];
+                    const int32_t j = LC_IDX(cs.ci[e], n);
                     const T pj = ldcg(pout + j);
                     if (j == i) pi = pj;
                     qi = fmaT(av[e], pj, qi);
@@ -909,7 +909,7 @@ struct OpCsr {
                 T qi = T(0), pi = T(0);
                 const int32_t e1 = cs.rp[i + 1];
                 for (int32_t e = cs.rp[i]; e < e1; ++e) {
-                    const int32_t j = cs.ci[e];
+                    const int32_t j = LC_IDX(cs.ci[e], n);
                     const T zj = ldcg(V.z + j);
                     const T pj = first ? zj : fmaT(beta, ldcg(pold + j), zj);
                     if (j == i) pi = pj;

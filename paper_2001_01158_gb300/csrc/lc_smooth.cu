@@ -50,7 +50,7 @@ __global__ void gs_csr_kernel(Csr cs, const uint8_t *__restrict__ colour, const 
         double r = b[i], d = 0.0;
         const int32_t e1 = cs.rp[i + 1];
         for (int32_t e = cs.rp[i]; e < e1; ++e) {
-            const int32_t j = cs.ci[e];
+            const int32_t j = LC_IDX(cs.ci[e], cs.n);
             if (j == i) d = cs.av[e];
             else r = fma(-cs.av[e], x[j], r);
         }

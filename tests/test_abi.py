@@ -117,3 +117,26 @@ def test_context_may_be_destroyed_before_its_operators():
     # a new context and operator are created without inheriting an error
     ctx2 = lcg.Context(0)
     lcg.StencilOperator(ctx2, (4, 4, 1), D, T, T)
+
+
+def test_checked_entry_points_in_an_ordinary_build():
+    """The bounds-checked diagnostics exist in every build; the ordinary one
+    answers LC_ERR_UNSUPPORTED, reports no failures and launches nothing
+    (callable without a GPU)."""
+    L = C.CDLL(build_library())
+    L.lc_checked_status.argtypes = [C.POINTER(C.c_int32), C.c_char_p, C.c_int32]
+    L.lc_checked_selftest.argtypes = [C.c_void_p]
+    n = C.c_int32(7)
+    buf = C.create_string_buffer(64)
+    assert L.lc_checked_status(C.byref(n), buf, len(buf)) == 8
+    assert n.value == 0 and buf.value == b"not a bounds-checked build"
+    assert L.lc_checked_status(None, None, 0) == 8
+    assert L.lc_checked_selftest(None) == 8
+
+
+def test_checked_library_is_selected_by_the_environment(monkeypatch):
+    from paper_2001_01158_gb300.build import CHECKED_LIB, LIB
+    monkeypatch.delenv("LC_CHECKED", raising=False)
+    assert lcg.library_path() == LIB
+    monkeypatch.setenv("LC_CHECKED", "1")
+    assert lcg.library_path() == CHECKED_LIB and CHECKED_LIB != LIB
