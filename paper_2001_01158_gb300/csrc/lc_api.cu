@@ -71,6 +71,7 @@ struct lc_op {
     float *D32 = nullptr, *Tx32 = nullptr, *Ty32 = nullptr, *Tz32 = nullptr, *dinv32 = nullptr;
     double *work = nullptr;          // residual / gradient (N)
     uint8_t *mask_tmp = nullptr, *mask_own = nullptr;
+    uint32_t *bits_a = nullptr, *bits_b = nullptr;   // stencils: bit-packed mask rows (threshold, dilation)
     double *tree_a = nullptr, *tree_b = nullptr;
     lc::ExtractWork ew{};
     lc_subsys sub{};                 // internal subsystem buffers
@@ -212,6 +213,9 @@ void carve(lc_op *op, Carver &c) {
         op->Tyh32 = c.take<float>(n);
         op->Tzh32 = op->st.dim == 3 ? c.take<float>(n) : nullptr;
         op->sq32 = c.take<float>(n);
+        const size_t words = (size_t)op->st.ny * op->st.nz * lc::bits_words(op->st);
+        op->bits_a = c.take<uint32_t>(words);
+        op->bits_b = c.take<uint32_t>(words);
     }
 }
 
@@ -258,27 +262,14 @@ int run_threshold_expand(lc_ctx *ctx, const lc_op *op, const double *v, const do
                          uint8_t *mask, cudaStream_t s) {
     uint8_t *tmp = op->mask_tmp;
     if (op->kind == 0) {
-        const int lmax = lc::max_layers_per_pass(op->st.dim);
         if (exp_mode == LC_EXP_DILATE && rounds > 0) {
-            const int first = rounds < lmax ? rounds : lmax;
-            const int rest = rounds - first;
-            const int passes = 1 + (rest + lmax - 1) / lmax;
-            uint8_t *dst = ((passes - 1) % 2 == 0) ? mask : tmp;
-            LC_CUDA(ctx, lc::launch_threshold_dilate_stencil(op->st, v, first, dst, op->ctrl, s));
-            int left = rest;
-            uint8_t *cur = dst;
-            while (left > 0) {
-                const int l = left < lmax ? left : lmax;
-                uint8_t *nxt = cur == mask ? tmp : mask;
-                LC_CUDA(ctx, lc::launch_dilate_stencil_pass(op->st, l, cur, nxt, s));
-                cur = nxt;
-                left -= l;
-            }
+            LC_CUDA(ctx, lc::launch_threshold_dilate_bits(op->st, v, rounds, mask, op->bits_a, op->bits_b, op->ctrl,
+                                                          s));
             return LC_OK;
         }
         if (exp_mode == LC_EXP_PAPER && rounds > 0) {
             uint8_t *cur = (rounds % 2 == 0) ? mask : tmp;
-            LC_CUDA(ctx, lc::launch_threshold_dilate_stencil(op->st, v, 0, cur, op->ctrl, s));
+            LC_CUDA(ctx, lc::launch_threshold_dilate_bits(op->st, v, 0, cur, op->bits_a, op->bits_b, op->ctrl, s));
             for (int m = 0; m < rounds; ++m) {
                 uint8_t *nxt = cur == mask ? tmp : mask;
                 LC_CUDA(ctx, lc::launch_expand_paper_stencil(op->st, v, x0, m, cur, nxt, op->ctrl, s));
@@ -286,7 +277,7 @@ int run_threshold_expand(lc_ctx *ctx, const lc_op *op, const double *v, const do
             }
             return LC_OK;
         }
-        LC_CUDA(ctx, lc::launch_threshold_dilate_stencil(op->st, v, 0, mask, op->ctrl, s));
+        LC_CUDA(ctx, lc::launch_threshold_dilate_bits(op->st, v, 0, mask, op->bits_a, op->bits_b, op->ctrl, s));
         return LC_OK;
     }
     const int32_t n = (int32_t)op->n;

@@ -83,6 +83,11 @@ cudaError_t launch_tau_relmax(double beta, Ctrl *ctrl, double *tau_out, cudaStre
 cudaError_t launch_threshold_dilate_stencil(const Stencil &op, const double *v, int layers, uint8_t *mask,
                                             Ctrl *ctrl, cudaStream_t s);
 cudaError_t launch_dilate_stencil_pass(const Stencil &op, int layers, const uint8_t *in, uint8_t *out, cudaStream_t s);
+// Threshold and `layers` graph layers through bit-packed rows (any layer
+// count): bits_a, bits_b hold ny nz bits_words(op) words each.
+int bits_words(const Stencil &op);
+cudaError_t launch_threshold_dilate_bits(const Stencil &op, const double *v, int layers, uint8_t *mask,
+                                         uint32_t *bits_a, uint32_t *bits_b, Ctrl *ctrl, cudaStream_t s);
 inline int max_layers_per_pass(int dim) { return dim == 3 ? 2 : 4; }
 cudaError_t launch_threshold_csr(int32_t n, const double *v, uint8_t *mask, Ctrl *ctrl, cudaStream_t s);
 cudaError_t launch_dilate_csr(const Csr &op, const uint8_t *in, uint8_t *out, cudaStream_t s);

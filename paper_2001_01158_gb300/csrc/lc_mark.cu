@@ -10,6 +10,9 @@
 // round-to-nearest intrinsics so that the compiler can neither fuse nor
 // reorder it; the masks are therefore bit-identical to a serial evaluation.
 // Abs, max and the threshold tests run on the integer bit patterns.
+#include <algorithm>
+#include <cstdint>
+
 #include "lc_internal.cuh"
 
 namespace lc {
@@ -240,6 +243,95 @@ __global__ void __launch_bounds__(256) threshold_dilate_kernel(Stencil op, TileG
             const int64_t i = gx + (int64_t)op.nx * (gy + (int64_t)op.ny * gz);
             const int e = (lx + g.L) + g.ex * ((ly + g.L) + g.ey * (lz + (op.dim == 3 ? g.L : 0)));
             mask_out[i] = f0[e];
+        }
+    }
+}
+
+// ---- bit-packed threshold and dilation (structured grids)
+//
+// The mask of a grid row (fixed y, z) as ceil(nx / 32) 32-bit words, bit b of
+// word w = cell x = 32 w + b.  L rounds of the 4- (6-) neighbour dilation
+// confined to the grid mark exactly the cells within L1 distance L of a
+// marked cell -- a shortest lattice path between two cells of a box stays in
+// the box -- so one pass ORs, for every row offset (dy, dz) with
+// |dy| + |dz| <= L, the source row spread along x by L - |dy| - |dz| cells
+// (funnel shifts across the neighbouring words).
+
+// Threshold: bits of |v_i| > tau; a warp packs 32 words (1024 cells) of one row
+// from coalesced loads, one ballot per word.
+__global__ void __launch_bounds__(256) threshold_bits_kernel(Stencil op, int W, const double *__restrict__ v,
+                                                             uint32_t *__restrict__ bits, Ctrl *ctrl) {
+    const unsigned long long tbits = abs_bits(ctrl->tau);
+    const int lane = threadIdx.x & 31;
+    const int chunks = (W + 31) / 32;
+    const int64_t tasks = (int64_t)op.ny * op.nz * chunks;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < tasks; t += nwarps) {
+        const int64_t row = t / chunks;
+        const int wx0 = (int)(t % chunks) * 32;
+        const double *vr = v + row * op.nx;
+        uint32_t mine = 0;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const int x = (wx0 + k) * 32 + lane;
+            const bool f = x < op.nx && abs_gt(vr[x], tbits);
+            const uint32_t w = __ballot_sync(kFull, f);
+            if (lane == k) mine = w;
+        }
+        if (wx0 + lane < W) bits[row * W + wx0 + lane] = mine;
+    }
+}
+
+// One pass of L layers over the word rows: into words (BYTES false) or into
+// the byte mask (BYTES true), one thread per word.
+template <bool BYTES>
+__global__ void __launch_bounds__(256) dilate_bits_kernel(Stencil op, int W, int L, const uint32_t *__restrict__ in,
+                                                          uint32_t *__restrict__ out, uint8_t *__restrict__ mask,
+                                                          int vec16) {
+    const int64_t rows = (int64_t)op.ny * op.nz;
+    const int64_t nw = rows * W;
+    const int tail = op.nx & 31;
+    const uint32_t last = tail ? (1u << tail) - 1u : 0xffffffffu;
+    const int Lz = op.dim == 3 ? L : 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nw; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = t / W;
+        const int wx = (int)(t - row * W);
+        const int y = (int)(row % op.ny), z = (int)(row / op.ny);
+        uint32_t o = 0;
+        for (int dz = -Lz; dz <= Lz; ++dz) {
+            const int zz = z + dz;
+            if (zz < 0 || zz >= op.nz) continue;
+            const int ry = L - (dz < 0 ? -dz : dz);
+            for (int dy = -ry; dy <= ry; ++dy) {
+                const int yy = y + dy;
+                if (yy < 0 || yy >= op.ny) continue;
+                const int r = ry - (dy < 0 ? -dy : dy);
+                const uint32_t *src = in + ((int64_t)zz * op.ny + yy) * W + wx;
+                const uint32_t c = src[0];
+                uint32_t acc = c;
+                if (r > 0) {
+                    const uint32_t lft = wx > 0 ? src[-1] : 0u, rgt = wx + 1 < W ? src[1] : 0u;
+                    for (int d = 1; d <= r; ++d)
+                        acc |= __funnelshift_l(lft, c, d) | __funnelshift_r(c, rgt, d);
+                }
+                o |= acc;
+            }
+        }
+        if (wx == W - 1) o &= last;
+        if constexpr (!BYTES) {
+            out[t] = o;
+        } else {
+            uint8_t *m = mask + row * op.nx + (int64_t)wx * 32;
+            if (vec16 && wx < W - 1 + (tail == 0)) {   // 32 whole, 16-byte aligned cells
+                uint32_t q[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) q[k] = (((o >> (4 * k)) & 15u) * 0x00204081u) & 0x01010101u;
+                reinterpret_cast<uint4 *>(m)[0] = make_uint4(q[0], q[1], q[2], q[3]);
+                reinterpret_cast<uint4 *>(m)[1] = make_uint4(q[4], q[5], q[6], q[7]);
+            } else {
+                const int nb = min(32, op.nx - wx * 32);
+                for (int k = 0; k < nb; ++k) m[k] = (uint8_t)((o >> k) & 1u);
+            }
         }
     }
 }
@@ -479,6 +571,35 @@ cudaError_t launch_threshold_dilate_stencil(const Stencil &op, const double *v, 
     const size_t smem = 2 * (size_t)g.ex * g.ey * g.ez;
     const unsigned nb = (unsigned)((int64_t)ntx * nty * ntz);
     threshold_dilate_kernel<true><<<nb, 256, smem, s>>>(op, g, v, nullptr, mask, ctrl);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+int bits_words(const Stencil &op) { return (op.nx + 31) / 32; }
+
+cudaError_t launch_threshold_dilate_bits(const Stencil &op, const double *v, int layers, uint8_t *mask,
+                                         uint32_t *bits_a, uint32_t *bits_b, Ctrl *ctrl, cudaStream_t s) {
+    const int W = bits_words(op);
+    const int64_t rows = (int64_t)op.ny * op.nz;
+    const int64_t tasks = rows * ((W + 31) / 32);
+    const unsigned nba = (unsigned)std::min<int64_t>((tasks + 7) / 8, 152 * 16);
+    threshold_bits_kernel<<<nba, 256, 0, s>>>(op, W, v, bits_a, ctrl);
+    note_launches(1);
+    const int lmax = op.dim == 3 ? 4 : 8;   // layers per pass: the pass costs O(L^dim) word operations
+    const unsigned nbb = (unsigned)std::min<int64_t>((rows * W + 255) / 256, 152 * 16);
+    const int vec16 = (op.nx % 16 == 0) && ((reinterpret_cast<uintptr_t>(mask) & 15) == 0);
+    const uint32_t *cur = bits_a;
+    uint32_t *nxt = bits_b;
+    int left = layers;
+    while (left > lmax) {
+        dilate_bits_kernel<false><<<nbb, 256, 0, s>>>(op, W, lmax, cur, nxt, nullptr, 0);
+        note_launches(1);
+        left -= lmax;
+        uint32_t *t = const_cast<uint32_t *>(cur);
+        cur = nxt;
+        nxt = t;
+    }
+    dilate_bits_kernel<true><<<nbb, 256, 0, s>>>(op, W, left, cur, nullptr, mask, vec16);
     note_launches(1);
     return cudaGetLastError();
 }
