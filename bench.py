@@ -8,15 +8,19 @@ log-uniform in [1, 1e3]) and a Gaussian hot front (sigma = 30 cells) that
 moves 8 cells per step over 20 steps.  System n is A x = x^{n-1}/dt + s^n,
 started from the reference solution x^{n-1} (computed once, before timing,
 by the global PCG of this library and kept resident in HBM).  Each step runs
-Alg 1: residual marking (tau = 1e-3 max|r0|, 2 dilation layers), extraction,
-local Jacobi-PCG, assembly, the check of x~ and the warm-started global
-Jacobi-PCG to relres 1e-8.  The same systems are also solved by plain global
-Jacobi-PCG and by Alg 1 with gradient marking, for comparison.
+Alg 1 with residual marking as the paper runs it (Sec. 2.3.1, Alg 3: tau =
+eps ||b||_2 / sqrt(N) with eps = 1e-8, the solve's tolerance, and E_max = 1),
+extraction, local Jacobi-PCG, assembly, the check of x~ and the warm-started
+global Jacobi-PCG to relres 1e-8.  The same systems are also solved by plain
+global Jacobi-PCG, by Alg 1 with gradient marking (Alg 2, alpha = 1e-4), with
+the relative threshold 1e-3 max|r0| and 2 dilation layers, with one
+Gauss-Seidel sweep, and in mixed precision, for comparison.
 
 The JSON line reports time-to-solution per system (lower is better), the
-roofline of the dominant kernel (the global PCG kernel), the kernel count,
-SM clocks sampled during the timed region, an end-to-end figure through the
-C ABI with host buffers, and the oracle timed on the host cores.
+roofline of the dominant kernel (the one with the largest share of the step),
+the kernel count, SM clocks sampled during the timed region, an end-to-end
+figure through the C ABI with host buffers, and the oracle timed on the host
+cores.
 
 `--impl reference` times the oracle (plain serial FP64 CPU code) instead.
 """
@@ -40,8 +44,18 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-solution per system and SpMV HBM GB/s: local-first vs global PCG at relres 1e-8"
 UNIT = "ms/system"
 WORKLOAD = ("2D 2048x2048 5-point FP64 diffusion, 64 rectangles k in [1,1e3], Gaussian front sigma=30 moving "
-            "8 cells/step, 20 backward-Euler steps; Alg 1 with residual marking (1e-3 max|r|, 2 layers), "
-            "Jacobi-PCG to relres 1e-8")
+            "8 cells/step, 20 backward-Euler steps; Alg 1 with residual marking (Alg 3: eps ||b||/sqrt(N), "
+            "eps = 1e-8, E_max = 1), Jacobi-PCG to relres 1e-8")
+
+# Alg 1 settings of the 2048^2 workload (keyword arguments of both the
+# binding's default_params and the oracle's solve_local_then_global).
+# Residual marking as the paper runs it (Sec. 2.3.1, Alg 3: eps = the
+# solve's tolerance, E_max = 1); gradient marking (Alg 2) with the paper's
+# alpha = 1e-4 and no further layers; and the relative threshold 1e-3 max|r0|
+# with 2 dilation layers, the marking stated for the 128 x 128 case.
+MARK_ALG3 = dict(mark_mode=0, thr_mode=0, thr_param=1e-8, exp_mode=2, exp_rounds=1)
+MARK_REL = dict(mark_mode=0, thr_mode=1, thr_param=1e-3, exp_mode=1, exp_rounds=2)
+MARK_GRAD = dict(mark_mode=1, alpha=1e-4, grad_layers=0)
 
 # Algorithmic bytes of a Jacobi-PCG iteration on the 2D FP64 operator, per
 # cell: set-up / true residual pass reads b, x, D, Tx, Ty, dinv and writes r, z
@@ -61,6 +75,12 @@ IMPL_ITER_BYTES = 92
 DP_SETUP = 10
 DP_ITER = 8
 DP_PEAK_GOPS = 152 * 2 * 2.07   # FP64 FMA instructions per second, in G (nominal 1.25 TFLOP/s)
+# Algorithmic bytes of a Jacobi-PCG iteration on a CSR matrix, per row and
+# per entry: row pointers 4 B; phase A z, p_old in and p, q out (32 B) plus
+# 12 B per entry (column index, value); phase B x, p, r, q, dinv in and x, r,
+# z out (64 B) -- 100 B per row and 12 B per entry.
+LOCAL_ROW_BYTES = 100
+LOCAL_ENTRY_BYTES = 12
 
 
 def parse():
@@ -208,6 +228,27 @@ def ncu_traffic_per_cell_iter():
         return None
 
 
+def ncu_local_traffic(mean_it_local: float):
+    """DRAM bytes per launch of the local solve kernel (scaled to the mean
+    iteration count) from the committed ncu summary, if it was taken on the
+    current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "pcg_local_csr_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as f:
+        for ln in f:
+            if "=" in ln and not ln.lstrip().startswith("#"):
+                k, v = ln.split("=", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("pcg_sources_sha256_16") != source_digest():
+        return None
+    try:
+        return float(vals["dram_bytes_per_iter"]) * mean_it_local + float(vals.get("dram_bytes_setup", "0"))
+    except (KeyError, ValueError):
+        return None
+
+
 # ----------------------------------------------------------------- oracle side
 
 class OracleChain:
@@ -230,14 +271,14 @@ class OracleChain:
         self.states = {0: np.zeros(self.A.n)}
 
     def solve(self, k: int):
-        """Alg 1 (residual marking 1e-3 max|r|, 2 layers, relres 1e-8) on
+        """Alg 1 (the headline's residual marking, Alg 3; relres 1e-8) on
         system k mod 20; returns (seconds, stats)."""
         import oracle
         j = k % self.seq.steps
         x0 = self.states[j]
         b = x0 / self.dt + self.seq.source(j + 1)
         t = time.perf_counter()
-        x, st, _ = oracle.solve_local_then_global(self.A, b, x0, tol=1e-8)
+        x, st, _ = oracle.solve_local_then_global(self.A, b, x0, **MARK_ALG3, tol=1e-8)
         dt = time.perf_counter() - t
         self.states.setdefault(j + 1, x)
         return dt, st
@@ -331,13 +372,14 @@ def run_gpu(args, rank, ws, local):
         xs.append(x)
     torch.cuda.synchronize(dev)
 
-    prm_res = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8)
-    prm_grad = lcg.default_params(lcg.MARK_GRADIENT, alpha=1e-3, grad_layers=2, tol=1e-8)
-    prm_mixed = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8,
-                                   precision=lcg.PREC_MIXED, inner_tol=1e-4)
+    prm_res = lcg.default_params(**MARK_ALG3, tol=1e-8)
+    prm_rel = lcg.default_params(**MARK_REL, tol=1e-8)
+    prm_grad = lcg.default_params(**MARK_GRAD, tol=1e-8)
+    prm_mixed = lcg.default_params(**MARK_ALG3, tol=1e-8, precision=lcg.PREC_MIXED, inner_tol=1e-4)
     # Alg 1 with its step-7 smoothing: one red-black Gauss-Seidel sweep, as in the paper's runs
-    prm_gs = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8, gs_sweeps=1)
-    prms = {"res": prm_res, "grad": prm_grad, "mixed": prm_mixed, "gs": prm_gs}
+    prm_gs = lcg.default_params(**MARK_ALG3, tol=1e-8, gs_sweeps=1)
+    prms = {"res": prm_res, "rel": prm_rel, "grad": prm_grad, "mixed": prm_mixed, "gs": prm_gs}
+    sp_mixed = lcg.SolveParams(1e-8, 200000, lcg.PREC_MIXED, 1e-4, 30)
     work = torch.empty(N, dtype=torch.float64, device=dev)
 
     def system(k):
@@ -349,6 +391,8 @@ def run_gpu(args, rank, ws, local):
         work.copy_(x0, non_blocking=True)
         if kind == "global":
             lcg.pcg_solve(ctx, gop, b, work, sp, stats)
+        elif kind == "global_mixed":
+            lcg.pcg_solve(ctx, gop, b, work, sp_mixed, stats)
         else:
             lcg.solve_local_then_global(ctx, gop, b, work, prms[kind], stats)
 
@@ -377,8 +421,10 @@ def run_gpu(args, rank, ws, local):
     clocks = cs.summary()
     ms_glob, per_glob, _ = timed_loop("global", args.steps, args.warmup)
     ms_grad, per_grad, _ = timed_loop("grad", args.steps, args.warmup)
+    ms_rel, per_rel, _ = timed_loop("rel", args.steps, args.warmup)
     ms_gs, per_gs, _ = timed_loop("gs", args.steps, args.warmup)
     ms_mixed, per_mixed, _ = timed_loop("mixed", args.steps, args.warmup)
+    ms_gmixed, per_gmixed, _ = timed_loop("global_mixed", args.steps, args.warmup)
     # system 0 (b = s^1, x0 = 0) by mixed precision and by FP64 Alg 1, kept
     # for the comparison with the oracle's FP64 solution (rank 0, below)
     solve("mixed", 0, lcg.Stats())
@@ -386,31 +432,58 @@ def run_gpu(args, rank, ws, local):
     solve("res", 0, lcg.Stats())
     x_res0 = work.cpu().numpy()
 
-    # roofline of the dominant kernel: the global PCG launch inside Alg 1,
-    # timed by CUDA events the library records on the launching stream
+    # rooflines, each over CUDA-event times the library records on the
+    # launching stream.  The global PCG kernel: the plain global solves
+    # (every launch a full solve from x^{n-1}).
     def pcg_bytes(s):
         checks = 1 + (0 if s["early_exit"] else 1 + s["restarts"])
         return N * (SETUP_BYTES * checks + ITER_BYTES * s["it_global"])
 
-    byts = sum(pcg_bytes(s) for s in per_res)
-    t_pcg = sum(s["t_global_ms"] for s in per_res) * 1e-3
-    achieved = byts / t_pcg / 1e9 if t_pcg > 0 else 0.0
     peak, peak_kind = measured_peaks()
-    tr = ncu_traffic_per_cell_iter()
-    mean_it = statistics.mean(s["it_global"] for s in per_res)
-    traffic = None
-    if tr is not None:
-        bpc_iter, bpc_setup = tr
-        traffic = float(N * (bpc_iter * mean_it + (bpc_setup if math.isfinite(bpc_setup) else SETUP_BYTES) * 2))
-    # the same kernel seen from FP64 issue (DP_ITER, DP_SETUP); peak = 152 SMs
-    # x 2 FP64 FMA/clk x 2.07 GHz (the nominal 1.25 TFLOP/s)
-    dp = sum(N * (DP_SETUP * (1 + (0 if s["early_exit"] else 1 + s["restarts"])) + DP_ITER * s["it_global"])
-             for s in per_res)
-    dp_achieved = dp / t_pcg / 1e9 if t_pcg > 0 else 0.0
-    # GB/s of the plain global PCG (the "SpMV HBM GB/s" half of the metric)
     byts_g = sum(pcg_bytes(s) for s in per_glob)
     t_g = sum(s["t_global_ms"] for s in per_glob) * 1e-3
     gbs_global = byts_g / t_g / 1e9 if t_g > 0 else 0.0
+    tr = ncu_traffic_per_cell_iter()
+    mean_it_g = statistics.mean(s["it_global"] for s in per_glob)
+    traffic_g = None
+    if tr is not None:
+        bpc_iter, bpc_setup = tr
+        traffic_g = float(N * (bpc_iter * mean_it_g + (bpc_setup if math.isfinite(bpc_setup) else SETUP_BYTES) * 2))
+    # the same kernel seen from FP64 issue (DP_ITER, DP_SETUP); peak = 152 SMs
+    # x 2 FP64 FMA/clk x 2.07 GHz (the nominal 1.25 TFLOP/s)
+    dp = sum(N * (DP_SETUP * (2 + s["restarts"]) + DP_ITER * s["it_global"]) for s in per_glob)
+    dp_achieved = dp / t_g / 1e9 if t_g > 0 else 0.0
+    roof_global = {"bound": "hbm", "achieved": gbs_global, "peak": peak, "unit": "GB/s", "frac": gbs_global / peak,
+                   "traffic": traffic_g,
+                   "kernel": "pcg_kernel<Op2DW<double,4,true,true,true>> "
+                             "(global Jacobi-PCG on D^-1/2 A D^-1/2, FP64 vectors)",
+                   "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_cell_iter": ITER_BYTES,
+                   "impl_bytes_per_cell_iter": IMPL_ITER_BYTES}
+    # The local solve inside Alg 1: Jacobi-PCG on the extracted CSR
+    # subsystem B (K rows, nnz(B) entries), algorithmic LOCAL_ROW_BYTES per
+    # row and LOCAL_ENTRY_BYTES per entry and iteration, over the local
+    # solve's event time.
+    byts_l = sum(s["K"] * LOCAL_ROW_BYTES * s["it_local"] + s["nnzB"] * LOCAL_ENTRY_BYTES * s["it_local"]
+                 for s in per_res)
+    t_l = sum(s["t_local_ms"] for s in per_res) * 1e-3
+    gbs_local = byts_l / t_l / 1e9 if t_l > 0 else 0.0
+    roof_local = {"bound": "hbm", "achieved": gbs_local, "peak": peak, "unit": "GB/s", "frac": gbs_local / peak,
+                  "traffic": ncu_local_traffic(statistics.mean(s["it_local"] for s in per_res)),
+                  "kernel": "pcg_kernel<OpCsr<double>,1,768> (local Jacobi-PCG on the extracted subsystem)",
+                  "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_row_iter": LOCAL_ROW_BYTES,
+                  "alg_bytes_per_entry_iter": LOCAL_ENTRY_BYTES,
+                  "note": "latency-bound: two grid-wide reductions per iteration; B and the vectors stay in L2"}
+    t_glob_in_alg1 = sum(s["t_global_ms"] for s in per_res) * 1e-3
+    dominant = "local_solve" if t_l >= t_glob_in_alg1 else "global_pcg"
+    if dominant == "global_pcg":   # the global kernel's figures over its launches inside Alg 1
+        byts = sum(pcg_bytes(s) for s in per_res)
+        ach = byts / t_glob_in_alg1 / 1e9 if t_glob_in_alg1 > 0 else 0.0
+        roofline = dict(roof_global, achieved=ach, frac=ach / peak, traffic=None)
+    else:
+        roofline = dict(roof_local)
+    roofline["dominant"] = dominant
+    roofline["share_of_step"] = max(t_l, t_glob_in_alg1) / (ms_res * 1e-3)
+    mean_it = statistics.mean(s["it_global"] for s in per_res)
 
     # end to end through the C ABI with host buffers: every system's b and x0
     # come from pinned host memory and its solution goes back to it.  The
@@ -467,16 +540,13 @@ def run_gpu(args, rank, ws, local):
         "config": {"workload": WORKLOAD.replace("2048x2048", f"{args.n}x{args.n}"), "N": N,
                    "systems": nsys, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (operator + 20 resident systems + PCG vectors > 1 GB)"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "pcg_kernel<Op2DW<double,4,true,true,true>> "
-                               "(global Jacobi-PCG on D^-1/2 A D^-1/2, FP64 vectors)",
-                     "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_cell_iter": ITER_BYTES,
-                     "impl_bytes_per_cell_iter": IMPL_ITER_BYTES},
-        "roofline_fp64_issue": {"bound": "alu", "achieved": dp_achieved, "peak": DP_PEAK_GOPS,
-                                "unit": "G FP64 instr/s", "frac": dp_achieved / DP_PEAK_GOPS,
-                                "alg_fp64_instr_per_cell_iter": DP_ITER,
-                                "note": "same kernel; ncu shows the FP64 pipe ~71% busy at ~57% DRAM throughput"},
+        "roofline": roofline,
+        "roofline_local_solve": roof_local,
+        "roofline_global_pcg": roof_global,
+        "roofline_global_pcg_fp64_issue": {
+            "bound": "alu", "achieved": dp_achieved, "peak": DP_PEAK_GOPS, "unit": "G FP64 instr/s",
+            "frac": dp_achieved / DP_PEAK_GOPS, "alg_fp64_instr_per_cell_iter": DP_ITER,
+            "note": "the global kernel; ncu shows its FP64 pipe ~71% busy at ~57% DRAM throughput"},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": e2e_ms / total_sys, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * N,
@@ -484,7 +554,9 @@ def run_gpu(args, rank, ws, local):
         "global_pcg": {"value": ms_glob / total_sys, "unit": UNIT,
                        "iterations": statistics.mean(s["it_global"] for s in per_glob), "hbm_gbs": gbs_global},
         "local_first_residual": {
-            "value": value, "eta": statistics.mean(s["eta"] for s in per_res),
+            "value": value, "marking": "Alg 3: tau = eps ||b||/sqrt(N), eps = 1e-8, E_max = 1",
+            "K": statistics.mean(s["K"] for s in per_res), "nnzB": statistics.mean(s["nnzB"] for s in per_res),
+            "eta": statistics.mean(s["eta"] for s in per_res),
             "it_local": statistics.mean(s["it_local"] for s in per_res),
             "it_global": mean_it, "early_exit_frac": statistics.mean(s["early_exit"] for s in per_res),
             "t_mark_ms": statistics.mean(s["t_mark_ms"] for s in per_res),
@@ -492,6 +564,14 @@ def run_gpu(args, rank, ws, local):
             "t_local_ms": statistics.mean(s["t_local_ms"] for s in per_res),
             "t_global_ms": statistics.mean(s["t_global_ms"] for s in per_res),
             "relres_max": max(s["relres_final"] for s in per_res)},
+        "local_first_relative_threshold": {
+            "value": ms_rel / total_sys, "marking": "tau = 1e-3 max|r0|, 2 dilation layers",
+            "eta": statistics.mean(s["eta"] for s in per_rel),
+            "it_local": statistics.mean(s["it_local"] for s in per_rel),
+            "it_global": statistics.mean(s["it_global"] for s in per_rel),
+            "t_local_ms": statistics.mean(s["t_local_ms"] for s in per_rel),
+            "t_global_ms": statistics.mean(s["t_global_ms"] for s in per_rel),
+            "relres_max": max(s["relres_final"] for s in per_rel)},
         "local_first_gs1": {
             "value": ms_gs / total_sys, "gs_sweeps": 1,
             "it_global": statistics.mean(s["it_global"] for s in per_gs),
@@ -499,7 +579,8 @@ def run_gpu(args, rank, ws, local):
             "relres_tilde": statistics.mean(s["relres_tilde"] for s in per_gs),
             "relres_max": max(s["relres_final"] for s in per_gs)},
         "local_first_gradient": {
-            "value": ms_grad / total_sys, "eta": statistics.mean(s["eta"] for s in per_grad),
+            "value": ms_grad / total_sys, "marking": "Alg 2: alpha = 1e-4",
+            "eta": statistics.mean(s["eta"] for s in per_grad),
             "it_local": statistics.mean(s["it_local"] for s in per_grad),
             "it_global": statistics.mean(s["it_global"] for s in per_grad),
             "relres_max": max(s["relres_final"] for s in per_grad)},
@@ -507,20 +588,28 @@ def run_gpu(args, rank, ws, local):
             "value": ms_mixed / total_sys, "inner_tol": 1e-4,
             "inner_iterations": statistics.mean(s["it_global"] for s in per_mixed),
             "refinement_sweeps": statistics.mean(s["restarts"] for s in per_mixed),
-            "relres_max": max(s["relres_final"] for s in per_mixed),
-            # the FP32 inner CG inside the global refinement: algorithmic 60 B per
-            # cell and inner iteration (FP32 Jacobi-PCG; the scaled kernel moves
-            # 52 B), FP64 residual passes at 48 B per cell and sweep, over the
+            "relres_max": max(s["relres_final"] for s in per_mixed)},
+        "global_pcg_mixed_precision": {
+            "value": ms_gmixed / total_sys, "unit": UNIT, "inner_tol": 1e-4,
+            "inner_iterations": statistics.mean(s["it_global"] for s in per_gmixed),
+            "refinement_sweeps": statistics.mean(s["restarts"] for s in per_gmixed),
+            "relres_max": max(s["relres_final"] for s in per_gmixed),
+            # the FP32 inner CG inside the refinement: algorithmic 60 B per cell
+            # and inner iteration (FP32 Jacobi-PCG; the scaled kernel moves 52
+            # B), FP64 residual passes at 48 B per cell and sweep, over the
             # launch's CUDA-event time
-            "roofline_global_solve": {
+            "roofline": {
                 "bound": "hbm", "unit": "GB/s", "peak": peak,
-                "achieved": sum(N * (60 * s["it_global"] + 48 * (1 + s["restarts"])) for s in per_mixed) /
-                (sum(s["t_global_ms"] for s in per_mixed) * 1e-3) / 1e9,
-                "frac": sum(N * (60 * s["it_global"] + 48 * (1 + s["restarts"])) for s in per_mixed) /
-                (sum(s["t_global_ms"] for s in per_mixed) * 1e-3) / 1e9 / peak,
+                "achieved": sum(N * (60 * s["it_global"] + 48 * (1 + s["restarts"])) for s in per_gmixed) /
+                (sum(s["t_global_ms"] for s in per_gmixed) * 1e-3) / 1e9,
+                "frac": sum(N * (60 * s["it_global"] + 48 * (1 + s["restarts"])) for s in per_gmixed) /
+                (sum(s["t_global_ms"] for s in per_gmixed) * 1e-3) / 1e9 / peak,
                 "kernel": "ir_kernel<Op2DW<double,2>, Op2DW<float,4,true>>"}},
         "speedup_vs_global_pcg": ms_glob / ms_res,
+        "speedup_relative_threshold_vs_global_pcg": ms_glob / ms_rel,
+        "speedup_gradient_vs_global_pcg": ms_glob / ms_grad,
         "speedup_mixed_vs_global_pcg": ms_glob / ms_mixed,
+        "speedup_global_mixed_vs_global_pcg": ms_glob / ms_gmixed,
     }
     if not args.no_batched:
         res["batched_512"] = run_batched(args, rank, dev, ws)
@@ -849,7 +938,7 @@ def batched_items(items, dev, reps, seq_alg1=False):
     return out
 
 
-PROFILE_CASES = ["global2d", "alg1", "alg1_gradient", "mixed2d", "fp64_3d", "mixed3d", "csr3t", "batched", "heat"]
+PROFILE_CASES = ["global2d", "alg1", "alg1_rel", "alg1_gradient", "mixed2d", "fp64_3d", "mixed3d", "csr3t", "batched", "heat"]
 
 
 def profile_case(args):
@@ -857,7 +946,10 @@ def profile_case(args):
 
     2D cases: the moving-front system 2 from x^1 (x^1 is solved first by the
     global PCG, so the launch of interest is the second pcg_kernel / ir_kernel
-    launch of the process: ncu -k regex:<kernel> -s 1 -c 1).  3D cases: the
+    launch of the process: ncu -k regex:<kernel> -s 1 -c 1): global2d the
+    global FP64 PCG, mixed2d the mixed-precision global solve, alg1 Alg 1 with
+    the paper's residual marking (Alg 3), alg1_rel with the relative
+    threshold and 2 layers, alg1_gradient with gradient marking (Alg 2).  3D cases: the
     anisotropic n^3 system from x0 = 0 (fp64_3d: one pcg_kernel launch;
     mixed3d: Alg 1 with FP32 inner CG, one ir_kernel launch).  csr3t: the 3T
     system on an n x n grid, one global pcg_kernel launch.  batched: the
@@ -878,7 +970,7 @@ def profile_case(args):
     sp = lcg.SolveParams(1e-8, 200000, lcg.PREC_FP64, 0.0, 0)
     st = lcg.Stats()
     kind, n = args.profile_case, args.n
-    if kind in ("global2d", "alg1", "alg1_gradient", "mixed2d"):
+    if kind in ("global2d", "alg1", "alg1_rel", "alg1_gradient", "mixed2d"):
         d = gen.cfg2_fronts2d(seed=0, n=n)
         op, seq = d["op"], d["seq"]
         gop = lcg.StencilOperator(ctx, op.shape, T(op.D), T(op.Tx), T(op.Ty))
@@ -888,14 +980,11 @@ def profile_case(args):
         x = x1.clone()
         if kind == "global2d":
             lcg.pcg_solve(ctx, gop, b2, x, sp, st)
-        elif kind == "mixed2d":
-            prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8,
-                                     precision=lcg.PREC_MIXED, inner_tol=1e-4)
-            lcg.solve_local_then_global(ctx, gop, b2, x, prm, st)
+        elif kind == "mixed2d":   # the mixed-precision global solve (one ir_kernel launch)
+            lcg.pcg_solve(ctx, gop, b2, x, lcg.SolveParams(1e-8, 200000, lcg.PREC_MIXED, 1e-4, 30), st)
         else:
-            prm = (lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-3, lcg.EXP_DILATE, 2, tol=1e-8)
-                   if kind == "alg1" else lcg.default_params(lcg.MARK_GRADIENT, alpha=1e-3, grad_layers=2, tol=1e-8))
-            lcg.solve_local_then_global(ctx, gop, b2, x, prm, st)
+            mark = {"alg1": MARK_ALG3, "alg1_rel": MARK_REL, "alg1_gradient": MARK_GRAD}[kind]
+            lcg.solve_local_then_global(ctx, gop, b2, x, lcg.default_params(**mark, tol=1e-8), st)
     elif kind in ("fp64_3d", "mixed3d"):
         d = gen.cfg3_aniso3d(seed=0, n=n)
         op = d["op"]

@@ -86,6 +86,7 @@ struct lc_op {
     // 256-thread CTAs: measured faster than the grid kernel below ~8K rows
     int local_cluster_rows = 8192;
     int local_single = 0;               // local solves: one grid reduction per iteration
+    int local_pipelined = 1;            // local solves: pipelined CG, one grid barrier per iteration
     int local_grid_cap = 0;             // local solves: blocks of the grid kernel (0 = one per SM)
     int local_cluster_threads = 256;
     int local_cluster_ctas = 0;         // CTAs of that cluster (0: the largest the GPU schedules)
@@ -195,6 +196,9 @@ void carve(lc_op *op, Carver &c) {
     op->pw.x32 = c.take<float>(n);
     op->pw.dinv32 = c.take<float>(n);
     op->pw.val32 = c.take<float>(nnz);
+    op->pw.bh = c.take<double>(n);
+    op->pw.xh = c.take<double>(n);
+    op->pw.ahat = c.take<double>(nnz);
     if (op->kind == 0) {
         op->dinv = c.take<double>(n);
         op->D32 = c.take<float>(n);
@@ -383,7 +387,9 @@ int pcg_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_
             LC_CUDA(ctx, lc::launch_pcg_csr_cluster(sub_csr(op), a, op->local_cluster_rows, op->local_cluster_threads,
                                                     op->local_cluster_ctas, ctrl, s));
         const int cap = op->local_grid_cap > 0 ? op->local_grid_cap : ctx->sms;
-        if (op->local_single && p->precision == LC_PREC_FP64)
+        if (op->local_pipelined && p->precision == LC_PREC_FP64)
+            LC_CUDA(ctx, lc::launch_pcg_csr_pipelined(sub_csr(op), a, w, ctrl, cap, s, cl));
+        else if (op->local_single && p->precision == LC_PREC_FP64)
             LC_CUDA(ctx, lc::launch_pcg_csr_single(sub_csr(op), a, w, ctrl, cap, s, cl));
         else
             LC_CUDA(ctx, lc::launch_pcg_csr(sub_csr(op), a, w, ctrl, cap, s, cl));
@@ -948,6 +954,11 @@ int lc_op_set_tuning(lc_op *op, const char *key, int32_t value) {
         op->pcg_wide = value;
         return LC_OK;
     }
+    if (!strcmp(key, "local_pipelined")) {
+        if (value < 0 || value > 1) return fail(op->ctx, LC_ERR_INVALID_ARG, "local_pipelined must be 0 or 1");
+        op->local_pipelined = value;
+        return LC_OK;
+    }
     if (!strcmp(key, "local_single")) {
         if (value < 0 || value > 1) return fail(op->ctx, LC_ERR_INVALID_ARG, "local_single must be 0 or 1");
         op->local_single = value;
@@ -977,6 +988,7 @@ int lc_op_get_tuning(const lc_op *op, const char *key, int32_t *value) {
     if (!strcmp(key, "local_cluster_threads")) { *value = op->local_cluster_threads; return LC_OK; }
     if (!strcmp(key, "local_cluster_ctas")) { *value = op->local_cluster_ctas; return LC_OK; }
     if (!strcmp(key, "local_single")) { *value = op->local_single; return LC_OK; }
+    if (!strcmp(key, "local_pipelined")) { *value = op->local_pipelined; return LC_OK; }
     if (!strcmp(key, "pcg_wide")) { *value = op->pcg_wide; return LC_OK; }
     if (!strcmp(key, "pcg_big")) { *value = op->pcg_big; return LC_OK; }
     if (!strcmp(key, "pcg_pairdot")) { *value = op->pcg_pairdot; return LC_OK; }

@@ -147,6 +147,8 @@ struct PcgWork {
     double *partials;                // kMaxGrid * 8
     float *r32, *z32, *p032, *p132, *q32, *x32, *dinv32;   // mixed precision (capacity n)
     float *val32;                    // mixed precision, CSR: FP32 values (capacity nnz)
+    double *bh, *xh;                 // pipelined local solve: scaled b and x (capacity n)
+    double *ahat;                    // pipelined local solve: D^-1/2 B D^-1/2 values (capacity nnz)
 };
 struct PcgArgs {
     const double *b;
@@ -180,6 +182,10 @@ cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ct
 // (lc_pcg1.cu); after_cluster as for launch_pcg_csr
 cudaError_t launch_pcg_csr_single(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                   cudaStream_t s, bool after_cluster);
+// Pipelined Jacobi-PCG (one grid barrier per iteration, the sums read while
+// the product runs) for the extracted local subsystem (lc_pcgpipe.cu).
+cudaError_t launch_pcg_csr_pipelined(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
+                                     cudaStream_t s, bool after_cluster);
 // FP64 Jacobi-PCG of a CSR system on one thread-block cluster (lc_cluster.cu),
 // when it has at most max_rows rows and they fit the cluster's shared memory
 // (cluster_local_rows(); 0 if the device cannot run the cluster); sets

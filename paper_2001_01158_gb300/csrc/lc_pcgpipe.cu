@@ -1,0 +1,380 @@
+// lc_pcgpipe.cu -- pipelined Jacobi-PCG (the Ghysels-Vanroose arrangement)
+// for CSR systems whose solve is bound by latency and FP64 issue: the
+// extracted local subsystem of Alg 1 (step 5).  One grid barrier per
+// iteration, the iteration's grid sums read while the matrix-vector product
+// runs, and the symmetrically scaled system so that the Jacobi
+// preconditioner is the identity.
+//
+// Jacobi-PCG on B x = b is CG on the scaled system  Bh xh = bh  with
+// S = diag(B)^-1/2, Bh = S B S (unit diagonal), bh = S b, x = S xh: the same
+// iterates in exact arithmetic, and the unscaled residual is r = S^-1 rh.
+// CG in the pipelined arrangement, w = Bh r carried along by recurrence:
+//   gamma_i = (r_i, r_i),  delta_i = (w_i, r_i),  n_i = Bh w_i
+//   beta_i = gamma_i / gamma_(i-1),  alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_(i-1))
+//   z_i = n_i + beta_i z_(i-1)  (= Bh s_i),  s_i = w_i + beta_i s_(i-1)  (= Bh p_i),
+//   p_i = r_i + beta_i p_(i-1)
+//   x_(i+1) = x_i + alpha_i p_i,  r_(i+1) = r_i - alpha_i s_i,  w_(i+1) = w_i - alpha_i z_i
+// The stopping norm ||r||^2 = sum_i d_i rh_i^2 is summed in FP32, rh_i scaled
+// by 2^-e with 2^(2e) ~ ||b||^2 to stay in FP32's range (approx_abs_f32;
+// relative error ~1e-7 in a test against tol^2 ||b||^2); the true residual
+// that confirms convergence is FP64.  FP64 instructions
+// per row and iteration: the row's entries (one FMA each), six vector
+// updates and two dot products (21 in the unscaled form).
+//
+// Per iteration, in one persistent cooperative launch:
+//   after the barrier: warp 0 of every block adds the block partials of
+//     gamma, delta and the stopping norm and derives alpha, beta and the
+//     stopping and breakdown flags, while the other warps form n = Bh w for
+//     their rows (the neighbours' w of the previous phase);
+//   block barrier; the other warps update z, s, p, x, r, w of their rows and
+//     form the partials of the next sums; block sums; grid barrier.
+// w is double-buffered (neighbours read it in the product while its owner
+// writes the next one); z, s, p, x, r, n are touched by their owner only.
+// The partial slots alternate between two sets: a block may write the next
+// partials while a slower one still reads these.  Stopping test,
+// true-residual confirmation and restarts follow the two-reduction kernel
+// (lc_pcg_impl.cuh), with the same Ctrl fields.
+#include "lc_pcg_impl.cuh"
+
+namespace lc {
+
+namespace {
+
+constexpr int kPipeThreads = 768;              // one block per SM
+constexpr int kPipeWarps = kPipeThreads / 32;  // warp 0 reduces, the others take rows
+
+struct PipeArgs {
+    Csr cs;                  // B (rows and columns of the subsystem)
+    const double *b;
+    double *x;
+    const double *ah;        // Bh values, B's pattern
+    const double *sd;        // S = diag(B)^-1/2
+    const float *d32;        // fl32(diag(B))
+    const double *bh;        // S b
+    double *xh;              // S^-1 x (the iterate)
+    double *r, *w[2], *z, *s, *p, *n;
+    double *part;
+    double tol;
+    int maxit, max_restarts;
+    Ctrl *ctrl;
+    const int32_t *done;   // set: a cluster kernel launched before may already have solved it
+};
+
+// S, fl32(D) of every row; then Bh's values, bh and the scaled start xh.
+__global__ void pipe_diag_kernel(Csr c, double *sd, float *d32) {
+    const int32_t n = c.n_dev ? *c.n_dev : c.n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        const int32_t e1 = c.rp[i + 1];
+        for (int32_t e = c.rp[i]; e < e1; ++e)
+            if (c.ci[e] == i) d = c.av[e];
+        sd[i] = 1.0 / sqrt(d);
+        d32[i] = (float)d;
+    }
+}
+
+__global__ void pipe_scale_kernel(Csr c, const double *sd, const double *b, const double *x, double *ah, double *bh,
+                                  double *xh) {
+    const int32_t n = c.n_dev ? *c.n_dev : c.n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double si = sd[i];
+        const int32_t e1 = c.rp[i + 1];
+        for (int32_t e = c.rp[i]; e < e1; ++e) {
+            const int32_t j = LC_IDX(c.ci[e], n);
+            ah[e] = j == i ? 1.0 : c.av[e] * si * sd[j];
+        }
+        bh[i] = b[i] * si;
+        xh[i] = x[i] / si;
+    }
+}
+
+__global__ void pipe_reset_kernel(Ctrl *ctrl) {
+    ctrl->bar_count = 0;
+    ctrl->iters = 0;
+    ctrl->restarts = 0;
+    ctrl->outer = 0;
+    ctrl->converged = 0;
+    ctrl->early = 0;
+}
+
+// Rows of this thread: warps 1.. of every block, dealt across blocks (global
+// row warp g = (warp - 1) x blocks + block takes rows 32 g .. 32 g + 31, then
+// every 32 G rows, G = (kPipeWarps - 1) x blocks), so a small system spreads
+// over all SMs.
+struct Rows {
+    int64_t first, step;
+    __device__ Rows() {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int64_t g = (int64_t)(warp - 1) * gridDim.x + blockIdx.x;
+        first = warp == 0 ? INT64_MAX : 32 * g + lane;
+        step = 32 * (int64_t)(kPipeWarps - 1) * gridDim.x;
+    }
+};
+
+// (Bh v)_i in the row's entry order; v of other rows through L2
+__device__ __forceinline__ double row_av(const Csr &cs, const double *__restrict__ ah, const double *v, int32_t n,
+                                         int64_t i) {
+    double acc = 0.0;
+    const int32_t e1 = cs.rp[i + 1];
+    for (int32_t e = cs.rp[i]; e < e1; ++e) acc = fma(ah[e], ldcg(v + LC_IDX(cs.ci[e], n)), acc);
+    return acc;
+}
+
+// Block sums of NV values into the partial slots slot0.. (thread 0 writes),
+// then the grid barrier; the totals are read later (pipe_totals).
+template <int NV>
+__device__ __forceinline__ bool pipe_publish(double (&v)[NV], int slot0, double *part, double *red, Ctrl *ctrl) {
+    block_sum<NV, double>(v, red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[(size_t)(slot0 + k) * kMaxGrid + blockIdx.x] = v[k];
+    return grid_sync(ctrl, gridDim.x);
+}
+
+// Warp 0: the totals of slots slot0.. (after pipe_publish's barrier), lane-
+// strided and reduced in a fixed order, identical in every block.
+template <int NV>
+__device__ __forceinline__ void pipe_totals(int slot0, const double *part, double (&t)[NV]) {
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += 32)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += ldcg(part + (size_t)(slot0 + k) * kMaxGrid + b);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) t[k] = warp_sum(acc[k]);
+}
+
+// rh = bh - Bh xh, then w = Bh rh (into w[0]); the sums b.b, ||b - B x||^2
+// (FP64) and gamma, delta.  Two grid barriers.  Every thread returns the
+// totals.
+__device__ bool pipe_setup(const PipeArgs &a, int32_t n, double *red, double &bb, double &rr, double &gam,
+                           double &del) {
+    const Csr &cs = a.cs;
+    const Rows R;
+    double acc[2] = {0.0, 0.0};
+    for (int64_t i = R.first; i < n; i += R.step) {
+        const double ri = a.bh[i] - row_av(cs, a.ah, a.xh, n, i);
+        a.r[i] = ri;
+        const double bi = a.b[i], ru = ri / a.sd[i];   // the unscaled residual
+        acc[0] = fma(bi, bi, acc[0]);
+        acc[1] = fma(ru, ru, acc[1]);
+    }
+    if (!pipe_publish<2>(acc, 0, a.part, red, a.ctrl)) return false;
+    double acc2[2] = {0.0, 0.0};
+    for (int64_t i = R.first; i < n; i += R.step) {
+        const double wi = row_av(cs, a.ah, a.r, n, i);
+        const double ri = a.r[i];
+        a.w[0][i] = wi;
+        acc2[0] = fma(ri, ri, acc2[0]);
+        acc2[1] = fma(wi, ri, acc2[1]);
+    }
+    double t1[2];
+    if (threadIdx.x < 32) {
+        pipe_totals<2>(0, a.part, t1);
+        if (threadIdx.x == 0) { red[96] = t1[0]; red[97] = t1[1]; }
+    }
+    __syncthreads();
+    bb = red[96];
+    rr = red[97];
+    __syncthreads();
+    if (!pipe_publish<2>(acc2, 2, a.part, red, a.ctrl)) return false;
+    double t2[2];
+    if (threadIdx.x < 32) {
+        pipe_totals<2>(2, a.part, t2);
+        if (threadIdx.x == 0) { red[96] = t2[0]; red[97] = t2[1]; }
+    }
+    __syncthreads();
+    gam = red[96];
+    del = red[97];
+    __syncthreads();
+    return true;
+}
+
+// Iterations from the state pipe_setup left (r, w[0], gamma, delta).
+// Returns 1 converged, 0 iteration limit, -1 breakdown, -2 wait timed out.
+__device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double gam, double del, double stop,
+                               int ns, int &it) {
+    const Csr &cs = a.cs;
+    const Rows R;
+    if (!(del > 0.0) || !isfinite(del)) return -1;
+    double alpha = gam / del, beta = 0.0;
+    bool first = true, pending = false;
+    int cur = 0;         // w[cur] holds this iteration's w
+    int pend_slot = 4;   // slots of the partials published last
+    while (true) {
+        // warps 1..: n = Bh w (neighbours' w of the last phase); warp 0
+        // meanwhile: the totals published last and the next step lengths
+        if (threadIdx.x < 32) {
+            if (pending) {
+                double t[3];
+                pipe_totals<3>(pend_slot, a.part, t);
+                if (threadIdx.x == 0) {
+                    const double bt = t[0] / gam;
+                    const double den = t[1] - bt * t[0] / alpha;
+                    const bool ok = den > 0.0 && isfinite(den);
+                    red[96] = t[0];
+                    red[97] = bt;
+                    red[98] = ok ? t[0] / den : 0.0;
+                    red[99] = t[2] <= stop ? 1.0 : 0.0;
+                    red[100] = ok ? 1.0 : 0.0;
+                }
+            }
+        } else {
+            const double *wc = a.w[cur];
+            for (int64_t i = R.first; i < n; i += R.step) a.n[i] = row_av(cs, a.ah, wc, n, i);
+        }
+        __syncthreads();
+        if (pending) {
+            const double g1 = red[96], b1 = red[97], a1 = red[98];
+            const bool conv = flag_set(red[99]), ok = flag_set(red[100]);
+            if (conv) return 1;   // (this iteration's product is not used)
+            if (it >= a.maxit) return 0;
+            if (!ok) return -1;
+            gam = g1;
+            beta = b1;
+            alpha = a1;
+            first = false;
+        }
+        // warps 1..: the vector updates of their rows and the next partials
+        const double *wc = a.w[cur];
+        double *wn = a.w[cur ^ 1];
+        double acc[2] = {0.0, 0.0};
+        float rrf = 0.f;
+        for (int64_t i = R.first; i < n; i += R.step) {
+            const double ri = a.r[i], wi = wc[i], ni = a.n[i];
+            double zi, si, pi;
+            if (first) {
+                zi = ni;
+                si = wi;
+                pi = ri;
+            } else {
+                zi = fma(beta, a.z[i], ni);
+                si = fma(beta, a.s[i], wi);
+                pi = fma(beta, a.p[i], ri);
+            }
+            const double xi = fma(alpha, pi, a.xh[i]);
+            const double rn = fma(-alpha, si, ri);
+            const double wnx = fma(-alpha, zi, wi);
+            a.z[i] = zi;
+            a.s[i] = si;
+            a.p[i] = pi;
+            a.xh[i] = xi;
+            a.r[i] = rn;
+            wn[i] = wnx;
+            acc[0] = fma(rn, rn, acc[0]);
+            acc[1] = fma(wnx, rn, acc[1]);
+            const float rf = approx_abs_f32(rn, ns);
+            rrf = fmaf(a.d32[i] * rf, rf, rrf);
+        }
+        double sums[3] = {acc[0], acc[1], (double)rrf};
+        pend_slot = cur ? 7 : 4;
+        if (!pipe_publish<3>(sums, pend_slot, a.part, red, a.ctrl)) return -2;   // (block_sum syncs red first)
+        ++it;
+        cur ^= 1;
+        pending = true;
+    }
+}
+
+__global__ void __launch_bounds__(kPipeThreads, 1) pcgpipe_kernel(PipeArgs a) {
+    __shared__ double red[128];
+    if (a.done && *a.done) return;
+    const int32_t n = a.cs.n_dev ? *a.cs.n_dev : a.cs.n;
+    Ctrl *ctrl = a.ctrl;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const Rows R;
+    double bb, rr, gam, del;
+    if (!pipe_setup(a, n, red, bb, rr, gam, del)) return;
+    const double stop = (a.tol * a.tol) * bb;
+    if (lead) {
+        ctrl->bnorm2 = bb;
+        ctrl->relres0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    }
+    if (bb == 0.0) {
+        for (int64_t i = R.first; i < n; i += R.step) a.x[i] = 0.0;
+        if (lead) { ctrl->converged = 1; ctrl->early = 1; ctrl->relres = 0.0; }
+        return;
+    }
+    if (rr <= stop) {   // the starting iterate is returned as it is
+        if (lead) { ctrl->converged = 1; ctrl->early = 1; ctrl->relres = sqrt(rr / bb); }
+        return;
+    }
+    // the FP32 stopping norm sums (|rh| 2^-ns)^2 d with 2^(2 ns) ~ b.b
+    const int ns = (((int)((__double_as_longlong(bb) >> 52) & 0x7ff)) - 1023) >> 1;
+    const double stop_rec = ldexp(stop, -2 * ns);
+    int it = 0, restarts = 0, result;
+    while (true) {
+        result = pipe_iterations(a, n, red, gam, del, stop_rec, ns, it);
+        if (result == -2) return;
+        if (result != 1) break;
+        // converged on the recurrence residual: confirm with the true one
+        double bb2;
+        if (!pipe_setup(a, n, red, bb2, rr, gam, del)) return;
+        if (rr <= stop) break;
+        result = 0;
+        if (++restarts > a.max_restarts || it >= a.maxit) break;
+    }
+    if (result == 0 && it >= a.maxit) {   // report the true residual of the last iterate
+        double bb2, g2, d2;
+        if (!pipe_setup(a, n, red, bb2, rr, g2, d2)) return;
+    }
+    for (int64_t i = R.first; i < n; i += R.step) a.x[i] = a.xh[i] * a.sd[i];
+    if (lead) {
+        ctrl->iters = it;
+        ctrl->restarts = restarts;
+        ctrl->converged = result;
+        ctrl->early = 0;
+        ctrl->relres = sqrt(rr / bb);
+        if (result == -1) atomicCAS(&ctrl->status, LC_OK, LC_ERR_BREAKDOWN);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pcg_csr_pipelined(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
+                                     cudaStream_t s, bool after_cluster) {
+    pipe_diag_kernel<<<152 * 4, 256, 0, s>>>(op, w.dinv, w.r32);
+    pipe_scale_kernel<<<152 * 4, 256, 0, s>>>(op, w.dinv, a.b, a.x, w.ahat, w.bh, w.xh);
+    note_launches(2);
+    if (!after_cluster) {
+        pipe_reset_kernel<<<1, 1, 0, s>>>(ctrl);
+        note_launches(1);
+    }
+    PipeArgs g;
+    g.cs = op;
+    g.b = a.b;
+    g.x = a.x;
+    g.ah = w.ahat;
+    g.sd = w.dinv;
+    g.d32 = w.r32;
+    g.bh = w.bh;
+    g.xh = w.xh;
+    g.r = w.r;
+    g.w[0] = w.q;
+    g.w[1] = w.e0;
+    g.z = w.z;
+    g.s = w.p0;
+    g.p = w.p1;
+    g.n = w.e1;
+    g.part = w.partials;
+    g.tol = a.tol;
+    g.maxit = a.maxit;
+    g.max_restarts = a.max_restarts;
+    g.ctrl = ctrl;
+    g.done = after_cluster ? &ctrl->done : nullptr;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t grid = sms;
+    if (grid_hint > 0 && grid > grid_hint) grid = grid_hint;
+    const int64_t units = ((int64_t)op.n + 32 * (kPipeWarps - 1) - 1) / (32 * (kPipeWarps - 1));
+    if (grid > units) grid = units;
+    if (grid > kMaxGrid) grid = kMaxGrid;
+    if (grid < 1) grid = 1;
+    void *args[] = {&g};
+    note_launches(1);
+    return cudaLaunchCooperativeKernel((const void *)pcgpipe_kernel, dim3((unsigned)grid), dim3(kPipeThreads), args,
+                                       0, s);
+}
+
+}  // namespace lc

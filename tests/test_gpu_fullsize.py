@@ -2,9 +2,11 @@
 times (the operators' default tuning):
 
 - 2048 x 2048 moving front (the bench workload), a system of the sequence's
-  form b = x0/dt + s^1 with x0 = s^0: residual marking, the subsystem and the
-  whole of Alg 1 against the oracle (masks and subsystem bit for bit, the
-  solution within 1e-9, relres by the oracle); gradient marking bit for bit.
+  form b = x0/dt + s^1 with x0 = s^0: residual marking (the relative
+  threshold with 2 layers, and the paper's Alg 3 marking of the bench's
+  headline), the subsystem and the whole of Alg 1 against the oracle (masks
+  and subsystem bit for bit, the solution within 1e-9, relres by the
+  oracle); gradient marking bit for bit.
 - 256^3 anisotropic 3D: marking and subsystem bit for bit; the FP64 and the
   mixed-precision solves to relres 1e-10, evaluated by the oracle, and both
   solutions against the oracle's own serial FP64 Jacobi-PCG solution of the
@@ -86,6 +88,29 @@ def test_front2048_marking_extraction_and_alg1(ctx, front2048):
     assert st.K == sr["K"] == K and st.nnzB == sr["nnzB"]
     assert abs(st.it_local - sr["it_local"]) <= 1 and abs(st.it_global - sr["it_global"]) <= 1
     assert st.relres_tilde == pytest.approx(sr["relres_tilde"], rel=1e-6)
+    assert oracle.relres(A, b, xg) <= 1e-8
+    assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
+
+
+def test_front2048_paper_marking_alg1(ctx, front2048):
+    """The bench's headline setting: residual marking as the paper runs it
+    (tau = eps ||b|| / sqrt(N), eps = 1e-8, Alg 3 with E_max = 1), the
+    default (pipelined) local solve, against the oracle's Alg 1."""
+    op, A, b, x0 = front2048
+    gop = stencil_op(ctx, op)
+    case = (lcg.THR_EPS_NORMB, 1e-8, lcg.EXP_PAPER, 1)
+    K = check_mark_and_extract(ctx, gop, A, b, x0, case)
+    xr, sr, _ = oracle.solve_local_then_global(A, b, x0, thr_mode=oracle.THR_EPS_NORMB, thr_param=1e-8,
+                                               exp_mode=oracle.EXP_PAPER, exp_rounds=1, tol=1e-8)
+    prm = lcg.default_params(lcg.MARK_RESIDUAL, *case, tol=1e-8)
+    assert gop.get_tuning("local_pipelined") == 1
+    x = cu(x0)
+    st = lcg.Stats()
+    lcg.solve_local_then_global(ctx, gop, cu(b), x, prm, st)
+    xg = x.cpu().numpy()
+    assert st.K == sr["K"] == K and st.nnzB == sr["nnzB"]
+    assert abs(st.it_local - sr["it_local"]) <= 1 and abs(st.it_global - sr["it_global"]) <= 1
+    assert st.early_exit == sr["early_exit"]
     assert oracle.relres(A, b, xg) <= 1e-8
     assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
 

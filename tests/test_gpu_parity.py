@@ -421,13 +421,15 @@ def test_local_grid_kernel_launch_shapes(ctx, big, cap):
 
 @pytest.mark.parametrize("n,radius,beta,rounds", [(96, 10, 1e-3, 2), (256, 40, 1e-3, 3), (384, 90, 1e-4, 4),
                                                    (300, 150, 1e-6, 8)])
-@pytest.mark.parametrize("cluster,threads,single", [(1 << 30, 256, 0), (1 << 30, 1024, 0), (0, 256, 0), (0, 256, 1)])
+@pytest.mark.parametrize("cluster,threads,single", [(1 << 30, 256, 0), (1 << 30, 1024, 0), (0, 256, 0), (0, 256, 1),
+                                                    (0, 256, 2)])
 def test_local_solve_cluster_and_grid_match_oracle(ctx, n, radius, beta, rounds, cluster, threads, single):
     """The local solve on one thread-block cluster (vectors in distributed
-    shared memory), on the whole grid, and on the whole grid with one
-    reduction per iteration give the oracle's local iteration count within
-    one and the same Alg 1 result; subsystems from a few hundred rows to more
-    than the cluster holds (that one falls back to the grid kernel)."""
+    shared memory), on the whole grid, on the whole grid with one reduction
+    per iteration (single = 1) and pipelined with one barrier per iteration
+    (single = 2) give the oracle's local iteration count within one and the
+    same Alg 1 result; subsystems from a few hundred rows to more than the
+    cluster holds (that one falls back to the grid kernel)."""
     d = gen.cfg1_heat2d(seed=n + radius, n=n, radius=radius)
     A = oracle.from_stencil(d["op"])
     tol = 1e-8
@@ -437,7 +439,8 @@ def test_local_solve_cluster_and_grid_match_oracle(ctx, n, radius, beta, rounds,
     gop = stencil_op(ctx, d["op"])
     gop.set_tuning("local_cluster_rows", cluster)
     gop.set_tuning("local_cluster_threads", threads)
-    gop.set_tuning("local_single", single)
+    gop.set_tuning("local_single", int(single == 1))
+    gop.set_tuning("local_pipelined", int(single == 2))
     assert gop.get_tuning("local_cluster_rows") == cluster and gop.get_tuning("local_cluster_threads") == threads
     x = cu(d["x0"])
     st = lcg.Stats()
@@ -578,10 +581,11 @@ def test_mixed_precision_rejects_bad_parameters(ctx):
 
 
 @pytest.mark.parametrize("mode", ["residual", "gradient"])
-@pytest.mark.parametrize("single", [0, 1])
+@pytest.mark.parametrize("single", [0, 1, 2])
 def test_local_single_reduction_on_csr_and_stencil(ctx, mode, single):
-    """Alg 1 with the single-reduction local solve (one grid barrier per CG
-    iteration) against the oracle, on stencil and CSR operators."""
+    """Alg 1 with the single-reduction local solve (single = 1) and the
+    pipelined one (single = 2; one grid barrier per CG iteration) against the
+    oracle, on stencil and CSR operators."""
     d = gen.cfg1_heat2d(seed=21, n=160, radius=14)
     A = oracle.from_stencil(d["op"])
     tol = 1e-8
@@ -594,7 +598,8 @@ def test_local_single_reduction_on_csr_and_stencil(ctx, mode, single):
         prm = lcg.default_params(lcg.MARK_GRADIENT, alpha=0.3, grad_layers=2, tol=tol)
     xr, sr, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], tol=tol, **okw)
     for gop in (stencil_op(ctx, d["op"]), csr_op(ctx, A)):
-        gop.set_tuning("local_single", single)
+        gop.set_tuning("local_single", int(single == 1))
+        gop.set_tuning("local_pipelined", int(single == 2))
         gop.set_tuning("local_cluster_rows", 0)
         x = cu(d["x0"])
         st = lcg.Stats()
