@@ -196,7 +196,6 @@ void carve(lc_op *op, Carver &c) {
     op->pw.x32 = c.take<float>(n);
     op->pw.dinv32 = c.take<float>(n);
     op->pw.val32 = c.take<float>(nnz);
-    op->pw.bh = c.take<double>(n);
     op->pw.xh = c.take<double>(n);
     op->pw.ahat = c.take<double>(nnz);
     if (op->kind == 0) {

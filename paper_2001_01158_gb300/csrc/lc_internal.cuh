@@ -147,7 +147,7 @@ struct PcgWork {
     double *partials;                // kMaxGrid * 8
     float *r32, *z32, *p032, *p132, *q32, *x32, *dinv32;   // mixed precision (capacity n)
     float *val32;                    // mixed precision, CSR: FP32 values (capacity nnz)
-    double *bh, *xh;                 // pipelined local solve: scaled b and x (capacity n)
+    double *xh;                      // pipelined local solve: the scaled iterate (capacity n)
     double *ahat;                    // pipelined local solve: D^-1/2 B D^-1/2 values (capacity nnz)
 };
 struct PcgArgs {

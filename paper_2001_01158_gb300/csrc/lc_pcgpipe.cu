@@ -18,8 +18,9 @@
 // by 2^-e with 2^(2e) ~ ||b||^2 to stay in FP32's range (approx_abs_f32;
 // relative error ~1e-7 in a test against tol^2 ||b||^2); the true residual
 // that confirms convergence is FP64.  FP64 instructions
-// per row and iteration: the row's entries (one FMA each), six vector
-// updates and two dot products (21 in the unscaled form).
+// per row and iteration: the row's entries (one FMA each) and six vector
+// updates (21 in the unscaled form); gamma and delta are summed on FP32 pairs
+// (split_f2, f2_add_prod: ~2^-45 relative per term), the block sums too.
 //
 // Per iteration, in one persistent cooperative launch:
 //   after the barrier: warp 0 of every block adds the block partials of
@@ -47,10 +48,9 @@ struct PipeArgs {
     Csr cs;                  // B (rows and columns of the subsystem)
     const double *b;
     double *x;
-    const double *ah;        // Bh values, B's pattern
-    const double *sd;        // S = diag(B)^-1/2
-    const float *d32;        // fl32(diag(B))
-    const double *bh;        // S b
+    double *ah;              // Bh values, B's pattern (formed by the kernel)
+    double *sd;              // S = diag(B)^-1/2 (formed by the kernel)
+    float *d32;              // fl32(diag(B)) (formed by the kernel)
     double *xh;              // S^-1 x (the iterate)
     double *r, *w[2], *z, *s, *p, *n;
     double *part;
@@ -59,34 +59,6 @@ struct PipeArgs {
     Ctrl *ctrl;
     const int32_t *done;   // set: a cluster kernel launched before may already have solved it
 };
-
-// S, fl32(D) of every row; then Bh's values, bh and the scaled start xh.
-__global__ void pipe_diag_kernel(Csr c, double *sd, float *d32) {
-    const int32_t n = c.n_dev ? *c.n_dev : c.n;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double d = 0.0;
-        const int32_t e1 = c.rp[i + 1];
-        for (int32_t e = c.rp[i]; e < e1; ++e)
-            if (c.ci[e] == i) d = c.av[e];
-        sd[i] = 1.0 / sqrt(d);
-        d32[i] = (float)d;
-    }
-}
-
-__global__ void pipe_scale_kernel(Csr c, const double *sd, const double *b, const double *x, double *ah, double *bh,
-                                  double *xh) {
-    const int32_t n = c.n_dev ? *c.n_dev : c.n;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double si = sd[i];
-        const int32_t e1 = c.rp[i + 1];
-        for (int32_t e = c.rp[i]; e < e1; ++e) {
-            const int32_t j = LC_IDX(c.ci[e], n);
-            ah[e] = j == i ? 1.0 : c.av[e] * si * sd[j];
-        }
-        bh[i] = b[i] * si;
-        xh[i] = x[i] / si;
-    }
-}
 
 __global__ void pipe_reset_kernel(Ctrl *ctrl) {
     ctrl->bar_count = 0;
@@ -131,6 +103,75 @@ __device__ __forceinline__ bool pipe_publish(double (&v)[NV], int slot0, double 
     return grid_sync(ctrl, gridDim.x);
 }
 
+// pipe_publish for FP32 pairs: value k is (h[k] + l[k]) 2^e[k]; warps and the
+// block add pairs with FP32 two-sums, thread 0 writes the block's pair.  (An FP64 warp instruction holds the FP64 pipe as long with one
+// active lane as with 32, so FP64 shuffle trees over every warp of the block
+// would cost about as much FP64 issue as the rows' own arithmetic.)
+template <int NV>
+__device__ __forceinline__ bool pipe_publish_pair(float (&h)[NV], float (&l)[NV], int slot0, double *part, double *red,
+                                                  Ctrl *ctrl) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float bh = __shfl_down_sync(kFull, h[k], o), bl = __shfl_down_sync(kFull, l[k], o);
+            pair_add(h[k], l[k], bh, bl);
+        }
+    float *fs = reinterpret_cast<float *>(red);   // 2 NV x 32 floats
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) { fs[(2 * k) * 32 + warp] = h[k]; fs[(2 * k + 1) * 32 + warp] = l[k]; }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            h[k] = lane < nw ? fs[(2 * k) * 32 + lane] : 0.0f;
+            l[k] = lane < nw ? fs[(2 * k + 1) * 32 + lane] : 0.0f;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const float bh = __shfl_down_sync(kFull, h[k], o), bl = __shfl_down_sync(kFull, l[k], o);
+                pair_add(h[k], l[k], bh, bl);
+            }
+        if (lane == 0)   // the block's pair itself (pipe_totals_pair adds pairs)
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                reinterpret_cast<float2 *>(part)[(size_t)(slot0 + k) * kMaxGrid + blockIdx.x] = make_float2(h[k], l[k]);
+    }
+    return grid_sync(ctrl, gridDim.x);
+}
+
+// Warp 0: the totals of pipe_publish_pair's slots, the blocks' pairs added
+// lane-strided and by a shuffle tree in a fixed order (identical in every
+// block); t[k] = (h + l) 2^e[k] in FP64.
+template <int NV>
+__device__ __forceinline__ void pipe_totals_pair(int slot0, const double *part, const int (&e)[NV], double (&t)[NV]) {
+    float h[NV], l[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) { h[k] = 0.f; l[k] = 0.f; }
+    const float2 *pp = reinterpret_cast<const float2 *>(part);
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += 32)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float2 v = __ldcg(pp + (size_t)(slot0 + k) * kMaxGrid + b);
+            pair_add(h[k], l[k], v.x, v.y);
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float bh = __shfl_down_sync(kFull, h[k], o), bl = __shfl_down_sync(kFull, l[k], o);
+            pair_add(h[k], l[k], bh, bl);
+        }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) t[k] = ldexp((double)h[k] + (double)l[k], e[k]);
+}
+
 // Warp 0: the totals of slots slot0.. (after pipe_publish's barrier), lane-
 // strided and reduced in a fixed order, identical in every block.
 template <int NV>
@@ -145,39 +186,32 @@ __device__ __forceinline__ void pipe_totals(int slot0, const double *part, doubl
     for (int k = 0; k < NV; ++k) t[k] = warp_sum(acc[k]);
 }
 
-// rh = bh - Bh xh, then w = Bh rh (into w[0]); the sums b.b, ||b - B x||^2
-// (FP64) and gamma, delta.  Two grid barriers.  Every thread returns the
-// totals.
-__device__ bool pipe_setup(const PipeArgs &a, int32_t n, double *red, double &bb, double &rr, double &gam,
-                           double &del) {
+// The second half of a set-up: w = Bh rh (into w[0]) from every row's rh,
+// the sums gamma, delta after a grid barrier.  With form_ah the own rows'
+// Bh values are formed first (S of the neighbours is then complete).
+__device__ bool pipe_setup_w(const PipeArgs &a, int32_t n, double *red, bool form_ah, double &gam, double &del) {
     const Csr &cs = a.cs;
     const Rows R;
-    double acc[2] = {0.0, 0.0};
-    for (int64_t i = R.first; i < n; i += R.step) {
-        const double ri = a.bh[i] - row_av(cs, a.ah, a.xh, n, i);
-        a.r[i] = ri;
-        const double bi = a.b[i], ru = ri / a.sd[i];   // the unscaled residual
-        acc[0] = fma(bi, bi, acc[0]);
-        acc[1] = fma(ru, ru, acc[1]);
-    }
-    if (!pipe_publish<2>(acc, 0, a.part, red, a.ctrl)) return false;
     double acc2[2] = {0.0, 0.0};
     for (int64_t i = R.first; i < n; i += R.step) {
-        const double wi = row_av(cs, a.ah, a.r, n, i);
+        double wi = 0.0;
+        if (form_ah) {   // the row's Bh values, and w from them as they are formed
+            const double si = a.sd[i];
+            const int32_t e1 = cs.rp[i + 1];
+            for (int32_t e = cs.rp[i]; e < e1; ++e) {
+                const int32_t j = LC_IDX(cs.ci[e], n);
+                const double v = j == i ? 1.0 : cs.av[e] * si * ldcg(a.sd + j);
+                a.ah[e] = v;
+                wi = fma(v, ldcg(a.r + j), wi);
+            }
+        } else {
+            wi = row_av(cs, a.ah, a.r, n, i);
+        }
         const double ri = a.r[i];
         a.w[0][i] = wi;
         acc2[0] = fma(ri, ri, acc2[0]);
         acc2[1] = fma(wi, ri, acc2[1]);
     }
-    double t1[2];
-    if (threadIdx.x < 32) {
-        pipe_totals<2>(0, a.part, t1);
-        if (threadIdx.x == 0) { red[96] = t1[0]; red[97] = t1[1]; }
-    }
-    __syncthreads();
-    bb = red[96];
-    rr = red[97];
-    __syncthreads();
     if (!pipe_publish<2>(acc2, 2, a.part, red, a.ctrl)) return false;
     double t2[2];
     if (threadIdx.x < 32) {
@@ -191,6 +225,70 @@ __device__ bool pipe_setup(const PipeArgs &a, int32_t n, double *red, double &bb
     return true;
 }
 
+// Warp 0 of every block: the totals of the two sums in slots 0, 1.
+__device__ void pipe_totals2(const PipeArgs &a, double *red, double &t0, double &t1) {
+    double t[2];
+    if (threadIdx.x < 32) {
+        pipe_totals<2>(0, a.part, t);
+        if (threadIdx.x == 0) { red[96] = t[0]; red[97] = t[1]; }
+    }
+    __syncthreads();
+    t0 = red[96];
+    t1 = red[97];
+    __syncthreads();
+}
+
+// The first set-up, from the unscaled system: per own row d = B_ii, S, fl32(D),
+// r = b - B x (FP64, the row's entry order), rh = S r, xh = S^-1 x; the sums
+// b.b and r.r; then Bh's values and w = Bh rh (pipe_setup_w).  Three grid
+// barriers.
+__device__ bool pipe_init(const PipeArgs &a, int32_t n, double *red, double &bb, double &rr, double &gam,
+                          double &del) {
+    const Csr &cs = a.cs;
+    const Rows R;
+    double acc[2] = {0.0, 0.0};
+    for (int64_t i = R.first; i < n; i += R.step) {
+        double ri = a.b[i], d = 0.0;
+        const int32_t e1 = cs.rp[i + 1];
+        for (int32_t e = cs.rp[i]; e < e1; ++e) {
+            const int32_t j = LC_IDX(cs.ci[e], n);
+            const double v = cs.av[e];
+            if (j == i) d = v;
+            ri = fma(-v, ldcg(a.x + j), ri);
+        }
+        const double q = sqrt(d), si = 1.0 / q;
+        a.sd[i] = si;
+        a.d32[i] = (float)d;
+        a.r[i] = si * ri;
+        a.xh[i] = a.x[i] * q;
+        acc[0] = fma(a.b[i], a.b[i], acc[0]);
+        acc[1] = fma(ri, ri, acc[1]);
+    }
+    if (!pipe_publish<2>(acc, 0, a.part, red, a.ctrl)) return false;
+    pipe_totals2(a, red, bb, rr);
+    return pipe_setup_w(a, n, red, true, gam, del);
+}
+
+// A later set-up (the true residual that confirms convergence): rh = S b - Bh
+// xh, the sums b.b and ||b - B x||^2 (FP64), then w = Bh rh.
+__device__ bool pipe_setup(const PipeArgs &a, int32_t n, double *red, double &bb, double &rr, double &gam,
+                           double &del) {
+    const Csr &cs = a.cs;
+    const Rows R;
+    double acc[2] = {0.0, 0.0};
+    for (int64_t i = R.first; i < n; i += R.step) {
+        const double si = a.sd[i], bi = a.b[i];
+        const double ri = bi * si - row_av(cs, a.ah, a.xh, n, i);
+        a.r[i] = ri;
+        const double ru = ri / si;   // the unscaled residual
+        acc[0] = fma(bi, bi, acc[0]);
+        acc[1] = fma(ru, ru, acc[1]);
+    }
+    if (!pipe_publish<2>(acc, 0, a.part, red, a.ctrl)) return false;
+    pipe_totals2(a, red, bb, rr);
+    return pipe_setup_w(a, n, red, false, gam, del);
+}
+
 // Iterations from the state pipe_setup left (r, w[0], gamma, delta).
 // Returns 1 converged, 0 iteration limit, -1 breakdown, -2 wait timed out.
 __device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double gam, double del, double stop,
@@ -202,13 +300,15 @@ __device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double
     bool first = true, pending = false;
     int cur = 0;         // w[cur] holds this iteration's w
     int pend_slot = 4;   // slots of the partials published last
+    int pend_e = 0;      // their scale: gamma, delta 2^-pend_e
     while (true) {
         // warps 1..: n = Bh w (neighbours' w of the last phase); warp 0
         // meanwhile: the totals published last and the next step lengths
         if (threadIdx.x < 32) {
             if (pending) {
                 double t[3];
-                pipe_totals<3>(pend_slot, a.part, t);
+                const int te[3] = {pend_e, pend_e, 0};
+                pipe_totals_pair<3>(pend_slot, a.part, te, t);
                 if (threadIdx.x == 0) {
                     const double bt = t[0] / gam;
                     const double den = t[1] - bt * t[0] / alpha;
@@ -239,8 +339,10 @@ __device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double
         // warps 1..: the vector updates of their rows and the next partials
         const double *wc = a.w[cur];
         double *wn = a.w[cur ^ 1];
-        double acc[2] = {0.0, 0.0};
-        float rrf = 0.f;
+        // gamma and delta on FP32 pairs of the values scaled by 2^-ps, ps half
+        // the exponent of the last gamma
+        const int ps = ((int)((__double_as_longlong(gam) >> 52) & 0x7ff) - 1023) >> 1;
+        float gh = 0.f, gl = 0.f, dh = 0.f, dl = 0.f, rrf = 0.f;
         for (int64_t i = R.first; i < n; i += R.step) {
             const double ri = a.r[i], wi = wc[i], ni = a.n[i];
             double zi, si, pi;
@@ -262,14 +364,18 @@ __device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double
             a.xh[i] = xi;
             a.r[i] = rn;
             wn[i] = wnx;
-            acc[0] = fma(rn, rn, acc[0]);
-            acc[1] = fma(wnx, rn, acc[1]);
+            float rh, rl, wh, wl;
+            split_f2(rn, ps, rh, rl);
+            split_f2(wnx, ps, wh, wl);
+            f2_add_prod(rh, rl, rh, rl, gh, gl);
+            f2_add_prod(wh, wl, rh, rl, dh, dl);
             const float rf = approx_abs_f32(rn, ns);
             rrf = fmaf(a.d32[i] * rf, rf, rrf);
         }
-        double sums[3] = {acc[0], acc[1], (double)rrf};
+        float sh[3] = {gh, dh, rrf}, sl[3] = {gl, dl, 0.f};
         pend_slot = cur ? 7 : 4;
-        if (!pipe_publish<3>(sums, pend_slot, a.part, red, a.ctrl)) return -2;   // (block_sum syncs red first)
+        pend_e = 2 * ps;
+        if (!pipe_publish_pair<3>(sh, sl, pend_slot, a.part, red, a.ctrl)) return -2;
         ++it;
         cur ^= 1;
         pending = true;
@@ -284,7 +390,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) pcgpipe_kernel(PipeArgs a) {
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const Rows R;
     double bb, rr, gam, del;
-    if (!pipe_setup(a, n, red, bb, rr, gam, del)) return;
+    if (!pipe_init(a, n, red, bb, rr, gam, del)) return;
     const double stop = (a.tol * a.tol) * bb;
     if (lead) {
         ctrl->bnorm2 = bb;
@@ -333,9 +439,6 @@ __global__ void __launch_bounds__(kPipeThreads, 1) pcgpipe_kernel(PipeArgs a) {
 
 cudaError_t launch_pcg_csr_pipelined(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                      cudaStream_t s, bool after_cluster) {
-    pipe_diag_kernel<<<152 * 4, 256, 0, s>>>(op, w.dinv, w.r32);
-    pipe_scale_kernel<<<152 * 4, 256, 0, s>>>(op, w.dinv, a.b, a.x, w.ahat, w.bh, w.xh);
-    note_launches(2);
     if (!after_cluster) {
         pipe_reset_kernel<<<1, 1, 0, s>>>(ctrl);
         note_launches(1);
@@ -347,7 +450,6 @@ cudaError_t launch_pcg_csr_pipelined(const Csr &op, const PcgArgs &a, PcgWork &w
     g.ah = w.ahat;
     g.sd = w.dinv;
     g.d32 = w.r32;
-    g.bh = w.bh;
     g.xh = w.xh;
     g.r = w.r;
     g.w[0] = w.q;
