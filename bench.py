@@ -197,12 +197,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def source_digest() -> str:
-    """Digest of the global PCG kernel's sources (the kernels, the 2D
-    launcher and the device header with its descriptors, barrier and
-    reductions)."""
+GLOBAL_SOURCES = ("lc_pcg_impl.cuh", "lc_pcg.cu", "lc_device.cuh")
+LOCAL_SOURCES = ("lc_pcgpipe.cu", "lc_pcg_impl.cuh", "lc_device.cuh", "lc_internal.cuh")
+
+
+def source_digest(names=GLOBAL_SOURCES) -> str:
+    """Digest of a kernel's sources (default: the global PCG kernel's -- the
+    kernels, the 2D launcher and the device header with its descriptors,
+    barrier and reductions)."""
     h = hashlib.sha256()
-    for name in ("lc_pcg_impl.cuh", "lc_pcg.cu", "lc_device.cuh"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_2001_01158_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -228,10 +232,11 @@ def ncu_traffic_per_cell_iter():
         return None
 
 
-def ncu_local_traffic(mean_it_local: float):
-    """DRAM bytes per launch of the local solve kernel (scaled to the mean
-    iteration count) from the committed ncu summary, if it was taken on the
-    current kernel source; else None."""
+def ncu_local_traffic(rows: float):
+    """DRAM bytes per launch of the local solve kernel, given the launch's
+    subsystem rows, from the committed ncu summary (bytes per row and launch:
+    the subsystem is read into L2 once and stays there) if it was taken on
+    the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", "pcg_local_csr_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -241,10 +246,10 @@ def ncu_local_traffic(mean_it_local: float):
             if "=" in ln and not ln.lstrip().startswith("#"):
                 k, v = ln.split("=", 1)
                 vals[k.strip()] = v.strip()
-    if vals.get("pcg_sources_sha256_16") != source_digest():
+    if vals.get("pcg_sources_sha256_16") != source_digest(LOCAL_SOURCES):
         return None
     try:
-        return float(vals["dram_bytes_per_iter"]) * mean_it_local + float(vals.get("dram_bytes_setup", "0"))
+        return float(vals["dram_bytes_per_row_launch"]) * rows
     except (KeyError, ValueError):
         return None
 
@@ -468,11 +473,12 @@ def run_gpu(args, rank, ws, local):
     t_l = sum(s["t_local_ms"] for s in per_res) * 1e-3
     gbs_local = byts_l / t_l / 1e9 if t_l > 0 else 0.0
     roof_local = {"bound": "hbm", "achieved": gbs_local, "peak": peak, "unit": "GB/s", "frac": gbs_local / peak,
-                  "traffic": ncu_local_traffic(statistics.mean(s["it_local"] for s in per_res)),
-                  "kernel": "pcg_kernel<OpCsr<double>,1,768> (local Jacobi-PCG on the extracted subsystem)",
+                  "traffic": ncu_local_traffic(statistics.mean(s["K"] for s in per_res)),
+                  "kernel": "pcgpipe_kernel (local Jacobi-PCG on the extracted subsystem: pipelined CG on "
+                            "diag(B)^-1/2 B diag(B)^-1/2)",
                   "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_row_iter": LOCAL_ROW_BYTES,
                   "alg_bytes_per_entry_iter": LOCAL_ENTRY_BYTES,
-                  "note": "latency-bound: two grid-wide reductions per iteration; B and the vectors stay in L2"}
+                  "note": "FP64 issue and latency: one grid barrier per iteration; B and the vectors stay in L2"}
     t_glob_in_alg1 = sum(s["t_global_ms"] for s in per_res) * 1e-3
     dominant = "local_solve" if t_l >= t_glob_in_alg1 else "global_pcg"
     if dominant == "global_pcg":   # the global kernel's figures over its launches inside Alg 1
@@ -938,7 +944,7 @@ def batched_items(items, dev, reps, seq_alg1=False):
     return out
 
 
-PROFILE_CASES = ["global2d", "alg1", "alg1_rel", "alg1_gradient", "mixed2d", "fp64_3d", "mixed3d", "csr3t", "batched", "heat"]
+PROFILE_CASES = ["global2d", "alg1", "alg1_rel", "alg1_gradient", "alg1_steps", "mixed2d", "fp64_3d", "mixed3d", "csr3t", "batched", "heat"]
 
 
 def profile_case(args):
@@ -949,7 +955,11 @@ def profile_case(args):
     launch of the process: ncu -k regex:<kernel> -s 1 -c 1): global2d the
     global FP64 PCG, mixed2d the mixed-precision global solve, alg1 Alg 1 with
     the paper's residual marking (Alg 3), alg1_rel with the relative
-    threshold and 2 layers, alg1_gradient with gradient marking (Alg 2).  3D cases: the
+    threshold and 2 layers, alg1_gradient with gradient marking (Alg 2);
+    alg1_steps the bench's timed step, Alg 1 with the headline marking on
+    systems 1 .. --systems of the sequence (the profiled part starts at the
+    first residual_stencil_kernel launch, after the global solves that build
+    the sequence).  3D cases: the
     anisotropic n^3 system from x0 = 0 (fp64_3d: one pcg_kernel launch;
     mixed3d: Alg 1 with FP32 inner CG, one ir_kernel launch).  csr3t: the 3T
     system on an n x n grid, one global pcg_kernel launch.  batched: the
@@ -985,6 +995,20 @@ def profile_case(args):
         else:
             mark = {"alg1": MARK_ALG3, "alg1_rel": MARK_REL, "alg1_gradient": MARK_GRAD}[kind]
             lcg.solve_local_then_global(ctx, gop, b2, x, lcg.default_params(**mark, tol=1e-8), st)
+    elif kind == "alg1_steps":
+        d = gen.cfg2_fronts2d(seed=0, n=n)
+        op, seq = d["op"], d["seq"]
+        gop = lcg.StencilOperator(ctx, op.shape, T(op.D), T(op.Tx), T(op.Ty))
+        k_max = min(args.systems, seq.steps)
+        xs = [torch.zeros(op.n, dtype=torch.float64, device=dev)]
+        for k in range(1, k_max + 1):   # the sequence's previous solutions, by the global PCG
+            x = xs[-1].clone()
+            lcg.pcg_solve(ctx, gop, xs[-1] / op.meta["dt"] + T(seq.source(k)), x, sp)
+            xs.append(x)
+        prm = lcg.default_params(**MARK_ALG3, tol=1e-8)
+        for k in range(1, k_max + 1):
+            x = xs[k - 1].clone()
+            lcg.solve_local_then_global(ctx, gop, xs[k - 1] / op.meta["dt"] + T(seq.source(k)), x, prm, st)
     elif kind in ("fp64_3d", "mixed3d"):
         d = gen.cfg3_aniso3d(seed=0, n=n)
         op = d["op"]
