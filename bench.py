@@ -645,9 +645,9 @@ def run_gpu(args, rank, ws, local):
             "status": st_o}
         if "aniso3d_256" in res:
             aniso3d_errors(res["aniso3d_256"])
-        # a bounded sample: the serial oracle on the chain's systems 0 and 1,
-        # the OpenMP build on systems 0, 1, 2
-        legs = oracle_legs(args.n, 2, 3)
+        # a bounded sample (about 15 s of serial CPU work): the serial oracle on
+        # the chain's 20 systems, the OpenMP build on the same systems
+        legs = oracle_legs(args.n, 20, 20)
         ser, omp = legs["serial"], legs["omp"]
         res["cpu_baseline"] = {
             "value": statistics.mean(ser["ms"]), "unit": UNIT, "cores": ser["threads"], "kind": "oracle",
