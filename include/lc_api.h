@@ -512,14 +512,14 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  *       lc_solve_local_then_global takes one grid-wide reduction per CG
  *       iteration (Chronopoulos-Gear arrangement: same iterates in exact
  *       arithmetic) instead of two.
- *   "local_cluster_rows" >= 0 (default 8192): the FP64 local solve of
+ *   "local_cluster_rows" >= 0 (default 2048): the FP64 local solve of
  *       lc_solve_local_then_global runs on one thread-block cluster, its
  *       vectors in distributed shared memory, when the subsystem has at most
  *       this many rows and they fit the cluster (about 76,000 rows on a
  *       GB300); larger subsystems, mixed precision, or 0 use the grid-wide
  *       kernel.  Same iteration, different rounding order of the dot
- *       products.  (16 SMs' FP64 throughput makes the cluster slower than the
- *       grid kernel above roughly 10,000 rows.)
+ *       products.  (Against the pipelined grid kernel the cluster is faster
+ *       below about 1,000 rows and slower above about 3,000.)
  *   "local_cluster_threads" 256, 512 or 1024 (default 256): threads per CTA
  *       of that cluster.
  *   "local_cluster_ctas" 0, 2, 4, 8 or 16 (default 0 = the largest cluster the

@@ -84,7 +84,7 @@ struct lc_op {
     int ncolours = 0;
     // local solves of up to this many rows on one thread-block cluster of
     // 256-thread CTAs: measured faster than the grid kernel below ~8K rows
-    int local_cluster_rows = 8192;
+    int local_cluster_rows = 2048;
     int local_single = 0;               // local solves: one grid reduction per iteration
     int local_pipelined = 1;            // local solves: pipelined CG, one grid barrier per iteration
     int local_grid_cap = 0;             // local solves: blocks of the grid kernel (0 = one per SM)

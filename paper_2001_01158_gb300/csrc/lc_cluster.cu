@@ -28,7 +28,7 @@
 // rows fit); it records the decision in ctrl->done, and the grid kernel
 // launched after it returns at once when the cluster already solved the
 // system.
-#include "lc_internal.cuh"
+#include "lc_pcg_impl.cuh"   // FP32-pair helpers (split_f2, f2_add_prod)
 
 #include <cooperative_groups.h>
 
@@ -107,6 +107,79 @@ __device__ __forceinline__ void cl_sums(cg::cluster_group &cl, double (&v)[NV], 
             double s = lane < C ? slots[lane * 4 + k] : 0.0;
             for (int o = top >> 1; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
             t[k] = s;
+        }
+        if (lane == 0) {
+            post(t);
+#pragma unroll
+            for (int k = 0; k < NV + ND; ++k) red[96 + k] = t[k];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV + ND; ++k) out[k] = red[96 + k];
+}
+
+// cl_sums on FP32 pairs: value k of a thread is (h[k] + l[k]) 2^e[k]; the
+// warps, the block and the cluster add pairs with FP32 two-sums, and only the
+// totals become FP64 (each block sum's FP64 shuffle tree cost about as much
+// FP64 issue as the rows' own arithmetic).  The slot rows hold the blocks'
+// pairs.
+template <int NV, int ND = 0, class Post = ClNoPost>
+__device__ __forceinline__ void cl_sums_pair(cg::cluster_group &cl, float (&h)[NV], float (&l)[NV],
+                                             const int (&e)[NV], double *slots, double *red, int C,
+                                             double (&out)[NV + ND], Post post = Post()) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float bh = __shfl_down_sync(kFull, h[k], o), bl = __shfl_down_sync(kFull, l[k], o);
+            pair_add(h[k], l[k], bh, bl);
+        }
+    float *fs = reinterpret_cast<float *>(red);   // 2 NV x 32 floats
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) { fs[(2 * k) * 32 + warp] = h[k]; fs[(2 * k + 1) * 32 + warp] = l[k]; }
+    __syncthreads();
+    const int rank = (int)cl.block_rank();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            h[k] = lane < nw ? fs[(2 * k) * 32 + lane] : 0.0f;
+            l[k] = lane < nw ? fs[(2 * k + 1) * 32 + lane] : 0.0f;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const float bh = __shfl_sync(kFull, h[k], lane + o), bl = __shfl_sync(kFull, l[k], lane + o);
+                if (lane + o < 32) pair_add(h[k], l[k], bh, bl);
+            }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) { h[k] = __shfl_sync(kFull, h[k], 0); l[k] = __shfl_sync(kFull, l[k], 0); }
+        if (lane < C) {
+            float2 *dst = reinterpret_cast<float2 *>(cl.map_shared_rank(slots, (unsigned)lane));
+#pragma unroll
+            for (int k = 0; k < NV; ++k) dst[rank * 4 + k] = make_float2(h[k], l[k]);
+        }
+    }
+    cl.sync();
+    if (warp == 0) {
+        int top = 1;
+        while (top < C) top <<= 1;
+        const float2 *src = reinterpret_cast<const float2 *>(slots);
+        double t[NV + ND];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            float sh = 0.f, sl = 0.f;
+            if (lane < C) { const float2 v = src[lane * 4 + k]; sh = v.x; sl = v.y; }
+            for (int o = top >> 1; o > 0; o >>= 1) {
+                const float bh = __shfl_down_sync(kFull, sh, o), bl = __shfl_down_sync(kFull, sl, o);
+                pair_add(sh, sl, bh, bl);
+            }
+            t[k] = ldexp((double)sh + (double)sl, e[k]);
         }
         if (lane == 0) {
             post(t);
@@ -285,26 +358,35 @@ __global__ void __launch_bounds__(kClThreads, 1)
         bool first = true;
         double beta = 0.0;
         int cur = 0;
+        double rr_last = rz;   // the scale of the stopping norm's pairs
         while (true) {
             double *p = pbuf[cur], *pold = pbuf[cur ^ 1];
-            double a1[1] = {0.0};
+            // the sums on FP32 pairs of the values scaled by 2^-ps, ps half the
+            // exponent of r.z (r.r: of its last total)
+            const int ps = ((int)((__double_as_longlong(rz) >> 52) & 0x7ff) - 1023) >> 1;
+            const int pr = ((int)((__double_as_longlong(rr_last) >> 52) & 0x7ff) - 1023) >> 1;
+            float h1[1] = {0.f}, l1[1] = {0.f};
             for (int i = r0 + tid; i < r1; i += nth) {
                 const int li = i - r0;
                 double pi;
                 const double qi = cl_row_dot_p(cl, cs, i, m.z, pold, first, beta, pt, rank, &pi);
                 p[li] = pi;
                 m.q[li] = qi;
-                a1[0] = fma(pi, qi, a1[0]);
+                float ph, pl, qh, ql;
+                split_f2(pi, ps, ph, pl);
+                split_f2(qi, ps, qh, ql);
+                f2_add_prod(ph, pl, qh, ql, h1[0], l1[0]);
             }
             double o1[3];   // p.q, alpha, breakdown flag
-            cl_sums<1, 2>(cl, a1, m.slotA, m.red, C, o1, [rz](double *t) {
+            const int e1[1] = {2 * ps};
+            cl_sums_pair<1, 2>(cl, h1, l1, e1, m.slotA, m.red, C, o1, [rz](double *t) {
                 const bool ok = t[0] > 0.0 && isfinite(t[0]);
                 t[1] = ok ? rz / t[0] : 0.0;
                 t[2] = ok ? 0.0 : 1.0;
             });
             if (cl_flag(o1[2])) return -1;
             const double alpha = o1[1];
-            double acc[2] = {0.0, 0.0};
+            float h2[2] = {0.f, 0.f}, l2[2] = {0.f, 0.f};
             for (int i = r0 + tid; i < r1; i += nth) {
                 const int li = i - r0;
                 const double xi = fma(alpha, p[li], m.x[li]);
@@ -313,11 +395,16 @@ __global__ void __launch_bounds__(kClThreads, 1)
                 m.x[li] = xi;
                 m.r[li] = ri;
                 m.z[li] = zi;
-                acc[0] = fma(ri, zi, acc[0]);
-                acc[1] = fma(ri, ri, acc[1]);
+                float rh, rl, zh, zl, sh, sl;
+                split_f2(ri, ps, rh, rl);
+                split_f2(zi, ps, zh, zl);
+                split_f2(ri, pr, sh, sl);
+                f2_add_prod(rh, rl, zh, zl, h2[0], l2[0]);
+                f2_add_prod(sh, sl, sh, sl, h2[1], l2[1]);
             }
             double o2[4];   // r.z, r.r, converged flag, beta
-            cl_sums<2, 2>(cl, acc, m.slotB, m.red, C, o2, [rz, stop](double *t) {
+            const int e2[2] = {2 * ps, 2 * pr};
+            cl_sums_pair<2, 2>(cl, h2, l2, e2, m.slotB, m.red, C, o2, [rz, stop](double *t) {
                 t[2] = t[1] <= stop ? 1.0 : 0.0;
                 t[3] = t[0] / rz;
             });
@@ -326,6 +413,7 @@ __global__ void __launch_bounds__(kClThreads, 1)
             if (it >= maxit) return 0;
             beta = o2[3];
             rz = o2[0];
+            rr_last = o2[1];
             first = false;
             cur ^= 1;
         }
