@@ -110,6 +110,7 @@ __device__ __forceinline__ bool pipe_publish(double (&v)[NV], int slot0, double 
 template <int NV>
 __device__ __forceinline__ bool pipe_publish_pair(float (&h)[NV], float (&l)[NV], int slot0, double *part, double *red,
                                                   Ctrl *ctrl) {
+    __shared__ int s_ok;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -119,12 +120,16 @@ __device__ __forceinline__ bool pipe_publish_pair(float (&h)[NV], float (&l)[NV]
             const float bh = __shfl_down_sync(kFull, h[k], o), bl = __shfl_down_sync(kFull, l[k], o);
             pair_add(h[k], l[k], bh, bl);
         }
-    float *fs = reinterpret_cast<float *>(red);   // 2 NV x 32 floats
-    __syncthreads();
+    // the warps' pairs into red[0..2 NV x 32) (floats): warp 0 last read them
+    // before the previous grid barrier, and the step lengths live above
+    float *fs = reinterpret_cast<float *>(red);
     if (lane == 0)
 #pragma unroll
         for (int k = 0; k < NV; ++k) { fs[(2 * k) * 32 + warp] = h[k]; fs[(2 * k + 1) * 32 + warp] = l[k]; }
     __syncthreads();
+    // warp 0: the block's pair into its slot, then the grid barrier (as
+    // grid_sync: counting arrival, bounded wait) while the other warps wait
+    // at the block barrier -- two block barriers in all
     if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
@@ -138,12 +143,27 @@ __device__ __forceinline__ bool pipe_publish_pair(float (&h)[NV], float (&l)[NV]
                 const float bh = __shfl_down_sync(kFull, h[k], o), bl = __shfl_down_sync(kFull, l[k], o);
                 pair_add(h[k], l[k], bh, bl);
             }
-        if (lane == 0)   // the block's pair itself (pipe_totals_pair adds pairs)
+        if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < NV; ++k)
                 reinterpret_cast<float2 *>(part)[(size_t)(slot0 + k) * kMaxGrid + blockIdx.x] = make_float2(h[k], l[k]);
+            const unsigned nb = gridDim.x;
+            const unsigned long long old = atom_add_release_u64(&ctrl->bar_count, 1ull);
+            const unsigned long long target = (old / nb + 1) * nb;
+            int ok = 1;
+            if (old + 1 < target) {
+                const long long t0 = clock64();
+                while (ld_acquire_u64(&ctrl->bar_count) < target) {
+                    if (clock64() - t0 > kBarrierTimeoutCycles) { ok = 0; break; }
+                }
+            }
+            if (!ok) atomicCAS(&ctrl->status, LC_OK, LC_ERR_TIMEOUT);
+            s_ok = ok;
+        }
+        __syncwarp();
     }
-    return grid_sync(ctrl, gridDim.x);
+    __syncthreads();
+    return s_ok != 0;
 }
 
 // Warp 0: the totals of pipe_publish_pair's slots, the blocks' pairs added
