@@ -309,18 +309,78 @@ __device__ bool pipe_setup(const PipeArgs &a, int32_t n, double *red, double &bb
     return pipe_setup_w(a, n, red, false, gam, del);
 }
 
+// Where a thread keeps the iteration state of its own rows: in the global
+// vectors (any K), or, when every thread has at most kPipeRowsSm rows, in
+// shared memory (row slot k of the thread at [k][thread]: r, z, s, p, xh, n,
+// its own w and fl32(D)), so the row updates read nothing back from L2.
+// Only w -- which the neighbours read -- goes to global memory every
+// iteration; xh goes back when the iterations end.
+constexpr int kPipeRowsSm = 3;
+constexpr int kPipeSmVecs = 7;   // r, z, s, p, xh, n, w
+constexpr size_t kPipeSmBytes = (size_t)kPipeRowsSm * kPipeThreads * (kPipeSmVecs * sizeof(double) + sizeof(float));
+
+template <bool SM>
+struct RowState {
+    const PipeArgs *a;
+    double *sm;    // SM: kPipeSmVecs x kPipeRowsSm x kPipeThreads doubles, then fl32(D)
+    __device__ double *vec(int v, int k) const { return sm + ((size_t)v * kPipeRowsSm + k) * kPipeThreads + threadIdx.x; }
+    __device__ float *d32s(int k) const {
+        return reinterpret_cast<float *>(sm + (size_t)kPipeSmVecs * kPipeRowsSm * kPipeThreads) + k * kPipeThreads +
+               threadIdx.x;
+    }
+    // v: 0 r, 1 z, 2 s, 3 p, 4 xh, 5 n
+    __device__ double *gvec(int v) const {
+        switch (v) {
+            case 0: return a->r;
+            case 1: return a->z;
+            case 2: return a->s;
+            case 3: return a->p;
+            case 4: return a->xh;
+            default: return a->n;
+        }
+    }
+    __device__ double get(int v, int k, int64_t i) const {
+        if constexpr (SM) return *vec(v, k);
+        else return gvec(v)[i];
+    }
+    __device__ void put(int v, int k, int64_t i, double x) const {
+        if constexpr (SM) *vec(v, k) = x;
+        else gvec(v)[i] = x;
+    }
+    __device__ double w_own(int k, int64_t i, const double *wc) const {
+        if constexpr (SM) return *vec(6, k);
+        else return wc[i];
+    }
+    __device__ float d32(int k, int64_t i) const {
+        if constexpr (SM) return *d32s(k);
+        else return a->d32[i];
+    }
+};
+
 // Iterations from the state pipe_setup left (r, w[0], gamma, delta).
 // Returns 1 converged, 0 iteration limit, -1 breakdown, -2 wait timed out.
-__device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double gam, double del, double stop,
-                               int ns, int &it) {
+template <bool SM>
+__device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double *smem, double gam, double del,
+                               double stop, int ns, int &it) {
     const Csr &cs = a.cs;
     const Rows R;
+    const RowState<SM> S{&a, smem};
+    if constexpr (SM) {   // the own rows' state into shared memory
+        int k = 0;
+        for (int64_t i = R.first; i < n; i += R.step, ++k) {
+            S.put(0, k, i, a.r[i]);
+            S.put(4, k, i, a.xh[i]);
+            *S.vec(6, k) = a.w[0][i];
+            *S.d32s(k) = a.d32[i];
+        }
+    }
     if (!(del > 0.0) || !isfinite(del)) return -1;
     double alpha = gam / del, beta = 0.0;
     bool first = true, pending = false;
     int cur = 0;         // w[cur] holds this iteration's w
     int pend_slot = 4;   // slots of the partials published last
     int pend_e = 0;      // their scale: gamma, delta 2^-pend_e
+    int result;
     while (true) {
         // warps 1..: n = Bh w (neighbours' w of the last phase); warp 0
         // meanwhile: the totals published last and the next step lengths
@@ -342,15 +402,16 @@ __device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double
             }
         } else {
             const double *wc = a.w[cur];
-            for (int64_t i = R.first; i < n; i += R.step) a.n[i] = row_av(cs, a.ah, wc, n, i);
+            int k = 0;
+            for (int64_t i = R.first; i < n; i += R.step, ++k) S.put(5, k, i, row_av(cs, a.ah, wc, n, i));
         }
         __syncthreads();
         if (pending) {
             const double g1 = red[96], b1 = red[97], a1 = red[98];
             const bool conv = flag_set(red[99]), ok = flag_set(red[100]);
-            if (conv) return 1;   // (this iteration's product is not used)
-            if (it >= a.maxit) return 0;
-            if (!ok) return -1;
+            if (conv) { result = 1; break; }   // (this iteration's product is not used)
+            if (it >= a.maxit) { result = 0; break; }
+            if (!ok) { result = -1; break; }
             gam = g1;
             beta = b1;
             alpha = a1;
@@ -363,34 +424,36 @@ __device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double
         // the exponent of the last gamma
         const int ps = ((int)((__double_as_longlong(gam) >> 52) & 0x7ff) - 1023) >> 1;
         float gh = 0.f, gl = 0.f, dh = 0.f, dl = 0.f, rrf = 0.f;
-        for (int64_t i = R.first; i < n; i += R.step) {
-            const double ri = a.r[i], wi = wc[i], ni = a.n[i];
+        int k = 0;
+        for (int64_t i = R.first; i < n; i += R.step, ++k) {
+            const double ri = S.get(0, k, i), wi = S.w_own(k, i, wc), ni = S.get(5, k, i);
             double zi, si, pi;
             if (first) {
                 zi = ni;
                 si = wi;
                 pi = ri;
             } else {
-                zi = fma(beta, a.z[i], ni);
-                si = fma(beta, a.s[i], wi);
-                pi = fma(beta, a.p[i], ri);
+                zi = fma(beta, S.get(1, k, i), ni);
+                si = fma(beta, S.get(2, k, i), wi);
+                pi = fma(beta, S.get(3, k, i), ri);
             }
-            const double xi = fma(alpha, pi, a.xh[i]);
+            const double xi = fma(alpha, pi, S.get(4, k, i));
             const double rn = fma(-alpha, si, ri);
             const double wnx = fma(-alpha, zi, wi);
-            a.z[i] = zi;
-            a.s[i] = si;
-            a.p[i] = pi;
-            a.xh[i] = xi;
-            a.r[i] = rn;
+            S.put(1, k, i, zi);
+            S.put(2, k, i, si);
+            S.put(3, k, i, pi);
+            S.put(4, k, i, xi);
+            S.put(0, k, i, rn);
             wn[i] = wnx;
+            if constexpr (SM) *S.vec(6, k) = wnx;
             float rh, rl, wh, wl;
             split_f2(rn, ps, rh, rl);
             split_f2(wnx, ps, wh, wl);
             f2_add_prod(rh, rl, rh, rl, gh, gl);
             f2_add_prod(wh, wl, rh, rl, dh, dl);
             const float rf = approx_abs_f32(rn, ns);
-            rrf = fmaf(a.d32[i] * rf, rf, rrf);
+            rrf = fmaf(S.d32(k, i) * rf, rf, rrf);
         }
         float sh[3] = {gh, dh, rrf}, sl[3] = {gl, dl, 0.f};
         pend_slot = cur ? 7 : 4;
@@ -400,10 +463,16 @@ __device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double
         cur ^= 1;
         pending = true;
     }
+    if constexpr (SM) {   // xh back to global memory (the true residual and x = S xh read it)
+        int k = 0;
+        for (int64_t i = R.first; i < n; i += R.step, ++k) a.xh[i] = *S.vec(4, k);
+    }
+    return result;
 }
 
 __global__ void __launch_bounds__(kPipeThreads, 1) pcgpipe_kernel(PipeArgs a) {
     __shared__ double red[128];
+    extern __shared__ __align__(16) double pipe_smem[];
     if (a.done && *a.done) return;
     const int32_t n = a.cs.n_dev ? *a.cs.n_dev : a.cs.n;
     Ctrl *ctrl = a.ctrl;
@@ -430,7 +499,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1) pcgpipe_kernel(PipeArgs a) {
     const double stop_rec = ldexp(stop, -2 * ns);
     int it = 0, restarts = 0, result;
     while (true) {
-        result = pipe_iterations(a, n, red, gam, del, stop_rec, ns, it);
+        // the row state in shared memory when every thread has at most kPipeRowsSm rows
+        result = n <= (int64_t)kPipeRowsSm * R.step
+                     ? pipe_iterations<true>(a, n, red, pipe_smem, gam, del, stop_rec, ns, it)
+                     : pipe_iterations<false>(a, n, red, pipe_smem, gam, del, stop_rec, ns, it);
         if (result == -2) return;
         if (result != 1) break;
         // converged on the recurrence residual: confirm with the true one
@@ -493,10 +565,13 @@ cudaError_t launch_pcg_csr_pipelined(const Csr &op, const PcgArgs &a, PcgWork &w
     if (grid > units) grid = units;
     if (grid > kMaxGrid) grid = kMaxGrid;
     if (grid < 1) grid = 1;
+    const cudaError_t e = cudaFuncSetAttribute((const void *)pcgpipe_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipeSmBytes);
+    if (e != cudaSuccess) return e;
     void *args[] = {&g};
     note_launches(1);
     return cudaLaunchCooperativeKernel((const void *)pcgpipe_kernel, dim3((unsigned)grid), dim3(kPipeThreads), args,
-                                       0, s);
+                                       kPipeSmBytes, s);
 }
 
 }  // namespace lc

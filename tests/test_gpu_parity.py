@@ -580,6 +580,32 @@ def test_mixed_precision_rejects_bad_parameters(ctx):
         assert e.value.code == lcg.LC_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("cap", [0, 5, 13])
+def test_pipelined_local_solve_row_state_in_shared_and_global_memory(ctx, cap):
+    """The pipelined local solve keeps a thread's rows in shared memory when
+    every thread has at most three rows, else in global memory; a capped grid
+    (5 or 13 blocks: 3,680 or 9,568 rows per row round) sends the same
+    49,365-row subsystem down the global-memory path, with ragged last
+    rounds.  Both against the oracle's Alg 1."""
+    d = gen.cfg1_heat2d(seed=440, n=320, radius=120)
+    A = oracle.from_stencil(d["op"])
+    tol = 1e-8
+    okw = dict(thr_mode=oracle.THR_REL_MAX, thr_param=1e-6, exp_mode=oracle.EXP_DILATE, exp_rounds=6)
+    xr, sr, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], tol=tol, **okw)
+    prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, 1e-6, lcg.EXP_DILATE, 6, tol=tol)
+    gop = stencil_op(ctx, d["op"])
+    gop.set_tuning("local_cluster_rows", 0)
+    gop.set_tuning("local_grid_cap", cap)
+    x = cu(d["x0"])
+    st = lcg.Stats()
+    lcg.solve_local_then_global(ctx, gop, cu(d["b"]), x, prm, st)
+    xg = x.cpu().numpy()
+    assert st.K == sr["K"] and (cap == 0 or st.K > 3 * 32 * 23 * cap)
+    assert abs(st.it_local - sr["it_local"]) <= 1 and abs(st.it_global - sr["it_global"]) <= 1
+    assert oracle.relres(A, d["b"], xg) <= tol
+    assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
+
+
 @pytest.mark.parametrize("mode", ["residual", "gradient"])
 @pytest.mark.parametrize("single", [0, 1, 2])
 def test_local_single_reduction_on_csr_and_stencil(ctx, mode, single):
