@@ -313,8 +313,9 @@ __device__ bool pipe_setup(const PipeArgs &a, int32_t n, double *red, double &bb
 // vectors (any K), or, when every thread has at most kPipeRowsSm rows, in
 // shared memory (row slot k of the thread at [k][thread]: r, z, s, p, xh, n,
 // its own w and fl32(D)), so the row updates read nothing back from L2.
-// Only w -- which the neighbours read -- goes to global memory every
-// iteration; xh goes back when the iterations end.
+// w -- which the neighbours read -- and xh -- which the true residual after
+// the iterations reads at the neighbours, right after the last grid barrier --
+// are also stored to global memory every iteration.
 constexpr int kPipeRowsSm = 3;
 constexpr int kPipeSmVecs = 7;   // r, z, s, p, xh, n, w
 constexpr size_t kPipeSmBytes = (size_t)kPipeRowsSm * kPipeThreads * (kPipeSmVecs * sizeof(double) + sizeof(float));
@@ -446,7 +447,10 @@ __device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double
             S.put(4, k, i, xi);
             S.put(0, k, i, rn);
             wn[i] = wnx;
-            if constexpr (SM) *S.vec(6, k) = wnx;
+            if constexpr (SM) {
+                *S.vec(6, k) = wnx;
+                a.xh[i] = xi;   // (stored, never read back: current at every grid barrier)
+            }
             float rh, rl, wh, wl;
             split_f2(rn, ps, rh, rl);
             split_f2(wnx, ps, wh, wl);
@@ -462,10 +466,6 @@ __device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double
         ++it;
         cur ^= 1;
         pending = true;
-    }
-    if constexpr (SM) {   // xh back to global memory (the true residual and x = S xh read it)
-        int k = 0;
-        for (int64_t i = R.first; i < n; i += R.step, ++k) a.xh[i] = *S.vec(4, k);
     }
     return result;
 }
