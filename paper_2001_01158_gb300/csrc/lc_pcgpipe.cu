@@ -41,7 +41,7 @@ namespace lc {
 
 namespace {
 
-constexpr int kPipeThreads = 768;              // one block per SM
+constexpr int kPipeThreads = 512;              // one block per SM (no register spills; 768: 80 registers, spills)
 constexpr int kPipeWarps = kPipeThreads / 32;  // warp 0 reduces, the others take rows
 
 struct PipeArgs {
