@@ -380,7 +380,9 @@ def run_gpu(args, rank, ws, local):
     prm_res = lcg.default_params(**MARK_ALG3, tol=1e-8)
     prm_rel = lcg.default_params(**MARK_REL, tol=1e-8)
     prm_grad = lcg.default_params(**MARK_GRAD, tol=1e-8)
-    prm_mixed = lcg.default_params(**MARK_ALG3, tol=1e-8, precision=lcg.PREC_MIXED, inner_tol=1e-4)
+    # inner_tol 1e-3: the pipelined FP32 inner solve's recurrences drift past
+    # a ~1e-3 reduction, so deeper inner solves only add iterations
+    prm_mixed = lcg.default_params(**MARK_ALG3, tol=1e-8, precision=lcg.PREC_MIXED, inner_tol=1e-3)
     # Alg 1 with its step-7 smoothing: one red-black Gauss-Seidel sweep, as in the paper's runs
     prm_gs = lcg.default_params(**MARK_ALG3, tol=1e-8, gs_sweeps=1)
     prms = {"res": prm_res, "rel": prm_rel, "grad": prm_grad, "mixed": prm_mixed, "gs": prm_gs}
@@ -591,7 +593,7 @@ def run_gpu(args, rank, ws, local):
             "it_global": statistics.mean(s["it_global"] for s in per_grad),
             "relres_max": max(s["relres_final"] for s in per_grad)},
         "local_first_mixed_precision": {
-            "value": ms_mixed / total_sys, "inner_tol": 1e-4,
+            "value": ms_mixed / total_sys, "inner_tol": 1e-3,
             "inner_iterations": statistics.mean(s["it_global"] for s in per_mixed),
             "refinement_sweeps": statistics.mean(s["restarts"] for s in per_mixed),
             "relres_max": max(s["relres_final"] for s in per_mixed)},

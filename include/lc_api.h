@@ -506,8 +506,10 @@ LC_EXPORT int lc_heat2d_step(lc_ctx *ctx, lc_op *op, const lc_heat2d_params *hp,
  *       Ghysels-Vanroose arrangement) on the symmetrically scaled subsystem
  *       diag(B)^-1/2 B diag(B)^-1/2 (Jacobi-PCG on B in exact arithmetic):
  *       one grid barrier per iteration, the iteration's sums read while the
- *       next product runs, and about 13 FP64 instructions per row and
- *       iteration instead of about 21.  Takes precedence over local_single.
+ *       next product runs, and about 11 FP64 instructions per row and
+ *       iteration instead of about 21.  In mixed precision the same
+ *       arrangement, in FP32, is the inner solve of the FP64 iterative
+ *       refinement.  Takes precedence over local_single.
  *   "local_single"  0 or 1 (default 0): the FP64 local solve of
  *       lc_solve_local_then_global takes one grid-wide reduction per CG
  *       iteration (Chronopoulos-Gear arrangement: same iterates in exact

@@ -386,7 +386,7 @@ int pcg_impl(lc_ctx *ctx, const lc_op *op, const double *b, double *x, const lc_
             LC_CUDA(ctx, lc::launch_pcg_csr_cluster(sub_csr(op), a, op->local_cluster_rows, op->local_cluster_threads,
                                                     op->local_cluster_ctas, ctrl, s));
         const int cap = op->local_grid_cap > 0 ? op->local_grid_cap : ctx->sms;
-        if (op->local_pipelined && p->precision == LC_PREC_FP64)
+        if (op->local_pipelined)   // FP64, or FP32 inner solves in FP64 refinement
             LC_CUDA(ctx, lc::launch_pcg_csr_pipelined(sub_csr(op), a, w, ctrl, cap, s, cl));
         else if (op->local_single && p->precision == LC_PREC_FP64)
             LC_CUDA(ctx, lc::launch_pcg_csr_single(sub_csr(op), a, w, ctrl, cap, s, cl));

@@ -183,7 +183,8 @@ cudaError_t launch_pcg_csr(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ct
 cudaError_t launch_pcg_csr_single(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                   cudaStream_t s, bool after_cluster);
 // Pipelined Jacobi-PCG (one grid barrier per iteration, the sums read while
-// the product runs) for the extracted local subsystem (lc_pcgpipe.cu).
+// the product runs) for the extracted local subsystem (lc_pcgpipe.cu); with
+// a.precision LC_PREC_MIXED its FP32 form inside FP64 iterative refinement.
 cudaError_t launch_pcg_csr_pipelined(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                      cudaStream_t s, bool after_cluster);
 // FP64 Jacobi-PCG of a CSR system on one thread-block cluster (lc_cluster.cu),

@@ -527,10 +527,375 @@ __global__ void __launch_bounds__(kPipeThreads, 1) pcgpipe_kernel(PipeArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- mixed precision
+//
+// Iterative refinement with the pipelined CG as its FP32 inner solve (the
+// deployment form with FP32 bulk iterations): the outer residual rh =
+// S b - Bh xh, its norms and the update xh += sigma d stay FP64; each inner
+// problem Bh d = rh / sigma (sigma = ||rh||) is solved in FP32 -- values of
+// Bh rounded to FP32, every vector FP32, the sums on FP32 pairs -- from d = 0
+// until its residual has dropped by inner_tol, or, when the outer test misses
+// by less, by half of what is still missing.  The FP32 row state of a thread
+// lives in shared memory under the same condition as the FP64 solve's.
+
+struct PipeMixArgs {
+    PipeArgs a;                 // the FP64 part: B, b, x, Bh, S, fl32(D), xh, rh (a.r)
+    float *ah32;                // fl32(Bh)
+    float *r, *w[2], *z, *s, *p, *n, *d;   // inner vectors (global-memory path)
+    double inner_tol;
+    int max_outer;
+};
+
+template <bool SM>
+struct RowState32 {
+    const PipeMixArgs *m;
+    float *sm;   // SM: 7 x kPipeRowsSm x kPipeThreads floats
+    __device__ float *vec(int v, int k) const { return sm + ((size_t)v * kPipeRowsSm + k) * kPipeThreads + threadIdx.x; }
+    // v: 0 r, 1 z, 2 s, 3 p, 4 d, 5 n, 6 own w
+    __device__ float *gvec(int v) const {
+        switch (v) {
+            case 0: return m->r;
+            case 1: return m->z;
+            case 2: return m->s;
+            case 3: return m->p;
+            case 4: return m->d;
+            default: return m->n;
+        }
+    }
+    __device__ float get(int v, int k, int64_t i) const {
+        if constexpr (SM) return *vec(v, k);
+        else return gvec(v)[i];
+    }
+    __device__ void put(int v, int k, int64_t i, float x) const {
+        if constexpr (SM) *vec(v, k) = x;
+        else gvec(v)[i] = x;
+    }
+};
+
+__device__ __forceinline__ float row_av32(const Csr &cs, const float *__restrict__ ah, const float *v, int32_t n,
+                                          int64_t i) {
+    float acc = 0.f;
+    const int32_t e1 = cs.rp[i + 1];
+    for (int32_t e = cs.rp[i]; e < e1; ++e) acc = fmaf(ah[e], __ldcg(v + LC_IDX(cs.ci[e], n)), acc);
+    return acc;
+}
+
+// One inner FP32 solve from the r (scaled, normalised), w = Bh r, gamma,
+// delta left by the caller, d = 0; stops when gamma <= stop, when the FP32
+// recurrences stop giving a positive step (1 in both cases), or at maxit
+// inner iterations in all (0).  -1: breakdown at the start (Bh not positive
+// on r: not SPD, or non-finite data); -2: a wait timed out.  d is stored to global memory every iteration (the
+// caller reads it after the last grid barrier).
+template <bool SM>
+__device__ int pipe_inner32(const PipeMixArgs &m, int32_t n, double *red, float *smem, double gam, double del,
+                            double stop, int maxit, int &it) {
+    const Csr &cs = m.a.cs;
+    const Rows R;
+    const RowState32<SM> S{&m, smem};
+    if constexpr (SM) {
+        int k = 0;
+        for (int64_t i = R.first; i < n; i += R.step, ++k) {
+            S.put(0, k, i, m.r[i]);
+            S.put(4, k, i, 0.f);
+            *S.vec(6, k) = m.w[0][i];
+        }
+    }
+    if (!(del > 0.0) || !isfinite(del)) return -1;
+    double alpha = gam / del, beta = 0.0;
+    bool first = true, pending = false;
+    int cur = 0, pend_slot = 4, result;
+    while (true) {
+        if (threadIdx.x < 32) {
+            if (pending) {
+                double t[2];
+                const int te[2] = {0, 0};
+                pipe_totals_pair<2>(pend_slot, m.a.part, te, t);
+                if (threadIdx.x == 0) {
+                    const double bt = t[0] / gam;
+                    const double den = t[1] - bt * t[0] / alpha;
+                    const bool ok = den > 0.0 && isfinite(den);
+                    red[96] = t[0];
+                    red[97] = bt;
+                    red[98] = ok ? t[0] / den : 0.0;
+                    red[99] = t[0] <= stop ? 1.0 : 0.0;
+                    red[100] = ok ? 1.0 : 0.0;
+                }
+            }
+        } else {
+            const float *wc = m.w[cur];
+            int k = 0;
+            for (int64_t i = R.first; i < n; i += R.step, ++k) S.put(5, k, i, row_av32(cs, m.ah32, wc, n, i));
+        }
+        __syncthreads();
+        if (pending) {
+            const double g1 = red[96], b1 = red[97], a1 = red[98];
+            const bool conv = flag_set(red[99]), ok = flag_set(red[100]);
+            if (conv) { result = 1; break; }
+            if (it >= maxit) { result = 0; break; }
+            // a step length the FP32 recurrences no longer give (p.Bh p from
+            // them not positive): the inner solve has gone as far as FP32
+            // takes it; the refinement continues from the iterate so far
+            if (!ok) { result = 1; break; }
+            gam = g1;
+            beta = b1;
+            alpha = a1;
+            first = false;
+        }
+        const float af = (float)alpha, bf = (float)beta;
+        const float *wc = m.w[cur];
+        float *wn = m.w[cur ^ 1];
+        float g = 0.f, dl = 0.f;
+        int k = 0;
+        for (int64_t i = R.first; i < n; i += R.step, ++k) {
+            const float ri = S.get(0, k, i), ni = S.get(5, k, i);
+            float wi;
+            if constexpr (SM) wi = *S.vec(6, k);
+            else wi = wc[i];
+            float zi, si, pi;
+            if (first) {
+                zi = ni;
+                si = wi;
+                pi = ri;
+            } else {
+                zi = fmaf(bf, S.get(1, k, i), ni);
+                si = fmaf(bf, S.get(2, k, i), wi);
+                pi = fmaf(bf, S.get(3, k, i), ri);
+            }
+            const float di = fmaf(af, pi, S.get(4, k, i));
+            const float rn = fmaf(-af, si, ri);
+            const float wnx = fmaf(-af, zi, wi);
+            S.put(1, k, i, zi);
+            S.put(2, k, i, si);
+            S.put(3, k, i, pi);
+            S.put(4, k, i, di);
+            S.put(0, k, i, rn);
+            wn[i] = wnx;
+            if constexpr (SM) {
+                *S.vec(6, k) = wnx;
+                m.d[i] = di;   // (stored, never read back: current at every grid barrier)
+            }
+            g = fmaf(rn, rn, g);
+            dl = fmaf(wnx, rn, dl);
+        }
+        float sh[2] = {g, dl}, sl[2] = {0.f, 0.f};
+        pend_slot = cur ? 7 : 4;
+        if (!pipe_publish_pair<2>(sh, sl, pend_slot, m.a.part, red, m.a.ctrl)) return -2;
+        ++it;
+        cur ^= 1;
+        pending = true;
+    }
+    return result;
+}
+
+// FP64 residual pass on the scaled system: rh = S b - Bh xh (own rows, into
+// m.a.r), the sums ||b - B x||^2 and ||rh||^2.
+__device__ bool pipe_mix_residual(const PipeMixArgs &m, int32_t n, double *red, double &rr, double &ss) {
+    const PipeArgs &a = m.a;
+    const Csr &cs = a.cs;
+    const Rows R;
+    double acc[2] = {0.0, 0.0};
+    for (int64_t i = R.first; i < n; i += R.step) {
+        const double si = a.sd[i];
+        const double ri = a.b[i] * si - row_av(cs, a.ah, a.xh, n, i);
+        a.r[i] = ri;
+        const double ru = ri / si;
+        acc[0] = fma(ru, ru, acc[0]);
+        acc[1] = fma(ri, ri, acc[1]);
+    }
+    if (!pipe_publish<2>(acc, 0, a.part, red, a.ctrl)) return false;
+    pipe_totals2(a, red, rr, ss);
+    return true;
+}
+
+__global__ void __launch_bounds__(kPipeThreads, 1) pcgpipe_mix_kernel(PipeMixArgs m) {
+    __shared__ double red[128];
+    extern __shared__ __align__(16) double pipe_smem[];
+    const PipeArgs &a = m.a;
+    if (a.done && *a.done) return;
+    const int32_t n = a.cs.n_dev ? *a.cs.n_dev : a.cs.n;
+    const Csr &cs = a.cs;
+    Ctrl *ctrl = a.ctrl;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const Rows R;
+    // set-up (FP64): S, fl32(D), rh = S (b - B x), xh = S^-1 x; b.b, r.r
+    double acc[2] = {0.0, 0.0};
+    for (int64_t i = R.first; i < n; i += R.step) {
+        double ri = a.b[i], d = 0.0;
+        const int32_t e1 = cs.rp[i + 1];
+        for (int32_t e = cs.rp[i]; e < e1; ++e) {
+            const int32_t j = LC_IDX(cs.ci[e], n);
+            const double v = cs.av[e];
+            if (j == i) d = v;
+            ri = fma(-v, ldcg(a.x + j), ri);
+        }
+        const double q = sqrt(d), si = 1.0 / q;
+        a.sd[i] = si;
+        a.d32[i] = (float)d;
+        a.r[i] = si * ri;
+        a.xh[i] = a.x[i] * q;
+        acc[0] = fma(a.b[i], a.b[i], acc[0]);
+        acc[1] = fma(ri, ri, acc[1]);
+    }
+    if (!pipe_publish<2>(acc, 0, a.part, red, ctrl)) return;
+    double bb, rr;
+    pipe_totals2(a, red, bb, rr);
+    const double stop = (a.tol * a.tol) * bb;
+    if (lead) {
+        ctrl->bnorm2 = bb;
+        ctrl->relres0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    }
+    if (bb == 0.0) {
+        for (int64_t i = R.first; i < n; i += R.step) a.x[i] = 0.0;
+        if (lead) { ctrl->converged = 1; ctrl->early = 1; ctrl->relres = 0.0; }
+        return;
+    }
+    if (rr <= stop) {
+        if (lead) { ctrl->converged = 1; ctrl->early = 1; ctrl->relres = sqrt(rr / bb); }
+        return;
+    }
+    // Bh's values (FP64, FP32) of the own rows (S of the neighbours is
+    // complete after the barrier), and ||rh||^2 of the set-up
+    double ss0[1] = {0.0};
+    for (int64_t i = R.first; i < n; i += R.step) {
+        const double si = a.sd[i];
+        const int32_t e1 = cs.rp[i + 1];
+        for (int32_t e = cs.rp[i]; e < e1; ++e) {
+            const int32_t j = LC_IDX(cs.ci[e], n);
+            const double v = j == i ? 1.0 : cs.av[e] * si * ldcg(a.sd + j);
+            a.ah[e] = v;
+            m.ah32[e] = (float)v;
+        }
+        const double ri = a.r[i];
+        ss0[0] = fma(ri, ri, ss0[0]);
+    }
+    if (!pipe_publish<1>(ss0, 2, a.part, red, ctrl)) return;
+    double ss;
+    {
+        double t[1];
+        if (threadIdx.x < 32) {
+            pipe_totals<1>(2, a.part, t);
+            if (threadIdx.x == 0) red[96] = t[0];
+        }
+        __syncthreads();
+        ss = red[96];
+        __syncthreads();
+    }
+    int it = 0, outer = 0, result = 0;
+    float *smem32 = reinterpret_cast<float *>(pipe_smem);
+    while (true) {
+        if (rr <= stop) { result = 1; break; }
+        if (outer >= m.max_outer || it >= a.maxit) { result = 0; break; }
+        // the inner problem: r = fl32(rh / sigma), d = 0, w = fl32(Bh) r
+        const double sigma = sqrt(ss), inv = 1.0 / sigma;
+        for (int64_t i = R.first; i < n; i += R.step) m.r[i] = (float)(a.r[i] * inv);
+        if (!grid_sync(ctrl, gridDim.x)) return;
+        double acc2[2] = {0.0, 0.0};
+        for (int64_t i = R.first; i < n; i += R.step) {
+            const float wi = row_av32(cs, m.ah32, m.r, n, i), ri = m.r[i];
+            m.w[0][i] = wi;
+            m.d[i] = 0.f;
+            acc2[0] = fma((double)ri, (double)ri, acc2[0]);
+            acc2[1] = fma((double)wi, (double)ri, acc2[1]);
+        }
+        if (!pipe_publish<2>(acc2, 0, a.part, red, ctrl)) return;
+        double g0, d0;
+        pipe_totals2(a, red, g0, d0);
+        // the inner target: inner_tol, or half of what the outer test still misses
+        const double miss = sqrt(stop / rr);
+        const double target = miss > m.inner_tol ? 0.5 * miss : m.inner_tol;
+        const double istop = target * target * g0;
+        const int r32 = n <= (int64_t)kPipeRowsSm * R.step
+                            ? pipe_inner32<true>(m, n, red, smem32, g0, d0, istop, a.maxit, it)
+                            : pipe_inner32<false>(m, n, red, smem32, g0, d0, istop, a.maxit, it);
+        if (r32 == -2) return;
+        if (r32 == -1) { result = -1; break; }
+        // xh += sigma d (FP64), then the true residual
+        for (int64_t i = R.first; i < n; i += R.step) a.xh[i] = fma(sigma, (double)m.d[i], a.xh[i]);
+        if (!grid_sync(ctrl, gridDim.x)) return;
+        if (!pipe_mix_residual(m, n, red, rr, ss)) return;
+        ++outer;
+    }
+    for (int64_t i = R.first; i < n; i += R.step) a.x[i] = a.xh[i] * a.sd[i];
+    if (lead) {
+        ctrl->iters = it;
+        ctrl->restarts = 0;
+        ctrl->outer = outer;
+        ctrl->converged = result;
+        ctrl->early = 0;
+        ctrl->relres = sqrt(rr / bb);
+        if (result == -1) atomicCAS(&ctrl->status, LC_OK, LC_ERR_BREAKDOWN);
+    }
+}
+
+}  // namespace
+
+namespace {
+int pipe_grid(const Csr &op, int grid_hint) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t grid = sms;
+    if (grid_hint > 0 && grid > grid_hint) grid = grid_hint;
+    const int64_t units = ((int64_t)op.n + 32 * (kPipeWarps - 1) - 1) / (32 * (kPipeWarps - 1));
+    if (grid > units) grid = units;
+    if (grid > kMaxGrid) grid = kMaxGrid;
+    return (int)(grid < 1 ? 1 : grid);
+}
+
+cudaError_t launch_pcg_csr_pipelined_mixed(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
+                                           cudaStream_t s, bool after_cluster) {
+    if (!after_cluster) {
+        pipe_reset_kernel<<<1, 1, 0, s>>>(ctrl);
+        note_launches(1);
+    }
+    PipeMixArgs m;
+    PipeArgs &g = m.a;
+    g.cs = op;
+    g.b = a.b;
+    g.x = a.x;
+    g.ah = w.ahat;
+    g.sd = w.dinv;
+    g.d32 = w.r32;
+    g.xh = w.xh;
+    g.r = w.r;
+    g.w[0] = w.q;
+    g.w[1] = w.e0;
+    g.z = w.z;
+    g.s = w.p0;
+    g.p = w.p1;
+    g.n = w.e1;
+    g.part = w.partials;
+    g.tol = a.tol;
+    g.maxit = a.maxit;
+    g.max_restarts = a.max_restarts;
+    g.ctrl = ctrl;
+    g.done = after_cluster ? &ctrl->done : nullptr;
+    // the FP32 inner vectors: the workspace's FP32 vectors, and two FP64
+    // vectors the mixed solve does not otherwise use
+    m.ah32 = w.val32;
+    m.r = w.z32;
+    m.w[0] = w.q32;
+    m.w[1] = w.dinv32;
+    m.z = w.p032;
+    m.s = w.p132;
+    m.p = w.x32;
+    m.n = reinterpret_cast<float *>(w.e1);
+    m.d = reinterpret_cast<float *>(w.z);
+    m.inner_tol = a.inner_tol;
+    m.max_outer = a.max_outer;
+    const cudaError_t e = cudaFuncSetAttribute((const void *)pcgpipe_mix_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipeSmBytes);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&m};
+    note_launches(1);
+    return cudaLaunchCooperativeKernel((const void *)pcgpipe_mix_kernel, dim3((unsigned)pipe_grid(op, grid_hint)),
+                                       dim3(kPipeThreads), args, kPipeSmBytes, s);
+}
 }  // namespace
 
 cudaError_t launch_pcg_csr_pipelined(const Csr &op, const PcgArgs &a, PcgWork &w, Ctrl *ctrl, int grid_hint,
                                      cudaStream_t s, bool after_cluster) {
+    if (a.precision == LC_PREC_MIXED) return launch_pcg_csr_pipelined_mixed(op, a, w, ctrl, grid_hint, s, after_cluster);
     if (!after_cluster) {
         pipe_reset_kernel<<<1, 1, 0, s>>>(ctrl);
         note_launches(1);
