@@ -493,6 +493,32 @@ def edge_case_problem():
     return op, A, b, x0, beta_for
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pipelined_local_solve_edge_sizes(ctx, precision):
+    """The pipelined grid kernel (cluster kernel off) on subsystems of 0, 1,
+    2, 5 and 17 rows -- fewer rows than row warps, most threads without a row
+    -- in FP64 and as the FP32 inner solve of mixed precision."""
+    op, A, b, x0, beta_for = edge_case_problem()
+    gop = stencil_op(ctx, op)
+    gop.set_tuning("local_cluster_rows", 0)
+    mixed = precision == "mixed"
+    for k in (0, 1, 2, 5, 17):
+        beta = 2.0 if k == 0 else beta_for(k)
+        prm = lcg.default_params(lcg.MARK_RESIDUAL, lcg.THR_REL_MAX, beta, lcg.EXP_NONE, 0, tol=1e-9,
+                                 precision=lcg.PREC_MIXED if mixed else lcg.PREC_FP64, inner_tol=1e-3)
+        xr, sr, _ = oracle.solve_local_then_global(A, b, x0, thr_mode=oracle.THR_REL_MAX, thr_param=beta,
+                                                   exp_mode=oracle.EXP_NONE, exp_rounds=0, tol=1e-9)
+        assert sr["K"] == k
+        x = cu(x0)
+        st = lcg.Stats()
+        lcg.solve_local_then_global(ctx, gop, cu(b), x, prm, st)
+        assert st.K == k and st.status == 0
+        if not mixed:
+            assert abs(st.it_local - sr["it_local"]) <= 1
+            assert st.relres_tilde == pytest.approx(sr["relres_tilde"], rel=1e-6)
+        assert oracle.relres(A, b, x.cpu().numpy()) <= 1e-9
+
+
 def test_local_then_global_edge_K_zero_and_full(ctx):
     d = gen.cfg1_heat2d(seed=2, n=40, radius=4)
     A = oracle.from_stencil(d["op"])
