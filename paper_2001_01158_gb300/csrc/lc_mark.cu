@@ -372,23 +372,26 @@ __global__ void __launch_bounds__(256) expand_paper_stencil_kernel(Stencil op, c
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < op.n; j += (int64_t)gridDim.x * blockDim.x) {
         uint8_t m = in[j];
         if (!m && !skip) {
-            const unsigned ux = (unsigned)(j % op.nx);
-            const unsigned uy = (unsigned)((j / op.nx) % op.ny);
-            const unsigned uz = DIM == 3 ? (unsigned)(j / sxy) : 0u;
+            // coordinates in 32-bit arithmetic (N < 2^31), the face and x0 of a
+            // neighbour read only when it is in the domain
+            const unsigned uj = (unsigned)j, unx = (unsigned)op.nx;
+            const unsigned ux = uj % unx;
+            const unsigned uy = (uj / unx) % (unsigned)op.ny;
+            const unsigned uz = DIM == 3 ? uj / (unsigned)sxy : 0u;
             bool nbr = false;
             double t = 0.0;
-            auto visit = [&](bool ok, int64_t i, double T) {
+            auto visit = [&](bool ok, int64_t i, const double *T, int64_t f) {
                 if (ok && in[i]) {
                     nbr = true;
-                    t = __dadd_rn(t, fabs(__dmul_rn(T, x0[i])));
+                    t = __dadd_rn(t, fabs(__dmul_rn(T[f], x0[i])));
                 }
             };
-            if (DIM == 3) visit(uz > 0, j - sxy, uz > 0 ? op.Tz[j - sxy] : 0.0);
-            visit(uy > 0, j - op.nx, uy > 0 ? op.Ty[j - op.nx] : 0.0);
-            visit(ux > 0, j - 1, ux > 0 ? op.Tx[j - 1] : 0.0);
-            visit(ux + 1 < (unsigned)op.nx, j + 1, ux + 1 < (unsigned)op.nx ? op.Tx[j] : 0.0);
-            visit(uy + 1 < (unsigned)op.ny, j + op.nx, uy + 1 < (unsigned)op.ny ? op.Ty[j] : 0.0);
-            if (DIM == 3) visit(uz + 1 < (unsigned)op.nz, j + sxy, uz + 1 < (unsigned)op.nz ? op.Tz[j] : 0.0);
+            if (DIM == 3) visit(uz > 0, j - sxy, op.Tz, j - sxy);
+            visit(uy > 0, j - op.nx, op.Ty, j - op.nx);
+            visit(ux > 0, j - 1, op.Tx, j - 1);
+            visit(ux + 1 < unx, j + 1, op.Tx, j);
+            visit(uy + 1 < (unsigned)op.ny, j + op.nx, op.Ty, j);
+            if (DIM == 3) visit(uz + 1 < (unsigned)op.nz, j + sxy, op.Tz, j);
             if (nbr) {
                 const double c = __dadd_rn(fabs(r[j]), t);
                 if (abs_gt(c, tbits)) { m = 1; ++added; }
