@@ -35,6 +35,9 @@
 // partials while a slower one still reads these.  Stopping test,
 // true-residual confirmation and restarts follow the two-reduction kernel
 // (lc_pcg_impl.cuh), with the same Ctrl fields.
+//
+// pcgpipe_mix_kernel (mixed precision, below) runs the same arrangement in
+// FP32 as the inner solve of FP64 iterative refinement.
 #include "lc_pcg_impl.cuh"
 
 namespace lc {
