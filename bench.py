@@ -28,10 +28,12 @@ from __future__ import annotations
 
 import argparse
 import contextlib
+import datetime
 import hashlib
 import json
 import math
 import os
+import shutil
 import statistics
 import subprocess
 import sys
@@ -86,7 +88,7 @@ LOCAL_ENTRY_BYTES = 12
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["lc", "reference"], default="lc")
     ap.add_argument("--side", "--n", dest="n", type=int, default=2048, help="grid side")
@@ -134,58 +136,79 @@ def max_over_ranks(v, ws, device=None):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms, each sample
+    with nvidia-smi's own timestamp so that the summary keeps only the samples
+    taken inside the timed window."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines = []
+        self.window = None
 
     def __enter__(self):
+        cmd = ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+               "-lms", "50"]
+        if shutil.which("stdbuf"):
+            cmd = ["stdbuf", "-oL"] + cmd   # one line per sample, not one block per 4 KB
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
             self.proc = None
+            return self
+        t_end = time.monotonic() + 3.0          # nvidia-smi takes a moment to start sampling
+        while not self.lines and time.monotonic() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
         return self
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def mark(self, t0: float, t1: float):
+        """The timed window, as wall-clock seconds (time.time())."""
+        self.window = (t0, t1)
+
     def __exit__(self, *a):
         if self.proc:
+            time.sleep(0.1)                     # the sample that closes the window
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+            self.t.join(timeout=2)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                sm, mx = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for name, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(name)
-        if not sm:
+            rows.append((ts, sm, mx, [n for n, v in zip(names, f[6:10]) if v.lower().startswith("active")]))
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        where = "timed region" if self.window else "sampler lifetime"
+        inside = rows
+        if self.window:
+            inside = [r for r in rows if self.window[0] <= r[0] <= self.window[1]]
+            if not inside:   # a window shorter than the sampling period: the samples around it
+                where = "warm-up and timed region"
+                inside = rows
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted({n for r in inside for n in r[3]}), "samples": len(inside), "sampled": where,
+                "window_ms": round((self.window[1] - self.window[0]) * 1e3, 1) if self.window else None}
 
 
 def measured_peaks():
@@ -346,6 +369,36 @@ def run_reference(args, rank, ws):
 
 # ----------------------------------------------------------------- GPU side
 
+def gpu_local_cpus(dev_index: int):
+    """Bind this process to the host CPUs next to the GPU (its PCI device's
+    local_cpulist, intersected with the CPUs the process may use), so that
+    the pinned host buffers of the end-to-end loop are first touched on the
+    GPU's own NUMA node.  Returns a short description, or None when the
+    topology is not readable."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev_index)
+        bus = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        base = f"/sys/bus/pci/devices/{bus}"
+        with open(f"{base}/local_cpulist") as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        allowed = os.sched_getaffinity(0)
+        inter = cpus & allowed
+        node = open(f"{base}/numa_node").read().strip() if os.path.exists(f"{base}/numa_node") else "?"
+        if inter and inter != allowed:
+            os.sched_setaffinity(0, inter)
+        return f"GPU {bus} NUMA node {node}: {len(inter) if inter else len(allowed)} of {len(allowed)} CPUs"
+    except Exception:
+        return None
+
+
 def run_gpu(args, rank, ws, local):
     import numpy as np
     import torch
@@ -412,19 +465,22 @@ def run_gpu(args, rank, ws, local):
         per = []
         launches0 = lcg.kernel_launch_count()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = time.time()
         e0.record(stream)
         for k in range(steps):
             solve(kind, warmup + k, st)
             per.append(st.as_dict())
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        if clocks is not None:
+            clocks.mark(w0, time.time())
         barrier(ws)
         launches = lcg.kernel_launch_count() - launches0
         ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
         return ms, per, launches
 
     with ClockSampler(local) as cs:
-        ms_res, per_res, launches = timed_loop("res", args.steps, args.warmup)
+        ms_res, per_res, launches = timed_loop("res", args.steps, args.warmup, cs)
     clocks = cs.summary()
     ms_glob, per_glob, _ = timed_loop("global", args.steps, args.warmup)
     ms_grad, per_grad, _ = timed_loop("grad", args.steps, args.warmup)
@@ -499,6 +555,7 @@ def run_gpu(args, rank, ws, local):
     # systems' solves (inputs double-buffered on the device), as a serving
     # loop would run them; each step's copies and solve are all inside the
     # timed region.
+    affinity = gpu_local_cpus(local)
     b_h = [bs[j].cpu().pin_memory() for j in range(nsys)]
     x_h = [xs[j].cpu().pin_memory() for j in range(nsys)]
     out_h = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(2)]
@@ -557,7 +614,7 @@ def run_gpu(args, rank, ws, local):
             "note": "the global kernel; ncu shows its FP64 pipe ~71% busy at ~57% DRAM throughput"},
         "gpu_launches": launches,
         "clocks": clocks,
-        "e2e": {"value": e2e_ms / total_sys, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * N,
+        "e2e": {"value": e2e_ms / total_sys, "unit": UNIT, "host_cpus": affinity, "h2d_bytes_per_step": 2 * 8 * N,
                 "d2h_bytes_per_step": 8 * N},
         "global_pcg": {"value": ms_glob / total_sys, "unit": UNIT,
                        "iterations": statistics.mean(s["it_global"] for s in per_glob), "hbm_gbs": gbs_global},
