@@ -361,6 +361,63 @@ struct RowState {
     }
 };
 
+// n = Bh w for the thread's rows when it has at most kPipeRowsSm of them: the
+// rows' entries are taken in step (entry t of every row, then entry t + 1),
+// so the neighbour loads of all rows are in flight together instead of one
+// row's chain of column and value loads after another.  Each row still adds
+// its entries in its own entry order: the same value as row_av (row_av32 in
+// FP32).  G is the warp's number of row groups (the same in all its lanes),
+// so a warp issues no instruction for a row group it does not have.
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <typename T, int G>
+__device__ __forceinline__ void rows_av_g(const Csr &cs, const T *__restrict__ ah, const T *v, int32_t n,
+                                          const int32_t (&eb)[kPipeRowsSm], const int32_t (&ee)[kPipeRowsSm],
+                                          int32_t len, T (&acc)[kPipeRowsSm]) {
+    for (int32_t t = 0; t < len; ++t) {
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const int32_t e = eb[k] + t;
+            if (e < ee[k]) acc[k] = fma_t(ah[e], __ldcg(v + LC_IDX(cs.ci[e], n)), acc[k]);
+        }
+    }
+}
+
+template <typename T, class State>
+__device__ __forceinline__ void rows_av_sm(const Csr &cs, const T *__restrict__ ah, const T *v, int32_t n,
+                                           const Rows &R, const State &S) {
+    static_assert(kPipeRowsSm == 3, "rows_av_sm takes one to three row groups");
+    // a warp's 32 rows of a group are consecutive: the group exists for the
+    // warp when its first row does (a ragged last group has lanes past n)
+    const int64_t warp_first = R.first - (threadIdx.x & 31);
+    int groups = 0;
+    int32_t eb[kPipeRowsSm], ee[kPipeRowsSm];
+    T acc[kPipeRowsSm];
+    int32_t len = 0;
+#pragma unroll
+    for (int k = 0; k < kPipeRowsSm; ++k) {
+        const int64_t i = R.first + k * R.step;
+        acc[k] = T(0);
+        eb[k] = 0;
+        ee[k] = 0;
+        if (warp_first + k * R.step < n) groups = k + 1;
+        if (i < n) {
+            eb[k] = cs.rp[i];
+            ee[k] = cs.rp[i + 1];
+            len = max(len, ee[k] - eb[k]);
+        }
+    }
+    if (groups == 3) rows_av_g<T, 3>(cs, ah, v, n, eb, ee, len, acc);
+    else if (groups == 2) rows_av_g<T, 2>(cs, ah, v, n, eb, ee, len, acc);
+    else if (groups == 1) rows_av_g<T, 1>(cs, ah, v, n, eb, ee, len, acc);
+#pragma unroll
+    for (int k = 0; k < kPipeRowsSm; ++k) {
+        const int64_t i = R.first + k * R.step;
+        if (i < n) S.put(5, k, i, acc[k]);
+    }
+}
+
 // Iterations from the state pipe_setup left (r, w[0], gamma, delta).
 // Returns 1 converged, 0 iteration limit, -1 breakdown, -2 wait timed out.
 template <bool SM>
@@ -406,8 +463,12 @@ __device__ int pipe_iterations(const PipeArgs &a, int32_t n, double *red, double
             }
         } else {
             const double *wc = a.w[cur];
-            int k = 0;
-            for (int64_t i = R.first; i < n; i += R.step, ++k) S.put(5, k, i, row_av(cs, a.ah, wc, n, i));
+            if constexpr (SM) {
+                rows_av_sm(cs, a.ah, wc, n, R, S);
+            } else {
+                int k = 0;
+                for (int64_t i = R.first; i < n; i += R.step, ++k) S.put(5, k, i, row_av(cs, a.ah, wc, n, i));
+            }
         }
         __syncthreads();
         if (pending) {
@@ -626,8 +687,12 @@ __device__ int pipe_inner32(const PipeMixArgs &m, int32_t n, double *red, float 
             }
         } else {
             const float *wc = m.w[cur];
-            int k = 0;
-            for (int64_t i = R.first; i < n; i += R.step, ++k) S.put(5, k, i, row_av32(cs, m.ah32, wc, n, i));
+            if constexpr (SM) {
+                rows_av_sm(cs, m.ah32, wc, n, R, S);
+            } else {
+                int k = 0;
+                for (int64_t i = R.first; i < n; i += R.step, ++k) S.put(5, k, i, row_av32(cs, m.ah32, wc, n, i));
+            }
         }
         __syncthreads();
         if (pending) {
