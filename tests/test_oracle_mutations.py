@@ -32,6 +32,8 @@ PIN_GROUPS = {
     "alg1": [(P.test_local_then_global_agrees_with_global, {}), (P.test_local_then_global_edge_cases, {}),
              (P.test_rtilde_identity_and_bound, {}), (P.test_example1_local_solve_converges_without_global, {})],
     "adjoint": [(P.test_adjoint_gradient_matches_finite_differences, {})],
+    "mark": [(P.test_mark_residual_rel_max_brute_force, {"k": k}) for k in ALL_K] + [
+        (P.test_strict_thresholds_at_equality, {}), (P.test_rtilde_identity_and_bound, {})],
     "relres": [(P.test_relres_matches_dense_norm, {"k": k}) for k in ALL_K] + [(P.test_relres_exact_values_and_zero_rhs, {})],
     "gs": [(P.test_gs_sweep_is_lexicographic_gs_on_colour_ordered_system, {"seed": sd, "shape": sh})
            for sd, sh in P.GS_CASES] + [(P.test_gs_sweep_diagonal_and_fixed_point, {}),
@@ -87,6 +89,17 @@ MUTANTS = [
     ("heat_kappa_from_Tn", "heat", "for (int32_t i = 0; i < n; ++i) kappa[i] = pow(T[i], p);",
      "for (int32_t i = 0; i < n; ++i) kappa[i] = pow(Tn[i], p);"),
     ("heat_wrong_neighbour", "heat", "const double kn = kappa[nb[f]];", "const double kn = kappa[i];"),
+    ("heat_rhs_without_dt", "heat", "double d = inv_dt, bi = Tn[i] * inv_dt;", "double d = inv_dt, bi = Tn[i];"),
+    ("heat_one_picard_iteration", "heat", "if (status != ORC_OK || hs->last_update < picard_tol) break;", "break;"),
+    ("dilate_extra_layer", "dilate", "for (int32_t l = 0; l < layers; ++l)", "for (int32_t l = 0; l <= layers; ++l)"),
+    ("expand_signed_coupling", "expand", "t = t + fabs(av[e] * x0[i]);", "t = t + av[e] * x0[i];"),
+    ("rel_max_signed", "mark", "if (fabs(r[i]) > mx) mx = fabs(r[i]);", "if (r[i] > mx) mx = r[i];"),
+    ("mark_gradient_absolute_threshold", "gradient", "double thr = alpha * gmax;", "double thr = alpha;"),
+    ("extract_xl0_zero", "extract", "xL0[l] = x0[i];", "xL0[l] = 0.0;"),
+    ("pcg_x_sign", "pcg", "x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }", "x[i] -= alpha * p[i]; r[i] -= alpha * q[i]; }"),
+    ("pcg_direction_unpreconditioned", "pcg", "p[i] = z[i] + beta * p[i];", "p[i] = r[i] + beta * p[i];"),
+    ("pcg_tolerance_not_squared", "pcg", "double stop = (tol * tol) * bb;", "double stop = tol * bb;"),
+    ("alg1_never_early_exit", "alg1", "if (st->relres_tilde <= prm->tol) {", "if (st->relres_tilde < 0.0) {"),
 ]
 
 
