@@ -369,6 +369,18 @@ def run_reference(args, rank, ws):
 
 # ----------------------------------------------------------------- GPU side
 
+def parse_cpulist(spec: str) -> set:
+    """CPU numbers of a sysfs cpulist ("0-3,8,10-11")."""
+    cpus = set()
+    for part in spec.strip().split(","):
+        if "-" in part:
+            lo, hi = part.split("-")
+            cpus.update(range(int(lo), int(hi) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
 def gpu_local_cpus(dev_index: int):
     """Bind this process to the host CPUs next to the GPU (its PCI device's
     local_cpulist, intersected with the CPUs the process may use), so that
@@ -381,14 +393,7 @@ def gpu_local_cpus(dev_index: int):
         bus = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
         base = f"/sys/bus/pci/devices/{bus}"
         with open(f"{base}/local_cpulist") as f:
-            spec = f.read().strip()
-        cpus = set()
-        for part in spec.split(","):
-            if "-" in part:
-                lo, hi = part.split("-")
-                cpus.update(range(int(lo), int(hi) + 1))
-            elif part:
-                cpus.add(int(part))
+            cpus = parse_cpulist(f.read())
         allowed = os.sched_getaffinity(0)
         inter = cpus & allowed
         node = open(f"{base}/numa_node").read().strip() if os.path.exists(f"{base}/numa_node") else "?"
