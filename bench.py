@@ -396,7 +396,10 @@ def gpu_local_cpus(dev_index: int):
             cpus = parse_cpulist(f.read())
         allowed = os.sched_getaffinity(0)
         inter = cpus & allowed
-        node = open(f"{base}/numa_node").read().strip() if os.path.exists(f"{base}/numa_node") else "?"
+        node = "?"
+        if os.path.exists(f"{base}/numa_node"):
+            with open(f"{base}/numa_node") as f:
+                node = f.read().strip()
         if inter and inter != allowed:
             os.sched_setaffinity(0, inter)
         return f"GPU {bus} NUMA node {node}: {len(inter) if inter else len(allowed)} of {len(allowed)} CPUs"
@@ -560,6 +563,7 @@ def run_gpu(args, rank, ws, local):
     # systems' solves (inputs double-buffered on the device), as a serving
     # loop would run them; each step's copies and solve are all inside the
     # timed region.
+    cpus0 = os.sched_getaffinity(0)
     affinity = gpu_local_cpus(local)
     b_h = [bs[j].cpu().pin_memory() for j in range(nsys)]
     x_h = [xs[j].cpu().pin_memory() for j in range(nsys)]
@@ -600,6 +604,7 @@ def run_gpu(args, rank, ws, local):
     e2e_run(args.warmup, args.steps)
     barrier(ws)
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, ws, dev)
+    os.sched_setaffinity(0, cpus0)   # the oracle's legs below use every CPU again
 
     total_sys = args.steps * ws
     value = ms_res / total_sys
