@@ -140,3 +140,16 @@ def test_checked_library_is_selected_by_the_environment(monkeypatch):
     assert lcg.library_path() == LIB
     monkeypatch.setenv("LC_CHECKED", "1")
     assert lcg.library_path() == CHECKED_LIB and CHECKED_LIB != LIB
+
+
+def test_binding_refuses_host_tensors():
+    """There is no CPU path: every array the binding hands to the library
+    must be a CUDA tensor of the declared type, and a host tensor is refused
+    before any call."""
+    import numpy as np
+    import torch
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        lcg._ptr(torch.zeros(4, dtype=torch.float64), torch.float64, "b")
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        lcg._ptr(np.zeros(4), torch.float64, "b")
+    assert lcg._ptr(None) is None
