@@ -83,6 +83,21 @@ DP_PEAK_GOPS = 152 * 2 * 2.07   # FP64 FMA instructions per second, in G (nomina
 # z out (64 B) -- 100 B per row and 12 B per entry.
 LOCAL_ROW_BYTES = 100
 LOCAL_ENTRY_BYTES = 12
+# FP64 instructions of the pipelined local solve per row and iteration
+# besides the product's one per entry of B: the six vector updates (z, s, p,
+# x^, r^, w); its sums run on FP32 pairs
+LOCAL_DP_ROW_ITER = 6
+
+
+def local_fp64_issue(per, t_s: float) -> dict:
+    """The local solve seen from FP64 issue: (nnz(B) + 6 K) FP64 instructions
+    per iteration over the solves' event time t_s (seconds), against the
+    nominal FP64 rate."""
+    dp = sum((s["nnzB"] + LOCAL_DP_ROW_ITER * s["K"]) * s["it_local"] for s in per)
+    ach = dp / t_s / 1e9 if t_s > 0 else 0.0
+    return {"bound": "alu", "achieved": ach, "peak": DP_PEAK_GOPS, "unit": "G FP64 instr/s",
+            "frac": ach / DP_PEAK_GOPS, "alg_fp64_instr_per_row_iter": f"1 per entry of B + {LOCAL_DP_ROW_ITER}",
+            "note": "the local solve kernel; neither this nor the HBM view is saturated: grid-barrier and L2 latency"}
 
 
 def parse():
@@ -617,6 +632,7 @@ def run_gpu(args, rank, ws, local):
                    "l2": "inputs larger than L2 (operator + 20 resident systems + PCG vectors > 1 GB)"},
         "roofline": roofline,
         "roofline_local_solve": roof_local,
+        "roofline_local_solve_fp64_issue": local_fp64_issue(per_res, t_l),
         "roofline_global_pcg": roof_global,
         "roofline_global_pcg_fp64_issue": {
             "bound": "alu", "achieved": dp_achieved, "peak": DP_PEAK_GOPS, "unit": "G FP64 instr/s",

@@ -43,3 +43,14 @@ def test_parse_cpulist():
     assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
     assert bench.parse_cpulist("5") == {5}
     assert bench.parse_cpulist("") == set()
+
+
+def test_local_fp64_issue_view():
+    # two solves of the 2048^2 headline's size: (nnz(B) + 6 K) x iterations
+    # FP64 instructions over the event time
+    per = [{"K": 160000, "nnzB": 800000, "it_local": 240}, {"K": 160000, "nnzB": 800000, "it_local": 240}]
+    v = bench.local_fp64_issue(per, 3.6e-3)
+    dp = 2 * (800000 + 6 * 160000) * 240
+    assert abs(v["achieved"] - dp / 3.6e-3 / 1e9) < 1e-9
+    assert v["bound"] == "alu" and abs(v["frac"] - v["achieved"] / (152 * 2 * 2.07)) < 1e-12
+    assert bench.local_fp64_issue(per, 0.0)["achieved"] == 0.0
