@@ -19,18 +19,22 @@ PIN_GROUPS = {
     "residual": [(P.test_residual_matches_dense, {"k": k}) for k in ALL_K] + [(P.test_example1_residual_exact_rational, {})],
     "sumsq": [(P.test_sumsq_tree_order_pinned, {}), (P.test_sumsq_error_bound, {"n": 4096 + 7}),
               (P.test_tau_formula_and_infinity_norm_criterion, {}), (P.test_example1_golden_trace, {})],
-    "dilate": [(P.test_dilation_is_graph_ball, {"k": k, "layers": 2}) for k in ALL_K],
+    "dilate": [(P.test_dilation_is_graph_ball, {"k": k, "layers": 2}) for k in ALL_K] +
+              [(P.test_stored_zero_is_no_coupling, {})],
     "expand": [(P.test_example1_golden_trace, {}), (P.test_paper_expansion_brute_force_random, {}),
-               (P.test_strict_thresholds_at_equality, {})],
+               (P.test_strict_thresholds_at_equality, {}), (P.test_stored_zero_is_no_coupling, {})],
     "gradient": [(P.test_gradient_definition, {"k": k}) for k in ALL_K] + [(P.test_gradient_five_point_formula, {}),
                                                                           (P.test_mark_gradient_edges_and_monotone, {}),
-                                                                          (P.test_strict_thresholds_at_equality, {})],
+                                                                          (P.test_strict_thresholds_at_equality, {}),
+                                                                          (P.test_stored_zero_is_no_coupling, {})],
     "extract": [(P.test_extract_matches_dense_blocks, {"k": k}) for k in ALL_K] + [(P.test_extract_empty_and_full, {})],
     "pcg": [(P.test_pcg_matches_dense_lu, {"k": k}) for k in ALL_K] + [(P.test_pcg_manufactured_and_warm_start, {}),
                                                                        (P.test_pcg_status_codes, {}),
-                                                                       (P.test_pcg_finite_termination, {})],
+                                                                       (P.test_pcg_finite_termination, {}),
+                                                                       (P.test_pcg_ok_only_when_the_true_residual_meets_the_tolerance, {})],
     "alg1": [(P.test_local_then_global_agrees_with_global, {}), (P.test_local_then_global_edge_cases, {}),
-             (P.test_rtilde_identity_and_bound, {}), (P.test_example1_local_solve_converges_without_global, {})],
+             (P.test_rtilde_identity_and_bound, {}), (P.test_example1_local_solve_converges_without_global, {}),
+             (P.test_local_tolerance_is_the_local_solves, {})],
     "adjoint": [(P.test_adjoint_gradient_matches_finite_differences, {})],
     "mark": [(P.test_mark_residual_rel_max_brute_force, {"k": k}) for k in ALL_K] + [
         (P.test_strict_thresholds_at_equality, {}), (P.test_rtilde_identity_and_bound, {})],
@@ -41,7 +45,8 @@ PIN_GROUPS = {
                                         (P.test_local_then_global_applies_gs_to_x_tilde, {})],
     "heat": [(P.test_heat_system_symmetric_and_conservative, {}), (P.test_heat_system_exact_on_linear_steady_profile, {}),
              (P.test_heat_system_exact_across_a_material_interface, {}),
-             (P.test_heat_step_steady_nonlinear_profile, {}), (P.test_heat_step_methods_agree_and_picard_fixed_point, {})],
+             (P.test_heat_step_steady_nonlinear_profile, {}), (P.test_heat_step_methods_agree_and_picard_fixed_point, {}),
+             (P.test_picard_stops_at_the_first_update_below_the_tolerance, {})],
 }
 
 # (name, pin group, original text, mutated text)
@@ -100,6 +105,18 @@ MUTANTS = [
     ("pcg_direction_unpreconditioned", "pcg", "p[i] = z[i] + beta * p[i];", "p[i] = r[i] + beta * p[i];"),
     ("pcg_tolerance_not_squared", "pcg", "double stop = (tol * tol) * bb;", "double stop = tol * bb;"),
     ("alg1_never_early_exit", "alg1", "if (st->relres_tilde <= prm->tol) {", "if (st->relres_tilde < 0.0) {"),
+    ("pcg_no_restart", "pcg", "for (int restart = 0; restart <= 3; ++restart) {",
+     "for (int restart = 0; restart < 1; ++restart) {"),
+    ("pcg_no_true_residual_check", "pcg", "if (dot(n, r, r) <= stop) { status = ORC_OK; break; }",
+     "{ status = ORC_OK; break; }"),
+    ("gradient_keeps_zero_couplings", "gradient", "if (j == i || av[e] == 0.0) continue;", "if (j == i) continue;"),
+    ("dilate_keeps_zero_couplings", "dilate", "if (ci[e] != i && av[e] != 0.0 && in[ci[e]]) m = 1;",
+     "if (ci[e] != i && in[ci[e]]) m = 1;"),
+    ("expand_zero_coupling_neighbour", "expand", "if (av[e] != 0.0) is_nbr = 1;", "is_nbr = 1;"),
+    ("alg1_local_tol_global", "alg1", "status = orc_pcg(K, brp, bci, bav, rhs, xl, prm->tol_local,",
+     "status = orc_pcg(K, brp, bci, bav, rhs, xl, prm->tol,"),
+    ("heat_picard_update_misreported", "heat", "hs->last_update = sqrt(d2);", "hs->last_update = sqrt(d2) / 1e3;"),
+    ("expand_count_empty_rounds", "expand", "if (k0 == 0) break;", "if (k0 == 0) { }"),
 ]
 
 

@@ -226,6 +226,35 @@ def test_dilation_is_graph_ball(k, layers):
     assert np.array_equal(oracle.dilate(A, mask, layers), ref.astype(np.uint8))
 
 
+def _chain_with_stored_zero():
+    """A 6-point chain, SPD, whose coupling between points 2 and 3 is stored
+    as an explicit 0.0 in both rows: the points are not neighbours (R4, R5:
+    a neighbour j of i has a stored a_ij != 0)."""
+    n = 6
+    rp, ci, av = [0], [], []
+    for i in range(n):
+        for j in (i - 1, i, i + 1):
+            if 0 <= j < n:
+                ci.append(j)
+                av.append(3.0 if j == i else (0.0 if {i, j} == {2, 3} else -1.0))
+        rp.append(len(ci))
+    return oracle.csr(rp, ci, av)
+
+
+def test_stored_zero_is_no_coupling():
+    A = _chain_with_stored_zero()
+    # dilation never crosses the stored zero
+    m = oracle.dilate(A, np.array([1, 0, 0, 0, 0, 0], np.uint8), 10)
+    assert m.tolist() == [1, 1, 1, 0, 0, 0]
+    # the gradient sums over true neighbours only
+    x = np.array([0.0, 1.0, 3.0, 7.0, 15.0, 31.0])
+    assert oracle.gradient(A, x).tolist() == [1.0, 3.0, 2.0, 8.0, 24.0, 16.0]
+    # Alg 3: point 3 is no candidate of the domain {0, 1, 2}, however large its residual
+    r0 = np.array([0.0, 0.0, 0.0, 5.0, 0.0, 0.0])
+    got, rounds, c = oracle.expand_paper(A, r0, np.ones(6), 0.5, np.array([1, 1, 1, 0, 0, 0], np.uint8), 2)
+    assert got.tolist() == [1, 1, 1, 0, 0, 0] and rounds == 0 and np.isnan(c[0, 3])
+
+
 @pytest.mark.parametrize("k", range(7))
 def test_mark_residual_rel_max_brute_force(k):
     A = small_ops()[k]
@@ -553,6 +582,35 @@ def test_pcg_finite_termination():
     assert st == oracle.OK and it == 2 and rr <= 1e-12
 
 
+def test_pcg_ok_only_when_the_true_residual_meets_the_tolerance():
+    """The criterion of Eq. rel-res-conv-criteria is on the true residual
+    b - A x.  Near FP64's attainable accuracy the CG recurrence residual keeps
+    falling while the true one stalls: at tol = 1e-15 these systems need a
+    restart from the true residual (R12) to reach it, and at tol = 1e-20 no
+    FP64 iterate can, so the status must not be OK."""
+    for k in (0, 1, 4):
+        A = small_ops()[k]
+        b = np.random.default_rng(k).standard_normal(A.n)
+        x, st, it, rr = oracle.pcg(A, b, np.zeros(A.n), tol=1e-15)
+        assert st == oracle.OK and oracle.relres(A, b, x) <= 1e-15, (k, st, rr)
+        x, st, it, rr = oracle.pcg(A, b, np.zeros(A.n), tol=1e-20, maxit=5000)
+        assert st != oracle.OK and rr > 1e-20, (k, st, rr)
+
+
+def test_local_tolerance_is_the_local_solves():
+    """Alg 1's local solve stops at its own tolerance (relative to ||rhs_L||):
+    a loose local tolerance takes fewer local iterations, and the global
+    solve still brings the whole system to the global one."""
+    d = gen.cfg1_heat2d(seed=6, n=32, radius=4)
+    A = oracle.from_stencil(d["op"])
+    runs = {}
+    for tl in (1e-2, 1e-12):
+        x, s, _ = oracle.solve_local_then_global(A, d["b"], d["x0"], tol=1e-10, tol_local=tl)
+        assert s["status"] == oracle.OK and s["relres_final"] <= 1e-10 and s["K"] > 0
+        runs[tl] = s
+    assert 0 < runs[1e-2]["it_local"] < runs[1e-12]["it_local"]
+
+
 # ------------------------------------------------------- Gauss-Seidel (Alg 1 step 7)
 
 GS_CASES = [(0, (7, 5, 1)), (1, (9, 9, 1)), (2, (1, 6, 1)), (3, (12, 10, 1)), (4, (4, 3, 5)), (5, (5, 5, 2))]
@@ -702,6 +760,26 @@ def test_heat_step_steady_nonlinear_profile():
         assert st["status"] == oracle.OK and st["last_update"] < 1e-12
         errs.append(np.abs(T - np.tile(np.sqrt(1.0 - 0.75 * xc), 3)).max())
     assert errs[0] < 1e-3 and 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_picard_stops_at_the_first_update_below_the_tolerance():
+    """Sec. 3.2's nonlinear test: the Picard iteration stops at the first
+    iterate whose update ||T^{s+1} - T^s||_2 is below 1e-8 (absolute), and
+    not before: the step's last update is recomputed from the iterates of
+    the same step cut one and two iterations short."""
+    n = 24
+    h, xc = heat_grid(n)
+    T0 = np.tile(np.exp(-100.0 * xc) + 1e-4, n)
+    bc = [oracle.BC_DIRICHLET, oracle.BC_DIRICHLET, oracle.BC_NEUMANN, oracle.BC_NEUMANN]
+    bv = [1.0, 1e-4, 0.0, 0.0]
+    T, s = oracle.heat2d_step(n, n, h, 1e-2, 3.5, bc, bv, T0, method=0)
+    its = s["picard_its"]
+    assert s["status"] == oracle.OK and its >= 3
+    T1, _ = oracle.heat2d_step(n, n, h, 1e-2, 3.5, bc, bv, T0, method=0, max_picard=its - 1)
+    T2, _ = oracle.heat2d_step(n, n, h, 1e-2, 3.5, bc, bv, T0, method=0, max_picard=its - 2)
+    last, before = np.linalg.norm(T - T1), np.linalg.norm(T1 - T2)
+    assert s["last_update"] == pytest.approx(last, rel=1e-12)
+    assert last < 1e-8 <= before
 
 
 def test_heat_step_methods_agree_and_picard_fixed_point():
