@@ -26,7 +26,9 @@ PIN_GROUPS = {
     "gradient": [(P.test_gradient_definition, {"k": k}) for k in ALL_K] + [(P.test_gradient_five_point_formula, {}),
                                                                           (P.test_mark_gradient_edges_and_monotone, {}),
                                                                           (P.test_strict_thresholds_at_equality, {}),
-                                                                          (P.test_stored_zero_is_no_coupling, {})],
+                                                                          (P.test_stored_zero_is_no_coupling, {}),
+                                                                          (P.test_mark_gradient_layers_brute_force,
+                                                                           {"layers": 2})],
     "extract": [(P.test_extract_matches_dense_blocks, {"k": k}) for k in ALL_K] + [(P.test_extract_empty_and_full, {})],
     "pcg": [(P.test_pcg_matches_dense_lu, {"k": k}) for k in ALL_K] + [(P.test_pcg_manufactured_and_warm_start, {}),
                                                                        (P.test_pcg_status_codes, {}),
@@ -117,6 +119,11 @@ MUTANTS = [
      "status = orc_pcg(K, brp, bci, bav, rhs, xl, prm->tol,"),
     ("heat_picard_update_misreported", "heat", "hs->last_update = sqrt(d2);", "hs->last_update = sqrt(d2) / 1e3;"),
     ("expand_count_empty_rounds", "expand", "if (k0 == 0) break;", "if (k0 == 0) { }"),
+    ("heat_columns_unsorted", "heat",
+     "if (nb[2] >= 0) { ci[nz] = nb[2]; av[nz++] = -tf[2]; }\n            if (nb[0] >= 0) { ci[nz] = nb[0]; av[nz++] = -tf[0]; }",
+     "if (nb[0] >= 0) { ci[nz] = nb[0]; av[nz++] = -tf[0]; }\n            if (nb[2] >= 0) { ci[nz] = nb[2]; av[nz++] = -tf[2]; }"),
+    ("mark_gradient_one_layer_short", "gradient", "if (layers > 0) orc_dilate(n, rp, ci, av, mask, layers);",
+     "if (layers > 1) orc_dilate(n, rp, ci, av, mask, layers - 1);"),
 ]
 
 

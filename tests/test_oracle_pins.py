@@ -343,6 +343,23 @@ def test_mark_gradient_edges_and_monotone():
     assert np.array_equal(m["mask"].astype(bool), g > 0.25 * g.max())
 
 
+@pytest.mark.parametrize("layers", [1, 2])
+def test_mark_gradient_layers_brute_force(layers):
+    """Alg 2's set {g > alpha g_max} widened by `layers` graph layers: every
+    point within graph distance `layers` of it (NumPy brute force on the
+    dense pattern)."""
+    A = oracle.from_stencil(gen.random_stencil_2d(8, 17, 13))
+    x = np.random.default_rng(8).standard_normal(A.n)
+    g = np.abs(x[:, None] - x[None, :])
+    g = (g * _adjacency(A)).sum(1)
+    ref = (g > 0.5 * g.max()).astype(int)
+    adj = _adjacency(A)
+    for _ in range(layers):
+        ref = ((ref + adj @ ref) > 0).astype(int)
+    m = oracle.mark_gradient(A, x, 0.5, layers)
+    assert np.array_equal(m["mask"], ref.astype(np.uint8)) and m["K"] == ref.sum()
+
+
 # ------------------------------------------------------------------ extraction
 
 @pytest.mark.parametrize("k", range(7))
@@ -711,6 +728,8 @@ def test_heat_system_symmetric_and_conservative():
     A, b = oracle.heat2d_system(nx, ny, h, dt, [oracle.BC_NEUMANN] * 4, [0.0] * 4, kappa, Tn)
     M = A.dense()
     assert np.array_equal(M, M.T)
+    # CSR rows with strictly ascending columns (the order R1's residual sums in)
+    assert all(np.all(np.diff(A.col[A.rowptr[i]:A.rowptr[i + 1]]) > 0) for i in range(A.n))
     assert np.allclose(M.sum(axis=1), 1.0 / dt, rtol=1e-12, atol=1e-9 * np.abs(M).max())
     assert np.allclose(b, Tn / dt, rtol=1e-15)
     assert np.all(np.linalg.eigvalsh(M) > 0)
