@@ -22,7 +22,8 @@ PIN_GROUPS = {
     "dilate": [(P.test_dilation_is_graph_ball, {"k": k, "layers": 2}) for k in ALL_K] +
               [(P.test_stored_zero_is_no_coupling, {})],
     "expand": [(P.test_example1_golden_trace, {}), (P.test_paper_expansion_brute_force_random, {}),
-               (P.test_strict_thresholds_at_equality, {}), (P.test_stored_zero_is_no_coupling, {})],
+               (P.test_strict_thresholds_at_equality, {}), (P.test_stored_zero_is_no_coupling, {}),
+               (P.test_mark_residual_alg3_brute_force, {})],
     "gradient": [(P.test_gradient_definition, {"k": k}) for k in ALL_K] + [(P.test_gradient_five_point_formula, {}),
                                                                           (P.test_mark_gradient_edges_and_monotone, {}),
                                                                           (P.test_strict_thresholds_at_equality, {}),
@@ -48,7 +49,8 @@ PIN_GROUPS = {
     "heat": [(P.test_heat_system_symmetric_and_conservative, {}), (P.test_heat_system_exact_on_linear_steady_profile, {}),
              (P.test_heat_system_exact_across_a_material_interface, {}),
              (P.test_heat_step_steady_nonlinear_profile, {}), (P.test_heat_step_methods_agree_and_picard_fixed_point, {}),
-             (P.test_picard_stops_at_the_first_update_below_the_tolerance, {})],
+             (P.test_picard_stops_at_the_first_update_below_the_tolerance, {}),
+             (P.test_picard_iteration_is_the_papers_algorithm, {})],
 }
 
 # (name, pin group, original text, mutated text)
@@ -124,6 +126,10 @@ MUTANTS = [
      "if (nb[0] >= 0) { ci[nz] = nb[0]; av[nz++] = -tf[0]; }\n            if (nb[2] >= 0) { ci[nz] = nb[2]; av[nz++] = -tf[2]; }"),
     ("mark_gradient_one_layer_short", "gradient", "if (layers > 0) orc_dilate(n, rp, ci, av, mask, layers);",
      "if (layers > 1) orc_dilate(n, rp, ci, av, mask, layers - 1);"),
+    ("alg3_tests_b_not_r0", "expand", "done = orc_expand_paper(n, rp, ci, av, r, x0, tau, mask, rounds, NULL);",
+     "done = orc_expand_paper(n, rp, ci, av, b, x0, tau, mask, rounds, NULL);"),
+    ("picard_solve_from_old_level", "heat", "memcpy(x, T, sizeof(double) * (size_t)n);",
+     "memcpy(x, Tn, sizeof(double) * (size_t)n);"),
 ]
 
 

@@ -300,6 +300,44 @@ def test_paper_expansion_brute_force_random():
         assert np.array_equal(got.astype(bool), ref)
 
 
+def test_mark_residual_alg3_brute_force():
+    """The whole of Alg 3 (tau = eps ||b||_2 / sqrt(N), the initial set
+    {|r0| > tau}, then up to E_max synchronous rounds of its rule) against a
+    NumPy restatement on random operators, with r0 = b - A x0 and ||b|| from
+    dense NumPy.  Half the cases put a large x0 where r0 vanishes and a
+    small one where it does not, so that b and r0 lead to different sets."""
+    for s in range(10):
+        A = small_ops()[(s + 2) % 7]
+        Ad = A.dense()
+        rng = np.random.default_rng(300 + s)
+        hot = rng.uniform(size=A.n) < 0.2
+        noise = hot * 3.0 * rng.standard_normal(A.n)
+        if s < 5:
+            x0 = rng.standard_normal(A.n)
+            eps = 0.3
+        else:
+            x0 = np.where(hot, 1e-3, 5.0 * np.abs(rng.standard_normal(A.n)))
+            eps = 0.01
+        b = Ad @ x0 + noise
+        r = b - Ad @ x0
+        tau = eps * np.linalg.norm(b) / math.sqrt(A.n)
+        m = oracle.mark_residual(A, b, x0, oracle.THR_EPS_NORMB, eps, oracle.EXP_PAPER, 3)
+        assert m["tau"] == pytest.approx(tau, rel=1e-13)
+        ref = np.abs(r) > tau
+        adj = _adjacency(A).astype(bool)
+        near = np.abs(np.abs(r) - tau) <= 1e-12 * tau
+        for _ in range(3):
+            cand = ~ref & adj[:, ref].any(1)
+            c = np.abs(r) + np.abs(Ad[:, ref] * x0[ref][None, :]).sum(1)
+            near |= cand & (np.abs(c - tau) <= 1e-12 * tau)
+            add = cand & (c > tau)
+            if not add.any():
+                break
+            ref = ref | add
+        assert not near.any()   # the seeds keep every decision clear of tau
+        assert np.array_equal(m["mask"].astype(bool), ref) and m["K"] == ref.sum()
+
+
 @pytest.mark.parametrize("k", range(7))
 def test_gradient_definition(k):
     A = small_ops()[k]
@@ -799,6 +837,25 @@ def test_picard_stops_at_the_first_update_below_the_tolerance():
     last, before = np.linalg.norm(T - T1), np.linalg.norm(T1 - T2)
     assert s["last_update"] == pytest.approx(last, rel=1e-12)
     assert last < 1e-8 <= before
+
+
+def test_picard_iteration_is_the_papers_algorithm():
+    """Sec. 3.2's algorithm, step by step: iteration s assembles the system
+    at kappa(T^{n+1,s}) with the old level T^n and solves it from the
+    previous Picard iterate T^{n+1,s}.  The step cut after two iterations
+    equals one iteration followed by that solve, bit for bit, with the CG
+    iterations of both solves counted."""
+    n = 16
+    h, xc = heat_grid(n)
+    Tn = np.tile(np.exp(-100.0 * xc) + 1e-4, n)
+    bc = [oracle.BC_DIRICHLET, oracle.BC_DIRICHLET, oracle.BC_NEUMANN, oracle.BC_NEUMANN]
+    bv = [1.0, 1e-4, 0.0, 0.0]
+    T1, s1 = oracle.heat2d_step(n, n, h, 1e-2, 3.5, bc, bv, Tn, method=0, max_picard=1)
+    T2, s2 = oracle.heat2d_step(n, n, h, 1e-2, 3.5, bc, bv, Tn, method=0, max_picard=2)
+    A, b = oracle.heat2d_system(n, n, h, 1e-2, bc, bv, T1 ** 3.5, Tn)
+    x, st, it, _ = oracle.pcg(A, b, T1, tol=1e-10)
+    assert st == oracle.OK and np.array_equal(T2, x)
+    assert s2["it_global"] == s1["it_global"] + it and s2["picard_its"] == 2
 
 
 def test_heat_step_methods_agree_and_picard_fixed_point():
