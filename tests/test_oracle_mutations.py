@@ -130,6 +130,8 @@ MUTANTS = [
      "done = orc_expand_paper(n, rp, ci, av, b, x0, tau, mask, rounds, NULL);"),
     ("picard_solve_from_old_level", "heat", "memcpy(x, T, sizeof(double) * (size_t)n);",
      "memcpy(x, Tn, sizeof(double) * (size_t)n);"),
+    ("gmax_skips_last_point", "gradient", "for (int32_t i = 0; i < n; ++i) if (g[i] > gmax) gmax = g[i];",
+     "for (int32_t i = 0; i + 1 < n; ++i) if (g[i] > gmax) gmax = g[i];"),
 ]
 
 

@@ -379,6 +379,10 @@ def test_mark_gradient_edges_and_monotone():
     m = oracle.mark_gradient(A, x, 0.25)
     assert m["gmax"] == g.max()
     assert np.array_equal(m["mask"].astype(bool), g > 0.25 * g.max())
+    # g_max over every point, the last one included
+    x[-1] = 100.0
+    g = oracle.gradient(A, x)
+    assert g.argmax() == A.n - 1 and oracle.mark_gradient(A, x, 0.25)["gmax"] == g[-1]
 
 
 @pytest.mark.parametrize("layers", [1, 2])
