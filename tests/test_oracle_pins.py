@@ -912,3 +912,23 @@ def test_general_csr_generators_are_spd_sorted_and_coloured(kind):
     rows = np.repeat(np.arange(A.n), np.diff(rp))
     off = ci != rows
     assert not np.any(col[rows[off]] == col[ci[off]])
+
+
+# ------------------------------------------------------------------ inputs
+
+def test_cfg1_time_stepped_reading_marks_only_the_source():
+    """The 128 x 128 heat step's right-hand side: read as a time step
+    (x_prev solved the previous step, b = A x_prev + s) the residual r0 = s
+    marks the source disc alone; the literal b = x_prev/dt + s leaves x_prev
+    out of equilibrium, and the Dirichlet boundary ring is marked too."""
+    ring = np.zeros((128, 128), bool)
+    ring[0, :] = ring[-1, :] = ring[:, 0] = ring[:, -1] = True
+    eta = {}
+    for literal in (False, True):
+        d = gen.cfg1_heat2d(seed=0, n=128, literal=literal)
+        A = oracle.from_stencil(d["op"])
+        m = oracle.mark_residual(A, d["b"], d["x0"], oracle.THR_REL_MAX, 1e-3, oracle.EXP_DILATE, 2)
+        marked = m["mask"].reshape(128, 128)
+        eta[literal] = m["K"] / A.n
+        assert marked[ring].mean() == (1.0 if literal else 0.0)
+    assert eta[False] < 0.03 < 0.1 < eta[True]
